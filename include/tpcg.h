@@ -1,0 +1,164 @@
+/*
+ * tpcg.h -- C ABI of libtpcg: pseudoinverse-preconditioned CG for the
+ * finite-difference Poisson problem  -Laplace(ups) = eta  on a 2D rectangle
+ * or 3D cuboid (Chumchal, Marton, Plesinger, Simunkova, "Tensor-structured PCG
+ * for finite difference solver of domain patterns in ferroelectric material").
+ *
+ * Operator (eq. ourproblem2, Sec. 3.3):
+ *     L = I_t (x) I_q (x) L_n  +  I_t (x) L_q (x) I_n  +  L_t (x) I_q (x) I_n,
+ * where L_l = L_l(alpha, beta, gamma) / h_l^2 is the 1D FD minus-Laplacian of
+ * eq. (lap1d) (Sec. 3.1) with the corner entries fixed by the axis' boundary
+ * condition.  Solver: PCG, Algorithm 1 (Sec. 4.1), with the Moore-Penrose
+ * pseudoinverse preconditioner of Algorithms 5 and 7 (Sec. 4.3.3): project on
+ * the 1D eigenvector bases by three mode products, multiply by the Hadamard
+ * pseudoinverse of all eigenvalue sums (zero on the null space), project back.
+ *
+ * Data layout.  A grid function is a contiguous array of nz*ny*nx doubles with
+ * x fastest, then y, then z -- the paper's vec() order (first index fastest,
+ * Sec. 2.1); as a PyTorch tensor it has shape (nz, ny, nx).  nz == 1 selects
+ * the 2D problem (Algorithms 4/6); bc[2] and h[2] are then ignored.
+ *
+ * Conventions.
+ *  - Every function returns a status code (TPCG_OK == 0).  No C++ exception
+ *    crosses this boundary.  tpcg_strerror() names a code.
+ *  - "device pointer" means memory of the CUDA device that was current when
+ *    the plan was created; "host pointer" means ordinary or pinned host memory.
+ *  - Work is issued on the plan's CUDA stream (stream-ordered).  Functions that
+ *    return a tpcg_info (or host data) synchronise that stream before they
+ *    return; the others only enqueue work.
+ *  - The caller owns eta/ups buffers; the plan owns its eigenbases and
+ *    workspaces and frees them in tpcg_plan_destroy().
+ *  - A plan is not thread-safe: one host thread at a time per plan.
+ */
+#ifndef TPCG_H
+#define TPCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define TPCG_OK                 0
+#define TPCG_ERR_INVALID_ARG    1  /* bad size, BC code, spacing, pointer or tolerance */
+#define TPCG_ERR_OOM            2  /* device or host allocation failed */
+#define TPCG_ERR_CUDA           3  /* a CUDA runtime/driver call failed */
+#define TPCG_ERR_NOT_CONVERGED  4  /* maxit reached; ups holds the last iterate */
+#define TPCG_ERR_BREAKDOWN      5  /* rho <= 0, <W,P> <= 0 or a non-finite scalar (e.g. NaN in eta) */
+#define TPCG_ERR_TIMEOUT        6  /* a bounded device-side wait gave up */
+#define TPCG_ERR_UNSUPPORTED    7  /* valid request this build cannot serve (e.g. axis > 256 for tensor-core forms) */
+#define TPCG_ERR_EIGENBASIS     8  /* closed-form eigenbasis failed its accuracy check */
+
+/* ---- boundary conditions per axis (list under eq. lap1d, Sec. 3.1) ---- */
+#define TPCG_BC_P   0  /* periodic:          (alpha, beta, gamma) = (2, 2, -1) */
+#define TPCG_BC_D   1  /* Dirichlet:                                (2, 2,  0) */
+#define TPCG_BC_N   2  /* Neumann:                                  (1, 1,  0) */
+#define TPCG_BC_DN  3  /* Dirichlet at index 1, Neumann at index n: (2, 1,  0) */
+#define TPCG_BC_ND  4  /* Neumann at index 1, Dirichlet at index n: (1, 2,  0) */
+
+/* ---- precision forms of the preconditioner (Algorithm 7) ---------------
+ * In every form the residual r = eta - L ups, the CG inner products, alpha,
+ * beta, the solution update and the null-space (mean) projection are FP64;
+ * only the three forward and three backward mode products change.        */
+#define TPCG_FP64         0  /* mode products in FP64 (CUDA cores)                   */
+#define TPCG_MIXED_TF32   1  /* reserved: TF32 tensor-core mode products             */
+#define TPCG_MIXED_BF16   2  /* BF16 tensor-core mode products, FP32 accumulation    */
+
+/* ---- tpcg_solve flags ---------------------------------------------------- */
+#define TPCG_ZERO_GUESS   1u  /* ignore ups on entry and start from ups = 0 */
+
+typedef struct tpcg_plan tpcg_plan;
+
+/* Per-solve report.  Residuals are relative to ||eta_hat||_2, where eta_hat is
+ * eta after the null-space projection of eq. (centering) (Sec. 3.4.1) when
+ * the operator is singular (every present axis P or N), else eta itself.   */
+typedef struct {
+  int    status;            /* same value the call returned                         */
+  int    iters;             /* PCG iterations s performed (Algorithm 1, line 9)     */
+  int    precond_applies;   /* applications of the preconditioner                  */
+  int    prec;              /* precision form used                                  */
+  double rel_res_true;      /* ||eta_hat - L ups||_2 / ||eta_hat||_2, FP64, at exit  */
+  double rel_res_recur;     /* ||R_s||_2 / ||eta_hat||_2 of the CG recurrence        */
+  double eta_norm;          /* ||eta_hat||_2                                        */
+  double removed_mean;      /* mean removed from eta (singular operators), else 0   */
+  double null_component;    /* mean removed from ups at exit (singular), else 0     */
+} tpcg_info;
+
+/* Create a plan for an nx x ny x nz grid (eq. lap1d requires n >= 3 on every
+ * present axis; nz == 1 is the 2D problem).  bc[3] holds TPCG_BC_* codes for
+ * x, y, z; h[3] the grid spacings (> 0; L_l is divided by h_l^2).  prec is a
+ * TPCG_FP64 / TPCG_MIXED_* form.  stream is a cudaStream_t (NULL = the legacy
+ * default stream) on which all of the plan's work is issued.
+ * Plan setup (Algorithm 5): per axis the eigenpairs of L_l from the closed
+ * forms of Lemmas spectrumP/D/N/M (Sec. 3.2), orthonormalised, checked
+ * against L_l (||V^T V - I||_max and ||L - V Lambda V^T||_F), and copied to
+ * the device with the workspaces.  On error *out is NULL.                   */
+int tpcg_plan_create(int nx, int ny, int nz, const int bc[3], const double h[3], int prec, void* stream,
+                     tpcg_plan** out);
+
+/* Release all device and host memory of a plan (synchronises its stream).  */
+int tpcg_plan_destroy(tpcg_plan* plan);
+
+/* Change the stream on which the plan issues its work.                     */
+int tpcg_plan_set_stream(tpcg_plan* plan, void* stream);
+
+/* Bytes of device memory the plan holds (eigenbases + workspaces).         */
+int tpcg_plan_device_bytes(const tpcg_plan* plan, size_t* bytes);
+
+/* Solve L ups = eta by PCG (Algorithm 1) with the pseudoinverse
+ * preconditioner (Algorithm 7).  eta, ups: device pointers, nz*ny*nx doubles
+ * each, layout above; eta is read only; ups holds the initial guess on entry
+ * (unless flags has TPCG_ZERO_GUESS) and the solution on exit.  Singular
+ * operators: eta is centred (eq. centering), Z is centred every iteration
+ * (Remark orthogonality) and ups is returned with zero mean (the minimum-norm
+ * solution).  Stops when the recurrence residual is <= tol*||eta_hat||
+ * and an FP64 evaluation of ||eta_hat - L ups|| confirms it (Remark
+ * stoppincrit: the paper stops at a fixed count; the true residual is used
+ * here).  tol in (0, 1), maxit >= 1.  info (host pointer, may be NULL)
+ * receives the report.  Synchronises the plan's stream.
+ * Returns TPCG_OK, TPCG_ERR_NOT_CONVERGED (ups = last iterate),
+ * TPCG_ERR_BREAKDOWN, TPCG_ERR_TIMEOUT or an argument/CUDA error.           */
+int tpcg_solve(tpcg_plan* plan, const double* eta, double* ups, double tol, int maxit, unsigned flags,
+               tpcg_info* info);
+
+/* As tpcg_solve, with eta and ups in HOST memory (pinned memory gives the
+ * fastest copies).  The copies in and out run on the plan's stream through
+ * plan-owned device buffers.                                               */
+int tpcg_solve_host(tpcg_plan* plan, const double* eta_host, double* ups_host, double tol, int maxit,
+                    unsigned flags, tpcg_info* info);
+
+/* z = M(r): one application of the preconditioner of Algorithm 7 in the
+ * plan's precision form, without centring.  r, z: device pointers of
+ * nz*ny*nx doubles (may not alias).  Enqueues only.                        */
+int tpcg_precond_apply(tpcg_plan* plan, const double* r, double* z);
+
+/* w = L x: the 7-point (5-point in 2D) Kronecker-sum stencil of eq.
+ * (ourproblem), FP64, per-axis corners of eq. (lap1d).  x, w: device
+ * pointers of nz*ny*nx doubles (may not alias).  Enqueues only.            */
+int tpcg_apply_laplacian(tpcg_plan* plan, const double* x, double* w);
+
+/* Fold constant nonhomogeneous boundary data into a right-hand side in place
+ * (Sec. 3.4.2).  bval[2m] is the value on the start face of axis m (index 1),
+ * bval[2m+1] on the end face (index n); periodic axes and the absent z axis
+ * ignore theirs.  A Dirichlet face adds u_B / h^2 to its boundary layer, a
+ * Neumann face adds e_B / h, where e_B is the outward normal derivative (the
+ * sign reading of Problem 2, Sec. 5.1).  eta: device pointer (nz*ny*nx
+ * doubles); bval: host pointer.  Enqueues only.                           */
+int tpcg_rhs_add_bc(tpcg_plan* plan, double* eta, const double bval[6]);
+
+/* Copy the FP64 eigenpairs of axis (0 = x, 1 = y, 2 = z) to host memory:
+ * lam[ell] (already divided by h^2) and V[ell*ell] row-major with column k
+ * the eigenvector of lam[k] (eq. eig-svd-decomp).  ell is the axis length
+ * (1 for the absent z axis of a 2D plan: lam = {0}, V = {1}).              */
+int tpcg_plan_eigenpairs(const tpcg_plan* plan, int axis, double* lam, double* V);
+
+/* Human-readable name of a status code (static string, never NULL).        */
+const char* tpcg_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TPCG_H */

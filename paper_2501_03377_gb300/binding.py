@@ -1,0 +1,231 @@
+"""ctypes binding of libtpcg (include/tpcg.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method.  ``Plan`` is a small convenience wrapper that
+passes PyTorch tensors' device pointers and the current CUDA stream.
+
+There is no CPU fallback: if ``libtpcg.so`` has not been built (see
+``paper_2501_03377_gb300.build``) every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtpcg.so")
+
+TPCG_OK = 0
+TPCG_ERR_INVALID_ARG = 1
+TPCG_ERR_OOM = 2
+TPCG_ERR_CUDA = 3
+TPCG_ERR_NOT_CONVERGED = 4
+TPCG_ERR_BREAKDOWN = 5
+TPCG_ERR_TIMEOUT = 6
+TPCG_ERR_UNSUPPORTED = 7
+TPCG_ERR_EIGENBASIS = 8
+
+BC = {"P": 0, "D": 1, "N": 2, "DN": 3, "ND": 4}
+TPCG_FP64 = 0
+TPCG_MIXED_TF32 = 1
+TPCG_MIXED_BF16 = 2
+PREC = {"fp64": TPCG_FP64, "tf32": TPCG_MIXED_TF32, "bf16": TPCG_MIXED_BF16}
+TPCG_ZERO_GUESS = 1
+
+
+class tpcg_info(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int),
+        ("iters", ctypes.c_int),
+        ("precond_applies", ctypes.c_int),
+        ("prec", ctypes.c_int),
+        ("rel_res_true", ctypes.c_double),
+        ("rel_res_recur", ctypes.c_double),
+        ("eta_norm", ctypes.c_double),
+        ("removed_mean", ctypes.c_double),
+        ("null_component", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+_SIGS = {
+    "tpcg_plan_create": (_I, [_I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _I, _P, ctypes.POINTER(_P)]),
+    "tpcg_plan_destroy": (_I, [_P]),
+    "tpcg_plan_set_stream": (_I, [_P, _P]),
+    "tpcg_plan_device_bytes": (_I, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "tpcg_solve": (_I, [_P, _P, _P, _D, _I, ctypes.c_uint, ctypes.POINTER(tpcg_info)]),
+    "tpcg_solve_host": (_I, [_P, _P, _P, _D, _I, ctypes.c_uint, ctypes.POINTER(tpcg_info)]),
+    "tpcg_precond_apply": (_I, [_P, _P, _P]),
+    "tpcg_apply_laplacian": (_I, [_P, _P, _P]),
+    "tpcg_rhs_add_bc": (_I, [_P, _P, ctypes.POINTER(_D)]),
+    "tpcg_plan_eigenpairs": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "tpcg_strerror": (ctypes.c_char_p, [_I]),
+}
+_lib = None
+
+
+def lib():
+    """Load libtpcg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libtpcg.so not built ({LIB_PATH}); run paper_2501_03377_gb300.build.build()")
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def declared_symbols():
+    return list(_SIGS)
+
+
+class TpcgError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__(f"{what}: {tpcg_strerror(status)} ({status})")
+
+
+def tpcg_strerror(status: int) -> str:
+    return lib().tpcg_strerror(int(status)).decode()
+
+
+def tpcg_plan_create(nx, ny, nz, bc, h, prec, stream):
+    bc_arr = (_I * 3)(*[BC[b] if isinstance(b, str) else int(b) for b in bc])
+    h_arr = (_D * 3)(*[float(v) for v in h])
+    out = _P()
+    st = lib().tpcg_plan_create(int(nx), int(ny), int(nz), bc_arr, h_arr, int(prec), _P(stream), ctypes.byref(out))
+    return st, out
+
+
+def tpcg_plan_destroy(plan):
+    return lib().tpcg_plan_destroy(plan)
+
+
+def tpcg_plan_set_stream(plan, stream):
+    return lib().tpcg_plan_set_stream(plan, _P(stream))
+
+
+def tpcg_plan_device_bytes(plan):
+    v = ctypes.c_size_t()
+    st = lib().tpcg_plan_device_bytes(plan, ctypes.byref(v))
+    return st, v.value
+
+
+def tpcg_solve(plan, eta_ptr, ups_ptr, tol, maxit, flags):
+    info = tpcg_info()
+    st = lib().tpcg_solve(plan, _P(eta_ptr), _P(ups_ptr), float(tol), int(maxit), int(flags), ctypes.byref(info))
+    return st, info
+
+
+def tpcg_solve_host(plan, eta_ptr, ups_ptr, tol, maxit, flags):
+    info = tpcg_info()
+    st = lib().tpcg_solve_host(plan, _P(eta_ptr), _P(ups_ptr), float(tol), int(maxit), int(flags), ctypes.byref(info))
+    return st, info
+
+
+def tpcg_precond_apply(plan, r_ptr, z_ptr):
+    return lib().tpcg_precond_apply(plan, _P(r_ptr), _P(z_ptr))
+
+
+def tpcg_apply_laplacian(plan, x_ptr, w_ptr):
+    return lib().tpcg_apply_laplacian(plan, _P(x_ptr), _P(w_ptr))
+
+
+def tpcg_rhs_add_bc(plan, eta_ptr, bval):
+    arr = (_D * 6)(*[float(v) for v in bval])
+    return lib().tpcg_rhs_add_bc(plan, _P(eta_ptr), arr)
+
+
+def tpcg_plan_eigenpairs(plan, axis, length):
+    lam = (_D * length)()
+    V = (_D * (length * length))()
+    st = lib().tpcg_plan_eigenpairs(plan, int(axis), lam, V)
+    return st, list(lam), list(V)
+
+
+# ---------------------------------------------------------------------------
+class Plan:
+    """Owns a tpcg_plan; tensors are torch float64 CUDA tensors of shape (nz, ny, nx)."""
+
+    def __init__(self, nx, ny, nz, bcs, h=(1.0, 1.0, 1.0), prec="fp64", stream=None):
+        import torch
+
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.shape = (nz, ny, nx)
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+        st, handle = tpcg_plan_create(nx, ny, nz, bcs, h, self.prec, stream)
+        if st != TPCG_OK:
+            raise TpcgError(st, "tpcg_plan_create")
+        self.handle = handle
+
+    def close(self):
+        if getattr(self, "handle", None):
+            tpcg_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, t):
+        import torch
+
+        if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous() and tuple(t.shape) == self.shape):
+            raise ValueError(f"expected contiguous float64 CUDA tensor of shape {self.shape}")
+
+    def solve(self, eta, ups, tol=1e-10, maxit=100, zero_guess=False, raise_on_error=False):
+        self._check(eta)
+        self._check(ups)
+        st, info = tpcg_solve(self.handle, eta.data_ptr(), ups.data_ptr(), tol, maxit,
+                              TPCG_ZERO_GUESS if zero_guess else 0)
+        if raise_on_error and st != TPCG_OK:
+            raise TpcgError(st, "tpcg_solve")
+        return st, info.as_dict()
+
+    def solve_host(self, eta_host, ups_host, tol=1e-10, maxit=100, zero_guess=False):
+        st, info = tpcg_solve_host(self.handle, eta_host.data_ptr(), ups_host.data_ptr(), tol, maxit,
+                                   TPCG_ZERO_GUESS if zero_guess else 0)
+        return st, info.as_dict()
+
+    def precond(self, r, z):
+        self._check(r)
+        self._check(z)
+        st = tpcg_precond_apply(self.handle, r.data_ptr(), z.data_ptr())
+        if st != TPCG_OK:
+            raise TpcgError(st, "tpcg_precond_apply")
+
+    def laplacian(self, x, w):
+        self._check(x)
+        self._check(w)
+        st = tpcg_apply_laplacian(self.handle, x.data_ptr(), w.data_ptr())
+        if st != TPCG_OK:
+            raise TpcgError(st, "tpcg_apply_laplacian")
+
+    def rhs_add_bc(self, eta, bval):
+        self._check(eta)
+        st = tpcg_rhs_add_bc(self.handle, eta.data_ptr(), bval)
+        if st != TPCG_OK:
+            raise TpcgError(st, "tpcg_rhs_add_bc")
+
+    def eigenpairs(self, axis):
+        length = (self.nx, self.ny, self.nz)[axis]
+        st, lam, V = tpcg_plan_eigenpairs(self.handle, axis, length)
+        if st != TPCG_OK:
+            raise TpcgError(st, "tpcg_plan_eigenpairs")
+        return lam, V
+
+    def device_bytes(self):
+        return tpcg_plan_device_bytes(self.handle)[1]

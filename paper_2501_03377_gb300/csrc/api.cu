@@ -1,0 +1,513 @@
+// C ABI of libtpcg (include/tpcg.h): plan setup and the PCG driver.
+//
+// tpcg_solve runs Algorithm 1 with every scalar (alpha, beta, rho, the stop
+// test) on the device.  The host only enqueues kernels in chunks of
+// iterations and reads the device state between chunks; kernels of an
+// iteration that starts after convergence return immediately.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "tpcg_dev.cuh"
+
+namespace tpcg {
+
+void launch_apply_laplacian(const tpcg_plan* p, const Geom& g, const double* x, double* w);
+void launch_init_residual(const tpcg_plan* p, const Geom& g, const double* eta, const double* U, bool zero_guess);
+void launch_eta_sum(const tpcg_plan* p, const Geom& g, const double* eta);
+void launch_direction(const tpcg_plan* p, const Geom& g);
+void launch_update(const tpcg_plan* p, const Geom& g, double* U);
+void launch_true_residual(const tpcg_plan* p, const Geom& g, const double* eta, const double* U, bool force);
+void launch_center_u(const tpcg_plan* p, const Geom& g, double* U);
+void launch_zero(const tpcg_plan* p, long long N, double* U);
+void launch_to_lp(const tpcg_plan* p, const Geom& g, const double* r);
+void launch_f32_to_f64(const tpcg_plan* p, long long N, const float* a, double* b);
+void launch_rhs_add_bc(const tpcg_plan* p, const Geom& g, double* eta, const double* bv);
+void run_precond_f64(const tpcg_plan* pl, const double* R, double* Z, SolveState* st);
+int run_precond_tc(const tpcg_plan* pl, float* Z, SolveState* st);
+int tc_plan_setup(tpcg_plan* pl);
+void tc_plan_release(tpcg_plan* pl);
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+int pad_to(int v, int m) { return ((v + m - 1) / m) * m; }
+
+Geom make_geom(const tpcg_plan* p) {
+  Geom g{};
+  g.nx = p->nx;
+  g.ny = p->ny;
+  g.nz = p->nz;
+  for (int m = 0; m < 3; ++m) {
+    g.bc[m] = p->bc[m];
+    g.ih2[m] = 1.0 / (p->h[m] * p->h[m]);
+  }
+  if (p->nz == 1) g.ih2[2] = 0.0;
+  g.N = p->N;
+  return g;
+}
+
+// The six (3D) or four (2D) mode-product passes of Algorithm 7.  Each pass
+// contracts the contiguous index of its input; its output strides make the
+// next contraction index contiguous.  padv = row-pitch granularity (elements).
+void build_stages(tpcg_plan* p, int padv, int first_pitch) {
+  const int n = p->nx, q = p->ny, t = p->nz;
+  const int np = pad_to(n, padv), qp = pad_to(q, padv), tp = pad_to(t, padv);
+  std::vector<StageParams> S;
+  auto mk = [](int A, int B, int C, int pitch, int axis, int dir, long long oa, long long ob, long long oc) {
+    StageParams s{};
+    s.A = A; s.B = B; s.C = C; s.Cout = C; s.in_pitch = pitch; s.axis = axis; s.dir = dir;
+    s.oa = oa; s.ob = ob; s.oc = oc;
+    s.lamA = s.lamB = s.lamC = 0;
+    return s;
+  };
+  if (t > 1) {
+    StageParams s1 = mk(t, q, n, first_pitch, 0, 0, qp, 1, (long long)t * qp);         // -> [n][t][q]
+    s1.out_rows = n * t; s1.out_C = q; s1.out_pitch_elems = qp;
+    StageParams s2 = mk(n, t, q, qp, 1, 0, (long long)q * tp, 1, tp);                  // -> [n][q][t]
+    s2.out_rows = n * q; s2.out_C = t; s2.out_pitch_elems = tp;
+    StageParams s3 = mk(n, q, t, tp, 2, 0, (long long)q * tp, tp, 1);                  // -> [n][q][t], x G
+    s3.scale = 1; s3.lamA = 0; s3.lamB = 1; s3.lamC = 2;
+    s3.out_rows = n * q; s3.out_C = t; s3.out_pitch_elems = tp;
+    StageParams s4 = mk(n, q, t, tp, 2, 1, qp, 1, (long long)n * qp);                  // -> [t][n][q]
+    s4.out_rows = t * n; s4.out_C = q; s4.out_pitch_elems = qp;
+    StageParams s5 = mk(t, n, q, qp, 1, 1, (long long)q * np, 1, np);                  // -> [t][q][n]
+    s5.out_rows = t * q; s5.out_C = n; s5.out_pitch_elems = np;
+    StageParams s6 = mk(t, q, n, np, 0, 1, (long long)q * n, n, 1);                    // -> Z [t][q][n]
+    s6.final_stage = 1;
+    s6.out_rows = t * q; s6.out_C = n; s6.out_pitch_elems = n;
+    S = {s1, s2, s3, s4, s5, s6};
+  } else {
+    StageParams s1 = mk(1, q, n, first_pitch, 0, 0, qp, 1, qp);                        // -> [n][q]
+    s1.out_rows = n; s1.out_C = q; s1.out_pitch_elems = qp;
+    StageParams s2 = mk(n, 1, q, qp, 1, 0, qp, 0, 1);                                   // -> [n][q], x G
+    s2.scale = 1; s2.lamA = 0; s2.lamB = 2; s2.lamC = 1;
+    s2.out_rows = n; s2.out_C = q; s2.out_pitch_elems = qp;
+    StageParams s5 = mk(1, n, q, qp, 1, 1, np, 1, np);                                  // -> [q][n]
+    s5.out_rows = q; s5.out_C = n; s5.out_pitch_elems = np;
+    StageParams s6 = mk(1, q, n, np, 0, 1, (long long)q * n, n, 1);                    // -> Z [q][n]
+    s6.final_stage = 1;
+    s6.out_rows = q; s6.out_C = n; s6.out_pitch_elems = n;
+    S = {s1, s2, s5, s6};
+  }
+  p->stages = S;
+  size_t mx = 0;
+  for (const auto& s : S)
+    if (!s.final_stage) mx = std::max(mx, (size_t)s.out_rows * (size_t)s.out_pitch_elems);
+  p->t_elems = mx;
+}
+
+template <class T>
+int dalloc(tpcg_plan* p, T** ptr, size_t count) {
+  *ptr = nullptr;
+  if (count == 0) count = 1;
+  if (cudaMalloc((void**)ptr, count * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return TPCG_ERR_OOM;
+  }
+  p->device_bytes += count * sizeof(T);
+  return TPCG_OK;
+}
+
+void free_plan(tpcg_plan* p) {
+  if (!p) return;
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  else cudaDeviceSynchronize();
+  tc_plan_release(p);
+  for (int a = 0; a < 3; ++a) {
+    for (int d = 0; d < 2; ++d) {
+      cudaFree(p->d_W64[a][d]);
+      cudaFree(p->d_Wt16[a][d]);
+    }
+    cudaFree(p->d_lam64[a]);
+    cudaFree(p->d_lam32[a]);
+  }
+  cudaFree(p->d_R);
+  cudaFree(p->d_P);
+  cudaFree(p->d_W);
+  cudaFree(p->d_Z);
+  cudaFree(p->d_Rlp);
+  cudaFree(p->d_T[0]);
+  cudaFree(p->d_T[1]);
+  cudaFree(p->d_eta_h);
+  cudaFree(p->d_ups_h);
+  cudaFree(p->d_state);
+  cudaFree(p->d_partials);
+  cudaFree(p->d_err);
+  if (p->h_state) cudaFreeHost(p->h_state);
+  delete p;
+}
+
+uint16_t host_bf16(double x) {
+  // round-to-nearest-even FP64 -> BF16 on the host (eigenbasis copies)
+  float f = (float)x;
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  const uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7fffu + lsb;
+  return (uint16_t)(u >> 16);
+}
+
+int run_precond(const tpcg_plan* p, const double* R, void* Z, SolveState* st) {
+  if (p->prec == TPCG_FP64) {
+    run_precond_f64(p, R, (double*)Z, st);
+    return TPCG_OK;
+  }
+  return run_precond_tc(p, (float*)Z, st);
+}
+
+int last_cuda_error() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    fprintf(stderr, "libtpcg: CUDA error %s\n", cudaGetErrorString(e));
+    return TPCG_ERR_CUDA;
+  }
+  return TPCG_OK;
+}
+
+int solve_impl(tpcg_plan* p, const double* eta, double* ups, double tol, int maxit, unsigned flags, tpcg_info* info) {
+  if (!p || !eta || !ups) return TPCG_ERR_INVALID_ARG;
+  if (!(tol > 0.0) || !(tol < 1.0) || maxit < 1) return TPCG_ERR_INVALID_ARG;
+  const Geom g = make_geom(p);
+  const bool zero_guess = (flags & TPCG_ZERO_GUESS) != 0;
+  SolveState* hs = p->h_state;
+  std::memset(hs, 0, sizeof(SolveState));
+  hs->maxit = maxit;
+  hs->tol2 = tol * tol;
+  hs->first = 1;
+  hs->zero_guess = zero_guess ? 1 : 0;
+  hs->singular = p->singular ? 1 : 0;
+  hs->status = TPCG_OK;
+  if (cudaMemcpyAsync(p->d_state, hs, sizeof(SolveState), cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
+    return TPCG_ERR_CUDA;
+  // Algorithm 1, lines 2-7 (eq. centering first when singular)
+  if (p->singular) launch_eta_sum(p, g, eta);
+  launch_init_residual(p, g, eta, ups, zero_guess);
+  int rc = run_precond(p, p->d_R, p->d_Z, p->d_state);
+  if (rc) return rc;
+  if ((rc = last_cuda_error())) return rc;
+  // lines 8-18, in chunks of iterations between host reads of the state
+  int issued = 0;
+  int chunk = (p->prec == TPCG_FP64) ? 2 : 4;
+  for (;;) {
+    if (cudaMemcpyAsync(hs, p->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess)
+      return TPCG_ERR_CUDA;
+    if (cudaStreamSynchronize(p->stream) != cudaSuccess) return last_cuda_error() ? TPCG_ERR_CUDA : TPCG_ERR_CUDA;
+    if (hs->done || issued > maxit + 1) break;
+    for (int c = 0; c < chunk; ++c) {
+      launch_direction(p, g);                              // lines 10-11 (P from line 17 of the previous pass)
+      launch_update(p, g, ups);                            // lines 12-13
+      launch_true_residual(p, g, eta, ups, false);         // stop test
+      if ((rc = run_precond(p, p->d_R, p->d_Z, p->d_state))) return rc;  // lines 14-16
+    }
+    issued += chunk;
+    chunk = (p->prec == TPCG_FP64) ? 1 : 2;
+    if ((rc = last_cuda_error())) return rc;
+  }
+  if (hs->done == 2) {
+    launch_zero(p, g.N, ups);  // eta_hat = 0: minimum-norm solution is 0
+  } else {
+    if (!hs->done || hs->status == TPCG_ERR_BREAKDOWN) {
+      launch_true_residual(p, g, eta, ups, true);  // report the true residual of the returned iterate
+      if (!hs->done) hs->status = TPCG_ERR_NOT_CONVERGED;
+    }
+    if (p->singular) launch_center_u(p, g, ups);
+  }
+  const int status_host = hs->status;
+  const int done_host = hs->done;
+  if (cudaMemcpyAsync(hs, p->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess)
+    return TPCG_ERR_CUDA;
+  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return TPCG_ERR_CUDA;
+  if ((rc = last_cuda_error())) return rc;
+  int status = hs->status;
+  if (!done_host) status = status_host;
+  if (hs->timeout) status = TPCG_ERR_TIMEOUT;
+  if (info) {
+    info->status = status;
+    info->iters = hs->iter;
+    info->precond_applies = hs->precond_applies;
+    info->prec = p->prec;
+    const double en = sqrt(hs->eta_norm2);
+    info->eta_norm = en;
+    info->rel_res_true = (done_host == 2 || en == 0.0) ? 0.0 : sqrt(hs->true_rr) / en;
+    info->rel_res_recur = (en == 0.0) ? 0.0 : sqrt(hs->rr) / en;
+    info->removed_mean = p->singular ? hs->mean_eta : 0.0;
+    info->null_component = (p->singular && done_host != 2) ? hs->sumU / (double)p->N : 0.0;
+  }
+  return status;
+}
+
+}  // namespace
+}  // namespace tpcg
+
+using namespace tpcg;
+
+extern "C" {
+
+int tpcg_plan_create(int nx, int ny, int nz, const int bc[3], const double h[3], int prec, void* stream,
+                     tpcg_plan** out) {
+  if (!out) return TPCG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!bc || !h) return TPCG_ERR_INVALID_ARG;
+  if (nx < 3 || ny < 3 || !(nz == 1 || nz >= 3)) return TPCG_ERR_INVALID_ARG;
+  const int naxes = (nz == 1) ? 2 : 3;
+  for (int m = 0; m < naxes; ++m) {
+    if (bc[m] < 0 || bc[m] > 4) return TPCG_ERR_INVALID_ARG;
+    if (!(h[m] > 0.0) || !std::isfinite(h[m])) return TPCG_ERR_INVALID_ARG;
+  }
+  if (prec != TPCG_FP64 && prec != TPCG_MIXED_BF16 && prec != TPCG_MIXED_TF32) return TPCG_ERR_INVALID_ARG;
+  if (prec == TPCG_MIXED_TF32) return TPCG_ERR_UNSUPPORTED;
+  if (prec != TPCG_FP64 && (nx > 256 || ny > 256 || nz > 256)) return TPCG_ERR_UNSUPPORTED;
+  const long long N = (long long)nx * ny * nz;
+  if (N > (1LL << 31)) return TPCG_ERR_UNSUPPORTED;
+
+  tpcg_plan* p = new (std::nothrow) tpcg_plan();
+  if (!p) return TPCG_ERR_OOM;
+  p->nx = nx; p->ny = ny; p->nz = nz;
+  for (int m = 0; m < 3; ++m) {
+    p->bc[m] = (m < naxes) ? bc[m] : kBcN;
+    p->h[m] = (m < naxes) ? h[m] : 1.0;
+  }
+  p->prec = prec;
+  p->stream = (cudaStream_t)stream;
+  p->is2d = (nz == 1);
+  p->N = N;
+  p->singular = true;
+  for (int m = 0; m < naxes; ++m)
+    if (!(p->bc[m] == kBcP || p->bc[m] == kBcN)) p->singular = false;
+  if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return TPCG_ERR_CUDA; }
+  cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+  if (p->num_sms <= 0) p->num_sms = 1;
+
+  // Algorithm 5, lines 2-4: eigenpairs per axis (closed forms, checked)
+  const int lens[3] = {nx, ny, nz};
+  for (int m = 0; m < 3; ++m) {
+    if (build_axis(lens[m], p->bc[m], p->h[m], p->ax[m]) != 0) { delete p; return TPCG_ERR_EIGENBASIS; }
+  }
+
+  int rc = TPCG_OK;
+  const int padv = (prec == TPCG_FP64) ? 1 : 8;
+  for (int m = 0; m < 3; ++m) p->pitch16[m] = pad_to(lens[m], 8);
+  build_stages(p, padv, (prec == TPCG_FP64) ? nx : p->pitch16[0]);
+
+  // eigenbases on the device
+  for (int m = 0; m < 3 && !rc; ++m) {
+    const int l = lens[m];
+    const AxisBasis& A = p->ax[m];
+    std::vector<double> VT((size_t)l * l);
+    for (int i = 0; i < l; ++i)
+      for (int j = 0; j < l; ++j) VT[(size_t)j * l + i] = A.V[(size_t)i * l + j];
+    std::vector<float> lam32(A.lam.begin(), A.lam.end());
+    if ((rc = dalloc(p, &p->d_W64[m][0], (size_t)l * l))) break;
+    if ((rc = dalloc(p, &p->d_W64[m][1], (size_t)l * l))) break;
+    if ((rc = dalloc(p, &p->d_lam64[m], (size_t)l))) break;
+    if ((rc = dalloc(p, &p->d_lam32[m], (size_t)l))) break;
+    cudaMemcpy(p->d_W64[m][0], A.V.data(), sizeof(double) * l * l, cudaMemcpyHostToDevice);   // W = V
+    cudaMemcpy(p->d_W64[m][1], VT.data(), sizeof(double) * l * l, cudaMemcpyHostToDevice);    // W = V^T
+    cudaMemcpy(p->d_lam64[m], A.lam.data(), sizeof(double) * l, cudaMemcpyHostToDevice);
+    cudaMemcpy(p->d_lam32[m], lam32.data(), sizeof(float) * l, cudaMemcpyHostToDevice);
+    if (prec != TPCG_FP64) {
+      // K-major W^T in BF16: dir 0 (W = V) -> element [c'][c] = V[c][c']; dir 1 (W = V^T) -> V[c'][c].
+      const int lp = p->pitch16[m];
+      std::vector<uint16_t> b0((size_t)l * lp, 0), b1((size_t)l * lp, 0);
+      for (int r = 0; r < l; ++r)
+        for (int c = 0; c < l; ++c) {
+          b0[(size_t)r * lp + c] = host_bf16(A.V[(size_t)c * l + r]);
+          b1[(size_t)r * lp + c] = host_bf16(A.V[(size_t)r * l + c]);
+        }
+      uint16_t *d0 = nullptr, *d1 = nullptr;
+      if ((rc = dalloc(p, &d0, b0.size()))) break;
+      p->d_Wt16[m][0] = d0;
+      if ((rc = dalloc(p, &d1, b1.size()))) break;
+      p->d_Wt16[m][1] = d1;
+      cudaMemcpy(d0, b0.data(), b0.size() * 2, cudaMemcpyHostToDevice);
+      cudaMemcpy(d1, b1.data(), b1.size() * 2, cudaMemcpyHostToDevice);
+    }
+  }
+  // PCG workspaces
+  if (!rc) rc = dalloc(p, &p->d_R, (size_t)N);
+  if (!rc) rc = dalloc(p, &p->d_P, (size_t)N);
+  if (!rc) rc = dalloc(p, &p->d_W, (size_t)N);
+  if (!rc) {
+    if (prec == TPCG_FP64) {
+      double* z = nullptr;
+      rc = dalloc(p, &z, (size_t)N);
+      p->d_Z = z;
+    } else {
+      float* z = nullptr;
+      rc = dalloc(p, &z, (size_t)N);
+      p->d_Z = z;
+    }
+  }
+  if (!rc && prec != TPCG_FP64) {
+    uint16_t* r = nullptr;
+    rc = dalloc(p, &r, (size_t)nz * ny * p->pitch16[0]);
+    p->d_Rlp = r;
+  }
+  for (int i = 0; i < 2 && !rc; ++i) {
+    if (prec == TPCG_FP64) {
+      double* t = nullptr;
+      rc = dalloc(p, &t, p->t_elems);
+      p->d_T[i] = t;
+    } else {
+      uint16_t* t = nullptr;
+      rc = dalloc(p, &t, p->t_elems);
+      p->d_T[i] = t;
+      if (!rc) cudaMemset(t, 0, p->t_elems * 2);
+    }
+  }
+  if (!rc) rc = dalloc(p, &p->d_state, 1);
+  {
+    // one slot of 4 doubles per block of the largest reducing launch
+    const int bx = (nx + 31) / 32, by = (ny + 7) / 8;
+    long long most = (long long)bx * by * nz + (long long)p->num_sms * 8;
+    const StageParams& fs = p->stages.back();
+    most = std::max(most, (((long long)fs.A * fs.B + 63) / 64) * ((fs.Cout + 63) / 64));
+    p->partial_slots = (size_t)std::max(16384LL, most) * 4;
+  }
+  if (!rc) rc = dalloc(p, &p->d_partials, p->partial_slots);
+  if (!rc) rc = dalloc(p, &p->d_err, 4);
+  if (!rc && cudaMallocHost((void**)&p->h_state, sizeof(SolveState)) != cudaSuccess) rc = TPCG_ERR_OOM;
+  if (!rc) {
+    cudaMemset(p->d_state, 0, sizeof(SolveState));
+    cudaMemset(p->d_err, 0, 16);
+  }
+  // launch configuration, fixed per plan (reproducible reductions)
+  if (!rc) {
+    p->st_block = dim3(32, 8, 1);
+    const int bx = (nx + 31) / 32, by = (ny + 7) / 8;
+    const int target = p->num_sms * 6;
+    int zsplit = std::max(1, std::min(nz, (target + bx * by - 1) / (bx * by)));
+    int zchunk = (nz + zsplit - 1) / zsplit;
+    zsplit = (nz + zchunk - 1) / zchunk;
+    p->st_grid = dim3(bx, by, zsplit);
+    p->st_zchunk = zchunk;
+    const long long want = (N + 255) / 256;
+    p->stream_blocks = (int)std::max(1LL, std::min<long long>(want, (long long)p->num_sms * 8));
+    if ((size_t)bx * by * zsplit * 4 > p->partial_slots) rc = TPCG_ERR_UNSUPPORTED;
+  }
+  if (!rc && prec != TPCG_FP64) rc = tc_plan_setup(p);
+  if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = TPCG_ERR_CUDA;
+  if (rc) {
+    cudaGetLastError();
+    free_plan(p);
+    return rc;
+  }
+  *out = p;
+  return TPCG_OK;
+}
+
+int tpcg_plan_destroy(tpcg_plan* plan) {
+  if (!plan) return TPCG_ERR_INVALID_ARG;
+  DeviceGuard dg(plan->device);
+  free_plan(plan);
+  return TPCG_OK;
+}
+
+int tpcg_plan_set_stream(tpcg_plan* plan, void* stream) {
+  if (!plan) return TPCG_ERR_INVALID_ARG;
+  plan->stream = (cudaStream_t)stream;
+  return TPCG_OK;
+}
+
+int tpcg_plan_device_bytes(const tpcg_plan* plan, size_t* bytes) {
+  if (!plan || !bytes) return TPCG_ERR_INVALID_ARG;
+  *bytes = plan->device_bytes;
+  return TPCG_OK;
+}
+
+int tpcg_solve(tpcg_plan* plan, const double* eta, double* ups, double tol, int maxit, unsigned flags,
+               tpcg_info* info) {
+  if (!plan) return TPCG_ERR_INVALID_ARG;
+  DeviceGuard dg(plan->device);
+  const int rc = solve_impl(plan, eta, ups, tol, maxit, flags, info);
+  if (info && rc != info->status) info->status = rc;
+  return rc;
+}
+
+int tpcg_solve_host(tpcg_plan* plan, const double* eta_host, double* ups_host, double tol, int maxit, unsigned flags,
+                    tpcg_info* info) {
+  if (!plan || !eta_host || !ups_host) return TPCG_ERR_INVALID_ARG;
+  DeviceGuard dg(plan->device);
+  const size_t bytes = sizeof(double) * (size_t)plan->N;
+  if (!plan->d_eta_h) {
+    if (dalloc(plan, &plan->d_eta_h, (size_t)plan->N) || dalloc(plan, &plan->d_ups_h, (size_t)plan->N))
+      return TPCG_ERR_OOM;
+  }
+  if (cudaMemcpyAsync(plan->d_eta_h, eta_host, bytes, cudaMemcpyHostToDevice, plan->stream) != cudaSuccess)
+    return TPCG_ERR_CUDA;
+  if (!(flags & TPCG_ZERO_GUESS) &&
+      cudaMemcpyAsync(plan->d_ups_h, ups_host, bytes, cudaMemcpyHostToDevice, plan->stream) != cudaSuccess)
+    return TPCG_ERR_CUDA;
+  const int rc = solve_impl(plan, plan->d_eta_h, plan->d_ups_h, tol, maxit, flags, info);
+  if (rc == TPCG_ERR_CUDA || rc == TPCG_ERR_INVALID_ARG) return rc;
+  if (cudaMemcpyAsync(ups_host, plan->d_ups_h, bytes, cudaMemcpyDeviceToHost, plan->stream) != cudaSuccess)
+    return TPCG_ERR_CUDA;
+  if (cudaStreamSynchronize(plan->stream) != cudaSuccess) return TPCG_ERR_CUDA;
+  return rc;
+}
+
+int tpcg_precond_apply(tpcg_plan* plan, const double* r, double* z) {
+  if (!plan || !r || !z || r == z) return TPCG_ERR_INVALID_ARG;
+  DeviceGuard dg(plan->device);
+  int rc;
+  if (plan->prec == TPCG_FP64) {
+    run_precond_f64(plan, r, z, nullptr);
+    return last_cuda_error();
+  }
+  const Geom g = make_geom(plan);
+  launch_to_lp(plan, g, r);
+  if ((rc = run_precond_tc(plan, (float*)plan->d_Z, nullptr))) return rc;
+  launch_f32_to_f64(plan, plan->N, (const float*)plan->d_Z, z);
+  return last_cuda_error();
+}
+
+int tpcg_apply_laplacian(tpcg_plan* plan, const double* x, double* w) {
+  if (!plan || !x || !w || x == w) return TPCG_ERR_INVALID_ARG;
+  DeviceGuard dg(plan->device);
+  launch_apply_laplacian(plan, make_geom(plan), x, w);
+  return last_cuda_error();
+}
+
+int tpcg_rhs_add_bc(tpcg_plan* plan, double* eta, const double bval[6]) {
+  if (!plan || !eta || !bval) return TPCG_ERR_INVALID_ARG;
+  DeviceGuard dg(plan->device);
+  launch_rhs_add_bc(plan, make_geom(plan), eta, bval);
+  return last_cuda_error();
+}
+
+int tpcg_plan_eigenpairs(const tpcg_plan* plan, int axis, double* lam, double* V) {
+  if (!plan || axis < 0 || axis > 2 || !lam || !V) return TPCG_ERR_INVALID_ARG;
+  const AxisBasis& A = plan->ax[axis];
+  std::memcpy(lam, A.lam.data(), sizeof(double) * A.len);
+  std::memcpy(V, A.V.data(), sizeof(double) * (size_t)A.len * A.len);
+  return TPCG_OK;
+}
+
+const char* tpcg_strerror(int status) {
+  switch (status) {
+    case TPCG_OK: return "ok";
+    case TPCG_ERR_INVALID_ARG: return "invalid argument";
+    case TPCG_ERR_OOM: return "out of memory";
+    case TPCG_ERR_CUDA: return "CUDA error";
+    case TPCG_ERR_NOT_CONVERGED: return "not converged within maxit";
+    case TPCG_ERR_BREAKDOWN: return "breakdown (non-positive or non-finite CG scalar)";
+    case TPCG_ERR_TIMEOUT: return "bounded device wait timed out";
+    case TPCG_ERR_UNSUPPORTED: return "unsupported configuration";
+    case TPCG_ERR_EIGENBASIS: return "eigenbasis accuracy check failed";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,450 @@
+// FP64 kernels of the PCG iteration (Algorithm 1, Sec. 4.1) around the
+// preconditioner: the matrix-free Kronecker-sum stencil of eq. (ourproblem),
+// the fused direction / update / residual kernels, centring (eq. centering),
+// and the deterministic reductions that produce alpha, beta and the stop test
+// on the device.
+//
+// Stencil scheme: a block owns a 32 x 8 tile of (x, y) columns and marches
+// along z through a chunk of planes.  Each plane of the field, with a one-point
+// halo in x and y, is staged in a 4-slot shared-memory ring, so the z
+// neighbours come from the ring as well and every field value is loaded (and,
+// for the direction kernel, formed) once per tile.  Boundary conditions enter
+// only through the halo ("ghost") values: periodic wraps, Dirichlet reads 0,
+// Neumann mirrors the boundary value -- which reproduces the corner entries
+// (alpha, beta, gamma) of eq. (lap1d) exactly.
+#include <cstdio>
+
+#include "tpcg_dev.cuh"
+
+namespace tpcg {
+
+constexpr int TX = 32, TY = 8;
+constexpr int SX = TX + 2, SY = TY + 2;
+
+// Map a possibly out-of-range coordinate to the index whose value the ghost
+// takes, or -1 for a Dirichlet (zero) ghost.
+__device__ __forceinline__ int ghost_index(int g, int n, int bc) {
+  if (g >= 0 && g < n) return g;
+  if (g == -1) {
+    if (bc == kBcP) return n - 1;
+    if (bc == kBcN || bc == kBcND) return 0;  // Neumann at the start: mirror
+    return -1;                                // Dirichlet at the start
+  }
+  if (g == n) {
+    if (bc == kBcP) return 0;
+    if (bc == kBcN || bc == kBcDN) return n - 1;  // Neumann at the end
+    return -1;
+  }
+  return -1;
+}
+
+// ------------------------------------------------------------------ fields
+struct FieldPlain {  // the stencil is applied to x itself
+  const double* __restrict__ x;
+  __device__ __forceinline__ double operator()(long long i) const { return __ldg(x + i); }
+};
+
+template <class ZT>
+struct FieldDirection {  // P = (Z - mean Z) + beta * P_old   (Algorithm 1, line 17; Remark orthogonality)
+  const ZT* __restrict__ z;
+  const double* __restrict__ pold;
+  double mZ, beta;
+  int first;
+  __device__ __forceinline__ double operator()(long long i) const {
+    double zi;
+    if constexpr (sizeof(ZT) == 4)
+      zi = f32_to_f64_int(__ldg(reinterpret_cast<const float*>(z) + i));
+    else
+      zi = __ldg(reinterpret_cast<const double*>(z) + i);
+    zi -= mZ;
+    return first ? zi : fma(beta, __ldg(pold + i), zi);
+  }
+};
+
+// ------------------------------------------------------------------ stencil driver
+// Calls op(idx, c, w, acc) for every grid point, where c is the field value
+// and w = (L field)(point).  Accumulates NQ sums and finishes with fin().
+template <int NQ, class Field, class Op, class Fin>
+__device__ __forceinline__ void stencil_sweep(const Geom& g, int zchunk, const Field& field, Op& op, double* partials,
+                                              unsigned* ticket, Fin fin) {
+  __shared__ double ring[4][SY][SX];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * TX + tx;
+  const int bx0 = blockIdx.x * TX, by0 = blockIdx.y * TY;
+  const int x = bx0 + tx, y = by0 + ty;
+  const int k0 = blockIdx.z * zchunk;
+  const int k1 = min(g.nz, k0 + zchunk);
+  const bool active = (x < g.nx) && (y < g.ny);
+  const bool has_z = g.nz > 1;
+  const long long plane = (long long)g.nx * g.ny;
+  double acc[NQ > 0 ? NQ : 1];
+#pragma unroll
+  for (int q = 0; q < (NQ > 0 ? NQ : 1); ++q) acc[q] = 0.0;
+
+  auto load_plane = [&](int kk) {
+    const int kz = has_z ? ghost_index(kk, g.nz, g.bc[2]) : kk;
+    double(*dst)[SX] = ring[kk & 3];
+    for (int e = tid; e < SX * SY; e += TX * TY) {
+      const int sx = e % SX, sy = e / SX;
+      const int gx = ghost_index(bx0 + sx - 1, g.nx, g.bc[0]);
+      const int gy = ghost_index(by0 + sy - 1, g.ny, g.bc[1]);
+      double v = 0.0;
+      if (kz >= 0 && gx >= 0 && gy >= 0 && bx0 + sx - 1 <= g.nx && by0 + sy - 1 <= g.ny)
+        v = field((long long)kz * plane + (long long)gy * g.nx + gx);
+      dst[sy][sx] = v;
+    }
+  };
+
+  if (k0 < k1) {
+    if (has_z) load_plane(k0 - 1);
+    load_plane(k0);
+    const double ihx = g.ih2[0], ihy = g.ih2[1], ihz = g.ih2[2];
+    const bool uniform = (ihx == ihy) && (!has_z || ihz == ihx);
+    for (int k = k0; k < k1; ++k) {
+      if (has_z) load_plane(k + 1);
+      __syncthreads();
+      if (active) {
+        const double(*cur)[SX] = ring[k & 3];
+        const double c = cur[ty + 1][tx + 1];
+        double w;
+        if (uniform) {
+          double s = (cur[ty + 1][tx] + cur[ty + 1][tx + 2]) + (cur[ty][tx + 1] + cur[ty + 2][tx + 1]);
+          double diag = 4.0;
+          if (has_z) {
+            s += ring[(k - 1) & 3][ty + 1][tx + 1] + ring[(k + 1) & 3][ty + 1][tx + 1];
+            diag = 6.0;
+          }
+          w = fma(diag, c, -s);
+          if (ihx != 1.0) w *= ihx;
+        } else {
+          const double wx = fma(2.0, c, -(cur[ty + 1][tx] + cur[ty + 1][tx + 2]));
+          const double wy = fma(2.0, c, -(cur[ty][tx + 1] + cur[ty + 2][tx + 1]));
+          w = fma(wx, ihx, wy * ihy);
+          if (has_z) {
+            const double wz = fma(2.0, c, -(ring[(k - 1) & 3][ty + 1][tx + 1] + ring[(k + 1) & 3][ty + 1][tx + 1]));
+            w = fma(wz, ihz, w);
+          }
+        }
+        const long long idx = (long long)k * plane + (long long)y * g.nx + x;
+        op(idx, c, w, acc);
+      }
+    }
+  }
+  if constexpr (NQ > 0) {
+    const int nblocks = gridDim.x * gridDim.y * gridDim.z;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    grid_reduce<NQ>(acc, partials, ticket, nblocks, bid, fin);
+  }
+}
+
+struct NoFin {
+  template <class T>
+  __device__ void operator()(T&) const {}
+};
+
+// ------------------------------------------------------------------ W = L x
+struct OpApply {
+  double* __restrict__ w;
+  __device__ __forceinline__ void operator()(long long i, double, double wv, double (&)[1]) { w[i] = wv; }
+};
+
+__global__ void __launch_bounds__(TX* TY) k_apply_laplacian(Geom g, int zchunk, const double* __restrict__ x,
+                                                            double* __restrict__ w) {
+  FieldPlain f{x};
+  OpApply op{w};
+  stencil_sweep<0>(g, zchunk, f, op, nullptr, nullptr, NoFin{});
+}
+
+// ------------------------------------------------------------------ low-precision copy of R
+__device__ __forceinline__ void store_lp(void* rlp, int pitch, int nx, long long i, double r) {
+  if (!rlp) return;
+  long long j = i;
+  if (pitch != nx) {
+    const long long row = i / nx;
+    j = row * pitch + (i - row * nx);
+  }
+  reinterpret_cast<uint16_t*>(rlp)[j] = f64_to_bf16_bits(r);
+}
+
+// ------------------------------------------------------------------ residual R = eta_hat - L U
+// Used for the initial residual (Algorithm 1, lines 3-4) and the FP64 check of
+// the true residual (stop test); the latter replaces R (residual replacement)
+// and accumulates sum(U) for the exit centring.
+struct OpResidual {
+  const double* __restrict__ eta;
+  double* __restrict__ R;
+  void* rlp;
+  int pitch, nx;
+  double mean;
+  __device__ __forceinline__ void operator()(long long i, double c, double w, double (&acc)[4]) {
+    const double e = __ldg(eta + i) - mean;
+    const double r = e - w;
+    R[i] = r;
+    store_lp(rlp, pitch, nx, i, r);
+    acc[0] = fma(r, r, acc[0]);
+    acc[1] += r;
+    acc[2] = fma(e, e, acc[2]);
+    acc[3] += c;
+  }
+};
+
+__device__ void fin_init(SolveState* st, const double (&s)[4]) {
+  st->rr = s[0];
+  st->sumR = s[1];
+  st->eta_norm2 = s[2];
+  st->tol2 = st->tol2 * s[2];  // tol^2 was stored; scale by ||eta_hat||^2
+  if (!isfinite(s[0]) || !isfinite(s[2])) {
+    st->status = TPCG_ERR_BREAKDOWN;
+    st->done = 1;
+  } else if (s[2] == 0.0) {  // eta_hat = 0: the minimum-norm solution is 0
+    st->status = TPCG_OK;
+    st->done = 2;
+  }
+}
+
+__global__ void __launch_bounds__(TX* TY) k_init_residual(Geom g, int zchunk, const double* __restrict__ eta,
+                                                          const double* __restrict__ U, double* __restrict__ R,
+                                                          void* rlp, int pitch, SolveState* st, double* partials) {
+  FieldPlain f{U};
+  OpResidual op{eta, R, rlp, pitch, g.nx, st->mean_eta};
+  stencil_sweep<4>(g, zchunk, f, op, partials, &st->tickets[kTkInit],
+                   [st](const double(&s)[4]) { fin_init(st, s); });
+}
+
+__device__ void fin_true(SolveState* st, const double (&s)[4]) {
+  st->true_rr = s[0];
+  st->sumU = s[3];
+  if (!isfinite(s[0])) {
+    st->status = TPCG_ERR_BREAKDOWN;
+    st->done = 1;
+    return;
+  }
+  if (s[0] <= st->tol2) {
+    st->status = TPCG_OK;
+    st->done = 1;
+  } else if (st->iter >= st->maxit) {
+    st->status = TPCG_ERR_NOT_CONVERGED;
+    st->done = 1;
+  } else {  // keep iterating from the replaced (true) residual
+    st->rr = s[0];
+    st->sumR = s[1];
+    st->need_check = 0;
+  }
+}
+
+__global__ void __launch_bounds__(TX* TY) k_true_residual(Geom g, int zchunk, const double* __restrict__ eta,
+                                                          const double* __restrict__ U, double* __restrict__ R,
+                                                          void* rlp, int pitch, SolveState* st, double* partials,
+                                                          int force) {
+  if (!force && (st->done || !st->need_check)) return;
+  FieldPlain f{U};
+  OpResidual op{eta, R, rlp, pitch, g.nx, st->mean_eta};
+  stencil_sweep<4>(g, zchunk, f, op, partials, &st->tickets[kTkTrue],
+                   [st, force](const double(&s)[4]) {
+                     if (force) {
+                       st->true_rr = s[0];
+                       st->sumU = s[3];
+                     } else {
+                       fin_true(st, s);
+                     }
+                   });
+}
+
+// ------------------------------------------------------------------ direction + W = L P
+// P_s = Z_s' + beta_s P_{s-1} (line 17, with Z centred), W = L P (line 10),
+// <W, P> and alpha = rho / <W, P> (line 11).
+struct OpDirection {
+  double* __restrict__ P;
+  double* __restrict__ W;
+  __device__ __forceinline__ void operator()(long long i, double c, double w, double (&acc)[1]) {
+    P[i] = c;
+    W[i] = w;
+    acc[0] = fma(w, c, acc[0]);
+  }
+};
+
+__device__ void fin_direction(SolveState* st, const double (&s)[1]) {
+  st->pWp = s[0];
+  st->first = 0;
+  if (!(s[0] > 0.0) || !isfinite(s[0])) {
+    st->status = TPCG_ERR_BREAKDOWN;
+    st->done = 1;
+    return;
+  }
+  st->alpha = st->rho / s[0];
+}
+
+template <class ZT>
+__global__ void __launch_bounds__(TX* TY) k_direction(Geom g, int zchunk, const ZT* __restrict__ Z,
+                                                      double* __restrict__ P, double* __restrict__ W, SolveState* st,
+                                                      double* partials) {
+  if (st->done) return;
+  FieldDirection<ZT> f{Z, P, st->mZ, st->beta, st->first};
+  OpDirection op{P, W};
+  stencil_sweep<1>(g, zchunk, f, op, partials, &st->tickets[kTkDir],
+                   [st](const double(&s)[1]) { fin_direction(st, s); });
+}
+
+// ------------------------------------------------------------------ streaming kernels
+// U += alpha P (line 12), R -= alpha W (line 13), low-precision copy of R,
+// ||R||^2 and sum(R); iteration counter and recurrence stop test.
+__device__ void fin_update(SolveState* st, const double (&s)[2]) {
+  st->rr = s[0];
+  st->sumR = s[1];
+  st->iter += 1;
+  st->zero_guess = 0;
+  if (!isfinite(s[0])) {
+    st->status = TPCG_ERR_BREAKDOWN;
+    st->done = 1;
+    return;
+  }
+  if (s[0] <= st->tol2 || st->iter >= st->maxit) st->need_check = 1;
+}
+
+__global__ void __launch_bounds__(256) k_update(long long N, int nx, double* __restrict__ U,
+                                                const double* __restrict__ P, const double* __restrict__ W,
+                                                double* __restrict__ R, void* rlp, int pitch, SolveState* st,
+                                                double* partials) {
+  if (st->done) return;
+  const double alpha = st->alpha;
+  const int zg = st->zero_guess;
+  double acc[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const double p = __ldg(P + i);
+    U[i] = zg ? alpha * p : fma(alpha, p, U[i]);
+    const double r = fma(-alpha, __ldg(W + i), R[i]);
+    R[i] = r;
+    store_lp(rlp, pitch, nx, i, r);
+    acc[0] = fma(r, r, acc[0]);
+    acc[1] += r;
+  }
+  grid_reduce<2>(acc, partials, &st->tickets[kTkUpd], gridDim.x, blockIdx.x,
+                 [st](const double(&s)[2]) { fin_update(st, s); });
+}
+
+// R = eta_hat (zero initial guess: lines 3-4 with U_0 = 0).
+__global__ void __launch_bounds__(256) k_init_zero(long long N, int nx, const double* __restrict__ eta,
+                                                   double* __restrict__ R, void* rlp, int pitch, SolveState* st,
+                                                   double* partials) {
+  const double mean = st->mean_eta;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const double r = __ldg(eta + i) - mean;
+    R[i] = r;
+    store_lp(rlp, pitch, nx, i, r);
+    acc[0] = fma(r, r, acc[0]);
+    acc[1] += r;
+  }
+  acc[2] = acc[0];
+  grid_reduce<4>(acc, partials, &st->tickets[kTkInit], gridDim.x, blockIdx.x,
+                 [st](const double(&s)[4]) { fin_init(st, s); });
+}
+
+// sum(eta) -> mean removed by eq. (centering).
+__global__ void __launch_bounds__(256) k_eta_sum(long long N, const double* __restrict__ eta, SolveState* st,
+                                                 double* partials) {
+  double acc[1] = {0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    acc[0] += __ldg(eta + i);
+  grid_reduce<1>(acc, partials, &st->tickets[kTkEta], gridDim.x, blockIdx.x,
+                 [st, N](const double(&s)[1]) { st->mean_eta = s[0] / (double)N; });
+}
+
+// U -= sum(U)/N: return the zero-mean (minimum-norm) representative.
+__global__ void __launch_bounds__(256) k_center_u(long long N, double* __restrict__ U, const SolveState* st) {
+  const double m = st->sumU / (double)N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    U[i] -= m;
+}
+
+__global__ void k_zero(long long N, double* __restrict__ U) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    U[i] = 0.0;
+}
+
+// BF16 copy of an FP64 field (preconditioner input for tpcg_precond_apply).
+__global__ void __launch_bounds__(256) k_to_lp(long long N, int nx, const double* __restrict__ r, void* rlp,
+                                               int pitch) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    store_lp(rlp, pitch, nx, i, __ldg(r + i));
+}
+
+// FP32 -> FP64 copy (Z of the mixed forms, for tpcg_precond_apply).
+__global__ void __launch_bounds__(256) k_f32_to_f64(long long N, const float* __restrict__ a, double* __restrict__ b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    b[i] = f32_to_f64_int(__ldg(a + i));
+}
+
+// Sec. 3.4.2: fold constant boundary data into the right-hand side.  bval[2m]
+// at the start face of axis m, bval[2m+1] at the end face; Dirichlet adds
+// u/h^2 to the boundary layer, Neumann adds e/h (e: outward derivative).
+__global__ void k_rhs_add_bc(Geom g, double* __restrict__ eta, double b0, double b1, double b2, double b3, double b4,
+                             double b5) {
+  const double bv[6] = {b0, b1, b2, b3, b4, b5};
+  const long long plane = (long long)g.nx * g.ny;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N; i += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(i / plane);
+    const long long rem = i - (long long)k * plane;
+    const int y = (int)(rem / g.nx), x = (int)(rem - (long long)y * g.nx);
+    const int pos[3] = {x, y, k};
+    const int len[3] = {g.nx, g.ny, g.nz};
+    double add = 0.0;
+    for (int m = 0; m < 3; ++m) {
+      if (len[m] == 1 || g.bc[m] == kBcP) continue;
+      const double ih2 = g.ih2[m];
+      const double ih = sqrt(ih2);
+      const int bc = g.bc[m];
+      const bool startD = (bc == kBcD || bc == kBcDN), endD = (bc == kBcD || bc == kBcND);
+      if (pos[m] == 0) add += startD ? bv[2 * m] * ih2 : bv[2 * m] * ih;
+      if (pos[m] == len[m] - 1) add += endD ? bv[2 * m + 1] * ih2 : bv[2 * m + 1] * ih;
+    }
+    if (add != 0.0) eta[i] += add;
+  }
+}
+
+// ------------------------------------------------------------------ host launchers
+void launch_apply_laplacian(const tpcg_plan* p, const Geom& g, const double* x, double* w) {
+  k_apply_laplacian<<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, x, w);
+}
+void launch_init_residual(const tpcg_plan* p, const Geom& g, const double* eta, const double* U, bool zero_guess) {
+  if (zero_guess)
+    k_init_zero<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, g.nx, eta, p->d_R, p->d_Rlp, p->pitch16[0], p->d_state,
+                                                          p->d_partials);
+  else
+    k_init_residual<<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, eta, U, p->d_R, p->d_Rlp,
+                                                                p->pitch16[0], p->d_state, p->d_partials);
+}
+void launch_eta_sum(const tpcg_plan* p, const Geom& g, const double* eta) {
+  k_eta_sum<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, eta, p->d_state, p->d_partials);
+}
+void launch_direction(const tpcg_plan* p, const Geom& g) {
+  if (p->prec == TPCG_FP64)
+    k_direction<double><<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, (const double*)p->d_Z, p->d_P,
+                                                                    p->d_W, p->d_state, p->d_partials);
+  else
+    k_direction<float><<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, (const float*)p->d_Z, p->d_P,
+                                                                   p->d_W, p->d_state, p->d_partials);
+}
+void launch_update(const tpcg_plan* p, const Geom& g, double* U) {
+  k_update<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, g.nx, U, p->d_P, p->d_W, p->d_R, p->d_Rlp, p->pitch16[0],
+                                                     p->d_state, p->d_partials);
+}
+void launch_true_residual(const tpcg_plan* p, const Geom& g, const double* eta, const double* U, bool force) {
+  k_true_residual<<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, eta, U, p->d_R, p->d_Rlp,
+                                                              p->pitch16[0], p->d_state, p->d_partials, force ? 1 : 0);
+}
+void launch_center_u(const tpcg_plan* p, const Geom& g, double* U) {
+  k_center_u<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, U, p->d_state);
+}
+void launch_zero(const tpcg_plan* p, long long N, double* U) { k_zero<<<p->stream_blocks, 256, 0, p->stream>>>(N, U); }
+void launch_to_lp(const tpcg_plan* p, const Geom& g, const double* r) {
+  k_to_lp<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, g.nx, r, p->d_Rlp, p->pitch16[0]);
+}
+void launch_f32_to_f64(const tpcg_plan* p, long long N, const float* a, double* b) {
+  k_f32_to_f64<<<p->stream_blocks, 256, 0, p->stream>>>(N, a, b);
+}
+void launch_rhs_add_bc(const tpcg_plan* p, const Geom& g, double* eta, const double* bv) {
+  k_rhs_add_bc<<<p->stream_blocks, 256, 0, p->stream>>>(g, eta, bv[0], bv[1], bv[2], bv[3], bv[4], bv[5]);
+}
+
+}  // namespace tpcg

@@ -1,0 +1,172 @@
+// Device-side definitions shared by the CUDA translation units of libtpcg.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include "tpcg_internal.h"
+
+namespace tpcg {
+
+// Scalars of one PCG solve (Algorithm 1), kept in device memory so that the
+// iteration runs without host round trips.  Written only by the last block
+// of a reduction ("finalize"), read by every later kernel.
+struct SolveState {
+  double mean_eta;     // mean removed from eta (eq. centering) when singular
+  double eta_norm2;    // ||eta_hat||^2
+  double tol2;         // tol^2 * ||eta_hat||^2
+  double rr;           // ||R_s||^2 of the recurrence
+  double sumR;         // sum(R_s)
+  double rho;          // rho_s = <R_s, Z_s'> with Z' the centred Z
+  double beta;         // beta_s
+  double alpha;        // alpha_s
+  double mZ;           // mean of Z_s (centring, Remark orthogonality)
+  double pWp;          // <W_s, P_{s-1}>
+  double true_rr;      // ||eta_hat - L U||^2 at the last FP64 check
+  double sumU;         // sum(U) at the last FP64 check
+  double zscale;       // power-of-two scale applied to R before low-precision conversion
+  int iter;            // s
+  int maxit;
+  int done;            // 1: stop issuing work
+  int status;          // TPCG_* code
+  int need_check;      // recurrence says converged (or maxit): evaluate the true residual
+  int first;           // 1 until the first direction P_0 = Z_0' has been formed
+  int zero_guess;      // U_0 = 0: the first update writes U instead of adding
+  int singular;
+  int precond_applies;
+  int timeout;         // a bounded device wait gave up
+  unsigned tickets[8]; // arrival counters of the last-block reductions
+};
+
+enum Ticket { kTkEta = 0, kTkInit = 1, kTkDir = 2, kTkUpd = 3, kTkTrue = 4, kTkPrec = 5, kTkMisc = 6 };
+
+// Geometry of a grid and its stencil (eq. lap1d / eq. ourproblem).
+struct Geom {
+  int nx, ny, nz;
+  int bc[3];
+  double ih2[3];   // 1/h^2 per axis (0 for an absent z axis)
+  long long N;     // nx*ny*nz
+};
+
+// Block-wide sum of NQ doubles; result valid in thread 0.  Fixed order: the
+// result is bitwise reproducible for a fixed launch configuration.
+template <int NQ>
+__device__ __forceinline__ void block_sum(double (&v)[NQ], double* sh /* NQ*32 doubles */) {
+  const int lane = threadIdx.x & 31;
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int warp = tid >> 5;
+  const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+  const int nwarps = (nthreads + 31) >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double x = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[q * 32 + warp] = x;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double x = (lane < nwarps) ? sh[q * 32 + lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      v[q] = x;
+    }
+  }
+  __syncthreads();
+}
+
+// Deterministic grid-wide reduction: every block stores its partial sums,
+// the last block to arrive adds all partials in block order and calls
+// fin(sums) from thread 0.  Returns true in the finishing thread.
+template <int NQ, class Fin>
+__device__ __forceinline__ void grid_reduce(double (&v)[NQ], double* partials, unsigned* ticket, int nblocks,
+                                            int block_id, Fin fin) {
+  __shared__ double sh[NQ * 32];
+  __shared__ bool last;
+  block_sum<NQ>(v, sh);
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) partials[(size_t)block_id * NQ + q] = v[q];
+    __threadfence();
+    unsigned t = atomicAdd(ticket, 1u);
+    last = (t == (unsigned)nblocks - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) s[q] = 0.0;
+  for (int b = tid; b < nblocks; b += nthreads) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) s[q] += __ldcg(&partials[(size_t)b * NQ + q]);
+  }
+  block_sum<NQ>(s, sh);
+  if (tid == 0) {
+    fin(s);
+    *ticket = 0u;
+  }
+}
+
+// FP64 -> BF16 with round-to-nearest-even done in integer arithmetic on the
+// bit pattern (the FP64 conversion pipe is slow on this part).  Values below
+// the BF16 normal range flush to signed zero; values above it saturate to the
+// largest finite BF16; NaN stays NaN.
+__device__ __forceinline__ uint16_t f64_to_bf16_bits(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const uint32_t hi = (uint32_t)(u >> 32);
+  const uint32_t sign = (hi >> 16) & 0x8000u;
+  const int e = (int)((hi >> 20) & 0x7ff);
+  if (e == 0x7ff) return (uint16_t)(sign | 0x7f80u | (((u & 0xfffffffffffffull) != 0) ? 0x40u : 0u));
+  const int eb = e - 1023 + 127;             // BF16 biased exponent
+  if (eb <= 0) return (uint16_t)sign;        // underflow: signed zero
+  const unsigned long long mant = u & 0xfffffffffffffull;  // 52 bits
+  uint32_t top = (uint32_t)(mant >> 45);     // 7 kept bits
+  const unsigned long long rest = mant & ((1ull << 45) - 1);
+  const unsigned long long halfway = 1ull << 44;
+  uint32_t bits = ((uint32_t)eb << 7) | top;
+  if (rest > halfway || (rest == halfway && (top & 1u))) bits += 1;  // carry may bump exponent: correct
+  if (bits >= 0x7f80u) bits = 0x7f7fu;       // saturate
+  return (uint16_t)(sign | bits);
+}
+
+// FP64 -> FP32 with round-to-nearest-even in integer arithmetic; underflow
+// to signed zero below the FP32 normal range, saturation above.
+__device__ __forceinline__ float f64_to_f32_int(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(u >> 32) & 0x80000000u;
+  const int e = (int)((u >> 52) & 0x7ff);
+  if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (((u & 0xfffffffffffffull) != 0) ? 0x400000u : 0u));
+  const int eb = e - 1023 + 127;
+  if (eb <= 0) return __uint_as_float(sign);
+  const unsigned long long mant = u & 0xfffffffffffffull;
+  uint32_t top = (uint32_t)(mant >> 29);     // 23 kept bits
+  const uint32_t rest = (uint32_t)(mant & ((1u << 29) - 1));
+  const uint32_t halfway = 1u << 28;
+  uint32_t bits = ((uint32_t)eb << 23) | top;
+  if (rest > halfway || (rest == halfway && (top & 1u))) bits += 1;
+  if (bits >= 0x7f800000u) bits = 0x7f7fffffu;
+  return __uint_as_float(sign | bits);
+}
+
+// FP32 -> FP64 is exact; done on the bit pattern as well.
+__device__ __forceinline__ double f32_to_f64_int(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t sign = b & 0x80000000u;
+  const uint32_t e = (b >> 23) & 0xff;
+  const uint32_t m = b & 0x7fffffu;
+  if (e == 0) {
+    if (m == 0) return __longlong_as_double((long long)((unsigned long long)sign << 32));
+    return (double)f;  // subnormal input: rare, hardware path
+  }
+  if (e == 0xff) return (double)f;
+  const unsigned long long bits = ((unsigned long long)sign << 32) | ((unsigned long long)(e - 127 + 1023) << 52) |
+                                  ((unsigned long long)m << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+}  // namespace tpcg

@@ -1,0 +1,98 @@
+// Internal declarations of libtpcg (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/tpcg.h"
+
+namespace tpcg {
+
+constexpr int kBcP = 0, kBcD = 1, kBcN = 2, kBcDN = 3, kBcND = 4;
+
+// FP64 eigenpairs of one axis (Algorithm 5, lines 2-4).  lam is divided by h^2.
+struct AxisBasis {
+  int len = 1;
+  int bc = 0;
+  double h = 1.0;
+  std::vector<double> lam;  // len
+  std::vector<double> V;    // len*len row-major, column k = eigenvector k
+  double orth_err = 0.0, recon_err = 0.0;
+};
+
+std::vector<double> lap1d_dense(int n, int bc);
+void closed_form_eigenpairs(int n, int bc, std::vector<double>& lam, std::vector<double>& V);
+void eigen_check(int n, int bc, const std::vector<double>& lam, const std::vector<double>& V, double* orth_err,
+                 double* recon_err);
+int build_axis(int len, int bc, double h, AxisBasis& ax);
+
+// One mode-product pass of Algorithm 7: for every row r = a*B + b of the
+// input (an A x B x C array with C contiguous, rows in_pitch elements apart)
+//     out[a*oa + b*ob + c'*oc] = sum_c X[r][c] * Wm[c][c']   (W = V or V^T),
+// optionally multiplied by the Hadamard pseudoinverse G (line 4).  The output
+// strides place the next contraction index contiguously, so every pass
+// contracts a contiguous index.
+struct StageParams {
+  int A, B, C, Cout;
+  int in_pitch;
+  long long oa, ob, oc;
+  int axis;        // 0 x, 1 y, 2 z
+  int dir;         // 0 forward (W = V), 1 backward (W = V^T)
+  int scale;       // apply G
+  int lamA, lamB, lamC;  // axis whose eigenvalue index is a / b / c'
+  int final_stage;
+  int out_pitch_elems;   // row pitch of the output viewed as the next stage's input
+  int out_rows;          // rows of the output viewed as the next stage's input
+  int out_C;             // contiguous extent of that view
+};
+
+struct SolveState;  // device-side scalars (tpcg_dev.cuh)
+
+}  // namespace tpcg
+
+struct tpcg_plan {
+  int nx = 0, ny = 0, nz = 0;
+  int bc[3] = {0, 0, 0};
+  double h[3] = {1, 1, 1};
+  int prec = TPCG_FP64;
+  cudaStream_t stream = nullptr;
+  bool singular = false;
+  bool is2d = false;
+  long long N = 0;
+  int device = 0;
+  int num_sms = 0;
+  tpcg::AxisBasis ax[3];
+
+  // device: eigenbases
+  double* d_W64[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};  // [axis][dir] FP64 W = V or V^T
+  double* d_lam64[3] = {nullptr, nullptr, nullptr};
+  float* d_lam32[3] = {nullptr, nullptr, nullptr};
+  void* d_Wt16[3][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};   // [axis][dir] BF16 W^T (K-major)
+  int pitch16[3] = {0, 0, 0};   // row pitch (elements) of BF16 arrays whose contiguous extent is axis l
+
+  // device: PCG workspaces
+  double* d_R = nullptr;
+  double* d_P = nullptr;
+  double* d_W = nullptr;
+  void* d_Z = nullptr;       // FP64 (FP64 form) or FP32 (mixed forms)
+  void* d_Rlp = nullptr;     // BF16 copy of R (mixed forms), row pitch pitch16[0]
+  void* d_T[2] = {nullptr, nullptr};  // mode-product intermediates
+  size_t t_elems = 0;
+  double* d_eta_h = nullptr;  // device copies for tpcg_solve_host
+  double* d_ups_h = nullptr;
+  tpcg::SolveState* d_state = nullptr;
+  tpcg::SolveState* h_state = nullptr;  // pinned
+  double* d_partials = nullptr;
+  size_t partial_slots = 0;
+  int* d_err = nullptr;   // device error word of bounded waits
+
+  std::vector<tpcg::StageParams> stages;
+  size_t device_bytes = 0;
+
+  // launch configuration (fixed per plan so that reductions are reproducible)
+  dim3 st_grid, st_block;   // stencil kernels
+  int st_zchunk = 1;
+  int stream_blocks = 0;    // streaming kernels
+};
