@@ -154,6 +154,25 @@ int tpcg_rhs_add_bc(tpcg_plan* plan, double* eta, const double bval[6]);
  * (1 for the absent z axis of a 2D plan: lam = {0}, V = {1}).              */
 int tpcg_plan_eigenpairs(const tpcg_plan* plan, int axis, double* lam, double* V);
 
+/* ---- instrumentation ------------------------------------------------------
+ * Number of CUDA kernels the plan has launched since it was created.       */
+int tpcg_plan_launch_count(const tpcg_plan* plan, unsigned long long* launches);
+
+/* Per-kernel-kind device time, measured with CUDA events recorded on the
+ * plan's stream around every launch between tpcg_profile_begin() and
+ * tpcg_profile_end().  Kinds: eta_sum, init_residual, direction, update,
+ * true_residual, center, laplacian, modeprod_f64, modeprod_tc, convert.    */
+typedef struct {
+  char name[24];
+  unsigned long long launches;  /* launches recorded while profiling          */
+  double total_ms;              /* summed event-to-event time of those launches */
+} tpcg_kernel_stat;
+
+int tpcg_profile_begin(tpcg_plan* plan);
+/* Synchronises the stream, stops recording, writes up to max_stats entries
+ * (kinds with at least one launch) and their count to *n_stats.            */
+int tpcg_profile_end(tpcg_plan* plan, tpcg_kernel_stat* stats, int max_stats, int* n_stats);
+
 /* Human-readable name of a status code (static string, never NULL).        */
 const char* tpcg_strerror(int status);
 

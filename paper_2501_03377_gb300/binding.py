@@ -50,6 +50,10 @@ class tpcg_info(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class tpcg_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_ulonglong), ("total_ms", ctypes.c_double)]
+
+
 _P = ctypes.c_void_p
 _D = ctypes.c_double
 _I = ctypes.c_int
@@ -64,6 +68,9 @@ _SIGS = {
     "tpcg_apply_laplacian": (_I, [_P, _P, _P]),
     "tpcg_rhs_add_bc": (_I, [_P, _P, ctypes.POINTER(_D)]),
     "tpcg_plan_eigenpairs": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "tpcg_plan_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "tpcg_profile_begin": (_I, [_P]),
+    "tpcg_profile_end": (_I, [_P, ctypes.POINTER(tpcg_kernel_stat), _I, ctypes.POINTER(_I)]),
     "tpcg_strerror": (ctypes.c_char_p, [_I]),
 }
 _lib = None
@@ -152,6 +159,24 @@ def tpcg_plan_eigenpairs(plan, axis, length):
     return st, list(lam), list(V)
 
 
+def tpcg_plan_launch_count(plan):
+    v = ctypes.c_ulonglong()
+    st = lib().tpcg_plan_launch_count(plan, ctypes.byref(v))
+    return st, v.value
+
+
+def tpcg_profile_begin(plan):
+    return lib().tpcg_profile_begin(plan)
+
+
+def tpcg_profile_end(plan, max_stats=16):
+    arr = (tpcg_kernel_stat * max_stats)()
+    n = _I()
+    st = lib().tpcg_profile_end(plan, arr, max_stats, ctypes.byref(n))
+    out = {arr[i].name.decode(): {"launches": arr[i].launches, "total_ms": arr[i].total_ms} for i in range(n.value)}
+    return st, out
+
+
 # ---------------------------------------------------------------------------
 class Plan:
     """Owns a tpcg_plan; tensors are torch float64 CUDA tensors of shape (nz, ny, nx)."""
@@ -226,6 +251,18 @@ class Plan:
         if st != TPCG_OK:
             raise TpcgError(st, "tpcg_plan_eigenpairs")
         return lam, V
+
+    def launch_count(self):
+        return tpcg_plan_launch_count(self.handle)[1]
+
+    def profile_begin(self):
+        tpcg_profile_begin(self.handle)
+
+    def profile_end(self):
+        st, stats = tpcg_profile_end(self.handle)
+        if st != TPCG_OK:
+            raise TpcgError(st, "tpcg_profile_end")
+        return stats
 
     def device_bytes(self):
         return tpcg_plan_device_bytes(self.handle)[1]

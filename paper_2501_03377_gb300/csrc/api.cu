@@ -16,8 +16,8 @@ namespace tpcg {
 void launch_apply_laplacian(const tpcg_plan* p, const Geom& g, const double* x, double* w);
 void launch_init_residual(const tpcg_plan* p, const Geom& g, const double* eta, const double* U, bool zero_guess);
 void launch_eta_sum(const tpcg_plan* p, const Geom& g, const double* eta);
-void launch_direction(const tpcg_plan* p, const Geom& g);
-void launch_update(const tpcg_plan* p, const Geom& g, double* U);
+void launch_direction(const tpcg_plan* p, const Geom& g, int k);
+void launch_update(const tpcg_plan* p, const Geom& g, double* U, int k);
 void launch_true_residual(const tpcg_plan* p, const Geom& g, const double* eta, const double* U, bool force);
 void launch_center_u(const tpcg_plan* p, const Geom& g, double* U);
 void launch_zero(const tpcg_plan* p, long long N, double* U);
@@ -28,6 +28,12 @@ void run_precond_f64(const tpcg_plan* pl, const double* R, double* Z, SolveState
 int run_precond_tc(const tpcg_plan* pl, float* Z, SolveState* st);
 int tc_plan_setup(tpcg_plan* pl);
 void tc_plan_release(tpcg_plan* pl);
+
+const char* kernel_kind_name(int kind) {
+  static const char* names[kKindCount] = {"eta_sum", "init_residual", "direction", "update", "true_residual",
+                                          "center", "laplacian", "modeprod_f64", "modeprod_tc", "convert"};
+  return (kind >= 0 && kind < kKindCount) ? names[kind] : "unknown";
+}
 
 namespace {
 
@@ -134,7 +140,8 @@ void free_plan(tpcg_plan* p) {
     cudaFree(p->d_lam32[a]);
   }
   cudaFree(p->d_R);
-  cudaFree(p->d_P);
+  cudaFree(p->d_P[0]);
+  cudaFree(p->d_P[1]);
   cudaFree(p->d_W);
   cudaFree(p->d_Z);
   cudaFree(p->d_Rlp);
@@ -146,17 +153,25 @@ void free_plan(tpcg_plan* p) {
   cudaFree(p->d_partials);
   cudaFree(p->d_err);
   if (p->h_state) cudaFreeHost(p->h_state);
+  for (cudaEvent_t e : p->prof.pool) cudaEventDestroy(e);
   delete p;
 }
 
 uint16_t host_bf16(double x) {
-  // round-to-nearest-even FP64 -> BF16 on the host (eigenbasis copies)
-  float f = (float)x;
-  uint32_t u;
-  std::memcpy(&u, &f, 4);
-  const uint32_t lsb = (u >> 16) & 1u;
-  u += 0x7fffu + lsb;
-  return (uint16_t)(u >> 16);
+  // FP64 -> BF16, one round-to-nearest-even step on the FP64 bit pattern
+  // (eigenbasis entries are finite and far inside the BF16 normal range).
+  uint64_t u;
+  std::memcpy(&u, &x, 8);
+  const uint32_t sign = (uint32_t)(u >> 48) & 0x8000u;
+  const int e = (int)((u >> 52) & 0x7ff);
+  const int eb = e - 1023 + 127;
+  if (e == 0 || eb <= 0) return (uint16_t)sign;
+  const uint64_t mant = u & 0xfffffffffffffull;
+  const uint32_t top = (uint32_t)(mant >> 45);
+  const uint64_t rest = mant & ((1ull << 45) - 1);
+  uint32_t bits = ((uint32_t)eb << 7) | top;
+  if (rest > (1ull << 44) || (rest == (1ull << 44) && (top & 1u))) bits += 1;
+  return (uint16_t)(sign | bits);
 }
 
 int run_precond(const tpcg_plan* p, const double* R, void* Z, SolveState* st) {
@@ -206,8 +221,9 @@ int solve_impl(tpcg_plan* p, const double* eta, double* ups, double tol, int max
     if (cudaStreamSynchronize(p->stream) != cudaSuccess) return last_cuda_error() ? TPCG_ERR_CUDA : TPCG_ERR_CUDA;
     if (hs->done || issued > maxit + 1) break;
     for (int c = 0; c < chunk; ++c) {
-      launch_direction(p, g);                              // lines 10-11 (P from line 17 of the previous pass)
-      launch_update(p, g, ups);                            // lines 12-13
+      const int k = issued + c;                            // P_k is written to d_P[k & 1], P_{k-1} read from the other
+      launch_direction(p, g, k);                           // lines 10-11 (P from line 17 of the previous pass)
+      launch_update(p, g, ups, k);                         // lines 12-13
       launch_true_residual(p, g, eta, ups, false);         // stop test
       if ((rc = run_precond(p, p->d_R, p->d_Z, p->d_state))) return rc;  // lines 14-16
     }
@@ -337,7 +353,8 @@ int tpcg_plan_create(int nx, int ny, int nz, const int bc[3], const double h[3],
   }
   // PCG workspaces
   if (!rc) rc = dalloc(p, &p->d_R, (size_t)N);
-  if (!rc) rc = dalloc(p, &p->d_P, (size_t)N);
+  if (!rc) rc = dalloc(p, &p->d_P[0], (size_t)N);
+  if (!rc) rc = dalloc(p, &p->d_P[1], (size_t)N);
   if (!rc) rc = dalloc(p, &p->d_W, (size_t)N);
   if (!rc) {
     if (prec == TPCG_FP64) {
@@ -492,6 +509,56 @@ int tpcg_plan_eigenpairs(const tpcg_plan* plan, int axis, double* lam, double* V
   const AxisBasis& A = plan->ax[axis];
   std::memcpy(lam, A.lam.data(), sizeof(double) * A.len);
   std::memcpy(V, A.V.data(), sizeof(double) * (size_t)A.len * A.len);
+  return TPCG_OK;
+}
+
+int tpcg_plan_launch_count(const tpcg_plan* plan, unsigned long long* launches) {
+  if (!plan || !launches) return TPCG_ERR_INVALID_ARG;
+  *launches = plan->launch_count;
+  return TPCG_OK;
+}
+
+int tpcg_profile_begin(tpcg_plan* plan) {
+  if (!plan) return TPCG_ERR_INVALID_ARG;
+  Profiler& pr = plan->prof;
+  pr.recs.clear();
+  pr.used = 0;
+  for (int k = 0; k < kKindCount; ++k) {
+    pr.ms[k] = 0.0;
+    pr.timed[k] = 0;
+  }
+  pr.on = true;
+  return TPCG_OK;
+}
+
+int tpcg_profile_end(tpcg_plan* plan, tpcg_kernel_stat* stats, int max_stats, int* n_stats) {
+  if (!plan || (max_stats > 0 && !stats) || !n_stats) return TPCG_ERR_INVALID_ARG;
+  DeviceGuard dg(plan->device);
+  Profiler& pr = plan->prof;
+  pr.on = false;
+  if (cudaStreamSynchronize(plan->stream) != cudaSuccess) return last_cuda_error();
+  for (auto& r : pr.recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.second.first, r.second.second) == cudaSuccess) {
+      pr.ms[r.first] += ms;
+      pr.timed[r.first] += 1;
+    }
+  }
+  cudaGetLastError();
+  pr.recs.clear();
+  pr.used = 0;
+  int n = 0;
+  for (int k = 0; k < kKindCount; ++k) {
+    if (!pr.timed[k]) continue;
+    if (n < max_stats) {
+      std::memset(stats[n].name, 0, sizeof(stats[n].name));
+      std::strncpy(stats[n].name, kernel_kind_name(k), sizeof(stats[n].name) - 1);
+      stats[n].launches = pr.timed[k];
+      stats[n].total_ms = pr.ms[k];
+    }
+    ++n;
+  }
+  *n_stats = n < max_stats ? n : max_stats;
   return TPCG_OK;
 }
 

@@ -276,10 +276,10 @@ __device__ void fin_direction(SolveState* st, const double (&s)[1]) {
 
 template <class ZT>
 __global__ void __launch_bounds__(TX* TY) k_direction(Geom g, int zchunk, const ZT* __restrict__ Z,
-                                                      double* __restrict__ P, double* __restrict__ W, SolveState* st,
-                                                      double* partials) {
+                                                      const double* __restrict__ Pold, double* __restrict__ P,
+                                                      double* __restrict__ W, SolveState* st, double* partials) {
   if (st->done) return;
-  FieldDirection<ZT> f{Z, P, st->mZ, st->beta, st->first};
+  FieldDirection<ZT> f{Z, Pold, st->mZ, st->beta, st->first};
   OpDirection op{P, W};
   stencil_sweep<1>(g, zchunk, f, op, partials, &st->tickets[kTkDir],
                    [st](const double(&s)[1]) { fin_direction(st, s); });
@@ -404,9 +404,11 @@ __global__ void k_rhs_add_bc(Geom g, double* __restrict__ eta, double b0, double
 
 // ------------------------------------------------------------------ host launchers
 void launch_apply_laplacian(const tpcg_plan* p, const Geom& g, const double* x, double* w) {
+  LaunchScope ls(p, kKApply);
   k_apply_laplacian<<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, x, w);
 }
 void launch_init_residual(const tpcg_plan* p, const Geom& g, const double* eta, const double* U, bool zero_guess) {
+  LaunchScope ls(p, kKInit);
   if (zero_guess)
     k_init_zero<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, g.nx, eta, p->d_R, p->d_Rlp, p->pitch16[0], p->d_state,
                                                           p->d_partials);
@@ -415,35 +417,48 @@ void launch_init_residual(const tpcg_plan* p, const Geom& g, const double* eta, 
                                                                 p->pitch16[0], p->d_state, p->d_partials);
 }
 void launch_eta_sum(const tpcg_plan* p, const Geom& g, const double* eta) {
+  LaunchScope ls(p, kKEtaSum);
   k_eta_sum<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, eta, p->d_state, p->d_partials);
 }
-void launch_direction(const tpcg_plan* p, const Geom& g) {
+void launch_direction(const tpcg_plan* p, const Geom& g, int k) {
+  LaunchScope ls(p, kKDirection);
+  const double* pold = p->d_P[(k + 1) & 1];
+  double* pnew = p->d_P[k & 1];
   if (p->prec == TPCG_FP64)
-    k_direction<double><<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, (const double*)p->d_Z, p->d_P,
+    k_direction<double><<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, (const double*)p->d_Z, pold, pnew,
                                                                     p->d_W, p->d_state, p->d_partials);
   else
-    k_direction<float><<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, (const float*)p->d_Z, p->d_P,
+    k_direction<float><<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, (const float*)p->d_Z, pold, pnew,
                                                                    p->d_W, p->d_state, p->d_partials);
 }
-void launch_update(const tpcg_plan* p, const Geom& g, double* U) {
-  k_update<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, g.nx, U, p->d_P, p->d_W, p->d_R, p->d_Rlp, p->pitch16[0],
-                                                     p->d_state, p->d_partials);
+void launch_update(const tpcg_plan* p, const Geom& g, double* U, int k) {
+  LaunchScope ls(p, kKUpdate);
+  k_update<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, g.nx, U, p->d_P[k & 1], p->d_W, p->d_R, p->d_Rlp,
+                                                     p->pitch16[0], p->d_state, p->d_partials);
 }
 void launch_true_residual(const tpcg_plan* p, const Geom& g, const double* eta, const double* U, bool force) {
+  LaunchScope ls(p, kKTrueRes);
   k_true_residual<<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, eta, U, p->d_R, p->d_Rlp,
                                                               p->pitch16[0], p->d_state, p->d_partials, force ? 1 : 0);
 }
 void launch_center_u(const tpcg_plan* p, const Geom& g, double* U) {
+  LaunchScope ls(p, kKCenter);
   k_center_u<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, U, p->d_state);
 }
-void launch_zero(const tpcg_plan* p, long long N, double* U) { k_zero<<<p->stream_blocks, 256, 0, p->stream>>>(N, U); }
+void launch_zero(const tpcg_plan* p, long long N, double* U) {
+  LaunchScope ls(p, kKConvert);
+  k_zero<<<p->stream_blocks, 256, 0, p->stream>>>(N, U);
+}
 void launch_to_lp(const tpcg_plan* p, const Geom& g, const double* r) {
+  LaunchScope ls(p, kKConvert);
   k_to_lp<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, g.nx, r, p->d_Rlp, p->pitch16[0]);
 }
 void launch_f32_to_f64(const tpcg_plan* p, long long N, const float* a, double* b) {
+  LaunchScope ls(p, kKConvert);
   k_f32_to_f64<<<p->stream_blocks, 256, 0, p->stream>>>(N, a, b);
 }
 void launch_rhs_add_bc(const tpcg_plan* p, const Geom& g, double* eta, const double* bv) {
+  LaunchScope ls(p, kKConvert);
   k_rhs_add_bc<<<p->stream_blocks, 256, 0, p->stream>>>(g, eta, bv[0], bv[1], bv[2], bv[3], bv[4], bv[5]);
 }
 

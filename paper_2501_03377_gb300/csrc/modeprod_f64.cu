@@ -22,27 +22,6 @@ __device__ __forceinline__ T ghat(const T* la, const T* lb, const T* lc, int a, 
   return T(1) / (la[a] + lb[b] + lc[c]);
 }
 
-// Finalize of one preconditioner application inside PCG (lines 14-16):
-// centre Z (Remark orthogonality), rho_s = <R_s, Z_s - mean Z_s>, beta_s.
-__device__ void fin_precond(SolveState* st, long long N, const double (&s)[2]) {
-  const double mZ = st->singular ? s[1] / (double)N : 0.0;
-  const double rho = s[0] - mZ * st->sumR;
-  st->mZ = mZ;
-  st->precond_applies += 1;
-  if (!isfinite(rho) || !(rho > 0.0)) {
-    if (st->rr == 0.0) {  // exact solution already reached
-      st->status = TPCG_OK;
-      st->done = 1;
-    } else {
-      st->status = TPCG_ERR_BREAKDOWN;
-      st->done = 1;
-    }
-    return;
-  }
-  st->beta = st->first ? 0.0 : rho / st->rho;
-  st->rho = rho;
-}
-
 struct ModeArgsF64 {
   StageParams p;
   const double* __restrict__ X;
@@ -159,6 +138,7 @@ void run_precond_f64(const tpcg_plan* pl, const double* R, double* Z, SolveState
     a.N = pl->N;
     const long long rows = (long long)p.A * p.B;
     dim3 grid((unsigned)((rows + MT - 1) / MT), (unsigned)((p.Cout + NT - 1) / NT));
+    LaunchScope ls(pl, kKModeF64);
     if (last && st)
       k_modeprod_f64<true><<<grid, 256, 0, pl->stream>>>(a);
     else

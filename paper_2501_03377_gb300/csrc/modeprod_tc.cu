@@ -1,9 +1,548 @@
-// Tensor-core (tcgen05) form of the mode products -- placeholder until the
-// BF16 kernels land.
+// Mixed-precision form of the pseudoinverse preconditioner (Algorithm 7,
+// Sec. 4.3.3) on the 5th-generation tensor cores: every mode-product pass is
+// a BF16 x BF16 -> FP32 tcgen05 GEMM that contracts the contiguous index of
+// its input against the l x l eigenbasis.
+//
+// One persistent, warp-specialised kernel serves every pass:
+//   warp 0      TMA producer: loads the whole BF16 eigenbasis W^T (K-major,
+//               128B-swizzled) into shared memory once, then streams 128-row
+//               x 64-column K-tiles of the input through an NS-slot ring;
+//   warp 1      allocates TMEM; lane 0 issues tcgen05.mma (M = 128) and
+//               tcgen05.commit to release ring slots / publish accumulators;
+//   warps 2..5  epilogue: tcgen05.ld of the FP32 accumulator (one TMEM lane
+//               per thread), optional Hadamard scaling by G = 1/(lam_a +
+//               lam_b + lam_c) with the null index zeroed (Algorithm 5,
+//               lines 5-6), BF16 (or FP32) stores, and in the last pass the
+//               PCG reductions <R, Z> and sum Z.
+// Two accumulator buffers in TMEM let the epilogue of tile i overlap the MMAs
+// of tile i+1.  Two operand forms keep the global stores coalesced:
+//   form 1: D[row][c'] = X[row][:] . W^T[c'][:]  (data = A, M = 128 rows,
+//           eigenbasis = B, N = Cout padded to 16); lanes walk the rows;
+//   form 2: D[c'][row] = W^T[c'][:] . X[row][:]  (eigenbasis = A in M-blocks
+//           of 128, data = B, N = 128); lanes walk the output index.
+// Every wait on an mbarrier is bounded (globaltimer); on expiry the CTA sets
+// an error word, stops issuing, drains its own copies/MMAs with bounded waits,
+// frees TMEM and returns.
+#include <cuda.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
 #include "tpcg_dev.cuh"
 
 namespace tpcg {
-int tc_plan_setup(tpcg_plan*) { return TPCG_ERR_UNSUPPORTED; }
-void tc_plan_release(tpcg_plan*) {}
-int run_precond_tc(const tpcg_plan*, float*, SolveState*) { return TPCG_ERR_UNSUPPORTED; }
+
+namespace {
+
+constexpr int kThreads = 192;
+constexpr int kTileRows = 128;
+constexpr int kKTile = 64;                 // BF16 elements per 128-byte swizzle row
+constexpr int kStageBytes = kTileRows * 128;
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+constexpr int kMaxSmem = 232448 - 2048;  // opt-in limit minus room for static shared memory
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+struct Abort {
+  volatile int* flag;  // shared
+  int* err;            // global error word
+  SolveState* st;
+};
+
+// Bounded wait for the phase of parity `parity` to complete.
+__device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity, const Abort& ab) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*ab.flag) return false;
+    if (gtimer() - t0 > kWaitLimitNs) {
+      *ab.flag = 1;
+      if (ab.err) atomicExch(ab.err, 1);
+      if (ab.st) ab.st->timeout = 1;
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(uint32_t d, unsigned long long a, unsigned long long b, uint32_t idesc,
+                                       uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row core groups 1024 bytes apart (tile base 1024-aligned).
+__device__ __forceinline__ unsigned long long sw128_desc(uint32_t saddr) {
+  unsigned long long d = 0;
+  d |= (unsigned long long)((saddr >> 4) & 0x3FFFu);
+  d |= (unsigned long long)1 << 16;             // leading-dimension byte offset (unused for swizzled K-major)
+  d |= (unsigned long long)(1024 >> 4) << 32;   // stride-dimension byte offset
+  d |= (unsigned long long)1 << 46;             // descriptor version
+  d |= (unsigned long long)2 << 61;             // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor of kind::f16: BF16 A and B, FP32 D, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+struct TcArgs {
+  int C, KT, Cout, VR, Np, MB, acc_cols, tmem_cols, NS;
+  int rows, B;
+  long long oa, ob, oc;
+  int scale, singular;
+  const float* lamA;
+  const float* lamB;
+  const float* lamC;
+  void* out;
+  const double* R;
+  SolveState* st;
+  double* partials;
+  long long N;
+  int* err;
+};
+
+__device__ __forceinline__ float ghat32(const TcArgs& a, int ia, int ib, int ic) {
+  if (a.singular && ia == 0 && ib == 0 && ic == 0) return 0.0f;
+  return 1.0f / (a.lamA[ia] + a.lamB[ib] + a.lamC[ic]);
+}
+
+template <class OutT>
+__device__ __forceinline__ void store_out(void* out, long long o, float v) {
+  if constexpr (sizeof(OutT) == 2)
+    reinterpret_cast<__nv_bfloat16*>(out)[o] = __float2bfloat16_rn(v);
+  else
+    reinterpret_cast<float*>(out)[o] = v;
+}
+
+template <int FORM, class OutT, bool FINAL>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_modeprod_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW, TcArgs a) {
+  if (a.st && a.st->done) return;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* sm = smem_raw + (base - raw);
+  const uint32_t sV = base;
+  const uint32_t sD = sV + (uint32_t)a.KT * a.VR * 128u;
+  uint8_t* barp = sm + (size_t)a.KT * a.VR * 128 + (size_t)a.NS * kStageBytes;
+  const uint32_t bars = smem_u32(barp);
+  const int NS = a.NS;
+  auto full = [&](int s) { return bars + 8u * s; };
+  auto empty = [&](int s) { return bars + 8u * (NS + s); };
+  auto tfull = [&](int b) { return bars + 8u * (2 * NS + b); };
+  auto tempty = [&](int b) { return bars + 8u * (2 * NS + 2 + b); };
+  const uint32_t vbar = bars + 8u * (2 * NS + 4);
+  const uint32_t drain = bars + 8u * (2 * NS + 5);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(barp + 8 * (2 * NS + 6));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+  const Abort ab{abort_flag, a.err, a.st};
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull(b), 1);
+      mbar_init(tempty(b), 4 * 32);
+    }
+    mbar_init(vbar, 1);
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                 "r"((uint32_t)a.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+  const int ntiles = (a.rows + kTileRows - 1) / kTileRows;
+
+  double red0 = 0.0;
+  float red1 = 0.0f;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    mbar_expect_tx(vbar, (uint32_t)a.KT * a.VR * 128u);
+    for (int kt = 0; kt < a.KT; ++kt) tma_load_2d(sV + (uint32_t)kt * a.VR * 128u, &tmW, kt * kKTile, 0, vbar);
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
+      for (int kt = 0; kt < a.KT; ++kt, ++it) {
+        const int s = it % NS;
+        const uint32_t ph = (uint32_t)((it / NS) & 1);
+        if (!wait_bounded(empty(s), ph ^ 1u, ab)) break;
+        mbar_expect_tx(full(s), kStageBytes);
+        tma_load_2d(sD + (uint32_t)s * kStageBytes, &tmX, kt * kKTile, tile * kTileRows, full(s));
+      }
+    }
+    // drain: every issued load has completed before the CTA may exit
+    if (*abort_flag) {
+      for (int j = (it > NS ? it - NS : 0); j < it; ++j) {
+        const unsigned long long t0 = gtimer();
+        while (!mbar_try_wait(full(j % NS), (uint32_t)((j / NS) & 1)) && gtimer() - t0 < kWaitLimitNs) {
+        }
+      }
+      const unsigned long long t0 = gtimer();
+      while (!mbar_try_wait(vbar, 0) && gtimer() - t0 < kWaitLimitNs) {
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    const uint32_t idesc = (FORM == 1) ? idesc_bf16(128, a.Np) : idesc_bf16(128, 128);
+    bool ok = wait_bounded(vbar, 0, ab);
+    int it = 0, tcount = 0;
+    for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++tcount) {
+      const int b = tcount & 1;
+      if (!(ok = wait_bounded(tempty(b), (uint32_t)(((tcount >> 1) & 1) ^ 1), ab))) break;
+      tc_fence_after();
+      const uint32_t dacc = tmem + (uint32_t)(b * a.acc_cols);
+      for (int kt = 0; kt < a.KT; ++kt, ++it) {
+        const int s = it % NS;
+        if (!(ok = wait_bounded(full(s), (uint32_t)((it / NS) & 1), ab))) break;
+        tc_fence_after();
+        const uint32_t xs = sD + (uint32_t)s * kStageBytes;
+        const uint32_t vs = sV + (uint32_t)kt * a.VR * 128u;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          if (kt * kKTile + kk * 16 >= a.C) break;
+          const uint32_t accum = (kt > 0 || kk > 0) ? 1u : 0u;
+          if (FORM == 1) {
+            tc_mma(dacc, sw128_desc(xs + kk * 32), sw128_desc(vs + kk * 32), idesc, accum);
+          } else {
+            for (int mb = 0; mb < a.MB; ++mb)
+              tc_mma(dacc + (uint32_t)(mb * 128), sw128_desc(vs + (uint32_t)mb * kStageBytes + kk * 32),
+                     sw128_desc(xs + kk * 32), idesc, accum);
+          }
+        }
+        tc_commit(empty(s));
+      }
+      if (!ok) break;
+      tc_commit(tfull(b));
+    }
+    // all MMAs issued by this thread are complete once `drain` fires
+    tc_commit(drain);
+    const unsigned long long t0 = gtimer();
+    while (!mbar_try_wait(drain, 0) && gtimer() - t0 < kWaitLimitNs) {
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue
+    const int q = warp & 3;  // TMEM lane quadrant this warp may access
+    int tcount = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tcount) {
+      const int b = tcount & 1;
+      if (!wait_bounded(tfull(b), (uint32_t)((tcount >> 1) & 1), ab)) break;
+      tc_fence_after();
+      const uint32_t tacc = tmem + (uint32_t)(b * a.acc_cols) + ((uint32_t)(q * 32) << 16);
+      const int row0 = tile * kTileRows;
+      if (FORM == 1) {
+        const int r = row0 + q * 32 + lane;
+        const bool valid = r < a.rows;
+        const int ia = valid ? r / a.B : 0;
+        const int ib = valid ? r - ia * a.B : 0;
+        const long long obase = (long long)ia * a.oa + (long long)ib * a.ob;
+        for (int c0 = 0; c0 < a.Np; c0 += 16) {
+          float v[16];
+          tc_ld16(tacc + (uint32_t)c0, v);
+          if (valid) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const int c = c0 + j;
+              if (c < a.Cout) {
+                float x = v[j];
+                if (a.scale) x *= ghat32(a, ia, ib, c);
+                const long long o = obase + (long long)c * a.oc;
+                store_out<OutT>(a.out, o, x);
+                if (FINAL) {
+                  red0 = fma(__ldg(a.R + o), f32_to_f64_int(x), red0);
+                  red1 += x;
+                }
+              }
+            }
+          }
+        }
+      } else {
+        for (int mb = 0; mb < a.MB; ++mb) {
+          const int c = mb * 128 + q * 32 + lane;
+          const bool cvalid = c < a.Cout;
+          const float lc = (a.scale && cvalid) ? a.lamC[c] : 0.0f;
+          for (int c0 = 0; c0 < kTileRows; c0 += 16) {
+            float v[16];
+            tc_ld16(tacc + (uint32_t)(mb * 128 + c0), v);
+            int r = row0 + c0;
+            int ia = r / a.B;
+            int ib = r - ia * a.B;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              if (cvalid && r < a.rows) {
+                float x = v[j];
+                if (a.scale) {
+                  const bool null = a.singular && ia == 0 && ib == 0 && c == 0;
+                  x = null ? 0.0f : x / (a.lamA[ia] + a.lamB[ib] + lc);
+                }
+                const long long o = (long long)ia * a.oa + (long long)ib * a.ob + (long long)c * a.oc;
+                store_out<OutT>(a.out, o, x);
+                if (FINAL) {
+                  red0 = fma(__ldg(a.R + o), f32_to_f64_int(x), red0);
+                  red1 += x;
+                }
+              }
+              ++r;
+              if (++ib == a.B) {
+                ib = 0;
+                ++ia;
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(tempty(b));
+    }
+  }
+
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)a.tmem_cols)
+                 : "memory");
+  }
+  if constexpr (FINAL) {
+    double acc[2] = {red0, (double)red1};
+    SolveState* st = a.st;
+    const long long N = a.N;
+    grid_reduce<2>(acc, a.partials, &st->tickets[kTkPrec], gridDim.x, blockIdx.x,
+                   [st, N](const double(&s)[2]) {
+                     if (!st->timeout) fin_precond(st, N, s);
+                     else {
+                       st->status = TPCG_ERR_TIMEOUT;
+                       st->done = 1;
+                     }
+                   });
+  }
+}
+
+// ------------------------------------------------------------------ host side
+struct TcStage {
+  CUtensorMap tmX;
+  CUtensorMap tmW;
+  int form;
+  TcArgs args;
+  int grid;
+  size_t smem;
+};
+
+struct TcPlan {
+  std::vector<TcStage> stages;
+};
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encoder() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+  }
+  return fn;
+}
+
+int encode_2d(CUtensorMap* map, const void* gaddr, int inner, long long outer, int pitch_elems, int box_inner,
+              int box_outer) {
+  EncodeTiledFn cuTensorMapEncodeTiled = encoder();
+  if (!cuTensorMapEncodeTiled) return -1;
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  cuuint64_t strides[1] = {(cuuint64_t)pitch_elems * 2};
+  cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = cuTensorMapEncodeTiled(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(gaddr), dims,
+                                      strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : -1;
+}
+
+template <int FORM, class OutT, bool FINAL>
+int set_smem_attr(size_t smem) {
+  return cudaFuncSetAttribute(k_modeprod_tc<FORM, OutT, FINAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem) == cudaSuccess
+             ? 0
+             : -1;
+}
+
+template <int FORM, class OutT, bool FINAL>
+void launch(const TcStage& s, const TcArgs& a, cudaStream_t stream) {
+  k_modeprod_tc<FORM, OutT, FINAL><<<s.grid, kThreads, s.smem, stream>>>(s.tmX, s.tmW, a);
+}
+
+}  // namespace
+
+int tc_plan_setup(tpcg_plan* p) {
+  if (p->prec != TPCG_MIXED_BF16) return TPCG_ERR_UNSUPPORTED;
+  TcPlan* tp = new TcPlan();
+  const int ns = (int)p->stages.size();
+  for (int si = 0; si < ns; ++si) {
+    const StageParams& sp = p->stages[si];
+    TcStage st{};
+    st.form = (sp.oc == 1) ? 2 : 1;  // lanes walk the contiguous output index (2) or the rows (1)
+    TcArgs& a = st.args;
+    a.C = sp.C;
+    a.KT = (sp.C + kKTile - 1) / kKTile;
+    a.Cout = sp.Cout;
+    a.Np = ((sp.Cout + 15) / 16) * 16;
+    a.MB = (sp.Cout + 127) / 128;
+    a.VR = (st.form == 1) ? ((sp.Cout + 7) / 8) * 8 : a.MB * 128;
+    if (st.form == 1) a.VR = std::max(a.VR, a.Np);
+    a.acc_cols = (st.form == 1) ? a.Np : a.MB * 128;
+    int cols = 32;
+    while (cols < 2 * a.acc_cols) cols <<= 1;
+    a.tmem_cols = cols;
+    a.rows = sp.A * sp.B;
+    a.B = sp.B;
+    a.oa = sp.oa;
+    a.ob = sp.ob;
+    a.oc = sp.oc;
+    a.scale = sp.scale;
+    a.singular = p->singular ? 1 : 0;
+    a.lamA = p->d_lam32[sp.lamA];
+    a.lamB = p->d_lam32[sp.lamB];
+    a.lamC = p->d_lam32[sp.lamC];
+    a.N = p->N;
+    a.err = p->d_err;
+    const size_t vbytes = (size_t)a.KT * a.VR * 128;
+    const size_t fixed = 1024 + vbytes + 256;
+    if (a.tmem_cols > 512 || a.VR > 256 || fixed + 2 * kStageBytes > (size_t)kMaxSmem) {
+      delete tp;
+      return TPCG_ERR_UNSUPPORTED;
+    }
+    a.NS = (int)std::min<size_t>(8, (kMaxSmem - fixed) / kStageBytes);
+    st.smem = fixed + (size_t)a.NS * kStageBytes;
+    const int ntiles = (a.rows + kTileRows - 1) / kTileRows;
+    st.grid = std::max(1, std::min(ntiles, p->num_sms));
+    // operands: stage si reads the output of stage si-1 (R in BF16 for the first)
+    const void* xin = (si == 0) ? p->d_Rlp : p->d_T[(si - 1) & 1];
+    const int wpitch = p->pitch16[sp.axis];
+    if (encode_2d(&st.tmX, xin, sp.C, (long long)a.rows, sp.in_pitch, kKTile, kTileRows) ||
+        encode_2d(&st.tmW, p->d_Wt16[sp.axis][sp.dir], sp.C, sp.Cout, wpitch, kKTile, a.VR)) {
+      delete tp;
+      return TPCG_ERR_CUDA;
+    }
+    tp->stages.push_back(st);
+  }
+  int bad = 0;
+  bad |= set_smem_attr<1, __nv_bfloat16, false>(kMaxSmem);
+  bad |= set_smem_attr<2, __nv_bfloat16, false>(kMaxSmem);
+  bad |= set_smem_attr<2, float, false>(kMaxSmem);
+  bad |= set_smem_attr<2, float, true>(kMaxSmem);
+  bad |= set_smem_attr<1, float, false>(kMaxSmem);
+  bad |= set_smem_attr<1, float, true>(kMaxSmem);
+  if (bad) {
+    delete tp;
+    return TPCG_ERR_CUDA;
+  }
+  p->tc_state = tp;
+  return TPCG_OK;
+}
+
+void tc_plan_release(tpcg_plan* p) {
+  delete reinterpret_cast<TcPlan*>(p->tc_state);
+  p->tc_state = nullptr;
+}
+
+// R (already converted to BF16 in d_Rlp) -> Z (FP32).  With st != nullptr the
+// last pass performs the PCG finalize.
+int run_precond_tc(const tpcg_plan* p, float* Z, SolveState* st) {
+  const TcPlan* tp = reinterpret_cast<const TcPlan*>(p->tc_state);
+  if (!tp) return TPCG_ERR_UNSUPPORTED;
+  const int ns = (int)tp->stages.size();
+  for (int si = 0; si < ns; ++si) {
+    const TcStage& s = tp->stages[si];
+    TcArgs a = s.args;
+    const bool last = (si == ns - 1);
+    a.out = last ? (void*)Z : p->d_T[si & 1];
+    a.st = st;
+    a.R = p->d_R;
+    a.partials = p->d_partials;
+    LaunchScope ls(p, kKModeTC);
+    if (!last) {
+      if (s.form == 1) launch<1, __nv_bfloat16, false>(s, a, p->stream);
+      else launch<2, __nv_bfloat16, false>(s, a, p->stream);
+    } else if (st) {
+      if (s.form == 1) launch<1, float, true>(s, a, p->stream);
+      else launch<2, float, true>(s, a, p->stream);
+    } else {
+      if (s.form == 1) launch<1, float, false>(s, a, p->stream);
+      else launch<2, float, false>(s, a, p->stream);
+    }
+  }
+  return TPCG_OK;
+}
+
 }  // namespace tpcg

@@ -48,6 +48,38 @@ struct Geom {
   long long N;     // nx*ny*nz
 };
 
+// Counts a kernel launch of the plan and, when profiling is on, brackets it
+// with CUDA events on the plan's stream.
+struct LaunchScope {
+  const tpcg_plan* p;
+  int kind;
+  cudaEvent_t b = nullptr;
+  LaunchScope(const tpcg_plan* plan, int k) : p(plan), kind(k) {
+    p->launch_count += 1;
+    p->prof.launches[k] += 1;
+    if (p->prof.on) {
+      cudaEvent_t a = take_event(), e = take_event();
+      if (a && e) {
+        cudaEventRecord(a, p->stream);
+        b = e;
+        p->prof.recs.push_back({k, {a, e}});
+      }
+    }
+  }
+  ~LaunchScope() {
+    if (b) cudaEventRecord(b, p->stream);
+  }
+  cudaEvent_t take_event() {
+    Profiler& pr = p->prof;
+    if (pr.used < pr.pool.size()) return pr.pool[pr.used++];
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
+    pr.pool.push_back(ev);
+    pr.used = pr.pool.size();
+    return ev;
+  }
+};
+
 // Block-wide sum of NQ doubles; result valid in thread 0.  Fixed order: the
 // result is bitwise reproducible for a fixed launch configuration.
 template <int NQ>
@@ -110,6 +142,27 @@ __device__ __forceinline__ void grid_reduce(double (&v)[NQ], double* partials, u
     fin(s);
     *ticket = 0u;
   }
+}
+
+// Finalize of one preconditioner application inside PCG (lines 14-16):
+// centre Z (Remark orthogonality), rho_s = <R_s, Z_s - mean Z_s>, beta_s.
+__device__ __forceinline__ void fin_precond(SolveState* st, long long N, const double (&s)[2]) {
+  const double mZ = st->singular ? s[1] / (double)N : 0.0;
+  const double rho = s[0] - mZ * st->sumR;
+  st->mZ = mZ;
+  st->precond_applies += 1;
+  if (!isfinite(rho) || !(rho > 0.0)) {
+    if (st->rr == 0.0) {  // exact solution already reached
+      st->status = TPCG_OK;
+      st->done = 1;
+    } else {
+      st->status = TPCG_ERR_BREAKDOWN;
+      st->done = 1;
+    }
+    return;
+  }
+  st->beta = st->first ? 0.0 : rho / st->rho;
+  st->rho = rho;
 }
 
 // FP64 -> BF16 with round-to-nearest-even done in integer arithmetic on the

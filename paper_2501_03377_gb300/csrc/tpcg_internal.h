@@ -50,6 +50,24 @@ struct StageParams {
 
 struct SolveState;  // device-side scalars (tpcg_dev.cuh)
 
+// Kernel kinds for the launch counter and the optional event profiler.
+enum KernelKind {
+  kKEtaSum = 0, kKInit, kKDirection, kKUpdate, kKTrueRes, kKCenter, kKApply, kKModeF64, kKModeTC, kKConvert,
+  kKindCount
+};
+const char* kernel_kind_name(int kind);
+
+// Optional per-launch CUDA-event timing (tpcg_profile_begin / _end).
+struct Profiler {
+  bool on = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  unsigned long long launches[kKindCount] = {};
+  double ms[kKindCount] = {};
+  unsigned long long timed[kKindCount] = {};
+};
+
 }  // namespace tpcg
 
 struct tpcg_plan {
@@ -74,7 +92,7 @@ struct tpcg_plan {
 
   // device: PCG workspaces
   double* d_R = nullptr;
-  double* d_P = nullptr;
+  double* d_P[2] = {nullptr, nullptr};  // direction, ping-pong: the stencil of the new P reads the old one
   double* d_W = nullptr;
   void* d_Z = nullptr;       // FP64 (FP64 form) or FP32 (mixed forms)
   void* d_Rlp = nullptr;     // BF16 copy of R (mixed forms), row pitch pitch16[0]
@@ -89,6 +107,9 @@ struct tpcg_plan {
   int* d_err = nullptr;   // device error word of bounded waits
 
   std::vector<tpcg::StageParams> stages;
+  void* tc_state = nullptr;   // tensor-core pass descriptors (tensor maps, launch shapes)
+  mutable unsigned long long launch_count = 0;   // kernels launched by this plan
+  mutable tpcg::Profiler prof;
   size_t device_bytes = 0;
 
   // launch configuration (fixed per plan so that reductions are reproducible)
