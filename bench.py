@@ -194,7 +194,10 @@ def kernel_work(kind, plan_prec, N, dims, iters_total, applies_total, ztype_byte
     if kind == "modeprod_f64":
         return applies_total * 4.0 * N * (n + q + t + 0.25) / 1e12, "TFLOP", "alu"
     if kind == "modeprod_tc":
-        return applies_total * 4.0 * N * (n + q + t + 0.25) / 1e12, "TFLOP", "tensor"
+        # HBM bytes per application (3D): BF16 in + BF16 out for passes 1-5 (4N each), pass 6 reads
+        # BF16 (2N) and R in FP64 (8N) and writes Z in FP32 (4N)
+        per_apply = (5 * 4 + 14) * N if t > 1 else (3 * 4 + 14) * N
+        return applies_total * per_apply / 1e9, "GB", "hbm"
     if kind == "direction":
         # FP64 flops per point: P = (Z - m) + beta P_old (3), 7-point stencil (7), <W, P> (2)
         return iters_total * 12.0 * N / 1e12, "TFLOP", "alu"

@@ -325,14 +325,15 @@ int tpcg_plan_create(int nx, int ny, int nz, const int bc[3], const double h[3],
     for (int i = 0; i < l; ++i)
       for (int j = 0; j < l; ++j) VT[(size_t)j * l + i] = A.V[(size_t)i * l + j];
     std::vector<float> lam32(A.lam.begin(), A.lam.end());
+    lam32.resize((size_t)pad_to(l, 16) + 16, 0.0f);  // 16-wide epilogue reads stay in bounds
     if ((rc = dalloc(p, &p->d_W64[m][0], (size_t)l * l))) break;
     if ((rc = dalloc(p, &p->d_W64[m][1], (size_t)l * l))) break;
     if ((rc = dalloc(p, &p->d_lam64[m], (size_t)l))) break;
-    if ((rc = dalloc(p, &p->d_lam32[m], (size_t)l))) break;
+    if ((rc = dalloc(p, &p->d_lam32[m], lam32.size()))) break;
     cudaMemcpy(p->d_W64[m][0], A.V.data(), sizeof(double) * l * l, cudaMemcpyHostToDevice);   // W = V
     cudaMemcpy(p->d_W64[m][1], VT.data(), sizeof(double) * l * l, cudaMemcpyHostToDevice);    // W = V^T
     cudaMemcpy(p->d_lam64[m], A.lam.data(), sizeof(double) * l, cudaMemcpyHostToDevice);
-    cudaMemcpy(p->d_lam32[m], lam32.data(), sizeof(float) * l, cudaMemcpyHostToDevice);
+    cudaMemcpy(p->d_lam32[m], lam32.data(), sizeof(float) * lam32.size(), cudaMemcpyHostToDevice);
     if (prec != TPCG_FP64) {
       // K-major W^T in BF16: dir 0 (W = V) -> element [c'][c] = V[c][c']; dir 1 (W = V^T) -> V[c'][c].
       const int lp = p->pitch16[m];

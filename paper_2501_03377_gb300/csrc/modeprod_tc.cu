@@ -35,7 +35,8 @@ namespace tpcg {
 
 namespace {
 
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;   // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
+constexpr int kEpiThreads = 256;
 constexpr int kTileRows = 128;
 constexpr int kKTile = 64;                 // BF16 elements per 128-byte swizzle row
 constexpr int kStageBytes = kTileRows * 128;
@@ -147,6 +148,7 @@ struct TcArgs {
   int rows, B;
   long long oa, ob, oc;
   int scale, singular;
+  int vec;   // 16-element runs of the output are contiguous and 16-byte aligned
   const float* lamA;
   const float* lamB;
   const float* lamC;
@@ -158,17 +160,32 @@ struct TcArgs {
   int* err;
 };
 
-__device__ __forceinline__ float ghat32(const TcArgs& a, int ia, int ib, int ic) {
-  if (a.singular && ia == 0 && ib == 0 && ic == 0) return 0.0f;
-  return 1.0f / (a.lamA[ia] + a.lamB[ib] + a.lamC[ic]);
-}
-
 template <class OutT>
 __device__ __forceinline__ void store_out(void* out, long long o, float v) {
   if constexpr (sizeof(OutT) == 2)
     reinterpret_cast<__nv_bfloat16*>(out)[o] = __float2bfloat16_rn(v);
   else
     reinterpret_cast<float*>(out)[o] = v;
+}
+
+// 16 consecutive outputs starting at element offset o (16-byte aligned).
+template <class OutT>
+__device__ __forceinline__ void store16(void* out, long long o, const float (&x)[16]) {
+  if constexpr (sizeof(OutT) == 2) {
+    uint32_t pk[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      __nv_bfloat162 h2 = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+      pk[i] = *reinterpret_cast<uint32_t*>(&h2);
+    }
+    uint4* d = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(out) + o);
+    d[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    d[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+  } else {
+    float4* d = reinterpret_cast<float4*>(reinterpret_cast<float*>(out) + o);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) d[i] = make_float4(x[4 * i], x[4 * i + 1], x[4 * i + 2], x[4 * i + 3]);
+  }
 }
 
 template <int FORM, class OutT, bool FINAL>
@@ -202,7 +219,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull(b), 1);
-      mbar_init(tempty(b), 4 * 32);
+      mbar_init(tempty(b), kEpiThreads);
     }
     mbar_init(vbar, 1);
     mbar_init(drain, 1);
@@ -288,8 +305,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     while (!mbar_try_wait(drain, 0) && gtimer() - t0 < kWaitLimitNs) {
     }
   } else if (warp >= 2) {
-    // ---------------- epilogue
-    const int q = warp & 3;  // TMEM lane quadrant this warp may access
+    // ---------------- epilogue: two warps per TMEM lane quadrant, each taking every other 16-column chunk
+    const int q = warp & 3;          // TMEM lane quadrant this warp may access
+    const int h = (warp - 2) >> 2;   // which half of the column chunks
     int tcount = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tcount) {
       const int b = tcount & 1;
@@ -298,61 +316,73 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t tacc = tmem + (uint32_t)(b * a.acc_cols) + ((uint32_t)(q * 32) << 16);
       const int row0 = tile * kTileRows;
       if (FORM == 1) {
+        // one thread per row; its 16 consecutive output columns are contiguous in memory (oc == 1)
         const int r = row0 + q * 32 + lane;
         const bool valid = r < a.rows;
         const int ia = valid ? r / a.B : 0;
         const int ib = valid ? r - ia * a.B : 0;
         const long long obase = (long long)ia * a.oa + (long long)ib * a.ob;
-        for (int c0 = 0; c0 < a.Np; c0 += 16) {
+        const float sab = (a.scale && valid) ? a.lamA[ia] + a.lamB[ib] : 0.0f;
+        const bool null_row = a.singular && ia == 0 && ib == 0;
+        for (int c0 = h * 16; c0 < a.Np; c0 += 32) {
           float v[16];
           tc_ld16(tacc + (uint32_t)c0, v);
-          if (valid) {
+          if (!valid) continue;
+          if (a.scale) {  // Algorithm 7 line 4: multiply by G = 1 / (lam_a + lam_b + lam_c)
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] *= __frcp_rn(sab + a.lamC[c0 + j]);
+            if (null_row && c0 == 0) v[0] = 0.0f;
+          }
+          if (a.vec && c0 + 16 <= a.Cout) {
+            store16<OutT>(a.out, obase + c0, v);
+            if (FINAL) {
+              const double2* rp = reinterpret_cast<const double2*>(a.R + obase + c0);
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                const double2 rr = __ldg(rp + i);
+                red0 = fma(rr.x, f32_to_f64_int(v[2 * i]), red0);
+                red0 = fma(rr.y, f32_to_f64_int(v[2 * i + 1]), red0);
+                red1 += v[2 * i] + v[2 * i + 1];
+              }
+            }
+          } else {
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
               const int c = c0 + j;
               if (c < a.Cout) {
-                float x = v[j];
-                if (a.scale) x *= ghat32(a, ia, ib, c);
                 const long long o = obase + (long long)c * a.oc;
-                store_out<OutT>(a.out, o, x);
+                store_out<OutT>(a.out, o, v[j]);
                 if (FINAL) {
-                  red0 = fma(__ldg(a.R + o), f32_to_f64_int(x), red0);
-                  red1 += x;
+                  red0 = fma(__ldg(a.R + o), f32_to_f64_int(v[j]), red0);
+                  red1 += v[j];
                 }
               }
             }
           }
         }
       } else {
+        // one thread per output index; its 16 consecutive rows are contiguous in memory (ob == 1)
         for (int mb = 0; mb < a.MB; ++mb) {
           const int c = mb * 128 + q * 32 + lane;
           const bool cvalid = c < a.Cout;
-          const float lc = (a.scale && cvalid) ? a.lamC[c] : 0.0f;
-          for (int c0 = 0; c0 < kTileRows; c0 += 16) {
+          for (int c0 = h * 16; c0 < kTileRows; c0 += 32) {
             float v[16];
             tc_ld16(tacc + (uint32_t)(mb * 128 + c0), v);
-            int r = row0 + c0;
-            int ia = r / a.B;
-            int ib = r - ia * a.B;
+            const int r0 = row0 + c0;
+            if (!cvalid || r0 >= a.rows) continue;
+            int ia = r0 / a.B;
+            int ib = r0 - ia * a.B;
+            if (a.vec && ib + 16 <= a.B && r0 + 16 <= a.rows) {
+              store16<OutT>(a.out, (long long)ia * a.oa + ib + (long long)c * a.oc, v);
+            } else {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              if (cvalid && r < a.rows) {
-                float x = v[j];
-                if (a.scale) {
-                  const bool null = a.singular && ia == 0 && ib == 0 && c == 0;
-                  x = null ? 0.0f : x / (a.lamA[ia] + a.lamB[ib] + lc);
+              for (int j = 0; j < 16; ++j) {
+                if (r0 + j < a.rows)
+                  store_out<OutT>(a.out, (long long)ia * a.oa + (long long)ib * a.ob + (long long)c * a.oc, v[j]);
+                if (++ib == a.B) {
+                  ib = 0;
+                  ++ia;
                 }
-                const long long o = (long long)ia * a.oa + (long long)ib * a.ob + (long long)c * a.oc;
-                store_out<OutT>(a.out, o, x);
-                if (FINAL) {
-                  red0 = fma(__ldg(a.R + o), f32_to_f64_int(x), red0);
-                  red1 += x;
-                }
-              }
-              ++r;
-              if (++ib == a.B) {
-                ib = 0;
-                ++ia;
               }
             }
           }
@@ -451,7 +481,9 @@ int tc_plan_setup(tpcg_plan* p) {
   for (int si = 0; si < ns; ++si) {
     const StageParams& sp = p->stages[si];
     TcStage st{};
-    st.form = (sp.oc == 1) ? 2 : 1;  // lanes walk the contiguous output index (2) or the rows (1)
+    // form 1 (thread = row) when the output index is contiguous, form 2 (thread = output index)
+    // when consecutive rows are: either way a thread owns 16 contiguous outputs
+    st.form = (sp.oc == 1) ? 1 : 2;
     TcArgs& a = st.args;
     a.C = sp.C;
     a.KT = (sp.C + kKTile - 1) / kKTile;
@@ -470,6 +502,14 @@ int tc_plan_setup(tpcg_plan* p) {
     a.ob = sp.ob;
     a.oc = sp.oc;
     a.scale = sp.scale;
+    if (st.form == 2 && (sp.scale || sp.final_stage)) {  // scaling and PCG sums live in form-1 epilogues
+      delete tp;
+      return TPCG_ERR_UNSUPPORTED;
+    }
+    if (st.form == 1)
+      a.vec = (sp.final_stage ? (sp.oa % 4 == 0 && sp.ob % 4 == 0) : (sp.oa % 8 == 0 && sp.ob % 8 == 0)) ? 1 : 0;
+    else
+      a.vec = (sp.ob == 1 && sp.oa % 8 == 0 && sp.oc % 8 == 0 && sp.B % 8 == 0) ? 1 : 0;
     a.singular = p->singular ? 1 : 0;
     a.lamA = p->d_lam32[sp.lamA];
     a.lamB = p->d_lam32[sp.lamB];

@@ -88,7 +88,7 @@ def emulate_bf16_precond(r_nqt, Vs, lams, singular):
     la = [np.asarray(l, dtype=np.float32) for l in lams]
     S = (la[0][:, None, None] + la[1][None, :, None]) + la[2][None, None, :]
     with np.errstate(divide="ignore"):
-        F = (F / S).astype(np.float32)
+        F = (F * (np.float32(1.0) / S).astype(np.float32)).astype(np.float32)
     if singular:
         F[0, 0, 0] = 0.0
     F = bf16_from_f32(F)
