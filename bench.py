@@ -39,7 +39,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="auto", choices=["auto", "bf16", "fp64"])
+    ap.add_argument("--prec", default="auto", choices=["auto", "fp16", "bf16", "fp64"])
+    ap.add_argument("--no-bf16-compare", action="store_true")
     ap.add_argument("--nz", type=int, default=128)
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -160,11 +161,13 @@ def pick_prec(args):
         return args.prec
     from paper_2501_03377_gb300 import Plan
 
-    try:
-        Plan(16, 16, 16, ("P", "P", "N"), prec="bf16").close()
-        return "bf16"
-    except Exception:
-        return "fp64"
+    for prec in ("fp16", "bf16"):
+        try:
+            Plan(16, 16, 16, ("P", "P", "N"), prec=prec).close()
+            return prec
+        except Exception:
+            pass
+    return "fp64"
 
 
 def time_steps(plan, etas, ups, steps, tol, torch, barrier, sampler=None):
@@ -293,6 +296,18 @@ def run_ours(args, rank, world, torch):
     e2e = {"value": world * args.steps / e2e_dt, "unit": "solves/s", "h2d_bytes_per_step": 8 * N,
            "d2h_bytes_per_step": 8 * N}
 
+    # the BF16 mixed form, same workload and timing rules
+    bf16_cmp = None
+    if prec == "fp16" and not args.no_bf16_compare:
+        pb = Plan(nx, ny, nz, w0["bcs"], prec="bf16")
+        for s in range(args.warmup):
+            pb.solve(etas[s % 4], ups, tol=args.tol, maxit=60, zero_guess=True)
+        dtb, infb, _ = time_steps(pb, etas, ups, args.steps, args.tol, torch, barrier)
+        bf16_cmp = {"value": world * args.steps / dtb, "unit": "solves/s", "steps": args.steps,
+                    "iters_per_solve": sum(i["iters"] for (_, i) in infb) / args.steps,
+                    "worst_rel_res_true": max(i["rel_res_true"] for (_, i) in infb)}
+        pb.close()
+
     # the plain FP64 form for comparison (fewer steps: it is ~100x slower)
     fp64_cmp = None
     if prec != "fp64" and not args.no_fp64_compare:
@@ -317,9 +332,9 @@ def run_ours(args, rank, world, torch):
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if prec == "fp64" else "f64+bf16(tensor)", "data": "synthetic",
+            "dtype": "f64" if prec == "fp64" else f"f64+{prec}(tensor)", "data": "synthetic",
             "config": {"workload": w0["name"], "grid": [nx, ny, nz], "bcs": ",".join(w0["bcs"]), "tol": args.tol,
-                       "form": "fp64" if prec == "fp64" else "mixed-bf16",
+                       "form": "fp64" if prec == "fp64" else f"mixed-{prec}",
                        "rhs": "2000 Gaussian defects sigma~U(1,4) cells, charges +-1, ||eta||=1/N",
                        "l2": "4 right-hand sides rotated (4 x 67 MB) + ~0.3 GB workspace per solve > 129 MB L2",
                        "parallelism": f"replicas x{world}"},
@@ -328,7 +343,7 @@ def run_ours(args, rank, world, torch):
             "worst_rel_res_true": worst_res, "failed_solves": len(bad),
             "gpu_launches": launches,
             "roofline": roofline, "kernels": kernels,
-            "e2e": e2e, "cpu_baseline": cpu, "fp64_form": fp64_cmp, "clocks": clocks,
+            "e2e": e2e, "cpu_baseline": cpu, "fp64_form": fp64_cmp, "bf16_form": bf16_cmp, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     plan.close()

@@ -65,6 +65,11 @@ extern "C" {
 #define TPCG_FP64         0  /* mode products in FP64 (CUDA cores)                   */
 #define TPCG_MIXED_TF32   1  /* reserved: TF32 tensor-core mode products             */
 #define TPCG_MIXED_BF16   2  /* BF16 tensor-core mode products, FP32 accumulation    */
+#define TPCG_MIXED_FP16   3  /* FP16 tensor-core mode products, FP32 accumulation;
+                                R is scaled by a power of two to unit RMS before the
+                                conversion and the Hadamard step by 2^-s so every
+                                intermediate stays inside the FP16 range; the scale
+                                is undone exactly on Z                              */
 
 /* ---- tpcg_solve flags ---------------------------------------------------- */
 #define TPCG_ZERO_GUESS   1u  /* ignore ups on entry and start from ups = 0 */

@@ -29,7 +29,8 @@ BC = {"P": 0, "D": 1, "N": 2, "DN": 3, "ND": 4}
 TPCG_FP64 = 0
 TPCG_MIXED_TF32 = 1
 TPCG_MIXED_BF16 = 2
-PREC = {"fp64": TPCG_FP64, "tf32": TPCG_MIXED_TF32, "bf16": TPCG_MIXED_BF16}
+TPCG_MIXED_FP16 = 3
+PREC = {"fp64": TPCG_FP64, "tf32": TPCG_MIXED_TF32, "bf16": TPCG_MIXED_BF16, "fp16": TPCG_MIXED_FP16}
 TPCG_ZERO_GUESS = 1
 
 

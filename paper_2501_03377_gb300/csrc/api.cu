@@ -22,6 +22,7 @@ void launch_true_residual(const tpcg_plan* p, const Geom& g, const double* eta, 
 void launch_center_u(const tpcg_plan* p, const Geom& g, double* U);
 void launch_zero(const tpcg_plan* p, long long N, double* U);
 void launch_to_lp(const tpcg_plan* p, const Geom& g, const double* r);
+void launch_norm_shift(const tpcg_plan* p, const Geom& g, const double* r);
 void launch_f32_to_f64(const tpcg_plan* p, long long N, const float* a, double* b);
 void launch_rhs_add_bc(const tpcg_plan* p, const Geom& g, double* eta, const double* bv);
 void run_precond_f64(const tpcg_plan* pl, const double* R, double* Z, SolveState* st);
@@ -174,6 +175,30 @@ uint16_t host_bf16(double x) {
   return (uint16_t)(sign | bits);
 }
 
+uint16_t host_f16(double x) {
+  // FP64 -> FP16 (binary16), one round-to-nearest-even step, subnormals kept
+  uint64_t u;
+  std::memcpy(&u, &x, 8);
+  const uint32_t sign = (uint32_t)(u >> 48) & 0x8000u;
+  const int e = (int)((u >> 52) & 0x7ff);
+  if (e == 0) return (uint16_t)sign;
+  const int E = e - 1023;
+  if (E > 15) return (uint16_t)(sign | 0x7bffu);
+  const uint64_t m = (u & 0xfffffffffffffull) | (1ull << 52);
+  int sh = 42;
+  uint32_t ef = 0;
+  if (E >= -14) ef = (uint32_t)(E + 15);
+  else {
+    sh = 28 - E;
+    if (sh > 62) return (uint16_t)sign;
+  }
+  const uint64_t qv = m >> sh, rem = m & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+  uint32_t bits = ef ? ((ef << 10) | ((uint32_t)qv & 0x3ffu)) : (uint32_t)qv;
+  if (rem > half || (rem == half && (qv & 1ull))) bits += 1;
+  if (bits >= 0x7c00u) bits = 0x7bffu;
+  return (uint16_t)(sign | bits);
+}
+
 int run_precond(const tpcg_plan* p, const double* R, void* Z, SolveState* st) {
   if (p->prec == TPCG_FP64) {
     run_precond_f64(p, R, (double*)Z, st);
@@ -207,8 +232,9 @@ int solve_impl(tpcg_plan* p, const double* eta, double* ups, double tol, int max
   if (cudaMemcpyAsync(p->d_state, hs, sizeof(SolveState), cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
     return TPCG_ERR_CUDA;
   // Algorithm 1, lines 2-7 (eq. centering first when singular)
-  if (p->singular) launch_eta_sum(p, g, eta);
+  launch_eta_sum(p, g, eta);  // mean (singular operators) and the first low-precision exponent
   launch_init_residual(p, g, eta, ups, zero_guess);
+  if (p->lp_kind == 2 && !zero_guess) launch_to_lp(p, g, p->d_R);  // re-scale FP16 copy to the actual R_0
   int rc = run_precond(p, p->d_R, p->d_Z, p->d_state);
   if (rc) return rc;
   if ((rc = last_cuda_error())) return rc;
@@ -282,7 +308,8 @@ int tpcg_plan_create(int nx, int ny, int nz, const int bc[3], const double h[3],
     if (bc[m] < 0 || bc[m] > 4) return TPCG_ERR_INVALID_ARG;
     if (!(h[m] > 0.0) || !std::isfinite(h[m])) return TPCG_ERR_INVALID_ARG;
   }
-  if (prec != TPCG_FP64 && prec != TPCG_MIXED_BF16 && prec != TPCG_MIXED_TF32) return TPCG_ERR_INVALID_ARG;
+  if (prec != TPCG_FP64 && prec != TPCG_MIXED_BF16 && prec != TPCG_MIXED_TF32 && prec != TPCG_MIXED_FP16)
+    return TPCG_ERR_INVALID_ARG;
   if (prec == TPCG_MIXED_TF32) return TPCG_ERR_UNSUPPORTED;
   if (prec != TPCG_FP64 && (nx > 256 || ny > 256 || nz > 256)) return TPCG_ERR_UNSUPPORTED;
   const long long N = (long long)nx * ny * nz;
@@ -296,6 +323,7 @@ int tpcg_plan_create(int nx, int ny, int nz, const int bc[3], const double h[3],
     p->h[m] = (m < naxes) ? h[m] : 1.0;
   }
   p->prec = prec;
+  p->lp_kind = (prec == TPCG_MIXED_BF16) ? 1 : (prec == TPCG_MIXED_FP16 ? 2 : 0);
   p->stream = (cudaStream_t)stream;
   p->is2d = (nz == 1);
   p->N = N;
@@ -335,13 +363,14 @@ int tpcg_plan_create(int nx, int ny, int nz, const int bc[3], const double h[3],
     cudaMemcpy(p->d_lam64[m], A.lam.data(), sizeof(double) * l, cudaMemcpyHostToDevice);
     cudaMemcpy(p->d_lam32[m], lam32.data(), sizeof(float) * lam32.size(), cudaMemcpyHostToDevice);
     if (prec != TPCG_FP64) {
-      // K-major W^T in BF16: dir 0 (W = V) -> element [c'][c] = V[c][c']; dir 1 (W = V^T) -> V[c'][c].
+      // K-major W^T in BF16 / FP16: dir 0 (W = V) -> element [c'][c] = V[c][c']; dir 1 (W = V^T) -> V[c'][c].
       const int lp = p->pitch16[m];
       std::vector<uint16_t> b0((size_t)l * lp, 0), b1((size_t)l * lp, 0);
       for (int r = 0; r < l; ++r)
         for (int c = 0; c < l; ++c) {
-          b0[(size_t)r * lp + c] = host_bf16(A.V[(size_t)c * l + r]);
-          b1[(size_t)r * lp + c] = host_bf16(A.V[(size_t)r * l + c]);
+          const double v0 = A.V[(size_t)c * l + r], v1 = A.V[(size_t)r * l + c];
+          b0[(size_t)r * lp + c] = (prec == TPCG_MIXED_FP16) ? host_f16(v0) : host_bf16(v0);
+          b1[(size_t)r * lp + c] = (prec == TPCG_MIXED_FP16) ? host_f16(v1) : host_bf16(v1);
         }
       uint16_t *d0 = nullptr, *d1 = nullptr;
       if ((rc = dalloc(p, &d0, b0.size()))) break;
@@ -485,6 +514,7 @@ int tpcg_precond_apply(tpcg_plan* plan, const double* r, double* z) {
     return last_cuda_error();
   }
   const Geom g = make_geom(plan);
+  launch_norm_shift(plan, g, r);
   launch_to_lp(plan, g, r);
   if ((rc = run_precond_tc(plan, (float*)plan->d_Z, nullptr))) return rc;
   launch_f32_to_f64(plan, plan->N, (const float*)plan->d_Z, z);

@@ -156,14 +156,22 @@ __global__ void __launch_bounds__(TX* TY) k_apply_laplacian(Geom g, int zchunk, 
 }
 
 // ------------------------------------------------------------------ low-precision copy of R
-__device__ __forceinline__ void store_lp(void* rlp, int pitch, int nx, long long i, double r) {
-  if (!rlp) return;
+// Input of the first tensor-core pass: BF16, or FP16 of R * 2^shift, rows
+// padded to `pitch` elements.  ptr == nullptr in the FP64 form.
+struct LowPrec {
+  void* ptr;
+  int kind;  // 1 BF16, 2 FP16
+  int pitch, nx;
+};
+
+__device__ __forceinline__ void store_lp(const LowPrec& lp, int shift, long long i, double r) {
+  if (!lp.ptr) return;
   long long j = i;
-  if (pitch != nx) {
-    const long long row = i / nx;
-    j = row * pitch + (i - row * nx);
+  if (lp.pitch != lp.nx) {
+    const long long row = i / lp.nx;
+    j = row * lp.pitch + (i - row * lp.nx);
   }
-  reinterpret_cast<uint16_t*>(rlp)[j] = f64_to_bf16_bits(r);
+  reinterpret_cast<uint16_t*>(lp.ptr)[j] = (lp.kind == 2) ? f64_to_f16_bits(r, shift) : f64_to_bf16_bits(r);
 }
 
 // ------------------------------------------------------------------ residual R = eta_hat - L U
@@ -173,14 +181,14 @@ __device__ __forceinline__ void store_lp(void* rlp, int pitch, int nx, long long
 struct OpResidual {
   const double* __restrict__ eta;
   double* __restrict__ R;
-  void* rlp;
-  int pitch, nx;
+  LowPrec lp;
+  int shift;
   double mean;
   __device__ __forceinline__ void operator()(long long i, double c, double w, double (&acc)[4]) {
     const double e = __ldg(eta + i) - mean;
     const double r = e - w;
     R[i] = r;
-    store_lp(rlp, pitch, nx, i, r);
+    store_lp(lp, shift, i, r);
     acc[0] = fma(r, r, acc[0]);
     acc[1] += r;
     acc[2] = fma(e, e, acc[2]);
@@ -188,11 +196,19 @@ struct OpResidual {
   }
 };
 
-__device__ void fin_init(SolveState* st, const double (&s)[4]) {
+// The low-precision copy just written used lp_shift; the next one uses the
+// exponent that scales the new residual to unit RMS.
+__device__ __forceinline__ void advance_shift(SolveState* st, double rr, long long N) {
+  st->lp_shift_applied = st->lp_shift;
+  st->lp_shift = lp_shift_for(rr, N);
+}
+
+__device__ void fin_init(SolveState* st, const double (&s)[4], long long N) {
   st->rr = s[0];
   st->sumR = s[1];
   st->eta_norm2 = s[2];
   st->tol2 = st->tol2 * s[2];  // tol^2 was stored; scale by ||eta_hat||^2
+  advance_shift(st, s[0], N);
   if (!isfinite(s[0]) || !isfinite(s[2])) {
     st->status = TPCG_ERR_BREAKDOWN;
     st->done = 1;
@@ -204,16 +220,18 @@ __device__ void fin_init(SolveState* st, const double (&s)[4]) {
 
 __global__ void __launch_bounds__(TX* TY) k_init_residual(Geom g, int zchunk, const double* __restrict__ eta,
                                                           const double* __restrict__ U, double* __restrict__ R,
-                                                          void* rlp, int pitch, SolveState* st, double* partials) {
+                                                          LowPrec lp, SolveState* st, double* partials) {
   FieldPlain f{U};
-  OpResidual op{eta, R, rlp, pitch, g.nx, st->mean_eta};
+  OpResidual op{eta, R, lp, st->lp_shift, st->mean_eta};
+  const long long N = g.N;
   stencil_sweep<4>(g, zchunk, f, op, partials, &st->tickets[kTkInit],
-                   [st](const double(&s)[4]) { fin_init(st, s); });
+                   [st, N](const double(&s)[4]) { fin_init(st, s, N); });
 }
 
-__device__ void fin_true(SolveState* st, const double (&s)[4]) {
+__device__ void fin_true(SolveState* st, const double (&s)[4], long long N) {
   st->true_rr = s[0];
   st->sumU = s[3];
+  advance_shift(st, s[0], N);
   if (!isfinite(s[0])) {
     st->status = TPCG_ERR_BREAKDOWN;
     st->done = 1;
@@ -234,18 +252,18 @@ __device__ void fin_true(SolveState* st, const double (&s)[4]) {
 
 __global__ void __launch_bounds__(TX* TY) k_true_residual(Geom g, int zchunk, const double* __restrict__ eta,
                                                           const double* __restrict__ U, double* __restrict__ R,
-                                                          void* rlp, int pitch, SolveState* st, double* partials,
-                                                          int force) {
+                                                          LowPrec lp, SolveState* st, double* partials, int force) {
   if (!force && (st->done || !st->need_check)) return;
   FieldPlain f{U};
-  OpResidual op{eta, R, rlp, pitch, g.nx, st->mean_eta};
+  OpResidual op{eta, R, lp, st->lp_shift, st->mean_eta};
+  const long long N = g.N;
   stencil_sweep<4>(g, zchunk, f, op, partials, &st->tickets[kTkTrue],
-                   [st, force](const double(&s)[4]) {
+                   [st, force, N](const double(&s)[4]) {
                      if (force) {
                        st->true_rr = s[0];
                        st->sumU = s[3];
                      } else {
-                       fin_true(st, s);
+                       fin_true(st, s, N);
                      }
                    });
 }
@@ -287,67 +305,96 @@ __global__ void __launch_bounds__(TX* TY) k_direction(Geom g, int zchunk, const 
 
 // ------------------------------------------------------------------ streaming kernels
 // U += alpha P (line 12), R -= alpha W (line 13), low-precision copy of R,
-// ||R||^2 and sum(R); iteration counter and recurrence stop test.
-__device__ void fin_update(SolveState* st, const double (&s)[2]) {
-  st->rr = s[0];
-  st->sumR = s[1];
+// ||R||^2 and sum(R) for the stop test and the centring correction of rho.
+// The two sums are accumulated per thread in FP32 from R * 2^lp_shift (exact
+// power-of-two scaling, unit RMS) and combined across threads in FP64: they
+// only steer the stop test, which the FP64 true residual confirms.
+__device__ void fin_update(SolveState* st, const double (&s)[2], int shift, long long N) {
+  const double rr = ldexp(s[0], -2 * shift), sumR = ldexp(s[1], -shift);
+  st->rr = rr;
+  st->sumR = sumR;
   st->iter += 1;
   st->zero_guess = 0;
-  if (!isfinite(s[0])) {
+  advance_shift(st, rr, N);
+  if (!isfinite(rr)) {
     st->status = TPCG_ERR_BREAKDOWN;
     st->done = 1;
     return;
   }
-  if (s[0] <= st->tol2 || st->iter >= st->maxit) st->need_check = 1;
+  if (rr <= st->tol2 || st->iter >= st->maxit) st->need_check = 1;
 }
 
-__global__ void __launch_bounds__(256) k_update(long long N, int nx, double* __restrict__ U,
-                                                const double* __restrict__ P, const double* __restrict__ W,
-                                                double* __restrict__ R, void* rlp, int pitch, SolveState* st,
-                                                double* partials) {
+__global__ void __launch_bounds__(256) k_update(long long N, double* __restrict__ U, const double* __restrict__ P,
+                                                const double* __restrict__ W, double* __restrict__ R, LowPrec lp,
+                                                SolveState* st, double* partials) {
   if (st->done) return;
   const double alpha = st->alpha;
+  const double nalpha = -alpha;
   const int zg = st->zero_guess;
-  double acc[2] = {0.0, 0.0};
+  const int shift = st->lp_shift;
+  float a0 = 0.0f, a1 = 0.0f;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
     const double p = __ldg(P + i);
     U[i] = zg ? alpha * p : fma(alpha, p, U[i]);
-    const double r = fma(-alpha, __ldg(W + i), R[i]);
+    const double r = fma(nalpha, __ldg(W + i), R[i]);
     R[i] = r;
-    store_lp(rlp, pitch, nx, i, r);
-    acc[0] = fma(r, r, acc[0]);
-    acc[1] += r;
+    store_lp(lp, shift, i, r);
+    const float r32 = f64_to_f32_int(r, shift);
+    a0 = fmaf(r32, r32, a0);
+    a1 += r32;
   }
+  double acc[2] = {(double)a0, (double)a1};
   grid_reduce<2>(acc, partials, &st->tickets[kTkUpd], gridDim.x, blockIdx.x,
-                 [st](const double(&s)[2]) { fin_update(st, s); });
+                 [st, shift, N](const double(&s)[2]) { fin_update(st, s, shift, N); });
 }
 
 // R = eta_hat (zero initial guess: lines 3-4 with U_0 = 0).
-__global__ void __launch_bounds__(256) k_init_zero(long long N, int nx, const double* __restrict__ eta,
-                                                   double* __restrict__ R, void* rlp, int pitch, SolveState* st,
+__global__ void __launch_bounds__(256) k_init_zero(long long N, const double* __restrict__ eta,
+                                                   double* __restrict__ R, LowPrec lp, SolveState* st,
                                                    double* partials) {
   const double mean = st->mean_eta;
+  const int shift = st->lp_shift;
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
     const double r = __ldg(eta + i) - mean;
     R[i] = r;
-    store_lp(rlp, pitch, nx, i, r);
+    store_lp(lp, shift, i, r);
     acc[0] = fma(r, r, acc[0]);
     acc[1] += r;
   }
   acc[2] = acc[0];
   grid_reduce<4>(acc, partials, &st->tickets[kTkInit], gridDim.x, blockIdx.x,
-                 [st](const double(&s)[4]) { fin_init(st, s); });
+                 [st, N](const double(&s)[4]) { fin_init(st, s, N); });
 }
 
-// sum(eta) -> mean removed by eq. (centering).
+// sum(eta) and sum(eta^2): the mean removed by eq. (centering) when the
+// operator is singular, and the exponent of the first low-precision copy.
 __global__ void __launch_bounds__(256) k_eta_sum(long long N, const double* __restrict__ eta, SolveState* st,
                                                  double* partials) {
+  double acc[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const double e = __ldg(eta + i);
+    acc[0] += e;
+    acc[1] = fma(e, e, acc[1]);
+  }
+  grid_reduce<2>(acc, partials, &st->tickets[kTkEta], gridDim.x, blockIdx.x, [st, N](const double(&s)[2]) {
+    const double mean = st->singular ? s[0] / (double)N : 0.0;
+    st->mean_eta = mean;
+    const double n2 = s[1] - mean * s[0];
+    st->lp_shift = lp_shift_for(n2 > 0.0 ? n2 : s[1], N);
+  });
+}
+
+// ||r||^2 -> exponent of the low-precision copy (tpcg_precond_apply).
+__global__ void __launch_bounds__(256) k_norm_shift(long long N, const double* __restrict__ r, SolveState* st,
+                                                    double* partials) {
   double acc[1] = {0.0};
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-    acc[0] += __ldg(eta + i);
-  grid_reduce<1>(acc, partials, &st->tickets[kTkEta], gridDim.x, blockIdx.x,
-                 [st, N](const double(&s)[1]) { st->mean_eta = s[0] / (double)N; });
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const double v = __ldg(r + i);
+    acc[0] = fma(v, v, acc[0]);
+  }
+  grid_reduce<1>(acc, partials, &st->tickets[kTkMisc], gridDim.x, blockIdx.x,
+                 [st, N](const double(&s)[1]) { st->lp_shift = lp_shift_for(s[0], N); });
 }
 
 // U -= sum(U)/N: return the zero-mean (minimum-norm) representative.
@@ -362,11 +409,14 @@ __global__ void k_zero(long long N, double* __restrict__ U) {
     U[i] = 0.0;
 }
 
-// BF16 copy of an FP64 field (preconditioner input for tpcg_precond_apply).
-__global__ void __launch_bounds__(256) k_to_lp(long long N, int nx, const double* __restrict__ r, void* rlp,
-                                               int pitch) {
+// Low-precision copy of an FP64 field with the state's current exponent
+// (tpcg_precond_apply, and the warm-started FP16 form after its first residual).
+__global__ void __launch_bounds__(256) k_to_lp(long long N, const double* __restrict__ r, LowPrec lp,
+                                               SolveState* st) {
+  const int shift = st->lp_shift;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-    store_lp(rlp, pitch, nx, i, __ldg(r + i));
+    store_lp(lp, shift, i, __ldg(r + i));
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->lp_shift_applied = shift;
 }
 
 // FP32 -> FP64 copy (Z of the mixed forms, for tpcg_precond_apply).
@@ -407,18 +457,23 @@ void launch_apply_laplacian(const tpcg_plan* p, const Geom& g, const double* x, 
   LaunchScope ls(p, kKApply);
   k_apply_laplacian<<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, x, w);
 }
+LowPrec lowprec(const tpcg_plan* p) { return LowPrec{p->d_Rlp, p->lp_kind, p->pitch16[0], p->nx}; }
+
 void launch_init_residual(const tpcg_plan* p, const Geom& g, const double* eta, const double* U, bool zero_guess) {
   LaunchScope ls(p, kKInit);
   if (zero_guess)
-    k_init_zero<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, g.nx, eta, p->d_R, p->d_Rlp, p->pitch16[0], p->d_state,
-                                                          p->d_partials);
+    k_init_zero<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, eta, p->d_R, lowprec(p), p->d_state, p->d_partials);
   else
-    k_init_residual<<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, eta, U, p->d_R, p->d_Rlp,
-                                                                p->pitch16[0], p->d_state, p->d_partials);
+    k_init_residual<<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, eta, U, p->d_R, lowprec(p),
+                                                                p->d_state, p->d_partials);
 }
 void launch_eta_sum(const tpcg_plan* p, const Geom& g, const double* eta) {
   LaunchScope ls(p, kKEtaSum);
   k_eta_sum<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, eta, p->d_state, p->d_partials);
+}
+void launch_norm_shift(const tpcg_plan* p, const Geom& g, const double* r) {
+  LaunchScope ls(p, kKConvert);
+  k_norm_shift<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, r, p->d_state, p->d_partials);
 }
 void launch_direction(const tpcg_plan* p, const Geom& g, int k) {
   LaunchScope ls(p, kKDirection);
@@ -433,13 +488,13 @@ void launch_direction(const tpcg_plan* p, const Geom& g, int k) {
 }
 void launch_update(const tpcg_plan* p, const Geom& g, double* U, int k) {
   LaunchScope ls(p, kKUpdate);
-  k_update<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, g.nx, U, p->d_P[k & 1], p->d_W, p->d_R, p->d_Rlp,
-                                                     p->pitch16[0], p->d_state, p->d_partials);
+  k_update<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, U, p->d_P[k & 1], p->d_W, p->d_R, lowprec(p), p->d_state,
+                                                     p->d_partials);
 }
 void launch_true_residual(const tpcg_plan* p, const Geom& g, const double* eta, const double* U, bool force) {
   LaunchScope ls(p, kKTrueRes);
-  k_true_residual<<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, eta, U, p->d_R, p->d_Rlp,
-                                                              p->pitch16[0], p->d_state, p->d_partials, force ? 1 : 0);
+  k_true_residual<<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, eta, U, p->d_R, lowprec(p), p->d_state,
+                                                              p->d_partials, force ? 1 : 0);
 }
 void launch_center_u(const tpcg_plan* p, const Geom& g, double* U) {
   LaunchScope ls(p, kKCenter);
@@ -451,7 +506,7 @@ void launch_zero(const tpcg_plan* p, long long N, double* U) {
 }
 void launch_to_lp(const tpcg_plan* p, const Geom& g, const double* r) {
   LaunchScope ls(p, kKConvert);
-  k_to_lp<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, g.nx, r, p->d_Rlp, p->pitch16[0]);
+  k_to_lp<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, r, lowprec(p), p->d_state);
 }
 void launch_f32_to_f64(const tpcg_plan* p, long long N, const float* a, double* b) {
   LaunchScope ls(p, kKConvert);

@@ -24,8 +24,11 @@
 // an error word, stops issuing, drains its own copies/MMAs with bounded waits,
 // frees TMEM and returns.
 #include <cuda.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
+#include <cmath>
+#include <type_traits>
 #include <cstdio>
 #include <vector>
 
@@ -138,9 +141,10 @@ __device__ __forceinline__ unsigned long long sw128_desc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor of kind::f16: BF16 A and B, FP32 D, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor of kind::f16: A and B both BF16 (fmt 1) or both FP16
+// (fmt 0), FP32 D, both K-major.
+__host__ __device__ constexpr uint32_t idesc_f16kind(int M, int N, uint32_t fmt) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 struct TcArgs {
@@ -149,6 +153,10 @@ struct TcArgs {
   long long oa, ob, oc;
   int scale, singular;
   int vec;   // 16-element runs of the output are contiguous and 16-byte aligned
+  int last;  // last pass: output is Z (FP32), undo the FP16 scaling
+  int sG;    // the Hadamard step is multiplied by 2^-sG (FP16 range), undone on Z
+  float gscale;          // 2^-sG
+  const int* shift_src;  // exponent the FP16 copy of R was scaled with (device)
   const float* lamA;
   const float* lamB;
   const float* lamC;
@@ -162,7 +170,9 @@ struct TcArgs {
 
 template <class OutT>
 __device__ __forceinline__ void store_out(void* out, long long o, float v) {
-  if constexpr (sizeof(OutT) == 2)
+  if constexpr (std::is_same<OutT, __half>::value)
+    reinterpret_cast<__half*>(out)[o] = __float2half_rn(v);
+  else if constexpr (sizeof(OutT) == 2)
     reinterpret_cast<__nv_bfloat16*>(out)[o] = __float2bfloat16_rn(v);
   else
     reinterpret_cast<float*>(out)[o] = v;
@@ -175,10 +185,15 @@ __device__ __forceinline__ void store16(void* out, long long o, const float (&x)
     uint32_t pk[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      __nv_bfloat162 h2 = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
-      pk[i] = *reinterpret_cast<uint32_t*>(&h2);
+      if constexpr (std::is_same<OutT, __half>::value) {
+        __half2 h2 = __floats2half2_rn(x[2 * i], x[2 * i + 1]);
+        pk[i] = *reinterpret_cast<uint32_t*>(&h2);
+      } else {
+        __nv_bfloat162 h2 = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+        pk[i] = *reinterpret_cast<uint32_t*>(&h2);
+      }
     }
-    uint4* d = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(out) + o);
+    uint4* d = reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(out) + o);
     d[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
     d[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
   } else {
@@ -188,7 +203,7 @@ __device__ __forceinline__ void store16(void* out, long long o, const float (&x)
   }
 }
 
-template <int FORM, class OutT, bool FINAL>
+template <int FORM, class InT, class OutT, bool FINAL>
 __global__ void __launch_bounds__(kThreads, 1)
     k_modeprod_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW, TcArgs a) {
   if (a.st && a.st->done) return;
@@ -268,7 +283,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
-    const uint32_t idesc = (FORM == 1) ? idesc_bf16(128, a.Np) : idesc_bf16(128, 128);
+    constexpr uint32_t fmt = std::is_same<InT, __half>::value ? 0u : 1u;
+    const uint32_t idesc = (FORM == 1) ? idesc_f16kind(128, a.Np, fmt) : idesc_f16kind(128, 128, fmt);
     bool ok = wait_bounded(vbar, 0, ab);
     int it = 0, tcount = 0;
     for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++tcount) {
@@ -324,14 +340,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         const long long obase = (long long)ia * a.oa + (long long)ib * a.ob;
         const float sab = (a.scale && valid) ? a.lamA[ia] + a.lamB[ib] : 0.0f;
         const bool null_row = a.singular && ia == 0 && ib == 0;
+        const float zs = (a.last && a.shift_src) ? ldexpf(1.0f, a.sG - *a.shift_src) : 1.0f;
         for (int c0 = h * 16; c0 < a.Np; c0 += 32) {
           float v[16];
           tc_ld16(tacc + (uint32_t)c0, v);
           if (!valid) continue;
           if (a.scale) {  // Algorithm 7 line 4: multiply by G = 1 / (lam_a + lam_b + lam_c)
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] *= __frcp_rn(sab + a.lamC[c0 + j]);
+            for (int j = 0; j < 16; ++j) v[j] *= __frcp_rn(sab + a.lamC[c0 + j]) * a.gscale;
             if (null_row && c0 == 0) v[0] = 0.0f;
+          }
+          if (a.last) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] *= zs;
           }
           if (a.vec && c0 + 16 <= a.Cout) {
             store16<OutT>(a.out, obase + c0, v);
@@ -426,6 +447,7 @@ struct TcStage {
 
 struct TcPlan {
   std::vector<TcStage> stages;
+  bool fp16 = false;
 };
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -446,37 +468,89 @@ EncodeTiledFn encoder() {
 }
 
 int encode_2d(CUtensorMap* map, const void* gaddr, int inner, long long outer, int pitch_elems, int box_inner,
-              int box_outer) {
+              int box_outer, bool fp16) {
   EncodeTiledFn cuTensorMapEncodeTiled = encoder();
   if (!cuTensorMapEncodeTiled) return -1;
   cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
   cuuint64_t strides[1] = {(cuuint64_t)pitch_elems * 2};
   cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = cuTensorMapEncodeTiled(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(gaddr), dims,
+  CUresult r = cuTensorMapEncodeTiled(map, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                                      2, const_cast<void*>(gaddr), dims,
                                       strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : -1;
 }
 
-template <int FORM, class OutT, bool FINAL>
+template <int FORM, class InT, class OutT, bool FINAL>
 int set_smem_attr(size_t smem) {
-  return cudaFuncSetAttribute(k_modeprod_tc<FORM, OutT, FINAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(k_modeprod_tc<FORM, InT, OutT, FINAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem) == cudaSuccess
              ? 0
              : -1;
 }
 
-template <int FORM, class OutT, bool FINAL>
+template <class InT>
+int set_all_smem_attrs() {
+  int bad = 0;
+  bad |= set_smem_attr<1, InT, InT, false>(kMaxSmem);
+  bad |= set_smem_attr<2, InT, InT, false>(kMaxSmem);
+  bad |= set_smem_attr<1, InT, float, false>(kMaxSmem);
+  bad |= set_smem_attr<1, InT, float, true>(kMaxSmem);
+  return bad;
+}
+
+template <int FORM, class InT, class OutT, bool FINAL>
 void launch(const TcStage& s, const TcArgs& a, cudaStream_t stream) {
-  k_modeprod_tc<FORM, OutT, FINAL><<<s.grid, kThreads, s.smem, stream>>>(s.tmX, s.tmW, a);
+  k_modeprod_tc<FORM, InT, OutT, FINAL><<<s.grid, kThreads, s.smem, stream>>>(s.tmX, s.tmW, a);
+}
+
+template <class InT>
+void launch_stage(const TcStage& s, const TcArgs& a, bool last, bool final_pcg, cudaStream_t stream) {
+  if (!last) {
+    if (s.form == 1) launch<1, InT, InT, false>(s, a, stream);
+    else launch<2, InT, InT, false>(s, a, stream);
+  } else if (final_pcg) {
+    launch<1, InT, float, true>(s, a, stream);
+  } else {
+    launch<1, InT, float, false>(s, a, stream);
+  }
+}
+
+// Smallest positive eigenvalue sum: the largest entry of G.
+double smallest_positive_sum(const tpcg_plan* p) {
+  std::vector<double> cand[3];
+  for (int m = 0; m < 3; ++m) {
+    std::vector<double> l = p->ax[m].lam;
+    std::sort(l.begin(), l.end());
+    l.erase(std::unique(l.begin(), l.end()), l.end());
+    cand[m].assign(l.begin(), l.begin() + std::min<size_t>(2, l.size()));
+  }
+  double best = 0.0;
+  for (double x : cand[0])
+    for (double y : cand[1])
+      for (double z : cand[2]) {
+        const double v = x + y + z;
+        if (v > 1e-300 && (best == 0.0 || v < best)) best = v;
+      }
+  return best;
 }
 
 }  // namespace
 
 int tc_plan_setup(tpcg_plan* p) {
-  if (p->prec != TPCG_MIXED_BF16) return TPCG_ERR_UNSUPPORTED;
+  if (p->prec != TPCG_MIXED_BF16 && p->prec != TPCG_MIXED_FP16) return TPCG_ERR_UNSUPPORTED;
   TcPlan* tp = new TcPlan();
+  tp->fp16 = (p->prec == TPCG_MIXED_FP16);
+  // FP16 range: R enters at unit RMS, so intermediates of the forward passes
+  // are bounded by sqrt(N); after G they are bounded by sqrt(N) * max G,
+  // which 2^-sG brings under 2^14 (below the FP16 maximum 65504).
+  int sG = 0;
+  if (tp->fp16) {
+    const double smin = smallest_positive_sum(p);
+    const double bound = std::sqrt((double)p->N) / (smin > 0 ? smin : 1.0);
+    sG = std::max(0, (int)std::ceil(std::log2(bound / 16384.0)));
+  }
   const int ns = (int)p->stages.size();
   for (int si = 0; si < ns; ++si) {
     const StageParams& sp = p->stages[si];
@@ -516,6 +590,10 @@ int tc_plan_setup(tpcg_plan* p) {
     a.lamC = p->d_lam32[sp.lamC];
     a.N = p->N;
     a.err = p->d_err;
+    a.last = sp.final_stage;
+    a.sG = sG;
+    a.gscale = std::ldexp(1.0f, -sG);
+    a.shift_src = tp->fp16 ? &p->d_state->lp_shift_applied : nullptr;
     const size_t vbytes = (size_t)a.KT * a.VR * 128;
     const size_t fixed = 1024 + vbytes + 256;
     if (a.tmem_cols > 512 || a.VR > 256 || fixed + 2 * kStageBytes > (size_t)kMaxSmem) {
@@ -529,20 +607,14 @@ int tc_plan_setup(tpcg_plan* p) {
     // operands: stage si reads the output of stage si-1 (R in BF16 for the first)
     const void* xin = (si == 0) ? p->d_Rlp : p->d_T[(si - 1) & 1];
     const int wpitch = p->pitch16[sp.axis];
-    if (encode_2d(&st.tmX, xin, sp.C, (long long)a.rows, sp.in_pitch, kKTile, kTileRows) ||
-        encode_2d(&st.tmW, p->d_Wt16[sp.axis][sp.dir], sp.C, sp.Cout, wpitch, kKTile, a.VR)) {
+    if (encode_2d(&st.tmX, xin, sp.C, (long long)a.rows, sp.in_pitch, kKTile, kTileRows, tp->fp16) ||
+        encode_2d(&st.tmW, p->d_Wt16[sp.axis][sp.dir], sp.C, sp.Cout, wpitch, kKTile, a.VR, tp->fp16)) {
       delete tp;
       return TPCG_ERR_CUDA;
     }
     tp->stages.push_back(st);
   }
-  int bad = 0;
-  bad |= set_smem_attr<1, __nv_bfloat16, false>(kMaxSmem);
-  bad |= set_smem_attr<2, __nv_bfloat16, false>(kMaxSmem);
-  bad |= set_smem_attr<2, float, false>(kMaxSmem);
-  bad |= set_smem_attr<2, float, true>(kMaxSmem);
-  bad |= set_smem_attr<1, float, false>(kMaxSmem);
-  bad |= set_smem_attr<1, float, true>(kMaxSmem);
+  const int bad = tp->fp16 ? set_all_smem_attrs<__half>() : set_all_smem_attrs<__nv_bfloat16>();
   if (bad) {
     delete tp;
     return TPCG_ERR_CUDA;
@@ -571,16 +643,8 @@ int run_precond_tc(const tpcg_plan* p, float* Z, SolveState* st) {
     a.R = p->d_R;
     a.partials = p->d_partials;
     LaunchScope ls(p, kKModeTC);
-    if (!last) {
-      if (s.form == 1) launch<1, __nv_bfloat16, false>(s, a, p->stream);
-      else launch<2, __nv_bfloat16, false>(s, a, p->stream);
-    } else if (st) {
-      if (s.form == 1) launch<1, float, true>(s, a, p->stream);
-      else launch<2, float, true>(s, a, p->stream);
-    } else {
-      if (s.form == 1) launch<1, float, false>(s, a, p->stream);
-      else launch<2, float, false>(s, a, p->stream);
-    }
+    if (tp->fp16) launch_stage<__half>(s, a, last, st != nullptr, p->stream);
+    else launch_stage<__nv_bfloat16>(s, a, last, st != nullptr, p->stream);
   }
   return TPCG_OK;
 }

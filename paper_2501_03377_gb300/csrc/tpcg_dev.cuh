@@ -35,6 +35,8 @@ struct SolveState {
   int singular;
   int precond_applies;
   int timeout;         // a bounded device wait gave up
+  int lp_shift;        // power-of-two exponent applied when R is next converted to FP16
+  int lp_shift_applied;  // exponent the current low-precision copy of R was converted with
   unsigned tickets[8]; // arrival counters of the last-block reductions
 };
 
@@ -187,14 +189,15 @@ __device__ __forceinline__ uint16_t f64_to_bf16_bits(double x) {
   return (uint16_t)(sign | bits);
 }
 
-// FP64 -> FP32 with round-to-nearest-even in integer arithmetic; underflow
-// to signed zero below the FP32 normal range, saturation above.
-__device__ __forceinline__ float f64_to_f32_int(double x) {
+// x * 2^shift -> FP32 with round-to-nearest-even in integer arithmetic;
+// underflow to signed zero below the FP32 normal range, saturation above.
+__device__ __forceinline__ float f64_to_f32_int(double x, int shift = 0) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const uint32_t sign = (uint32_t)(u >> 32) & 0x80000000u;
   const int e = (int)((u >> 52) & 0x7ff);
   if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (((u & 0xfffffffffffffull) != 0) ? 0x400000u : 0u));
-  const int eb = e - 1023 + 127;
+  if (e == 0) return __uint_as_float(sign);
+  const int eb = e - 1023 + 127 + shift;
   if (eb <= 0) return __uint_as_float(sign);
   const unsigned long long mant = u & 0xfffffffffffffull;
   uint32_t top = (uint32_t)(mant >> 29);     // 23 kept bits
@@ -204,6 +207,44 @@ __device__ __forceinline__ float f64_to_f32_int(double x) {
   if (rest > halfway || (rest == halfway && (top & 1u))) bits += 1;
   if (bits >= 0x7f800000u) bits = 0x7f7fffffu;
   return __uint_as_float(sign | bits);
+}
+
+// x * 2^shift -> FP16 (binary16), round-to-nearest-even in integer arithmetic,
+// gradual underflow to FP16 subnormals, saturation to the largest finite
+// value (65504) above the range; NaN/Inf pass through.
+__device__ __forceinline__ uint16_t f64_to_f16_bits(double x, int shift) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const uint32_t sign = (uint32_t)(u >> 48) & 0x8000u;
+  const int e = (int)((u >> 52) & 0x7ff);
+  if (e == 0x7ff) return (uint16_t)(sign | 0x7c00u | (((u & 0xfffffffffffffull) != 0) ? 0x200u : 0u));
+  if (e == 0) return (uint16_t)sign;
+  const int E = e - 1023 + shift;
+  if (E > 15) return (uint16_t)(sign | 0x7bffu);
+  const unsigned long long m = (u & 0xfffffffffffffull) | (1ull << 52);
+  int sh = 42;
+  uint32_t ef = 0;
+  if (E >= -14) {
+    ef = (uint32_t)(E + 15);
+  } else {
+    sh = 28 - E;
+    if (sh > 62) return (uint16_t)sign;
+  }
+  const unsigned long long qv = m >> sh;
+  const unsigned long long rem = m & ((1ull << sh) - 1);
+  const unsigned long long half = 1ull << (sh - 1);
+  uint32_t bits = ef ? ((ef << 10) | ((uint32_t)qv & 0x3ffu)) : (uint32_t)qv;
+  if (rem > half || (rem == half && (qv & 1ull))) bits += 1;
+  if (bits >= 0x7c00u) bits = 0x7bffu;
+  return (uint16_t)(sign | bits);
+}
+
+// Exponent s with rms * 2^s in [0.5, 1) for the FP16 copy of a vector of
+// squared 2-norm n2 and length N (0 when the vector is zero).
+__device__ __forceinline__ int lp_shift_for(double n2, long long N) {
+  if (!(n2 > 0.0) || !isfinite(n2)) return 0;
+  const double rms = sqrt(n2 / (double)N);
+  int s = -ilogb(rms) - 1;
+  return s < -120 ? -120 : (s > 120 ? 120 : s);
 }
 
 // FP32 -> FP64 is exact; done on the bit pattern as well.

@@ -95,7 +95,8 @@ struct tpcg_plan {
   double* d_P[2] = {nullptr, nullptr};  // direction, ping-pong: the stencil of the new P reads the old one
   double* d_W = nullptr;
   void* d_Z = nullptr;       // FP64 (FP64 form) or FP32 (mixed forms)
-  void* d_Rlp = nullptr;     // BF16 copy of R (mixed forms), row pitch pitch16[0]
+  void* d_Rlp = nullptr;     // BF16 / FP16 copy of R (mixed forms), row pitch pitch16[0]
+  int lp_kind = 0;           // 0 none (FP64 form), 1 BF16, 2 FP16 scaled by 2^lp_shift
   void* d_T[2] = {nullptr, nullptr};  // mode-product intermediates
   size_t t_elems = 0;
   double* d_eta_h = nullptr;  // device copies for tpcg_solve_host

@@ -1,4 +1,4 @@
-"""GPU parity of the mixed BF16 tensor-core path, called through the C ABI.
+"""GPU parity of the mixed tensor-core forms (BF16, FP16 scaled), called through the C ABI.
 
 Two references:
   * a numpy emulation of the same BF16 pipeline (identical rounding points:
@@ -75,27 +75,60 @@ def mode(M, X, m):
     return np.moveaxis(Y, 0, m).astype(np.float32)
 
 
-def emulate_bf16_precond(r_nqt, Vs, lams, singular):
-    """The BF16 tensor-core form of Algorithm 7 with its rounding points."""
+def f16_from_f32(x):
+    return np.asarray(x, dtype=np.float32).astype(np.float16).astype(np.float32)
+
+
+def f16_from_f64(x, shift=0):
+    """x * 2^shift rounded once to binary16 (nearest-even), returned as float32."""
+    return np.ldexp(np.asarray(x, dtype=np.float64), shift).astype(np.float16).astype(np.float32)
+
+
+def lp_shift(r):
+    rms = np.sqrt(np.mean(np.asarray(r, dtype=np.float64) ** 2))
+    return 0 if rms == 0 else int(np.clip(-np.floor(np.log2(rms)) - 1, -120, 120))
+
+
+def fp16_gscale_exponent(lams, N):
+    cands = [np.unique(np.asarray(l))[:2] for l in lams]
+    sums = [x + y + z for x in cands[0] for y in cands[1] for z in cands[2] if x + y + z > 1e-300]
+    bound = np.sqrt(N) / min(sums)
+    return max(0, int(np.ceil(np.log2(bound / 16384.0))))
+
+
+def emulate_precond(r_nqt, Vs, lams, singular, prec="bf16"):
+    """The tensor-core form of Algorithm 7 with its rounding points (BF16, or FP16 with the
+    power-of-two scalings that keep every intermediate in range)."""
     three_d = r_nqt.shape[2] > 1
-    Vb = [bf16_from_f64(V) for V in Vs]
-    F = bf16_from_f64(r_nqt)
-    F = bf16_from_f32(mode(Vb[0].T, F, 0))
+    if prec == "bf16":
+        rin, rd, Vb = (lambda x: bf16_from_f64(x)), bf16_from_f32, [bf16_from_f64(V) for V in Vs]
+        s, sG = 0, 0
+    else:
+        s = lp_shift(r_nqt)
+        sG = fp16_gscale_exponent(lams, r_nqt.size)
+        rin, rd, Vb = (lambda x: f16_from_f64(x, s)), f16_from_f32, [f16_from_f64(V) for V in Vs]
+    F = rin(r_nqt)
+    F = rd(mode(Vb[0].T, F, 0))
     F = mode(Vb[1].T, F, 1)
     if three_d:
-        F = bf16_from_f32(F)
+        F = rd(F)
         F = mode(Vb[2].T, F, 2)
     la = [np.asarray(l, dtype=np.float32) for l in lams]
     S = (la[0][:, None, None] + la[1][None, :, None]) + la[2][None, None, :]
     with np.errstate(divide="ignore"):
-        F = (F * (np.float32(1.0) / S).astype(np.float32)).astype(np.float32)
+        g = ((np.float32(1.0) / S).astype(np.float32) * np.float32(2.0 ** -sG)).astype(np.float32)
+        F = (F * g).astype(np.float32)
     if singular:
         F[0, 0, 0] = 0.0
-    F = bf16_from_f32(F)
+    F = rd(F)
     if three_d:
-        F = bf16_from_f32(mode(Vb[2], F, 2))
-    F = bf16_from_f32(mode(Vb[1], F, 1))
-    return mode(Vb[0], F, 0)
+        F = rd(mode(Vb[2], F, 2))
+    F = rd(mode(Vb[1], F, 1))
+    return (mode(Vb[0], F, 0) * np.float32(2.0 ** (sG - s))).astype(np.float32)
+
+
+def emulate_bf16_precond(r_nqt, Vs, lams, singular):
+    return emulate_precond(r_nqt, Vs, lams, singular, "bf16")
 
 
 def plan_bases(pl, shape):
@@ -122,11 +155,12 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
 @pytest.mark.parametrize("shape,bcs", CASES)
-def test_precond_bf16_matches_emulation_and_oracle(shape, bcs):
+def test_precond_tc_matches_emulation_and_oracle(shape, bcs, prec):
     nx, ny, nz = shape
     r = synth.random_field(nx, ny, nz, seed=21)
-    pl = _plan(nx, ny, nz, bcs)
+    pl = _plan(nx, ny, nz, bcs, prec)
     rd = _dev(r)
     zd = torch.empty_like(rd)
     pl.precond(rd, zd)
@@ -135,14 +169,15 @@ def test_precond_bf16_matches_emulation_and_oracle(shape, bcs):
     sh = (nx, ny, nz)
     ob = oracle_bcs(bcs, nz)
     Vs, lams = plan_bases(pl, sh)
-    emu = from_oracle(emulate_bf16_precond(to_oracle(r), Vs, lams, o.is_singular(sh, ob)))
+    emu = from_oracle(emulate_precond(to_oracle(r), Vs, lams, o.is_singular(sh, ob), prec))
     e_emu = rel_err(z, emu)
     Vo, _, G = o.pinv_init(sh, ob)
     ref = from_oracle(o.pinv_apply(to_oracle(r), Vo, G))
     e_ref = rel_err(z, ref)
-    print(f"{shape} {bcs}: |z - bf16 emulation| = {e_emu:.2e}, |z - fp64 oracle| = {e_ref:.2e}")
-    assert e_emu <= 4e-3
-    assert e_ref <= 5e-2
+    print(f"{prec} {shape} {bcs}: |z - emulation| = {e_emu:.2e}, |z - fp64 oracle| = {e_ref:.2e}")
+    # one ulp: 2^-8 (BF16), 2^-11 (FP16); summation-order flips are rare
+    assert e_emu <= (4e-3 if prec == "bf16" else 5e-4)
+    assert e_ref <= (5e-2 if prec == "bf16" else 6e-3)
 
 
 SOLVE_CASES = [
@@ -155,11 +190,12 @@ SOLVE_CASES = [
 ]
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
 @pytest.mark.parametrize("shape,bcs", SOLVE_CASES)
-def test_solve_bf16_matches_oracle(shape, bcs):
+def test_solve_tc_matches_oracle(shape, bcs, prec):
     nx, ny, nz = shape
     eta = synth.defect_rhs(nx, ny, nz, bcs, 8, 1.5, seed=22, noise_std=1e-3)
-    pl = _plan(nx, ny, nz, bcs)
+    pl = _plan(nx, ny, nz, bcs, prec)
     ed = _dev(eta)
     ud = torch.zeros_like(ed)
     st, info = pl.solve(ed, ud, tol=1e-10, maxit=60, zero_guess=True)
@@ -169,7 +205,7 @@ def test_solve_bf16_matches_oracle(shape, bcs):
     res = o.pcg(sh, ob, (1, 1, 1), to_oracle(eta), tol=1e-13)
     u = ud.cpu().numpy()
     err = rel_err(u, from_oracle(res.U))
-    print(f"{shape} {bcs}: iters={info['iters']} rel_res_true={info['rel_res_true']:.2e} rel_err={err:.2e}")
+    print(f"{prec} {shape} {bcs}: iters={info['iters']} rel_res_true={info['rel_res_true']:.2e} rel_err={err:.2e}")
     assert err <= 1e-9
     L = o.kron_sum(sh, ob)
     etah = to_oracle(eta) - (to_oracle(eta).mean() if o.is_singular(sh, ob) else 0.0)
@@ -179,10 +215,11 @@ def test_solve_bf16_matches_oracle(shape, bcs):
         assert abs(u.mean()) <= 1e-14 * np.abs(u).max()
 
 
-def test_bf16_solve_deterministic():
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_tc_solve_deterministic(prec):
     nx, ny, nz, bcs = 64, 48, 32, ("P", "P", "N")
     eta = synth.defect_rhs(nx, ny, nz, bcs, 20, 1.5, seed=23)
-    pl = _plan(nx, ny, nz, bcs)
+    pl = _plan(nx, ny, nz, bcs, prec)
     ed = _dev(eta)
     outs = []
     for _ in range(2):
@@ -193,12 +230,13 @@ def test_bf16_solve_deterministic():
     assert np.array_equal(outs[0], outs[1])
 
 
-def test_cuboid_256_bf16_full_size():
-    """256x256x128 P/P/N cuboid (singular), mixed BF16, tol 1e-10, in the bench's launch configuration.
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_cuboid_256_tc_full_size(prec):
+    """256x256x128 P/P/N cuboid (singular), mixed forms, tol 1e-10, in the bench's launch configuration.
     Checked by properties that hold at any size (true residual recomputed on the host with the
     assembled operator, zero mean) and against the oracle's direct pseudoinverse solution."""
     w = synth.workload_cuboid_256(seed=0)
-    pl = _plan(w["nx"], w["ny"], w["nz"], w["bcs"])
+    pl = _plan(w["nx"], w["ny"], w["nz"], w["bcs"], prec)
     ed = _dev(w["eta"])
     ud = torch.zeros_like(ed)
     st, info = pl.solve(ed, ud, tol=1e-10, maxit=60, zero_guess=True)
@@ -208,7 +246,7 @@ def test_cuboid_256_bf16_full_size():
     L = o.kron_sum(sh, w["bcs"])
     etah = o.center(to_oracle(w["eta"]))
     true_res = np.linalg.norm(o.vec(etah) - L @ o.vec(to_oracle(u))) / np.linalg.norm(etah)
-    print(f"256x256x128 bf16: iters={info['iters']} rel_res_true={true_res:.2e}")
+    print(f"256x256x128 {prec}: iters={info['iters']} rel_res_true={true_res:.2e}")
     assert true_res <= 1e-10
     assert abs(u.mean()) <= 1e-14 * np.abs(u).max()
     Vs, _, G = o.pinv_init(sh, w["bcs"])
