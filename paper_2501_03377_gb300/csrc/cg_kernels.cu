@@ -303,6 +303,110 @@ __global__ void __launch_bounds__(TX* TY) k_direction(Geom g, int zchunk, const 
                    [st](const double(&s)[1]) { fin_direction(st, s); });
 }
 
+// ------------------------------------------------------------------ direction, mixed forms
+// Z arrives in FP32.  It enters the stencil as exact fixed point
+// round(Z * 2^k) (int32, |.| < 2^27, k from max|Z| of the preconditioner
+// output), so the second differences are exact integers and
+//     W_s = L P_s = L Z_s + beta_s W_{s-1}        (Algorithm 1, lines 10, 17)
+// needs only two FP64 FMAs per point besides <W, P>.  P_s = Z_s + beta P_{s-1}
+// keeps the constant (null-space) component of Z: L annihilates it, so W and
+// <W, P> are those of the centred Z (Remark orthogonality), rho is corrected by
+// -mean(Z) sum(R), and the resulting constant offset of U is removed at exit.
+template <int NQ, class Field, class Op, class Fin>
+__device__ __forceinline__ void stencil_sweep_int(const Geom& g, int zchunk, const Field& field, Op& op,
+                                                  double* partials, unsigned* ticket, Fin fin) {
+  __shared__ int ring[4][SY][SX];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * TX + tx;
+  const int bx0 = blockIdx.x * TX, by0 = blockIdx.y * TY;
+  const int x = bx0 + tx, y = by0 + ty;
+  const int k0 = blockIdx.z * zchunk;
+  const int k1 = min(g.nz, k0 + zchunk);
+  const bool active = (x < g.nx) && (y < g.ny);
+  const bool has_z = g.nz > 1;
+  const long long plane = (long long)g.nx * g.ny;
+  double acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+
+  auto load_plane = [&](int kk) {
+    const int kz = has_z ? ghost_index(kk, g.nz, g.bc[2]) : kk;
+    int(*dst)[SX] = ring[kk & 3];
+    for (int e = tid; e < SX * SY; e += TX * TY) {
+      const int sx = e % SX, sy = e / SX;
+      const int gx = ghost_index(bx0 + sx - 1, g.nx, g.bc[0]);
+      const int gy = ghost_index(by0 + sy - 1, g.ny, g.bc[1]);
+      int v = 0;
+      if (kz >= 0 && gx >= 0 && gy >= 0) v = field((long long)kz * plane + (long long)gy * g.nx + gx);
+      dst[sy][sx] = v;
+    }
+  };
+
+  if (k0 < k1) {
+    if (has_z) load_plane(k0 - 1);
+    load_plane(k0);
+    for (int k = k0; k < k1; ++k) {
+      if (has_z) load_plane(k + 1);
+      __syncthreads();
+      if (active) {
+        const int(*cur)[SX] = ring[k & 3];
+        const int c = cur[ty + 1][tx + 1];
+        const int dx = 2 * c - cur[ty + 1][tx] - cur[ty + 1][tx + 2];
+        const int dy = 2 * c - cur[ty][tx + 1] - cur[ty + 2][tx + 1];
+        const int dz = has_z ? 2 * c - ring[(k - 1) & 3][ty + 1][tx + 1] - ring[(k + 1) & 3][ty + 1][tx + 1] : 0;
+        op((long long)k * plane + (long long)y * g.nx + x, c, dx, dy, dz, acc);
+      }
+    }
+  }
+  const int nblocks = gridDim.x * gridDim.y * gridDim.z;
+  const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  grid_reduce<NQ>(acc, partials, ticket, nblocks, bid, fin);
+}
+
+struct FieldFixed {
+  const float* __restrict__ z;
+  int k;
+  __device__ __forceinline__ int operator()(long long i) const { return f32_to_fixed(__ldg(z + i), k); }
+};
+
+struct OpDirectionFx {
+  const double* pold;
+  const double* wold;
+  double* p;
+  double* w;
+  double beta, ih0, ih1, ih2;
+  int first, e, uniform;
+  __device__ __forceinline__ void operator()(long long i, int c, int dx, int dy, int dz, double (&acc)[1]) {
+    const double zf = i32_to_f64_scaled(c, e);
+    double lz;
+    if (uniform) {
+      lz = i32_to_f64_scaled(dx + dy + dz, e);
+      if (ih0 != 1.0) lz *= ih0;
+    } else {
+      lz = fma(i32_to_f64_scaled(dx, e), ih0, i32_to_f64_scaled(dy, e) * ih1);
+      if (dz) lz = fma(i32_to_f64_scaled(dz, e), ih2, lz);
+    }
+    const double pv = first ? zf : fma(beta, __ldg(pold + i), zf);
+    const double wv = first ? lz : fma(beta, wold[i], lz);
+    p[i] = pv;
+    w[i] = wv;
+    acc[0] = fma(wv, pv, acc[0]);
+  }
+};
+
+__global__ void __launch_bounds__(TX* TY) k_direction_fx(Geom g, int zchunk, const float* __restrict__ Z,
+                                                         const double* Pold, double* P, double* W, SolveState* st,
+                                                         double* partials) {
+  if (st->done) return;
+  const int k = st->zfx_shift;
+  FieldFixed f{Z, k};
+  const bool has_z = g.nz > 1;
+  const int uniform = (g.ih2[0] == g.ih2[1]) && (!has_z || g.ih2[2] == g.ih2[0]);
+  OpDirectionFx op{Pold, W, P, W, st->beta, g.ih2[0], g.ih2[1], g.ih2[2], st->first, -k, uniform};
+  stencil_sweep_int<1>(g, zchunk, f, op, partials, &st->tickets[kTkDir],
+                       [st](const double(&s)[1]) { fin_direction(st, s); });
+}
+
 // ------------------------------------------------------------------ streaming kernels
 // U += alpha P (line 12), R -= alpha W (line 13), low-precision copy of R,
 // ||R||^2 and sum(R) for the stop test and the centring correction of rho.
@@ -483,8 +587,8 @@ void launch_direction(const tpcg_plan* p, const Geom& g, int k) {
     k_direction<double><<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, (const double*)p->d_Z, pold, pnew,
                                                                     p->d_W, p->d_state, p->d_partials);
   else
-    k_direction<float><<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, (const float*)p->d_Z, pold, pnew,
-                                                                   p->d_W, p->d_state, p->d_partials);
+    k_direction_fx<<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, (const float*)p->d_Z, pold, pnew,
+                                                               p->d_W, p->d_state, p->d_partials);
 }
 void launch_update(const tpcg_plan* p, const Geom& g, double* U, int k) {
   LaunchScope ls(p, kKUpdate);

@@ -255,6 +255,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   double red0 = 0.0;
   float red1 = 0.0f;
+  float zmax = 0.0f;
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
@@ -364,6 +365,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 red0 = fma(rr.x, f32_to_f64_int(v[2 * i]), red0);
                 red0 = fma(rr.y, f32_to_f64_int(v[2 * i + 1]), red0);
                 red1 += v[2 * i] + v[2 * i + 1];
+                zmax = fmaxf(zmax, fmaxf(fabsf(v[2 * i]), fabsf(v[2 * i + 1])));
               }
             }
           } else {
@@ -376,6 +378,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (FINAL) {
                   red0 = fma(__ldg(a.R + o), f32_to_f64_int(v[j]), red0);
                   red1 += v[j];
+                  zmax = fmaxf(zmax, fabsf(v[j]));
                 }
               }
             }
@@ -421,11 +424,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                  : "memory");
   }
   if constexpr (FINAL) {
+    // max |Z| of the block -> one atomicMax (order-independent, so deterministic)
+    __shared__ float smax[kThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) zmax = fmaxf(zmax, __shfl_xor_sync(0xffffffffu, zmax, o));
+    if (lane == 0) smax[warp] = zmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float m = 0.0f;
+      for (int w = 0; w < kThreads / 32; ++w) m = fmaxf(m, smax[w]);
+      atomicMax(&a.st->zmax_bits, __float_as_uint(m));
+    }
     double acc[2] = {red0, (double)red1};
     SolveState* st = a.st;
     const long long N = a.N;
     grid_reduce<2>(acc, a.partials, &st->tickets[kTkPrec], gridDim.x, blockIdx.x,
                    [st, N](const double(&s)[2]) {
+                     st->zfx_shift = fixed_shift_for(atomicExch(&st->zmax_bits, 0u));
                      if (!st->timeout) fin_precond(st, N, s);
                      else {
                        st->status = TPCG_ERR_TIMEOUT;

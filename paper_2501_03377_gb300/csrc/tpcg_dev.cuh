@@ -35,6 +35,8 @@ struct SolveState {
   int singular;
   int precond_applies;
   int timeout;         // a bounded device wait gave up
+  unsigned zmax_bits;  // max |Z| of the current preconditioner output (FP32 bits; atomicMax)
+  int zfx_shift;       // Z enters the stencil as round(Z * 2^zfx_shift), |.| < 2^27
   int lp_shift;        // power-of-two exponent applied when R is next converted to FP16
   int lp_shift_applied;  // exponent the current low-precision copy of R was converted with
   unsigned tickets[8]; // arrival counters of the last-block reductions
@@ -245,6 +247,46 @@ __device__ __forceinline__ int lp_shift_for(double n2, long long N) {
   const double rms = sqrt(n2 / (double)N);
   int s = -ilogb(rms) - 1;
   return s < -120 ? -120 : (s > 120 ? 120 : s);
+}
+
+// round(z * 2^k) as int32 for |z * 2^k| < 2^30 (round-to-nearest-even, integer
+// arithmetic on the bit pattern).  FP32 subnormals map to 0.
+__device__ __forceinline__ int f32_to_fixed(float z, int k) {
+  const uint32_t b = __float_as_uint(z);
+  const int e = (int)((b >> 23) & 0xff);
+  if (e == 0) return 0;
+  const uint32_t m = (b & 0x7fffffu) | 0x800000u;
+  const int sh = e - 150 + k;  // z * 2^k = m * 2^sh
+  uint32_t q;
+  if (sh >= 0) {
+    q = m << sh;
+  } else if (sh < -25) {
+    q = 0;
+  } else {
+    q = m >> -sh;
+    const uint32_t rem = m & ((1u << -sh) - 1u), half = 1u << (-sh - 1);
+    if (rem > half || (rem == half && (q & 1u))) ++q;
+  }
+  return (b >> 31) ? -(int)q : (int)q;
+}
+
+// v * 2^e as FP64 for |v| < 2^31 (exact), built on the bit pattern.
+__device__ __forceinline__ double i32_to_f64_scaled(int v, int e) {
+  if (v == 0) return 0.0;
+  const uint32_t a = v < 0 ? (uint32_t)(-(long long)v) : (uint32_t)v;
+  const int msb = 31 - __clz(a);
+  const unsigned long long mant = ((unsigned long long)a << (52 - msb)) & 0xfffffffffffffull;
+  const unsigned long long bits = ((unsigned long long)(v < 0) << 63) |
+                                  ((unsigned long long)(msb + e + 1023) << 52) | mant;
+  return __longlong_as_double((long long)bits);
+}
+
+// Exponent k with max|Z| * 2^k < 2^27 from the FP32 bit pattern of max|Z|.
+__device__ __forceinline__ int fixed_shift_for(unsigned zmax_bits) {
+  const float zm = __uint_as_float(zmax_bits);
+  if (!(zm > 0.0f) || !isfinite(zm)) return 0;
+  const int k = 26 - ilogbf(zm);
+  return k < -900 ? -900 : (k > 900 ? 900 : k);
 }
 
 // FP32 -> FP64 is exact; done on the bit pattern as well.
