@@ -168,6 +168,14 @@ struct TcArgs {
   int* err;
 };
 
+// FP32 reciprocal, hardware approximation (max error ~1 ulp): far below the
+// FP16/BF16 rounding of the value it scales.
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 template <class OutT>
 __device__ __forceinline__ void store_out(void* out, long long o, float v) {
   if constexpr (std::is_same<OutT, __half>::value)
@@ -342,28 +350,51 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float sab = (a.scale && valid) ? a.lamA[ia] + a.lamB[ib] : 0.0f;
         const bool null_row = a.singular && ia == 0 && ib == 0;
         const float zs = (a.last && a.shift_src) ? ldexpf(1.0f, a.sG - *a.shift_src) : 1.0f;
+        const bool vec = a.vec && valid;
+        // last pass: the residual R of the same 16 outputs is fetched one chunk ahead
+        double2 rnext[8];
+        if (FINAL && vec && h * 16 + 16 <= a.Cout) {
+          const double2* rp = reinterpret_cast<const double2*>(a.R + obase + h * 16);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) rnext[i] = __ldg(rp + i);
+        }
         for (int c0 = h * 16; c0 < a.Np; c0 += 32) {
+          double2 rcur[8];
+          if (FINAL) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) rcur[i] = rnext[i];
+            if (vec && c0 + 48 <= a.Cout) {
+              const double2* rp = reinterpret_cast<const double2*>(a.R + obase + c0 + 32);
+#pragma unroll
+              for (int i = 0; i < 8; ++i) rnext[i] = __ldg(rp + i);
+            }
+          }
           float v[16];
           tc_ld16(tacc + (uint32_t)c0, v);
           if (!valid) continue;
           if (a.scale) {  // Algorithm 7 line 4: multiply by G = 1 / (lam_a + lam_b + lam_c)
+            const float4* lc4 = reinterpret_cast<const float4*>(a.lamC + c0);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] *= __frcp_rn(sab + a.lamC[c0 + j]) * a.gscale;
+            for (int i = 0; i < 4; ++i) {
+              const float4 l = __ldg(lc4 + i);
+              v[4 * i + 0] *= rcp_approx(sab + l.x) * a.gscale;
+              v[4 * i + 1] *= rcp_approx(sab + l.y) * a.gscale;
+              v[4 * i + 2] *= rcp_approx(sab + l.z) * a.gscale;
+              v[4 * i + 3] *= rcp_approx(sab + l.w) * a.gscale;
+            }
             if (null_row && c0 == 0) v[0] = 0.0f;
           }
           if (a.last) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] *= zs;
           }
-          if (a.vec && c0 + 16 <= a.Cout) {
+          if (vec && c0 + 16 <= a.Cout) {
             store16<OutT>(a.out, obase + c0, v);
             if (FINAL) {
-              const double2* rp = reinterpret_cast<const double2*>(a.R + obase + c0);
 #pragma unroll
               for (int i = 0; i < 8; ++i) {
-                const double2 rr = __ldg(rp + i);
-                red0 = fma(rr.x, f32_to_f64_int(v[2 * i]), red0);
-                red0 = fma(rr.y, f32_to_f64_int(v[2 * i + 1]), red0);
+                red0 = fma(rcur[i].x, f32_to_f64_int(v[2 * i]), red0);
+                red0 = fma(rcur[i].y, f32_to_f64_int(v[2 * i + 1]), red0);
                 red1 += v[2 * i] + v[2 * i + 1];
                 zmax = fmaxf(zmax, fmaxf(fabsf(v[2 * i]), fabsf(v[2 * i + 1])));
               }
