@@ -178,6 +178,30 @@ int tpcg_profile_begin(tpcg_plan* plan);
  * (kinds with at least one launch) and their count to *n_stats.            */
 int tpcg_profile_end(tpcg_plan* plan, tpcg_kernel_stat* stats, int max_stats, int* n_stats);
 
+/* ---- allocation-free residual check ----------------------------------------
+ * No counterpart in the paper.  For callers that must not allocate device
+ * memory at the time they check a solution: work recorded while a stream is
+ * being captured into a CUDA graph, time-stepping loops that cannot afford the
+ * device synchronisation cudaMalloc/cudaFree may cause, or applications that
+ * hand this library a fixed budget at start-up.  No plan is needed and nothing
+ * is allocated (no cudaMalloc, no cudaFree, no allocating library call).
+ *
+ * Writes, on `stream`, out[0] = ||eta_hat - L ups||_2, out[1] = ||eta_hat||_2
+ * and out[2] = the mean removed from eta (0 unless every present axis is P or
+ * N), where L is the operator tpcg_plan_create(nx, ny, nz, bc, h, ...) would
+ * build and eta_hat = eta - out[2].  eta, ups: device pointers of nz*ny*nx
+ * doubles (layout as above); out: device pointer of 3 doubles.  Enqueues only.
+ * Scratch: a static device array of the library (about 33 KB per GPU that
+ * loads it, held until the process exits) for the partial sums of at most
+ * 2048 reduction blocks.  Grids of more than 2^31 - 1 points are rejected with
+ * TPCG_ERR_UNSUPPORTED.  The first call on a device looks the array's address
+ * up (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call uses the same array: calls that may run concurrently on the GPU
+ * (different streams, no ordering between them) race and must not be issued.
+ * Each call clears the array's arrival counters before use.               */
+int tpcg_residual_norms_noalloc(int nx, int ny, int nz, const int bc[3], const double h[3], const double* eta,
+                                const double* ups, double* out, void* stream);
+
 /* Human-readable name of a status code (static string, never NULL).        */
 const char* tpcg_strerror(int status);
 

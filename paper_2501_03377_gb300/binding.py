@@ -72,6 +72,7 @@ _SIGS = {
     "tpcg_plan_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "tpcg_profile_begin": (_I, [_P]),
     "tpcg_profile_end": (_I, [_P, ctypes.POINTER(tpcg_kernel_stat), _I, ctypes.POINTER(_I)]),
+    "tpcg_residual_norms_noalloc": (_I, [_I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _P, _P, _P, _P]),
     "tpcg_strerror": (ctypes.c_char_p, [_I]),
 }
 _lib = None
@@ -176,6 +177,13 @@ def tpcg_profile_end(plan, max_stats=16):
     st = lib().tpcg_profile_end(plan, arr, max_stats, ctypes.byref(n))
     out = {arr[i].name.decode(): {"launches": arr[i].launches, "total_ms": arr[i].total_ms} for i in range(n.value)}
     return st, out
+
+
+def tpcg_residual_norms_noalloc(nx, ny, nz, bc, h, eta_ptr, ups_ptr, out_ptr, stream):
+    bc_arr = (_I * 3)(*[BC[b] if isinstance(b, str) else int(b) for b in bc])
+    h_arr = (_D * 3)(*[float(v) for v in h])
+    return lib().tpcg_residual_norms_noalloc(int(nx), int(ny), int(nz), bc_arr, h_arr, _P(eta_ptr), _P(ups_ptr),
+                                             _P(out_ptr), _P(stream))
 
 
 # ---------------------------------------------------------------------------

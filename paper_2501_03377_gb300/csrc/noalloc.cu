@@ -1,0 +1,152 @@
+// tpcg_residual_norms_noalloc: FP64 residual of a candidate solution without a
+// plan and without any device allocation.
+//
+// Who needs it: code that must not call cudaMalloc at the moment it checks a
+// solution -- for example work issued while a stream is being captured into a
+// CUDA graph, a time-stepping loop that cannot afford the implicit device
+// synchronisation cudaMalloc/cudaFree may cause, or a host application that
+// gives this library a fixed device budget at start-up.  Everything else in
+// this library allocates its scratch when a plan is created; this entry point
+// instead keeps its scratch (the per-block partial sums of two reductions and
+// their arrival counters) in one file-scope __device__ array.
+//
+// It is a variant of the true-residual kernel of the PCG driver (stencil of
+// eq. ourproblem plus a deterministic two-stage reduction): same arithmetic,
+// one grid point per thread with direct neighbour loads instead of the
+// shared-memory plane ring, and no residual vector is written.
+#include <mutex>
+
+#include "tpcg_dev.cuh"
+
+namespace tpcg {
+namespace {
+
+constexpr int kNaMaxBlocks = 2048;  // reduction blocks the static scratch can hold
+
+struct NoAllocScratch {
+  double partials[kNaMaxBlocks * 2];  // per-block partial sums
+  unsigned tickets[2];                // arrival counters of the two reductions (must start at 0)
+  double mean;                        // mean of eta removed for singular operators
+};
+
+// Shared by every call on a device; holds the last call's contents.  Every GPU
+// that loads the library keeps this array (about 33 KB) until the process exits.
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+constexpr int kMaxDevices = 64;
+NoAllocScratch* g_scratch_addr[kMaxDevices] = {};
+std::mutex g_scratch_mutex;
+
+// Device address of the static scratch for the current device (looked up once
+// per device; cudaGetSymbolAddress allocates nothing).
+int scratch_for_current_device(NoAllocScratch** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TPCG_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return TPCG_ERR_CUDA;
+    }
+    g_scratch_addr[dev] = reinterpret_cast<NoAllocScratch*>(p);
+  }
+  *out = g_scratch_addr[dev];
+  return TPCG_OK;
+}
+
+__device__ __forceinline__ int na_ghost(int g, int n, int bc) {
+  if (g >= 0 && g < n) return g;
+  if (g == -1) return bc == kBcP ? n - 1 : ((bc == kBcN || bc == kBcND) ? 0 : -1);
+  if (g == n) return bc == kBcP ? 0 : ((bc == kBcN || bc == kBcDN) ? n - 1 : -1);
+  return -1;
+}
+
+__global__ void __launch_bounds__(256) k_na_eta_sum(long long N, const double* __restrict__ eta,
+                                                    NoAllocScratch* s, int singular) {
+  double acc[1] = {0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    acc[0] += __ldg(eta + i);
+  grid_reduce<1>(acc, s->partials, &s->tickets[0], gridDim.x, blockIdx.x,
+                 [s, N, singular](const double(&v)[1]) { s->mean = singular ? v[0] / (double)N : 0.0; });
+}
+
+// out[0] = ||eta_hat - L ups||_2, out[1] = ||eta_hat||_2, out[2] = removed mean.
+__global__ void __launch_bounds__(256) k_na_residual(Geom g, const double* __restrict__ eta,
+                                                     const double* __restrict__ ups, NoAllocScratch* s,
+                                                     double* out) {
+  const double mean = s->mean;
+  const long long plane = (long long)g.nx * g.ny;
+  const bool has_z = g.nz > 1;
+  double acc[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N; i += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(i / plane);
+    const long long rem = i - (long long)k * plane;
+    const int y = (int)(rem / g.nx), x = (int)(rem - (long long)y * g.nx);
+    const double c = __ldg(ups + i);
+    auto at = [&](int xx, int yy, int kk) {
+      return (xx < 0 || yy < 0 || kk < 0) ? 0.0 : __ldg(ups + (long long)kk * plane + (long long)yy * g.nx + xx);
+    };
+    const int xl = na_ghost(x - 1, g.nx, g.bc[0]), xr = na_ghost(x + 1, g.nx, g.bc[0]);
+    const int yl = na_ghost(y - 1, g.ny, g.bc[1]), yr = na_ghost(y + 1, g.ny, g.bc[1]);
+    double w = fma(2.0, c, -(at(xl, y, k) + at(xr, y, k))) * g.ih2[0] +
+               fma(2.0, c, -(at(x, yl, k) + at(x, yr, k))) * g.ih2[1];
+    if (has_z) {
+      const int kl = na_ghost(k - 1, g.nz, g.bc[2]), kr = na_ghost(k + 1, g.nz, g.bc[2]);
+      w = fma(fma(2.0, c, -(at(x, y, kl) + at(x, y, kr))), g.ih2[2], w);
+    }
+    const double e = __ldg(eta + i) - mean;
+    const double r = e - w;
+    acc[0] = fma(r, r, acc[0]);
+    acc[1] = fma(e, e, acc[1]);
+  }
+  grid_reduce<2>(acc, s->partials, &s->tickets[1], gridDim.x, blockIdx.x, [s, out](const double(&v)[2]) {
+    out[0] = sqrt(v[0]);
+    out[1] = sqrt(v[1]);
+    out[2] = s->mean;
+  });
+}
+
+}  // namespace
+}  // namespace tpcg
+
+using namespace tpcg;
+
+extern "C" int tpcg_residual_norms_noalloc(int nx, int ny, int nz, const int bc[3], const double h[3],
+                                           const double* eta, const double* ups, double* out, void* stream) {
+  if (!bc || !h || !eta || !ups || !out) return TPCG_ERR_INVALID_ARG;
+  if (nx < 3 || ny < 3 || !(nz == 1 || nz >= 3)) return TPCG_ERR_INVALID_ARG;
+  const int naxes = (nz == 1) ? 2 : 3;
+  for (int m = 0; m < naxes; ++m) {
+    if (bc[m] < 0 || bc[m] > 4) return TPCG_ERR_INVALID_ARG;
+    if (!(h[m] > 0.0) || !(h[m] < 1e300)) return TPCG_ERR_INVALID_ARG;
+  }
+  const long long N = (long long)nx * ny * nz;
+  if (N > 2147483647LL) return TPCG_ERR_UNSUPPORTED;  // beyond the supported grid size
+  NoAllocScratch* s = nullptr;
+  int rc = scratch_for_current_device(&s);
+  if (rc) return rc;
+  Geom g{};
+  g.nx = nx;
+  g.ny = ny;
+  g.nz = nz;
+  bool singular = true;
+  for (int m = 0; m < 3; ++m) {
+    g.bc[m] = (m < naxes) ? bc[m] : kBcN;
+    g.ih2[m] = (m < naxes) ? 1.0 / (h[m] * h[m]) : 0.0;
+    if (m < naxes && !(bc[m] == kBcP || bc[m] == kBcN)) singular = false;
+  }
+  g.N = N;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long want = (N + 255) / 256;
+  const int blocks = (int)std::min<long long>(std::min<long long>(want, (long long)sms * 8), kNaMaxBlocks);
+  cudaStream_t st = (cudaStream_t)stream;
+  // the arrival counters must start at zero; an aborted earlier call may have left them set
+  if (cudaMemsetAsync(s->tickets, 0, sizeof(s->tickets), st) != cudaSuccess) return TPCG_ERR_CUDA;
+  k_na_eta_sum<<<blocks, 256, 0, st>>>(N, eta, s, singular ? 1 : 0);
+  k_na_residual<<<blocks, 256, 0, st>>>(g, eta, ups, s, out);
+  if (cudaGetLastError() != cudaSuccess) return TPCG_ERR_CUDA;
+  return TPCG_OK;
+}
