@@ -134,6 +134,22 @@ int tpcg_solve(tpcg_plan* plan, const double* eta, double* ups, double tol, int 
 int tpcg_solve_host(tpcg_plan* plan, const double* eta_host, double* ups_host, double tol, int maxit,
                     unsigned flags, tpcg_info* info);
 
+/* Many independent solves in one call (the batched form of tpcg_solve).
+ * Solve s uses plans[s] and has nrhs[s] right-hand sides (nrhs == NULL: one
+ * each) stored back to back: right-hand side r is eta[s] + r*N_s and its
+ * solution ups[s] + r*N_s, N_s = nx*ny*nz of plans[s] (device pointers).
+ * tol[s] is the tolerance of solve s (tol == NULL: 1e-10); maxit and flags
+ * apply to every solve.  infos (host, may be NULL) receives one tpcg_info per
+ * right-hand side, in order.  The right-hand sides of one plan are solved one
+ * after another (a plan's workspace serves one solve at a time; a plan may
+ * appear more than once); different plans advance concurrently, one host
+ * thread driving all of them, so plans created on distinct streams overlap
+ * on the GPU.  Each result equals the result of tpcg_solve on the same input.
+ * Returns TPCG_OK if every solve succeeded, else the first failing status
+ * (per-solve statuses are in infos), or an argument/CUDA error.            */
+int tpcg_solve_batched(tpcg_plan* const* plans, int nsolves, const int* nrhs, const double* const* eta,
+                       double* const* ups, const double* tol, int maxit, unsigned flags, tpcg_info* infos);
+
 /* z = M(r): one application of the preconditioner of Algorithm 7 in the
  * plan's precision form, without centring.  r, z: device pointers of
  * nz*ny*nx doubles (may not alias).  Enqueues only.                        */

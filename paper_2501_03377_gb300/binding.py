@@ -65,6 +65,8 @@ _SIGS = {
     "tpcg_plan_device_bytes": (_I, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     "tpcg_solve": (_I, [_P, _P, _P, _D, _I, ctypes.c_uint, ctypes.POINTER(tpcg_info)]),
     "tpcg_solve_host": (_I, [_P, _P, _P, _D, _I, ctypes.c_uint, ctypes.POINTER(tpcg_info)]),
+    "tpcg_solve_batched": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_I), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                ctypes.POINTER(_D), _I, ctypes.c_uint, ctypes.POINTER(tpcg_info)]),
     "tpcg_precond_apply": (_I, [_P, _P, _P]),
     "tpcg_apply_laplacian": (_I, [_P, _P, _P]),
     "tpcg_rhs_add_bc": (_I, [_P, _P, ctypes.POINTER(_D)]),
@@ -139,6 +141,15 @@ def tpcg_solve_host(plan, eta_ptr, ups_ptr, tol, maxit, flags):
     info = tpcg_info()
     st = lib().tpcg_solve_host(plan, _P(eta_ptr), _P(ups_ptr), float(tol), int(maxit), int(flags), ctypes.byref(info))
     return st, info
+
+
+def tpcg_solve_batched(plans, nrhs, eta_ptrs, ups_ptrs, tols, maxit, flags):
+    n = len(plans)
+    total = sum(nrhs)
+    infos = (tpcg_info * max(1, total))()
+    st = lib().tpcg_solve_batched((_P * n)(*plans), n, (_I * n)(*nrhs), (_P * n)(*eta_ptrs), (_P * n)(*ups_ptrs),
+                                  (_D * n)(*tols), int(maxit), int(flags), infos)
+    return st, [infos[i].as_dict() for i in range(total)]
 
 
 def tpcg_precond_apply(plan, r_ptr, z_ptr):

@@ -7,7 +7,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <chrono>
 #include <new>
+#include <thread>
 
 #include "tpcg_dev.cuh"
 
@@ -154,6 +156,7 @@ void free_plan(tpcg_plan* p) {
   cudaFree(p->d_partials);
   cudaFree(p->d_err);
   if (p->h_state) cudaFreeHost(p->h_state);
+  if (p->ev_state) cudaEventDestroy(p->ev_state);
   for (cudaEvent_t e : p->prof.pool) cudaEventDestroy(e);
   delete p;
 }
@@ -216,15 +219,41 @@ int last_cuda_error() {
   return TPCG_OK;
 }
 
-int solve_impl(tpcg_plan* p, const double* eta, double* ups, double tol, int maxit, unsigned flags, tpcg_info* info) {
-  if (!p || !eta || !ups) return TPCG_ERR_INVALID_ARG;
-  if (!(tol > 0.0) || !(tol < 1.0) || maxit < 1) return TPCG_ERR_INVALID_ARG;
+int enqueue_state_readback(tpcg_plan* p) {
+  if (cudaMemcpyAsync(p->h_state, p->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess)
+    return TPCG_ERR_CUDA;
+  if (cudaEventRecord(p->ev_state, p->stream) != cudaSuccess) return TPCG_ERR_CUDA;
+  return last_cuda_error();
+}
+
+// lines 8-18: `count` iterations; kernels of iterations after convergence return at once
+int enqueue_iterations(SolveJob& j, int count) {
+  tpcg_plan* p = j.p;
   const Geom g = make_geom(p);
-  const bool zero_guess = (flags & TPCG_ZERO_GUESS) != 0;
+  for (int c = 0; c < count; ++c) {
+    const int k = j.issued + c;                         // P_k is written to d_P[k & 1], P_{k-1} read from the other
+    launch_direction(p, g, k);                          // lines 10-11 (P from line 17 of the previous pass)
+    launch_update(p, g, j.ups, k);                      // lines 12-13
+    launch_true_residual(p, g, j.eta, j.ups, false);    // stop test
+    const int rc = run_precond(p, p->d_R, p->d_Z, p->d_state);  // lines 14-16
+    if (rc) return rc;
+  }
+  j.issued += count;
+  return TPCG_OK;
+}
+
+}  // namespace
+
+int job_start(SolveJob& j) {
+  tpcg_plan* p = j.p;
+  if (!p || !j.eta || !j.ups) return TPCG_ERR_INVALID_ARG;
+  if (!(j.tol > 0.0) || !(j.tol < 1.0) || j.maxit < 1) return TPCG_ERR_INVALID_ARG;
+  const Geom g = make_geom(p);
+  const bool zero_guess = (j.flags & TPCG_ZERO_GUESS) != 0;
   SolveState* hs = p->h_state;
   std::memset(hs, 0, sizeof(SolveState));
-  hs->maxit = maxit;
-  hs->tol2 = tol * tol;
+  hs->maxit = j.maxit;
+  hs->tol2 = j.tol * j.tol;
   hs->first = 1;
   hs->zero_guess = zero_guess ? 1 : 0;
   hs->singular = p->singular ? 1 : 0;
@@ -232,62 +261,82 @@ int solve_impl(tpcg_plan* p, const double* eta, double* ups, double tol, int max
   if (cudaMemcpyAsync(p->d_state, hs, sizeof(SolveState), cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
     return TPCG_ERR_CUDA;
   // Algorithm 1, lines 2-7 (eq. centering first when singular)
-  launch_eta_sum(p, g, eta);  // mean (singular operators) and the first low-precision exponent
-  launch_init_residual(p, g, eta, ups, zero_guess);
+  launch_eta_sum(p, g, j.eta);  // mean (singular operators) and the first low-precision exponent
+  launch_init_residual(p, g, j.eta, j.ups, zero_guess);
   if (p->lp_kind == 2 && !zero_guess) launch_to_lp(p, g, p->d_R);  // re-scale FP16 copy to the actual R_0
   int rc = run_precond(p, p->d_R, p->d_Z, p->d_state);
   if (rc) return rc;
-  if ((rc = last_cuda_error())) return rc;
-  // lines 8-18, in chunks of iterations between host reads of the state
-  int issued = 0;
-  int chunk = (p->prec == TPCG_FP64) ? 2 : 4;
-  for (;;) {
-    if (cudaMemcpyAsync(hs, p->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess)
-      return TPCG_ERR_CUDA;
-    if (cudaStreamSynchronize(p->stream) != cudaSuccess) return last_cuda_error() ? TPCG_ERR_CUDA : TPCG_ERR_CUDA;
-    if (hs->done || issued > maxit + 1) break;
-    for (int c = 0; c < chunk; ++c) {
-      const int k = issued + c;                            // P_k is written to d_P[k & 1], P_{k-1} read from the other
-      launch_direction(p, g, k);                           // lines 10-11 (P from line 17 of the previous pass)
-      launch_update(p, g, ups, k);                         // lines 12-13
-      launch_true_residual(p, g, eta, ups, false);         // stop test
-      if ((rc = run_precond(p, p->d_R, p->d_Z, p->d_state))) return rc;  // lines 14-16
+  j.issued = 0;
+  j.chunk = (p->prec == TPCG_FP64) ? 2 : 4;
+  if ((rc = enqueue_iterations(j, j.chunk))) return rc;
+  j.chunk = (p->prec == TPCG_FP64) ? 1 : 2;
+  j.phase = 1;
+  return enqueue_state_readback(p);
+}
+
+bool job_ready(const SolveJob& j) { return cudaEventQuery(j.p->ev_state) != cudaErrorNotReady; }
+
+int job_step(SolveJob& j) {
+  tpcg_plan* p = j.p;
+  SolveState* hs = p->h_state;
+  if (cudaEventSynchronize(p->ev_state) != cudaSuccess) return last_cuda_error() ? TPCG_ERR_CUDA : TPCG_ERR_CUDA;
+  if (j.phase == 1) {
+    if (!hs->done && j.issued <= j.maxit + 1) {
+      int rc = enqueue_iterations(j, j.chunk);
+      if (rc) return rc;
+      return enqueue_state_readback(p);
     }
-    issued += chunk;
-    chunk = (p->prec == TPCG_FP64) ? 1 : 2;
-    if ((rc = last_cuda_error())) return rc;
-  }
-  if (hs->done == 2) {
-    launch_zero(p, g.N, ups);  // eta_hat = 0: minimum-norm solution is 0
-  } else {
-    if (!hs->done || hs->status == TPCG_ERR_BREAKDOWN) {
-      launch_true_residual(p, g, eta, ups, true);  // report the true residual of the returned iterate
-      if (!hs->done) hs->status = TPCG_ERR_NOT_CONVERGED;
+    const Geom g = make_geom(p);
+    j.status_host = hs->status;
+    j.done_host = hs->done;
+    if (hs->done == 2) {
+      launch_zero(p, g.N, j.ups);  // eta_hat = 0: minimum-norm solution is 0
+    } else {
+      if (!hs->done || hs->status == TPCG_ERR_BREAKDOWN) {
+        launch_true_residual(p, g, j.eta, j.ups, true);  // report the true residual of the returned iterate
+        if (!hs->done) j.status_host = TPCG_ERR_NOT_CONVERGED;
+      }
+      if (p->singular) launch_center_u(p, g, j.ups);
     }
-    if (p->singular) launch_center_u(p, g, ups);
+    j.phase = 2;
+    return enqueue_state_readback(p);
   }
-  const int status_host = hs->status;
-  const int done_host = hs->done;
-  if (cudaMemcpyAsync(hs, p->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, p->stream) != cudaSuccess)
-    return TPCG_ERR_CUDA;
-  if (cudaStreamSynchronize(p->stream) != cudaSuccess) return TPCG_ERR_CUDA;
-  if ((rc = last_cuda_error())) return rc;
-  int status = hs->status;
-  if (!done_host) status = status_host;
-  if (hs->timeout) status = TPCG_ERR_TIMEOUT;
-  if (info) {
-    info->status = status;
-    info->iters = hs->iter;
-    info->precond_applies = hs->precond_applies;
-    info->prec = p->prec;
+  if (j.phase == 2) {
+    int status = hs->status;
+    if (!j.done_host) status = j.status_host;
+    if (hs->timeout) status = TPCG_ERR_TIMEOUT;
+    tpcg_info& info = j.info;
+    info.status = status;
+    info.iters = hs->iter;
+    info.precond_applies = hs->precond_applies;
+    info.prec = p->prec;
     const double en = sqrt(hs->eta_norm2);
-    info->eta_norm = en;
-    info->rel_res_true = (done_host == 2 || en == 0.0) ? 0.0 : sqrt(hs->true_rr) / en;
-    info->rel_res_recur = (en == 0.0) ? 0.0 : sqrt(hs->rr) / en;
-    info->removed_mean = p->singular ? hs->mean_eta : 0.0;
-    info->null_component = (p->singular && done_host != 2) ? hs->sumU / (double)p->N : 0.0;
+    info.eta_norm = en;
+    info.rel_res_true = (j.done_host == 2 || en == 0.0) ? 0.0 : sqrt(hs->true_rr) / en;
+    info.rel_res_recur = (en == 0.0) ? 0.0 : sqrt(hs->rr) / en;
+    info.removed_mean = p->singular ? hs->mean_eta : 0.0;
+    info.null_component = (p->singular && j.done_host != 2) ? hs->sumU / (double)p->N : 0.0;
+    j.status = status;
+    j.phase = 3;
   }
-  return status;
+  return TPCG_OK;
+}
+
+namespace {
+
+int solve_impl(tpcg_plan* p, const double* eta, double* ups, double tol, int maxit, unsigned flags, tpcg_info* info) {
+  SolveJob j;
+  j.p = p;
+  j.eta = eta;
+  j.ups = ups;
+  j.tol = tol;
+  j.maxit = maxit;
+  j.flags = flags;
+  int rc = job_start(j);
+  while (!rc && j.phase != 3) rc = job_step(j);
+  if (rc) return rc;
+  if (info) *info = j.info;
+  return j.status;
 }
 
 }  // namespace
@@ -426,6 +475,7 @@ int tpcg_plan_create(int nx, int ny, int nz, const int bc[3], const double h[3],
   if (!rc) rc = dalloc(p, &p->d_partials, p->partial_slots);
   if (!rc) rc = dalloc(p, &p->d_err, 4);
   if (!rc && cudaMallocHost((void**)&p->h_state, sizeof(SolveState)) != cudaSuccess) rc = TPCG_ERR_OOM;
+  if (!rc && cudaEventCreateWithFlags(&p->ev_state, cudaEventDisableTiming) != cudaSuccess) rc = TPCG_ERR_CUDA;
   if (!rc) {
     cudaMemset(p->d_state, 0, sizeof(SolveState));
     cudaMemset(p->d_err, 0, 16);
@@ -481,6 +531,94 @@ int tpcg_solve(tpcg_plan* plan, const double* eta, double* ups, double tol, int 
   const int rc = solve_impl(plan, eta, ups, tol, maxit, flags, info);
   if (info && rc != info->status) info->status = rc;
   return rc;
+}
+
+int tpcg_solve_batched(tpcg_plan* const* plans, int nsolves, const int* nrhs, const double* const* eta,
+                       double* const* ups, const double* tol, int maxit, unsigned flags, tpcg_info* infos) {
+  if (nsolves < 0 || (nsolves > 0 && (!plans || !eta || !ups))) return TPCG_ERR_INVALID_ARG;
+  if (nsolves == 0) return TPCG_OK;
+  for (int s = 0; s < nsolves; ++s) {
+    if (!plans[s] || !eta[s] || !ups[s]) return TPCG_ERR_INVALID_ARG;
+    if (nrhs && nrhs[s] < 0) return TPCG_ERR_INVALID_ARG;
+    if (tol && !(tol[s] > 0.0 && tol[s] < 1.0)) return TPCG_ERR_INVALID_ARG;
+  }
+  if (maxit < 1) return TPCG_ERR_INVALID_ARG;
+  DeviceGuard dg(plans[0]->device);
+  // one queue per distinct plan (a plan's workspace serves one solve at a time);
+  // queues of different plans advance concurrently on the plans' streams
+  struct Item {
+    const double* eta;
+    double* ups;
+    double tol;
+    int info_index;
+  };
+  std::vector<tpcg_plan*> qplan;
+  std::vector<std::vector<Item>> queue;
+  int index = 0;
+  for (int s = 0; s < nsolves; ++s) {
+    size_t q = 0;
+    while (q < qplan.size() && qplan[q] != plans[s]) ++q;
+    if (q == qplan.size()) {
+      qplan.push_back(plans[s]);
+      queue.emplace_back();
+    }
+    const int nr = nrhs ? nrhs[s] : 1;
+    for (int r = 0; r < nr; ++r) {
+      const size_t off = (size_t)r * (size_t)plans[s]->N;
+      queue[q].push_back(Item{eta[s] + off, ups[s] + off, tol ? tol[s] : 1e-10, index++});
+    }
+  }
+  std::vector<SolveJob> job(qplan.size());
+  std::vector<size_t> next(qplan.size(), 0);
+  int first_bad = TPCG_OK;
+  auto start_next = [&](size_t q) -> int {
+    while (next[q] < queue[q].size()) {
+      const Item& it = queue[q][next[q]];
+      SolveJob j;
+      j.p = qplan[q];
+      j.eta = it.eta;
+      j.ups = it.ups;
+      j.tol = it.tol;
+      j.maxit = maxit;
+      j.flags = flags;
+      job[q] = j;
+      const int rc = job_start(job[q]);
+      if (!rc) return TPCG_OK;
+      if (rc == TPCG_ERR_CUDA) return rc;
+      if (infos) {
+        std::memset(&infos[it.info_index], 0, sizeof(tpcg_info));
+        infos[it.info_index].status = rc;
+      }
+      if (first_bad == TPCG_OK) first_bad = rc;
+      ++next[q];
+    }
+    job[q].phase = -1;  // queue exhausted
+    return TPCG_OK;
+  };
+  int rc = TPCG_OK;
+  for (size_t q = 0; q < qplan.size() && !rc; ++q) rc = start_next(q);
+  size_t active = qplan.size();
+  while (!rc && active > 0) {
+    active = 0;
+    bool progressed = false;
+    for (size_t q = 0; q < qplan.size() && !rc; ++q) {
+      if (job[q].phase == -1) continue;
+      ++active;
+      if (!job_ready(job[q])) continue;
+      progressed = true;
+      if ((rc = job_step(job[q]))) break;
+      if (job[q].phase == 3) {
+        const Item& it = queue[q][next[q]];
+        if (infos) infos[it.info_index] = job[q].info;
+        if (job[q].status != TPCG_OK && first_bad == TPCG_OK) first_bad = job[q].status;
+        ++next[q];
+        rc = start_next(q);
+      }
+    }
+    if (!progressed && active > 0) std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+  if (rc) return rc;
+  return first_bad;
 }
 
 int tpcg_solve_host(tpcg_plan* plan, const double* eta_host, double* ups_host, double tol, int maxit, unsigned flags,

@@ -68,6 +68,28 @@ struct Profiler {
   unsigned long long timed[kKindCount] = {};
 };
 
+// One PCG solve driven as a resumable job: job_start() enqueues the set-up
+// (Algorithm 1, lines 2-7) and the first chunk of iterations; whenever the
+// plan's state event has completed, job_step() inspects the device state and
+// enqueues the next chunk or the exit work.  Many jobs on different plans (and
+// streams) can be driven by one host thread.
+struct SolveJob {
+  tpcg_plan* p = nullptr;
+  const double* eta = nullptr;
+  double* ups = nullptr;
+  double tol = 1e-10;
+  int maxit = 100;
+  unsigned flags = 0;
+  int issued = 0, chunk = 0;
+  int phase = 0;  // 0 not started, 1 iterating, 2 finishing, 3 finished
+  int done_host = 0, status_host = 0;
+  int status = 0;
+  tpcg_info info{};
+};
+int job_start(SolveJob& j);
+bool job_ready(const SolveJob& j);
+int job_step(SolveJob& j);
+
 }  // namespace tpcg
 
 struct tpcg_plan {
@@ -103,6 +125,7 @@ struct tpcg_plan {
   double* d_ups_h = nullptr;
   tpcg::SolveState* d_state = nullptr;
   tpcg::SolveState* h_state = nullptr;  // pinned
+  cudaEvent_t ev_state = nullptr;        // recorded after each read-back of the device state
   double* d_partials = nullptr;
   size_t partial_slots = 0;
   int* d_err = nullptr;   // device error word of bounded waits
