@@ -50,6 +50,10 @@ extern "C" {
 #define TPCG_ERR_TIMEOUT        6  /* a bounded device-side wait gave up */
 #define TPCG_ERR_UNSUPPORTED    7  /* valid request this build cannot serve (e.g. axis > 256 for tensor-core forms) */
 #define TPCG_ERR_EIGENBASIS     8  /* closed-form eigenbasis failed its accuracy check */
+#define TPCG_ERR_ADMISSION      9  /* server: the request can never fit the device-memory budget */
+#define TPCG_PENDING           10  /* server: the request has not finished yet */
+#define TPCG_ERR_UNKNOWN_TICKET 11 /* server: no such (unreleased) request */
+#define TPCG_ERR_CANCELLED     12  /* server: request still queued when the server was destroyed */
 
 /* ---- boundary conditions per axis (list under eq. lap1d, Sec. 3.1) ---- */
 #define TPCG_BC_P   0  /* periodic:          (alpha, beta, gamma) = (2, 2, -1) */
@@ -174,6 +178,56 @@ int tpcg_rhs_add_bc(tpcg_plan* plan, double* eta, const double bval[6]);
  * the eigenvector of lam[k] (eq. eig-svd-decomp).  ell is the axis length
  * (1 for the absent z axis of a 2D plan: lam = {0}, V = {1}).              */
 int tpcg_plan_eigenpairs(const tpcg_plan* plan, int axis, double* lam, double* V);
+
+/* ---- serving: continuous batching of independent solves -------------------
+ * A domain-structure simulation issues a Poisson solve every time step (the
+ * motivation of Sec. 1 and Sec. 6).  A server owns one worker thread on the
+ * device that was current at tpcg_server_create.  Requests wait in arrival
+ * order and are admitted as soon as a slot (at most max_slots solves run at
+ * once) and device memory are free; each admitted solve runs on its own plan
+ * and CUDA stream, so solves of different sizes overlap on the GPU while new
+ * requests keep arriving.  Plans are cached by (grid, BCs, spacing,
+ * precision) and evicted least-recently-used when idle and memory is needed.
+ * A request with session != 0 starts from the previous solution of that
+ * session (warm start), which stays on the device; the requests of one
+ * session run in submission order, so every result equals the result the
+ * same sequence of requests gives when run alone.                           */
+typedef struct tpcg_server tpcg_server;
+
+typedef struct {
+  int nx, ny, nz;                /* grid; nz == 1: 2D                                     */
+  int bc[3];                     /* TPCG_BC_* per axis                                    */
+  double h[3];                   /* spacings                                              */
+  int prec;                      /* TPCG_FP64 / TPCG_MIXED_*                              */
+  unsigned long long session;    /* 0: start from zero; else warm start within the session */
+  const double* eta;             /* HOST pointer, nz*ny*nx doubles, copied by submit      */
+  double tol;                    /* relative residual tolerance, (0, 1)                   */
+  int maxit;                     /* >= 1                                                  */
+} tpcg_request;
+
+typedef struct {
+  unsigned long long submitted, completed, failed, rejected;
+  int queued, running;
+  size_t device_bytes;           /* plans, session solutions and buffers now held         */
+  double p50_ms, p99_ms, mean_ms; /* submit -> result-on-host latency of finished requests */
+  double elapsed_s;              /* since the first submit                                */
+} tpcg_server_stats;
+
+/* hbm_budget: device bytes the server may hold (0: 90% of the free memory). */
+int tpcg_server_create(size_t hbm_budget, int max_slots, tpcg_server** out);
+/* Queue a request (eta is copied before the call returns); *ticket names it. */
+int tpcg_server_submit(tpcg_server* server, const tpcg_request* req, unsigned long long* ticket);
+/* Non-blocking: TPCG_PENDING, or the request's final status; the result
+ * (ups_out: host, nz*ny*nx doubles, may be NULL; info may be NULL) is handed
+ * out once and the ticket released.  TPCG_ERR_ADMISSION: the request alone
+ * exceeds the budget.                                                        */
+int tpcg_server_poll(tpcg_server* server, unsigned long long ticket, double* ups_out, tpcg_info* info);
+/* As poll, blocking up to timeout_s seconds (< 0: no limit).                */
+int tpcg_server_wait(tpcg_server* server, unsigned long long ticket, double timeout_s, double* ups_out,
+                     tpcg_info* info);
+int tpcg_server_get_stats(tpcg_server* server, tpcg_server_stats* stats);
+/* Lets running requests finish, cancels queued ones, releases everything.  */
+int tpcg_server_destroy(tpcg_server* server);
 
 /* ---- instrumentation ------------------------------------------------------
  * Number of CUDA kernels the plan has launched since it was created.       */

@@ -24,6 +24,10 @@ TPCG_ERR_BREAKDOWN = 5
 TPCG_ERR_TIMEOUT = 6
 TPCG_ERR_UNSUPPORTED = 7
 TPCG_ERR_EIGENBASIS = 8
+TPCG_ERR_ADMISSION = 9
+TPCG_PENDING = 10
+TPCG_ERR_UNKNOWN_TICKET = 11
+TPCG_ERR_CANCELLED = 12
 
 BC = {"P": 0, "D": 1, "N": 2, "DN": 3, "ND": 4}
 TPCG_FP64 = 0
@@ -55,6 +59,22 @@ class tpcg_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_ulonglong), ("total_ms", ctypes.c_double)]
 
 
+class tpcg_request(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("bc", ctypes.c_int * 3),
+                ("h", ctypes.c_double * 3), ("prec", ctypes.c_int), ("session", ctypes.c_ulonglong),
+                ("eta", ctypes.c_void_p), ("tol", ctypes.c_double), ("maxit", ctypes.c_int)]
+
+
+class tpcg_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_ulonglong), ("completed", ctypes.c_ulonglong), ("failed", ctypes.c_ulonglong),
+                ("rejected", ctypes.c_ulonglong), ("queued", ctypes.c_int), ("running", ctypes.c_int),
+                ("device_bytes", ctypes.c_size_t), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("elapsed_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _P = ctypes.c_void_p
 _D = ctypes.c_double
 _I = ctypes.c_int
@@ -75,6 +95,12 @@ _SIGS = {
     "tpcg_profile_begin": (_I, [_P]),
     "tpcg_profile_end": (_I, [_P, ctypes.POINTER(tpcg_kernel_stat), _I, ctypes.POINTER(_I)]),
     "tpcg_residual_norms_noalloc": (_I, [_I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _P, _P, _P, _P]),
+    "tpcg_server_create": (_I, [ctypes.c_size_t, _I, ctypes.POINTER(_P)]),
+    "tpcg_server_submit": (_I, [_P, ctypes.POINTER(tpcg_request), ctypes.POINTER(ctypes.c_ulonglong)]),
+    "tpcg_server_poll": (_I, [_P, ctypes.c_ulonglong, _P, ctypes.POINTER(tpcg_info)]),
+    "tpcg_server_wait": (_I, [_P, ctypes.c_ulonglong, _D, _P, ctypes.POINTER(tpcg_info)]),
+    "tpcg_server_get_stats": (_I, [_P, ctypes.POINTER(tpcg_server_stats)]),
+    "tpcg_server_destroy": (_I, [_P]),
     "tpcg_strerror": (ctypes.c_char_p, [_I]),
 }
 _lib = None
@@ -195,6 +221,104 @@ def tpcg_residual_norms_noalloc(nx, ny, nz, bc, h, eta_ptr, ups_ptr, out_ptr, st
     h_arr = (_D * 3)(*[float(v) for v in h])
     return lib().tpcg_residual_norms_noalloc(int(nx), int(ny), int(nz), bc_arr, h_arr, _P(eta_ptr), _P(ups_ptr),
                                              _P(out_ptr), _P(stream))
+
+
+def tpcg_server_create(hbm_budget, max_slots):
+    out = _P()
+    st = lib().tpcg_server_create(int(hbm_budget), int(max_slots), ctypes.byref(out))
+    return st, out
+
+
+def tpcg_server_submit(server, req):
+    t = ctypes.c_ulonglong()
+    st = lib().tpcg_server_submit(server, ctypes.byref(req), ctypes.byref(t))
+    return st, t.value
+
+
+def tpcg_server_poll(server, ticket, ups_ptr):
+    info = tpcg_info()
+    st = lib().tpcg_server_poll(server, ctypes.c_ulonglong(ticket), _P(ups_ptr), ctypes.byref(info))
+    return st, info
+
+
+def tpcg_server_wait(server, ticket, timeout_s, ups_ptr):
+    info = tpcg_info()
+    st = lib().tpcg_server_wait(server, ctypes.c_ulonglong(ticket), float(timeout_s), _P(ups_ptr),
+                                ctypes.byref(info))
+    return st, info
+
+
+def tpcg_server_get_stats(server):
+    out = tpcg_server_stats()
+    st = lib().tpcg_server_get_stats(server, ctypes.byref(out))
+    return st, out
+
+
+def tpcg_server_destroy(server):
+    return lib().tpcg_server_destroy(server)
+
+
+class Server:
+    """Owns a tpcg_server; right-hand sides and solutions are host numpy float64 arrays (nz, ny, nx)."""
+
+    def __init__(self, hbm_budget=0, max_slots=8):
+        st, h = tpcg_server_create(hbm_budget, max_slots)
+        if st != TPCG_OK:
+            raise TpcgError(st, "tpcg_server_create")
+        self.handle = h
+        self.shapes = {}
+
+    def submit(self, eta, bcs, h=(1.0, 1.0, 1.0), prec="fp16", session=0, tol=1e-10, maxit=60):
+        import numpy as np
+
+        eta = np.ascontiguousarray(eta, dtype=np.float64)
+        nz, ny, nx = eta.shape
+        req = tpcg_request()
+        req.nx, req.ny, req.nz = nx, ny, nz
+        for m in range(3):
+            b = bcs[m] if m < len(bcs) else "P"
+            req.bc[m] = BC[b] if isinstance(b, str) else int(b)
+            req.h[m] = float(h[m])
+        req.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+        req.session = int(session)
+        req.eta = eta.ctypes.data
+        req.tol = float(tol)
+        req.maxit = int(maxit)
+        st, t = tpcg_server_submit(self.handle, req)
+        if st != TPCG_OK:
+            raise TpcgError(st, "tpcg_server_submit")
+        self.shapes[t] = eta.shape
+        return t
+
+    def _result(self, fn, ticket, *args):
+        import numpy as np
+
+        out = np.empty(self.shapes[ticket])
+        st, info = fn(self.handle, ticket, *args, out.ctypes.data)
+        if st == TPCG_PENDING:
+            return st, None, None
+        self.shapes.pop(ticket, None)
+        return st, out, info.as_dict()
+
+    def poll(self, ticket):
+        return self._result(tpcg_server_poll, ticket)
+
+    def wait(self, ticket, timeout_s=-1.0):
+        return self._result(tpcg_server_wait, ticket, timeout_s)
+
+    def stats(self):
+        return tpcg_server_get_stats(self.handle)[1].as_dict()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            tpcg_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---------------------------------------------------------------------------

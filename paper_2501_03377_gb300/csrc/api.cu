@@ -495,7 +495,8 @@ int tpcg_plan_create(int nx, int ny, int nz, const int bc[3], const double h[3],
     if ((size_t)bx * by * zsplit * 4 > p->partial_slots) rc = TPCG_ERR_UNSUPPORTED;
   }
   if (!rc && prec != TPCG_FP64) rc = tc_plan_setup(p);
-  if (!rc && cudaDeviceSynchronize() != cudaSuccess) rc = TPCG_ERR_CUDA;
+  // the set-up copies ran on the legacy stream; wait for them only (not for other streams' work)
+  if (!rc && cudaStreamSynchronize(0) != cudaSuccess) rc = TPCG_ERR_CUDA;
   if (rc) {
     cudaGetLastError();
     free_plan(p);
@@ -742,6 +743,10 @@ const char* tpcg_strerror(int status) {
     case TPCG_ERR_TIMEOUT: return "bounded device wait timed out";
     case TPCG_ERR_UNSUPPORTED: return "unsupported configuration";
     case TPCG_ERR_EIGENBASIS: return "eigenbasis accuracy check failed";
+    case TPCG_ERR_ADMISSION: return "request exceeds the server's device-memory budget";
+    case TPCG_PENDING: return "pending";
+    case TPCG_ERR_UNKNOWN_TICKET: return "unknown ticket";
+    case TPCG_ERR_CANCELLED: return "cancelled";
     default: return "unknown status";
   }
 }
