@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=400)
+    ap.add_argument("--serving-rate", type=float, default=200.0)
+    ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
 
@@ -191,6 +194,95 @@ def time_steps(plan, etas, ups, steps, tol, torch, barrier, sampler=None):
     return dt, infos, clocks
 
 
+def run_serving(args, prec):
+    """Poisson request stream from 16 warm-started sessions (grids 64..256 x 64..256 x 32..192, random BCs)."""
+    import numpy as np
+
+    from inputs import synth
+    from paper_2501_03377_gb300 import Server
+
+    import torch
+
+    sessions = synth.serving_sessions(seed=0)
+    steps = 3
+    rhs = []
+    for ses in sessions:  # pinned host right-hand sides, lent to the server (no copy at submit)
+        per = []
+        for _ in range(steps):
+            per.append(torch.from_numpy(ses.rhs()).pin_memory())
+            ses.step()
+        rhs.append(per)
+    arrivals = synth.poisson_arrivals(args.serving_rate, args.serving_requests, seed=1)
+    order = np.random.default_rng(2).integers(0, len(sessions), size=args.serving_requests)
+    srv = Server(max_slots=8)
+    # warm-up outside the measurement: one request per session builds its plan and session state
+    for i in range(len(sessions)):
+        srv.wait(srv.submit(rhs[i][0], sessions[i].bcs, prec=prec, session=i + 1, borrow=True), 120.0)
+    srv.reset_stats()
+    counters = [1] * len(sessions)
+    tickets = []
+    t0 = time.perf_counter()
+    for k in range(args.serving_requests):
+        delay = t0 + arrivals[k] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        i = int(order[k])
+        tickets.append(srv.submit(rhs[i][counters[i] % steps], sessions[i].bcs, prec=prec, session=i + 1,
+                                  borrow=True))
+        counters[i] += 1
+    worst, bad, iters = 0.0, 0, []
+    for t in tickets:
+        st, _, info = srv.wait(t, 300.0)
+        bad += st != 0
+        if info:
+            worst = max(worst, info["rel_res_true"])
+            iters.append(info["iters"])
+    t1 = time.perf_counter()
+    stats = srv.stats()
+    srv.close()
+    # latency percentiles of the measured requests only
+    return {"requests": args.serving_requests, "rate_hz": args.serving_rate, "sessions": len(sessions),
+            "form": f"mixed-{prec}", "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"],
+            "mean_ms": stats["mean_ms"], "solves_per_s": stats["completed"] / stats["elapsed_s"],
+            "offered_span_s": float(arrivals[-1]),
+            "failed": bad, "worst_rel_res_true": worst, "mean_iters": float(np.mean(iters)) if iters else None,
+            "latency_note": "submit call -> solution in pinned host memory (H2D of the lent pinned eta, the "
+                            "solve, D2H); one warm-up request per session excluded",
+            "warmup_requests": len(sessions)}
+
+
+def run_batched(prec, torch):
+    """48 independent solves, grids {64..160}^2 x {32..96}, random BCs, 1-8 right-hand sides each."""
+    import numpy as np
+
+    from inputs import synth
+    from paper_2501_03377_gb300 import Plan, binding
+
+    specs = synth.batched_specs(seed=0)
+    plans, etas, ups, streams = [], [], [], []
+    for sp in specs:
+        st = torch.cuda.Stream()
+        streams.append(st)
+        plans.append(Plan(sp["nx"], sp["ny"], sp["nz"], sp["bcs"], prec=prec, stream=st.cuda_stream))
+        e = torch.from_numpy(np.stack([synth.batched_rhs(sp, r) for r in range(sp["nrhs"])])).cuda()
+        etas.append(e)
+        ups.append(torch.zeros_like(e))
+    args = ([p.handle for p in plans], [sp["nrhs"] for sp in specs], [e.data_ptr() for e in etas],
+            [u.data_ptr() for u in ups], [1e-10] * len(specs), 60, binding.TPCG_ZERO_GUESS)
+    binding.tpcg_solve_batched(*args)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, infos = binding.tpcg_solve_batched(*args)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    nrhs = sum(sp["nrhs"] for sp in specs)
+    points = sum(sp["nrhs"] * sp["nx"] * sp["ny"] * sp["nz"] for sp in specs)
+    return {"solves": len(specs), "rhs": nrhs, "form": f"mixed-{prec}", "seconds": dt, "rhs_per_s": nrhs / dt,
+            "mpoints_per_s": points / dt / 1e6, "status": st,
+            "worst_rel_res_true": max(i["rel_res_true"] for i in infos),
+            "mean_iters": float(np.mean([i["iters"] for i in infos]))}
+
+
 def kernel_work(kind, plan_prec, N, dims, iters_total, applies_total, ztype_bytes):
     """Algorithmic work of one kernel kind over the timed region: (amount, unit, bound)."""
     n, q, t = dims
@@ -321,6 +413,13 @@ def run_ours(args, rank, world, torch):
                     "worst_rel_res_true": max(i["rel_res_true"] for (_, i) in inf64)}
         p64.close()
 
+    serving = batched = None
+    if rank == 0 and world == 1 and prec != "fp64":
+        if args.serving_requests > 0:
+            serving = run_serving(args, prec)
+        if not args.no_batched:
+            batched = run_batched(prec, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dtc, res = cpu_oracle_solve(ws[0], args.tol)
@@ -343,7 +442,8 @@ def run_ours(args, rank, world, torch):
             "worst_rel_res_true": worst_res, "failed_solves": len(bad),
             "gpu_launches": launches,
             "roofline": roofline, "kernels": kernels,
-            "e2e": e2e, "cpu_baseline": cpu, "fp64_form": fp64_cmp, "bf16_form": bf16_cmp, "clocks": clocks,
+            "e2e": e2e, "cpu_baseline": cpu, "fp64_form": fp64_cmp, "bf16_form": bf16_cmp,
+            "serving": serving, "batched": batched, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     plan.close()

@@ -187,7 +187,8 @@ int tpcg_plan_eigenpairs(const tpcg_plan* plan, int axis, double* lam, double* V
  * once) and device memory are free; each admitted solve runs on its own plan
  * and CUDA stream, so solves of different sizes overlap on the GPU while new
  * requests keep arriving.  Plans are cached by (grid, BCs, spacing,
- * precision) and evicted least-recently-used when idle and memory is needed.
+ * precision), as many as the budget holds, and evicted least-recently-used
+ * when idle and memory is needed.
  * A request with session != 0 starts from the previous solution of that
  * session (warm start), which stays on the device; the requests of one
  * session run in submission order, so every result equals the result the
@@ -203,14 +204,21 @@ typedef struct {
   const double* eta;             /* HOST pointer, nz*ny*nx doubles, copied by submit      */
   double tol;                    /* relative residual tolerance, (0, 1)                   */
   int maxit;                     /* >= 1                                                  */
+  unsigned flags;                /* TPCG_REQ_* below                                      */
 } tpcg_request;
+
+/* tpcg_request.flags: by default submit copies eta.  With a BORROW flag the
+ * server reads eta from the caller's buffer when the request is admitted; the
+ * buffer must stay valid and unchanged until the result has been taken.      */
+#define TPCG_REQ_BORROW_HOST   1u  /* eta is host memory (pinned gives the fastest copy) */
+#define TPCG_REQ_BORROW_DEVICE 2u  /* eta is device memory of the server's device        */
 
 typedef struct {
   unsigned long long submitted, completed, failed, rejected;
   int queued, running;
   size_t device_bytes;           /* plans, session solutions and buffers now held         */
   double p50_ms, p99_ms, mean_ms; /* submit -> result-on-host latency of finished requests */
-  double elapsed_s;              /* since the first submit                                */
+  double elapsed_s;              /* first submit -> last finished request                 */
 } tpcg_server_stats;
 
 /* hbm_budget: device bytes the server may hold (0: 90% of the free memory). */
@@ -226,6 +234,8 @@ int tpcg_server_poll(tpcg_server* server, unsigned long long ticket, double* ups
 int tpcg_server_wait(tpcg_server* server, unsigned long long ticket, double timeout_s, double* ups_out,
                      tpcg_info* info);
 int tpcg_server_get_stats(tpcg_server* server, tpcg_server_stats* stats);
+/* Clear the counters and the latency record (e.g. after a warm-up phase).  */
+int tpcg_server_reset_stats(tpcg_server* server);
 /* Lets running requests finish, cancels queued ones, releases everything.  */
 int tpcg_server_destroy(tpcg_server* server);
 

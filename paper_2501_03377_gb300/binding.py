@@ -36,6 +36,8 @@ TPCG_MIXED_BF16 = 2
 TPCG_MIXED_FP16 = 3
 PREC = {"fp64": TPCG_FP64, "tf32": TPCG_MIXED_TF32, "bf16": TPCG_MIXED_BF16, "fp16": TPCG_MIXED_FP16}
 TPCG_ZERO_GUESS = 1
+TPCG_REQ_BORROW_HOST = 1
+TPCG_REQ_BORROW_DEVICE = 2
 
 
 class tpcg_info(ctypes.Structure):
@@ -62,7 +64,8 @@ class tpcg_kernel_stat(ctypes.Structure):
 class tpcg_request(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("bc", ctypes.c_int * 3),
                 ("h", ctypes.c_double * 3), ("prec", ctypes.c_int), ("session", ctypes.c_ulonglong),
-                ("eta", ctypes.c_void_p), ("tol", ctypes.c_double), ("maxit", ctypes.c_int)]
+                ("eta", ctypes.c_void_p), ("tol", ctypes.c_double), ("maxit", ctypes.c_int),
+                ("flags", ctypes.c_uint)]
 
 
 class tpcg_server_stats(ctypes.Structure):
@@ -100,6 +103,7 @@ _SIGS = {
     "tpcg_server_poll": (_I, [_P, ctypes.c_ulonglong, _P, ctypes.POINTER(tpcg_info)]),
     "tpcg_server_wait": (_I, [_P, ctypes.c_ulonglong, _D, _P, ctypes.POINTER(tpcg_info)]),
     "tpcg_server_get_stats": (_I, [_P, ctypes.POINTER(tpcg_server_stats)]),
+    "tpcg_server_reset_stats": (_I, [_P]),
     "tpcg_server_destroy": (_I, [_P]),
     "tpcg_strerror": (ctypes.c_char_p, [_I]),
 }
@@ -254,6 +258,10 @@ def tpcg_server_get_stats(server):
     return st, out
 
 
+def tpcg_server_reset_stats(server):
+    return lib().tpcg_server_reset_stats(server)
+
+
 def tpcg_server_destroy(server):
     return lib().tpcg_server_destroy(server)
 
@@ -268,11 +276,20 @@ class Server:
         self.handle = h
         self.shapes = {}
 
-    def submit(self, eta, bcs, h=(1.0, 1.0, 1.0), prec="fp16", session=0, tol=1e-10, maxit=60):
+    def submit(self, eta, bcs, h=(1.0, 1.0, 1.0), prec="fp16", session=0, tol=1e-10, maxit=60, borrow=False):
+        """eta: numpy array (copied by the server), or with borrow=True a torch tensor (pinned host or
+        CUDA) that the caller keeps alive and unchanged until the result is taken."""
         import numpy as np
 
-        eta = np.ascontiguousarray(eta, dtype=np.float64)
-        nz, ny, nx = eta.shape
+        flags = 0
+        if borrow:
+            nz, ny, nx = eta.shape
+            ptr = eta.data_ptr()
+            flags = TPCG_REQ_BORROW_DEVICE if eta.is_cuda else TPCG_REQ_BORROW_HOST
+        else:
+            eta = np.ascontiguousarray(eta, dtype=np.float64)
+            nz, ny, nx = eta.shape
+            ptr = eta.ctypes.data
         req = tpcg_request()
         req.nx, req.ny, req.nz = nx, ny, nz
         for m in range(3):
@@ -281,13 +298,14 @@ class Server:
             req.h[m] = float(h[m])
         req.prec = PREC[prec] if isinstance(prec, str) else int(prec)
         req.session = int(session)
-        req.eta = eta.ctypes.data
+        req.eta = ptr
         req.tol = float(tol)
         req.maxit = int(maxit)
+        req.flags = flags
         st, t = tpcg_server_submit(self.handle, req)
         if st != TPCG_OK:
             raise TpcgError(st, "tpcg_server_submit")
-        self.shapes[t] = eta.shape
+        self.shapes[t] = tuple(eta.shape)
         return t
 
     def _result(self, fn, ticket, *args):
@@ -308,6 +326,9 @@ class Server:
 
     def stats(self):
         return tpcg_server_get_stats(self.handle)[1].as_dict()
+
+    def reset_stats(self):
+        tpcg_server_reset_stats(self.handle)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -128,14 +128,26 @@ void eigen_check(int n, int bc, const std::vector<double>& lam, const std::vecto
                  double* recon_err) {
   const std::vector<double> L = lap1d_dense(n, bc);
   double oe = 0.0, re2 = 0.0;
+  // FP64 accumulation (long double is software quad precision on some hosts);
+  // the acceptance bounds below leave ample room for its rounding.
+  std::vector<double> VT((size_t)n * n), VL((size_t)n * n);
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < n; ++k) {
+      VT[(size_t)k * n + j] = V[(size_t)j * n + k];
+      VL[(size_t)j * n + k] = V[(size_t)j * n + k] * lam[k];
+    }
   for (int a = 0; a < n; ++a) {
+    const double* va = &VT[(size_t)a * n];
+    const double* la = &VL[(size_t)a * n];
     for (int b = 0; b < n; ++b) {
-      long double g = 0.0L, r = 0.0L;
-      for (int j = 0; j < n; ++j) g += (long double)V[(size_t)j * n + a] * V[(size_t)j * n + b];
-      for (int k = 0; k < n; ++k) r += (long double)V[(size_t)a * n + k] * lam[k] * V[(size_t)b * n + k];
-      const double ge = fabs((double)g - (a == b ? 1.0 : 0.0));
+      const double* vb = &VT[(size_t)b * n];
+      const double* rb = &V[(size_t)b * n];
+      double g = 0.0, r = 0.0;
+      for (int j = 0; j < n; ++j) g += va[j] * vb[j];
+      for (int k = 0; k < n; ++k) r += la[k] * rb[k];
+      const double ge = fabs(g - (a == b ? 1.0 : 0.0));
       if (ge > oe) oe = ge;
-      const double d = L[(size_t)a * n + b] - (double)r;
+      const double d = L[(size_t)a * n + b] - r;
       re2 += d * d;
     }
   }

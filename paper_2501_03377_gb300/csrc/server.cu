@@ -1,7 +1,7 @@
 // Request server with continuous batching (tpcg_server_*).
 //
 // One worker thread owns the device work.  Requests wait in a FIFO queue and
-// are admitted into slots as soon as a slot and device memory are free; every
+// are admitted as soon as fewer than max_slots solves run and device memory is free; every
 // admitted solve is a SolveJob on its own plan and stream, so solves of
 // different sizes and boundary conditions overlap on the GPU while new ones
 // keep arriving.  Plans (eigenbases and workspaces) are cached by (grid, BCs,
@@ -54,6 +54,7 @@ PlanKey make_key(const tpcg_request& r) {
 struct Request {
   unsigned long long ticket = 0;
   tpcg_request req{};
+  const double* eta_borrowed = nullptr;  // caller's buffer (TPCG_REQ_BORROW_*)
   PlanKey key{};
   double* eta_host = nullptr;  // pinned copy of eta
   double* ups_host = nullptr;  // pinned result
@@ -106,7 +107,7 @@ struct tpcg_server {
   unsigned long long submitted = 0, completed = 0, failed = 0, rejected = 0;
   std::vector<double> latencies_ms;
   std::multimap<size_t, void*> pinned_pool;  // released pinned host buffers, by size
-  tpcg::Clock::time_point t_first;
+  tpcg::Clock::time_point t_first, t_last_done;
   bool have_first = false;
 };
 
@@ -181,6 +182,7 @@ int running_slots(const tpcg_server* s) {
 void finish_request(tpcg_server* s, Request* r, int status) {
   r->status = status;
   r->t_done = Clock::now();
+  s->t_last_done = r->t_done;
   const double ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
   s->latencies_ms.push_back(ms);
   if (status == TPCG_OK) ++s->completed;
@@ -216,14 +218,6 @@ bool try_admit(tpcg_server* s, Request* r, bool* reject) {
   auto unreserve = [&]() {
     if (slot != s->slots.end()) slot->req = nullptr;
   };
-  if (slot == s->slots.end() && (int)s->slots.size() >= s->max_slots) {
-    // make a slot available by evicting an idle one of another key
-    auto victim = s->slots.end();
-    for (auto it = s->slots.begin(); it != s->slots.end(); ++it)
-      if (!it->req && (victim == s->slots.end() || it->last_used < victim->last_used)) victim = it;
-    if (victim == s->slots.end()) return false;
-    release_slot(s, victim);
-  }
   if (slot_need + ses_need > s->budget) {
     unreserve();
     *reject = true;  // can never fit
@@ -293,7 +287,14 @@ bool try_admit(tpcg_server* s, Request* r, bool* reject) {
   sl.stage = 1;
   double* ups = ses ? ses->d_ups : sl.d_ups;
   const bool warm = ses && ses->has_solution;
-  if (cudaMemcpyAsync(sl.d_eta, r->eta_host, (size_t)r->N * 8, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess) {
+  const double* eta_src = r->eta_borrowed ? r->eta_borrowed : r->eta_host;
+  const double* eta_dev = sl.d_eta;
+  cudaError_t ce = cudaSuccess;
+  if (r->req.flags & TPCG_REQ_BORROW_DEVICE)
+    eta_dev = eta_src;  // read in place: the solve never writes eta
+  else
+    ce = cudaMemcpyAsync(sl.d_eta, eta_src, (size_t)r->N * 8, cudaMemcpyHostToDevice, sl.stream);
+  if (ce != cudaSuccess) {
     cudaGetLastError();
     sl.req = nullptr;
     sl.stage = 0;
@@ -302,7 +303,7 @@ bool try_admit(tpcg_server* s, Request* r, bool* reject) {
   }
   SolveJob j;
   j.p = sl.plan;
-  j.eta = sl.d_eta;
+  j.eta = eta_dev;
   j.ups = ups;
   j.tol = r->req.tol;
   j.maxit = r->req.maxit;
@@ -456,17 +457,22 @@ int tpcg_server_submit(tpcg_server* s, const tpcg_request* req, unsigned long lo
     delete r;
     return TPCG_ERR_INVALID_ARG;
   }
-  r->eta_host = pinned_get(s, bytes);
+  const bool borrow = (req->flags & (TPCG_REQ_BORROW_HOST | TPCG_REQ_BORROW_DEVICE)) != 0;
+  r->eta_host = borrow ? nullptr : pinned_get(s, bytes);
   r->ups_host = pinned_get(s, bytes);
-  if (!r->eta_host || !r->ups_host) {
+  if ((!borrow && !r->eta_host) || !r->ups_host) {
     pinned_put(s, bytes, r->eta_host);
     pinned_put(s, bytes, r->ups_host);
     delete r;
     return TPCG_ERR_OOM;
   }
-  lock.unlock();
-  std::memcpy(r->eta_host, req->eta, bytes);  // outside the lock: the worker keeps running
-  lock.lock();
+  if (borrow) {
+    r->eta_borrowed = req->eta;
+  } else {
+    lock.unlock();
+    std::memcpy(r->eta_host, req->eta, bytes);  // outside the lock: the worker keeps running
+    lock.lock();
+  }
   r->ticket = s->next_ticket++;
   r->t_submit = t_call;
   if (!s->have_first) {
@@ -546,7 +552,17 @@ int tpcg_server_get_stats(tpcg_server* s, tpcg_server_stats* out) {
     for (double v : l) sum += v;
     out->mean_ms = sum / (double)l.size();
   }
-  if (s->have_first) out->elapsed_s = std::chrono::duration<double>(Clock::now() - s->t_first).count();
+  if (s->have_first && (s->completed + s->failed) > 0)
+    out->elapsed_s = std::chrono::duration<double>(s->t_last_done - s->t_first).count();
+  return TPCG_OK;
+}
+
+int tpcg_server_reset_stats(tpcg_server* s) {
+  if (!s) return TPCG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(s->mu);
+  s->latencies_ms.clear();
+  s->submitted = s->completed = s->failed = s->rejected = 0;
+  s->have_first = false;
   return TPCG_OK;
 }
 

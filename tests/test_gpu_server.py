@@ -121,3 +121,20 @@ def test_server_poll_pending_and_unknown_ticket():
     assert binding.tpcg_server_poll(srv.handle, t, 0)[0] == binding.TPCG_ERR_UNKNOWN_TICKET
     assert binding.tpcg_server_poll(srv.handle, 987654, 0)[0] == binding.TPCG_ERR_UNKNOWN_TICKET
     srv.close()
+
+
+def test_server_borrowed_rhs_equal_copied():
+    from paper_2501_03377_gb300 import Server
+
+    bcs = ("P", "D", "N")
+    eta = synth.defect_rhs(40, 32, 16, bcs, 10, 1.5, seed=5)
+    srv = Server(max_slots=3)
+    t_copy = srv.submit(eta, bcs)
+    eh = torch.from_numpy(eta.copy()).pin_memory()
+    t_host = srv.submit(eh, bcs, borrow=True)
+    ed = torch.from_numpy(eta.copy()).cuda()
+    t_dev = srv.submit(ed, bcs, borrow=True)
+    out = [srv.wait(t, 60.0) for t in (t_copy, t_host, t_dev)]
+    srv.close()
+    assert all(st == 0 for st, _, _ in out)
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][1], out[2][1])
