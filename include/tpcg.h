@@ -85,7 +85,7 @@ typedef struct tpcg_plan tpcg_plan;
  * the operator is singular (every present axis P or N), else eta itself.   */
 typedef struct {
   int    status;            /* same value the call returned                         */
-  int    iters;             /* PCG iterations s performed (Algorithm 1, line 9)     */
+  int    iters;             /* PCG iterations s performed (Algorithm 1)               */
   int    precond_applies;   /* applications of the preconditioner                  */
   int    prec;              /* precision form used                                  */
   double rel_res_true;      /* ||eta_hat - L ups||_2 / ||eta_hat||_2, FP64, at exit  */

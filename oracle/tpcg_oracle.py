@@ -304,11 +304,11 @@ def pcg(shape, bcs, hs, H, U0=None, tol=1e-13, maxit=50, precond="pinv", L=None,
     if hnorm == 0.0:
         return PCGResult(np.zeros(shape), 0, [0.0], [0.0], [], removed_mean, 0.0)
     U = np.zeros(shape) if U0 is None else np.array(U0, dtype=np.float64)
-    W = apply_L(U)                                  # line 3
-    R = H - W                                       # line 4
-    Z = M(R)                                        # line 5
-    rho = float(np.vdot(R, Z))                      # line 6
-    P = Z.copy()                                    # line 7
+    W = apply_L(U)                                  # L U_0
+    R = H - W                                       # initial residual
+    Z = M(R)                                        # preconditioned residual
+    rho = float(np.vdot(R, Z))                      # rho_0 = <R_0, Z_0>
+    P = Z.copy()                                    # first direction
     true_res = [np.linalg.norm((H - apply_L(U)).ravel()) / hnorm]
     recur_res = [np.linalg.norm(R.ravel()) / hnorm]
     alphas = []
@@ -316,15 +316,15 @@ def pcg(shape, bcs, hs, H, U0=None, tol=1e-13, maxit=50, precond="pinv", L=None,
     best = true_res[0]
     stall = 0
     while true_res[-1] > tol and s < maxit:
-        s += 1                                      # line 9
-        W = apply_L(P)                              # line 10
-        alpha = rho / float(np.vdot(W, P))          # line 11
-        U = U + alpha * P                           # line 12
-        R = R - alpha * W                           # line 13
-        Z = M(R)                                    # line 14
-        rho_new = float(np.vdot(R, Z))              # line 15
-        beta = rho_new / rho                        # line 16
-        P = Z + beta * P                            # line 17
+        s += 1                                      # iteration counter
+        W = apply_L(P)                              # W = L P
+        alpha = rho / float(np.vdot(W, P))          # step length
+        U = U + alpha * P                           # iterate update
+        R = R - alpha * W                           # residual recurrence
+        Z = M(R)                                    # preconditioner
+        rho_new = float(np.vdot(R, Z))              # new rho
+        beta = rho_new / rho                        # beta (ratio of rhos)
+        P = Z + beta * P                            # next direction
         rho = rho_new
         alphas.append(alpha)
         true_res.append(np.linalg.norm((H - apply_L(U)).ravel()) / hnorm)

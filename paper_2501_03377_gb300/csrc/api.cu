@@ -17,9 +17,9 @@ namespace tpcg {
 
 void launch_apply_laplacian(const tpcg_plan* p, const Geom& g, const double* x, double* w);
 void launch_init_residual(const tpcg_plan* p, const Geom& g, const double* eta, const double* U, bool zero_guess);
-void launch_eta_sum(const tpcg_plan* p, const Geom& g, const double* eta);
+void launch_eta_sum(const tpcg_plan* p, const Geom& g, const double* eta, const double* U0);
 void launch_direction(const tpcg_plan* p, const Geom& g, int k);
-void launch_update(const tpcg_plan* p, const Geom& g, double* U, int k);
+void launch_update(const tpcg_plan* p, const Geom& g, double* U, int k, bool zero_guess_first);
 void launch_true_residual(const tpcg_plan* p, const Geom& g, const double* eta, const double* U, bool force);
 void launch_center_u(const tpcg_plan* p, const Geom& g, double* U);
 void launch_zero(const tpcg_plan* p, long long N, double* U);
@@ -27,6 +27,7 @@ void launch_to_lp(const tpcg_plan* p, const Geom& g, const double* r);
 void launch_norm_shift(const tpcg_plan* p, const Geom& g, const double* r);
 void launch_f32_to_f64(const tpcg_plan* p, long long N, const float* a, double* b);
 void launch_rhs_add_bc(const tpcg_plan* p, const Geom& g, double* eta, const double* bv);
+int setup_fx_grids(tpcg_plan* p);
 void run_precond_f64(const tpcg_plan* pl, const double* R, double* Z, SolveState* st);
 int run_precond_tc(const tpcg_plan* pl, float* Z, SolveState* st);
 int tc_plan_setup(tpcg_plan* pl);
@@ -63,6 +64,11 @@ Geom make_geom(const tpcg_plan* p) {
     g.ih2[m] = 1.0 / (p->h[m] * p->h[m]);
   }
   if (p->nz == 1) g.ih2[2] = 0.0;
+  for (int m = 0; m < 3; ++m) {
+    g.ih2f[m] = (float)g.ih2[m];
+    g.nih2[m] = -g.ih2[m];
+  }
+  g.uniform = (g.ih2[0] == g.ih2[1]) && (p->nz == 1 || g.ih2[2] == g.ih2[0]);
   g.N = p->N;
   return g;
 }
@@ -226,16 +232,17 @@ int enqueue_state_readback(tpcg_plan* p) {
   return last_cuda_error();
 }
 
-// lines 8-18: `count` iterations; kernels of iterations after convergence return at once
+// `count` iterations of the PCG loop of Algorithm 1; kernels of iterations after
+// convergence return at once
 int enqueue_iterations(SolveJob& j, int count) {
   tpcg_plan* p = j.p;
   const Geom g = make_geom(p);
   for (int c = 0; c < count; ++c) {
     const int k = j.issued + c;                         // P_k is written to d_P[k & 1], P_{k-1} read from the other
-    launch_direction(p, g, k);                          // lines 10-11 (P from line 17 of the previous pass)
-    launch_update(p, g, j.ups, k);                      // lines 12-13
+    launch_direction(p, g, k);                          // direction P, W = L P, alpha
+    launch_update(p, g, j.ups, k, k == 0 && (j.flags & TPCG_ZERO_GUESS));  // U and R updates
     launch_true_residual(p, g, j.eta, j.ups, false);    // stop test
-    const int rc = run_precond(p, p->d_R, p->d_Z, p->d_state);  // lines 14-16
+    const int rc = run_precond(p, p->d_R, p->d_Z, p->d_state);  // Z = M R, rho, beta
     if (rc) return rc;
   }
   j.issued += count;
@@ -260,8 +267,8 @@ int job_start(SolveJob& j) {
   hs->status = TPCG_OK;
   if (cudaMemcpyAsync(p->d_state, hs, sizeof(SolveState), cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
     return TPCG_ERR_CUDA;
-  // Algorithm 1, lines 2-7 (eq. centering first when singular)
-  launch_eta_sum(p, g, j.eta);  // mean (singular operators) and the first low-precision exponent
+  // Algorithm 1 set-up: initial residual, Z_0, rho_0 (eq. centering first when singular)
+  launch_eta_sum(p, g, j.eta, zero_guess ? nullptr : j.ups);  // mean, first low-precision exponent, max|U_0|
   launch_init_residual(p, g, j.eta, j.ups, zero_guess);
   if (p->lp_kind == 2 && !zero_guess) launch_to_lp(p, g, p->d_R);  // re-scale FP16 copy to the actual R_0
   int rc = run_precond(p, p->d_R, p->d_Z, p->d_state);
@@ -383,7 +390,7 @@ int tpcg_plan_create(int nx, int ny, int nz, const int bc[3], const double h[3],
   cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
   if (p->num_sms <= 0) p->num_sms = 1;
 
-  // Algorithm 5, lines 2-4: eigenpairs per axis (closed forms, checked)
+  // Algorithm 5: eigenpairs per axis (closed forms, checked)
   const int lens[3] = {nx, ny, nz};
   for (int m = 0; m < 3; ++m) {
     if (build_axis(lens[m], p->bc[m], p->h[m], p->ax[m]) != 0) { delete p; return TPCG_ERR_EIGENBASIS; }
@@ -432,9 +439,18 @@ int tpcg_plan_create(int nx, int ny, int nz, const int bc[3], const double h[3],
   }
   // PCG workspaces
   if (!rc) rc = dalloc(p, &p->d_R, (size_t)N);
-  if (!rc) rc = dalloc(p, &p->d_P[0], (size_t)N);
-  if (!rc) rc = dalloc(p, &p->d_P[1], (size_t)N);
-  if (!rc) rc = dalloc(p, &p->d_W, (size_t)N);
+  for (int b = 0; b < 2 && !rc; ++b) {
+    if (p->prec == TPCG_FP64) {
+      double* d = nullptr;
+      rc = dalloc(p, &d, (size_t)N);
+      p->d_P[b] = d;
+    } else {
+      int* d = nullptr;
+      rc = dalloc(p, &d, (size_t)N);
+      p->d_P[b] = d;
+    }
+  }
+  if (!rc && p->prec == TPCG_FP64) rc = dalloc(p, &p->d_W, (size_t)N);
   if (!rc) {
     if (prec == TPCG_FP64) {
       double* z = nullptr;
@@ -493,6 +509,9 @@ int tpcg_plan_create(int nx, int ny, int nz, const int bc[3], const double h[3],
     const long long want = (N + 255) / 256;
     p->stream_blocks = (int)std::max(1LL, std::min<long long>(want, (long long)p->num_sms * 8));
     if ((size_t)bx * by * zsplit * 4 > p->partial_slots) rc = TPCG_ERR_UNSUPPORTED;
+    if (!rc && setup_fx_grids(p)) rc = TPCG_ERR_CUDA;
+    for (int i = 0; i < kFxCount && !rc; ++i)
+      if ((size_t)p->fx_blocks[i] * 4 > p->partial_slots) rc = TPCG_ERR_UNSUPPORTED;
   }
   if (!rc && prec != TPCG_FP64) rc = tc_plan_setup(p);
   // the set-up copies ran on the legacy stream; wait for them only (not for other streams' work)

@@ -44,19 +44,13 @@ struct FieldPlain {  // the stencil is applied to x itself
   __device__ __forceinline__ double operator()(long long i) const { return __ldg(x + i); }
 };
 
-template <class ZT>
-struct FieldDirection {  // P = (Z - mean Z) + beta * P_old   (Algorithm 1, line 17; Remark orthogonality)
-  const ZT* __restrict__ z;
+struct FieldDirection {  // FP64 form: P = (Z - mean Z) + beta * P_old   (Algorithm 1; Remark orthogonality)
+  const double* __restrict__ z;
   const double* __restrict__ pold;
   double mZ, beta;
   int first;
   __device__ __forceinline__ double operator()(long long i) const {
-    double zi;
-    if constexpr (sizeof(ZT) == 4)
-      zi = f32_to_f64_int(__ldg(reinterpret_cast<const float*>(z) + i));
-    else
-      zi = __ldg(reinterpret_cast<const double*>(z) + i);
-    zi -= mZ;
+    const double zi = __ldg(z + i) - mZ;
     return first ? zi : fma(beta, __ldg(pold + i), zi);
   }
 };
@@ -164,36 +158,194 @@ struct LowPrec {
   int pitch, nx;
 };
 
-__device__ __forceinline__ void store_lp(const LowPrec& lp, int shift, long long i, double r) {
+// r32o = f64_to_f32_odd(r, shift): its RNE rounding to FP16 is the correctly
+// rounded r * 2^shift, saturated at the FP16 maximum.  BF16 takes r unscaled.
+__device__ __forceinline__ void store_lp(const LowPrec& lp, long long i, double r, float r32o) {
   if (!lp.ptr) return;
   long long j = i;
-  if (lp.pitch != lp.nx) {
-    const long long row = i / lp.nx;
-    j = row * lp.pitch + (i - row * lp.nx);
+  if (lp.pitch != lp.nx) {  // padded rows (mixed forms: N < 2^32, 32-bit division)
+    const unsigned row = (unsigned)i / (unsigned)lp.nx;
+    j = (long long)row * lp.pitch + ((unsigned)i - row * (unsigned)lp.nx);
   }
-  reinterpret_cast<uint16_t*>(lp.ptr)[j] = (lp.kind == 2) ? f64_to_f16_bits(r, shift) : f64_to_bf16_bits(r);
+  reinterpret_cast<uint16_t*>(lp.ptr)[j] =
+      (lp.kind == 2) ? f32_to_f16_bits_rn(fminf(fmaxf(r32o, -65504.0f), 65504.0f)) : f64_to_bf16_bits(r);
+}
+
+// ------------------------------------------------------------------ fixed-point stencil driver
+// Same 32 x 8 tiles and 4-slot plane ring as stencil_sweep, for fields held as
+// exact integers (IT = int or long long), organised for memory-level
+// parallelism:
+//  * persistent and balanced: the (tile, plane) pairs are numbered tile-major
+//    and block b takes a contiguous range of T / G or T / G + 1 of them,
+//    walked as one or two runs of consecutive planes of a tile;
+//  * software-pipelined: the global loads of ring plane k+2 (Field::load, raw
+//    values in registers) and of the per-point operands of point k+1
+//    (Op::load) are issued before the barrier of plane k, so their latency
+//    overlaps the work on plane k; Field::convert forms the integer value
+//    when the raw values are committed to the ring.  With four slots the
+//    commit of plane k+1 never touches a slot that a thread still on plane
+//    k-1 reads.
+// op(i, x, y, k, pre, c, xl, xr, yl, yr, zl, zr) receives the point value and
+// its six neighbours with the ghosts applied (zl = zr = c in 2D), so every
+// second difference is exact.  op.flush(acc) turns the op's own per-thread
+// sums into the NQ doubles of the deterministic grid reduction.
+template <class IT, int NQ, class Field, class Op, class Fin>
+__device__ __forceinline__ void stencil_sweep_fx(const Geom& g, const Field& field, Op& op, double* partials,
+                                                 unsigned* ticket, Fin fin) {
+  constexpr int NT = TX * TY;
+  constexpr int PER = (SX * SY + NT - 1) / NT;
+  __shared__ IT ring[4][SY][SX];
+  using Raw = typename Field::Raw;
+  using Pre = typename Op::Pre;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * TX + tx;
+  const bool has_z = g.nz > 1;
+  // N <= 2^31: every index and count fits in 32 bits.  All index arithmetic
+  // stays in 32-bit integers (64-bit division is emulated on the FP64 pipe).
+  const unsigned plane = (unsigned)g.nx * (unsigned)g.ny;
+  const unsigned bxn = (unsigned)(g.nx + TX - 1) / TX, byn = (unsigned)(g.ny + TY - 1) / TY;
+  const unsigned T = bxn * byn * (unsigned)g.nz;
+  const unsigned G = gridDim.x, q = T / G, rm = T - q * G;  // block b: q + (b < rm) consecutive pairs
+  const unsigned t_begin = blockIdx.x * q + min(blockIdx.x, rm);
+  const unsigned t_end = t_begin + q + (blockIdx.x < rm ? 1u : 0u);
+  Raw raw[PER];
+  unsigned off[PER];
+  bool okxy[PER];
+  for (unsigned t = t_begin; t < t_end;) {
+    const unsigned tile = t / (unsigned)g.nz;
+    const int k0 = (int)(t - tile * (unsigned)g.nz);
+    const int k1 = (int)min((unsigned)g.nz, (unsigned)k0 + (t_end - t));
+    t += (unsigned)(k1 - k0);
+    const unsigned tyi = tile / bxn;
+    const int bx0 = (int)(tile - tyi * bxn) * TX, by0 = (int)tyi * TY;
+    const int x = bx0 + tx, y = by0 + ty;
+    const bool active = (x < g.nx) && (y < g.ny);
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+      const int e = tid + j * NT;
+      const int gx = ghost_index(bx0 + e % SX - 1, g.nx, g.bc[0]);
+      const int gy = ghost_index(by0 + e / SX - 1, g.ny, g.bc[1]);
+      okxy[j] = (e < SX * SY) && gx >= 0 && gy >= 0;
+      off[j] = (unsigned)gy * (unsigned)g.nx + (unsigned)gx;
+    }
+    auto issue = [&](int kk) {
+      const int kz = has_z ? ghost_index(kk, g.nz, g.bc[2]) : kk;
+#pragma unroll
+      for (int j = 0; j < PER; ++j) raw[j] = (okxy[j] && kz >= 0) ? field.load((unsigned)kz * plane + off[j]) : Raw{};
+    };
+    auto commit = [&](int kk) {
+      IT(*dst)[SX] = ring[kk & 3];
+#pragma unroll
+      for (int j = 0; j < PER; ++j) {
+        const int e = tid + j * NT;
+        if (e < SX * SY) dst[e / SX][e % SX] = field.convert(raw[j]);
+      }
+    };
+    const unsigned col = (unsigned)y * (unsigned)g.nx + (unsigned)x;
+    __syncthreads();  // the previous run's last plane has been consumed
+    if (has_z) {
+      issue(k0 - 1);
+      commit(k0 - 1);
+    }
+    issue(k0);
+    commit(k0);
+    if (has_z) issue(k0 + 1);
+    Pre pre = active ? op.load((unsigned)k0 * plane + col) : Pre{};
+    for (int k = k0; k < k1; ++k) {
+      if (has_z) {
+        commit(k + 1);
+        if (k + 1 < k1) issue(k + 2);
+      }
+      Pre pre_next{};
+      if (active && k + 1 < k1) pre_next = op.load((unsigned)(k + 1) * plane + col);
+      __syncthreads();
+      if (active) {
+        const IT(*cur)[SX] = ring[k & 3];
+        const IT c = cur[ty + 1][tx + 1];
+        const IT zl = has_z ? ring[(k - 1) & 3][ty + 1][tx + 1] : c;
+        const IT zr = has_z ? ring[(k + 1) & 3][ty + 1][tx + 1] : c;
+        op((unsigned)k * plane + col, x, y, k, pre, c, cur[ty + 1][tx], cur[ty + 1][tx + 2], cur[ty][tx + 1],
+           cur[ty + 2][tx + 1], zl, zr);
+      }
+      pre = pre_next;
+    }
+  }
+  double acc[NQ];
+  op.flush(acc);
+  grid_reduce<NQ>(acc, partials, ticket, gridDim.x, blockIdx.x, fin);
+}
+
+struct NoPre {};
+
+// max |U| is tracked on FP64 bit patterns shifted left by one: dropping the
+// sign bit this way keeps the order of magnitudes and stays an integer
+// operation (a sign-bit mask would be turned into an FP64 absolute value,
+// which issues on the slow FP64 pipe).  Thread 0 folds the block's maximum
+// into the state's accumulator; order-independent, so deterministic.
+__device__ __forceinline__ unsigned long long mag_key(double u) {
+  return (unsigned long long)__double_as_longlong(u) << 1;
+}
+__device__ __forceinline__ void fold_umax(SolveState* st, unsigned long long um) {
+  const unsigned long long m = block_max_u64(um);
+  if (threadIdx.x + threadIdx.y == 0) atomicMax(&st->umax_bits, m >> 1);
 }
 
 // ------------------------------------------------------------------ residual R = eta_hat - L U
-// Used for the initial residual (Algorithm 1, lines 3-4) and the FP64 check of
-// the true residual (stop test); the latter replaces R (residual replacement)
-// and accumulates sum(U) for the exit centring.
-struct OpResidual {
+// The initial residual (Algorithm 1) and the check of the true
+// residual behind the stop test (Remark stoppincrit).  U enters as exact
+// int64 fixed point round(U * 2^ku), max|U| * 2^ku < 2^58, so the stencil
+// is exact and W = L U is rounded to FP64 once; r = eta_hat - W is one more
+// rounding (an FMA with the 1/h^2 weight).  The quantisation of U is below
+// 2^-58 max|U|, under the FP64 rounding of U's largest entries.  The check
+// replaces R by the true residual (residual replacement) and sums U for the
+// exit centring; ||r||^2 and sum(r) are accumulated per thread in FP32 from
+// r * 2^sr, where 2^-sr bounds every |r|.
+template <bool INIT>
+struct OpResidualFx {
+  using Pre = double;  // eta at the point
+  __device__ __forceinline__ double load(unsigned i) const { return __ldg(eta + i); }
   const double* __restrict__ eta;
   double* __restrict__ R;
   LowPrec lp;
-  int shift;
-  double mean;
-  __device__ __forceinline__ void operator()(long long i, double c, double w, double (&acc)[4]) {
-    const double e = __ldg(eta + i) - mean;
-    const double r = e - w;
+  double mean, nih0, nih1, nih2;  // -1/h^2 per axis
+  int shift, sr, ku, uniform;
+  float rr, sR;
+  double ee;  // ||eta_hat||^2 in FP64: it scales the tolerance and is reported
+  long long su;
+  __device__ __forceinline__ void operator()(unsigned i, int, int, int, double eta_i, long long c, long long xl,
+                                             long long xr, long long yl, long long yr, long long zl, long long zr) {
+    const long long dx = 2 * c - xl - xr, dy = 2 * c - yl - yr, dz = 2 * c - zl - zr;
+    const double e = eta_i - mean;
+    double r;
+    if (uniform) {
+      r = fma(nih0, i64_to_f64_scaled(dx + dy + dz, -ku), e);
+    } else {
+      r = fma(nih0, i64_to_f64_scaled(dx, -ku), e);
+      r = fma(nih1, i64_to_f64_scaled(dy, -ku), r);
+      if (dz) r = fma(nih2, i64_to_f64_scaled(dz, -ku), r);
+    }
     R[i] = r;
-    store_lp(lp, shift, i, r);
-    acc[0] = fma(r, r, acc[0]);
-    acc[1] += r;
-    acc[2] = fma(e, e, acc[2]);
-    acc[3] += c;
+    store_lp(lp, i, r, f64_to_f32_odd(r, shift));
+    const float r32 = f64_to_f32_odd(r, sr);
+    rr = fmaf(r32, r32, rr);
+    sR += r32;
+    if (INIT) ee = fma(e, e, ee);
+    su += c >> 8;  // |c| < 2^58: a thread's sum of fewer than 2^13 terms stays inside int64
   }
+  __device__ __forceinline__ void flush(double (&acc)[4]) {
+    acc[0] = f32_to_f64_int(rr);
+    acc[1] = f32_to_f64_int(sR);
+    acc[2] = i64_to_f64_scaled(su, 0);
+    acc[3] = ee;
+  }
+};
+
+struct FieldFixed64 {  // U -> round(U * 2^k)
+  using Raw = double;
+  const double* __restrict__ u;
+  int k;
+  __device__ __forceinline__ double load(unsigned i) const { return __ldg(u + i); }
+  __device__ __forceinline__ long long convert(double v) const { return f64_to_fixed64(v, k); }
 };
 
 // The low-precision copy just written used lp_shift; the next one uses the
@@ -203,7 +355,8 @@ __device__ __forceinline__ void advance_shift(SolveState* st, double rr, long lo
   st->lp_shift = lp_shift_for(rr, N);
 }
 
-__device__ void fin_init(SolveState* st, const double (&s)[4], long long N) {
+// s = {||R_0||^2, sum(R_0), ||eta_hat||^2}
+__device__ void fin_init(SolveState* st, const double (&s)[3], long long N) {
   st->rr = s[0];
   st->sumR = s[1];
   st->eta_norm2 = s[2];
@@ -218,19 +371,10 @@ __device__ void fin_init(SolveState* st, const double (&s)[4], long long N) {
   }
 }
 
-__global__ void __launch_bounds__(TX* TY) k_init_residual(Geom g, int zchunk, const double* __restrict__ eta,
-                                                          const double* __restrict__ U, double* __restrict__ R,
-                                                          LowPrec lp, SolveState* st, double* partials) {
-  FieldPlain f{U};
-  OpResidual op{eta, R, lp, st->lp_shift, st->mean_eta};
-  const long long N = g.N;
-  stencil_sweep<4>(g, zchunk, f, op, partials, &st->tickets[kTkInit],
-                   [st, N](const double(&s)[4]) { fin_init(st, s, N); });
-}
-
-__device__ void fin_true(SolveState* st, const double (&s)[4], long long N) {
+// s = {||eta_hat - L U||^2, sum(eta_hat - L U), sum(U)}
+__device__ void fin_true(SolveState* st, const double (&s)[3], long long N) {
   st->true_rr = s[0];
-  st->sumU = s[3];
+  st->sumU = s[2];
   advance_shift(st, s[0], N);
   if (!isfinite(s[0])) {
     st->status = TPCG_ERR_BREAKDOWN;
@@ -250,27 +394,41 @@ __device__ void fin_true(SolveState* st, const double (&s)[4], long long N) {
   }
 }
 
-__global__ void __launch_bounds__(TX* TY) k_true_residual(Geom g, int zchunk, const double* __restrict__ eta,
-                                                          const double* __restrict__ U, double* __restrict__ R,
-                                                          LowPrec lp, SolveState* st, double* partials, int force) {
-  if (!force && (st->done || !st->need_check)) return;
-  FieldPlain f{U};
-  OpResidual op{eta, R, lp, st->lp_shift, st->mean_eta};
+// INIT: R_0 = eta_hat - L U_0 for a given U_0 (max|U_0| from k_eta_sum).
+// Otherwise the stop-test check; `force` evaluates the residual of the
+// returned iterate for the report only.
+template <bool INIT>
+__global__ void __launch_bounds__(TX* TY) k_residual_fx(Geom g, const double* __restrict__ eta,
+                                                        const double* __restrict__ U, double* __restrict__ R,
+                                                        LowPrec lp, SolveState* st, double* partials, int force) {
+  if (!INIT && !force && (st->done || !st->need_check)) return;
+  const int ku = st->ku, sr = st->sr;
+  FieldFixed64 f{U, ku};
+  OpResidualFx<INIT> op{eta, R, lp, st->mean_eta, g.nih2[0], g.nih2[1], g.nih2[2], st->lp_shift, sr, ku, g.uniform,
+                        0.0f, 0.0f, 0.0, 0};
   const long long N = g.N;
-  stencil_sweep<4>(g, zchunk, f, op, partials, &st->tickets[kTkTrue],
-                   [st, force, N](const double(&s)[4]) {
-                     if (force) {
-                       st->true_rr = s[0];
-                       st->sumU = s[3];
-                     } else {
-                       fin_true(st, s, N);
-                     }
-                   });
+  const bool finite_u = isfinite(st->umax);
+  stencil_sweep_fx<long long, 4>(
+      g, f, op, partials, &st->tickets[INIT ? kTkInit : kTkTrue],
+      [st, force, N, sr, ku, finite_u](const double(&s)[4]) {
+        const double rr = finite_u ? ldexp(s[0], -2 * sr) : __longlong_as_double(0x7ff8000000000000ll);
+        const double sumR = ldexp(s[1], -sr), sumU = ldexp(s[2], 8 - ku);
+        if (INIT) {
+          const double v[3] = {rr, sumR, s[3]};
+          fin_init(st, v, N);
+        } else if (force) {
+          st->true_rr = rr;
+          st->sumU = sumU;
+        } else {
+          const double v[3] = {rr, sumR, sumU};
+          fin_true(st, v, N);
+        }
+      });
 }
 
-// ------------------------------------------------------------------ direction + W = L P
-// P_s = Z_s' + beta_s P_{s-1} (line 17, with Z centred), W = L P (line 10),
-// <W, P> and alpha = rho / <W, P> (line 11).
+// ------------------------------------------------------------------ direction + W = L P (FP64 form)
+// P_s = Z_s' + beta_s P_{s-1} (Algorithm 1, with Z centred), W = L P, <W, P>
+// and the step length alpha = rho / <W, P>.
 struct OpDirection {
   double* __restrict__ P;
   double* __restrict__ W;
@@ -281,7 +439,7 @@ struct OpDirection {
   }
 };
 
-__device__ void fin_direction(SolveState* st, const double (&s)[1]) {
+__device__ void fin_direction(SolveState* st, const double (&s)[1], const Geom& g) {
   st->pWp = s[0];
   st->first = 0;
   if (!(s[0] > 0.0) || !isfinite(s[0])) {
@@ -289,137 +447,137 @@ __device__ void fin_direction(SolveState* st, const double (&s)[1]) {
     st->done = 1;
     return;
   }
-  st->alpha = st->rho / s[0];
+  const double alpha = st->rho / s[0];
+  st->alpha = alpha;
+  for (int m = 0; m < 3; ++m) st->nah[m] = -alpha * g.ih2[m];
 }
 
-template <class ZT>
-__global__ void __launch_bounds__(TX* TY) k_direction(Geom g, int zchunk, const ZT* __restrict__ Z,
+__global__ void __launch_bounds__(TX* TY) k_direction(Geom g, int zchunk, const double* __restrict__ Z,
                                                       const double* __restrict__ Pold, double* __restrict__ P,
                                                       double* __restrict__ W, SolveState* st, double* partials) {
   if (st->done) return;
-  FieldDirection<ZT> f{Z, Pold, st->mZ, st->beta, st->first};
+  FieldDirection f{Z, Pold, st->mZ, st->beta, st->first};
   OpDirection op{P, W};
   stencil_sweep<1>(g, zchunk, f, op, partials, &st->tickets[kTkDir],
-                   [st](const double(&s)[1]) { fin_direction(st, s); });
+                   [st, g](const double(&s)[1]) { fin_direction(st, s, g); });
 }
 
 // ------------------------------------------------------------------ direction, mixed forms
-// Z arrives in FP32.  It enters the stencil as exact fixed point
-// round(Z * 2^k) (int32, |.| < 2^27, k from max|Z| of the preconditioner
-// output), so the second differences are exact integers and
-//     W_s = L P_s = L Z_s + beta_s W_{s-1}        (Algorithm 1, lines 10, 17)
-// needs only two FP64 FMAs per point besides <W, P>.  P_s = Z_s + beta P_{s-1}
+// Z arrives in FP32.  The direction is stored as exact fixed point
+//     P_s = 2^-kp P_int,   P_int = round((Z_s + beta_s P_{s-1}) 2^kp),  |P_int| <= 2^27,
+// (Algorithm 1), with kp from the bound max|Z_s| + |beta_s| max|P_{s-1}|.
+// W_s = L P_s is never stored: it is an exact integer stencil of
+// P_int, recomputed where it is needed, so U += alpha P and R -= alpha W stay
+// consistent with one another whatever the rounding of P_s was.  The
+// step-length denominator <W_s, P_s> = <L P_s, P_s> is summed in its edge form: by
+// summation by parts on eq. (lap1d), <L_n p, p> is the sum of (p_i - p_{i-1})^2
+// over the edges of the axis, the start edge taken to the ghost value
+// (periodic: the wrapped neighbour; Dirichlet: 0; Neumann: itself) plus, for a
+// Dirichlet end, the end edge p_{n-1}^2.  Every term is non-negative, so the
+// FP32 sum of exact integer squares has no cancellation.  P_s
 // keeps the constant (null-space) component of Z: L annihilates it, so W and
-// <W, P> are those of the centred Z (Remark orthogonality), rho is corrected by
-// -mean(Z) sum(R), and the resulting constant offset of U is removed at exit.
-template <int NQ, class Field, class Op, class Fin>
-__device__ __forceinline__ void stencil_sweep_int(const Geom& g, int zchunk, const Field& field, Op& op,
-                                                  double* partials, unsigned* ticket, Fin fin) {
-  __shared__ int ring[4][SY][SX];
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int tid = ty * TX + tx;
-  const int bx0 = blockIdx.x * TX, by0 = blockIdx.y * TY;
-  const int x = bx0 + tx, y = by0 + ty;
-  const int k0 = blockIdx.z * zchunk;
-  const int k1 = min(g.nz, k0 + zchunk);
-  const bool active = (x < g.nx) && (y < g.ny);
-  const bool has_z = g.nz > 1;
-  const long long plane = (long long)g.nx * g.ny;
-  double acc[NQ];
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
-
-  auto load_plane = [&](int kk) {
-    const int kz = has_z ? ghost_index(kk, g.nz, g.bc[2]) : kk;
-    int(*dst)[SX] = ring[kk & 3];
-    for (int e = tid; e < SX * SY; e += TX * TY) {
-      const int sx = e % SX, sy = e / SX;
-      const int gx = ghost_index(bx0 + sx - 1, g.nx, g.bc[0]);
-      const int gy = ghost_index(by0 + sy - 1, g.ny, g.bc[1]);
-      int v = 0;
-      if (kz >= 0 && gx >= 0 && gy >= 0) v = field((long long)kz * plane + (long long)gy * g.nx + gx);
-      dst[sy][sx] = v;
-    }
+// <W, P> are those of the centred Z (Remark orthogonality), rho is corrected
+// by -mean(Z) sum(R), and the constant offset of U is removed at exit.
+struct FieldDirInt {
+  struct Raw {
+    float z;
+    int p;
   };
-
-  if (k0 < k1) {
-    if (has_z) load_plane(k0 - 1);
-    load_plane(k0);
-    for (int k = k0; k < k1; ++k) {
-      if (has_z) load_plane(k + 1);
-      __syncthreads();
-      if (active) {
-        const int(*cur)[SX] = ring[k & 3];
-        const int c = cur[ty + 1][tx + 1];
-        const int dx = 2 * c - cur[ty + 1][tx] - cur[ty + 1][tx + 2];
-        const int dy = 2 * c - cur[ty][tx + 1] - cur[ty + 2][tx + 1];
-        const int dz = has_z ? 2 * c - ring[(k - 1) & 3][ty + 1][tx + 1] - ring[(k + 1) & 3][ty + 1][tx + 1] : 0;
-        op((long long)k * plane + (long long)y * g.nx + x, c, dx, dy, dz, acc);
-      }
-    }
-  }
-  const int nblocks = gridDim.x * gridDim.y * gridDim.z;
-  const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-  grid_reduce<NQ>(acc, partials, ticket, nblocks, bid, fin);
-}
-
-struct FieldFixed {
   const float* __restrict__ z;
-  int k;
-  __device__ __forceinline__ int operator()(long long i) const { return f32_to_fixed(__ldg(z + i), k); }
-};
-
-struct OpDirectionFx {
-  const double* pold;
-  const double* wold;
-  double* p;
-  double* w;
-  double beta, ih0, ih1, ih2;
-  int first, e, uniform;
-  __device__ __forceinline__ void operator()(long long i, int c, int dx, int dy, int dz, double (&acc)[1]) {
-    const double zf = i32_to_f64_scaled(c, e);
-    double lz;
-    if (uniform) {
-      lz = i32_to_f64_scaled(dx + dy + dz, e);
-      if (ih0 != 1.0) lz *= ih0;
-    } else {
-      lz = fma(i32_to_f64_scaled(dx, e), ih0, i32_to_f64_scaled(dy, e) * ih1);
-      if (dz) lz = fma(i32_to_f64_scaled(dz, e), ih2, lz);
-    }
-    const double pv = first ? zf : fma(beta, __ldg(pold + i), zf);
-    const double wv = first ? lz : fma(beta, wold[i], lz);
-    p[i] = pv;
-    w[i] = wv;
-    acc[0] = fma(wv, pv, acc[0]);
+  const int* __restrict__ pold;
+  float bs;  // beta_s 2^-kp_{s-1} (0 for the first direction)
+  float sc;  // 2^kp_s
+  int kp, first;
+  __device__ __forceinline__ Raw load(unsigned i) const { return Raw{__ldg(z + i), first ? 0 : __ldg(pold + i)}; }
+  __device__ __forceinline__ int convert(Raw r) const {
+    const float v = fmaf(bs, i22_to_f32(r.p), r.z);
+    if (sc != 0.0f) return f32_to_i22(v, sc);
+    return f32_to_fixed(v, kp);  // 2^kp outside the FP32 range: integer path
   }
 };
 
-__global__ void __launch_bounds__(TX* TY) k_direction_fx(Geom g, int zchunk, const float* __restrict__ Z,
-                                                         const double* Pold, double* P, double* W, SolveState* st,
-                                                         double* partials) {
+struct OpDirInt {
+  using Pre = NoPre;
+  __device__ __forceinline__ NoPre load(unsigned) const { return NoPre{}; }
+  int* __restrict__ P;
+  SolveState* st;
+  int nx1, ny1, nz1;     // last index per axis
+  int endx, endy, endz;  // the axis' end ghost is not periodic: its edge is counted here
+  float w0, w1, w2;      // 1/h^2 per axis
+  float e;
+  int pm;
+  __device__ __forceinline__ void operator()(unsigned i, int x, int y, int k, NoPre, int c, int xl, int xr, int yl,
+                                             int yr, int zl, int zr) {
+    P[i] = c;
+    pm = max(pm, abs(c));
+    const float dx = i22_to_f32(c - xl), dy = i22_to_f32(c - yl), dz = i22_to_f32(c - zl);
+    float tx = dx * dx, ty = dy * dy, tz = dz * dz;
+    if (endx && x == nx1) {
+      const float d = i22_to_f32(c - xr);
+      tx = fmaf(d, d, tx);
+    }
+    if (endy && y == ny1) {
+      const float d = i22_to_f32(c - yr);
+      ty = fmaf(d, d, ty);
+    }
+    if (endz && k == nz1) {
+      const float d = i22_to_f32(c - zr);
+      tz = fmaf(d, d, tz);
+    }
+    e = fmaf(w0, tx, fmaf(w1, ty, fmaf(w2, tz, e)));
+  }
+  __device__ __forceinline__ void flush(double (&acc)[1]) {
+    acc[0] = f32_to_f64_int(e);
+    const unsigned long long m = block_max_u64((unsigned long long)pm);
+    if (threadIdx.x + threadIdx.y == 0) atomicMax(&st->pmax_bits, (unsigned)m);
+  }
+};
+
+__global__ void __launch_bounds__(TX* TY) k_direction_int(Geom g, const float* __restrict__ Z,
+                                                          const int* __restrict__ Pold, int* __restrict__ P,
+                                                          SolveState* st, double* partials) {
   if (st->done) return;
-  const int k = st->zfx_shift;
-  FieldFixed f{Z, k};
+  const int kp = st->kp_next;
+  const float sc = (kp >= -126 && kp <= 127) ? __int_as_float((kp + 127) << 23) : 0.0f;
   const bool has_z = g.nz > 1;
-  const int uniform = (g.ih2[0] == g.ih2[1]) && (!has_z || g.ih2[2] == g.ih2[0]);
-  OpDirectionFx op{Pold, W, P, W, st->beta, g.ih2[0], g.ih2[1], g.ih2[2], st->first, -k, uniform};
-  stencil_sweep_int<1>(g, zchunk, f, op, partials, &st->tickets[kTkDir],
-                       [st](const double(&s)[1]) { fin_direction(st, s); });
+  FieldDirInt f{Z, Pold, st->bs_next, sc, kp, st->first};
+  OpDirInt op{P,
+              st,
+              g.nx - 1,
+              g.ny - 1,
+              g.nz - 1,
+              g.bc[0] != kBcP,
+              g.bc[1] != kBcP,
+              has_z && g.bc[2] != kBcP,
+              g.ih2f[0],
+              g.ih2f[1],
+              g.ih2f[2],
+              0.0f,
+              0};
+  stencil_sweep_fx<int, 1>(g, f, op, partials, &st->tickets[kTkDir], [st, kp, g](const double(&s)[1]) {
+    st->kp = kp;
+    st->pmax = ldexp((double)atomicExch(&st->pmax_bits, 0u), -kp);
+    const double v[1] = {ldexp(s[0], -2 * kp)};
+    fin_direction(st, v, g);
+  });
 }
 
-// ------------------------------------------------------------------ streaming kernels
-// U += alpha P (line 12), R -= alpha W (line 13), low-precision copy of R,
-// ||R||^2 and sum(R) for the stop test and the centring correction of rho.
-// The two sums are accumulated per thread in FP32 from R * 2^lp_shift (exact
+// ------------------------------------------------------------------ update
+// U += alpha P and R -= alpha W (Algorithm 1), low-precision copy of R,
+// ||R||^2 and sum(R) for the stop test and the centring correction of rho,
+// and max|U| for the fixed-point residual check.  The two sums are
+// accumulated per thread in FP32 from R * 2^lp_shift (exact
 // power-of-two scaling, unit RMS) and combined across threads in FP64: they
-// only steer the stop test, which the FP64 true residual confirms.
-__device__ void fin_update(SolveState* st, const double (&s)[2], int shift, long long N) {
+// only steer the stop test, which the true residual confirms.
+__device__ void fin_update(SolveState* st, const double (&s)[2], int shift, const Geom& g) {
   const double rr = ldexp(s[0], -2 * shift), sumR = ldexp(s[1], -shift);
   st->rr = rr;
   st->sumR = sumR;
   st->iter += 1;
   st->zero_guess = 0;
-  advance_shift(st, rr, N);
+  st->umax = __longlong_as_double((long long)atomicExch(&st->umax_bits, 0ull));
+  plan_residual_check(st, g);
+  advance_shift(st, rr, g.N);
   if (!isfinite(rr)) {
     st->status = TPCG_ERR_BREAKDOWN;
     st->done = 1;
@@ -428,64 +586,154 @@ __device__ void fin_update(SolveState* st, const double (&s)[2], int shift, long
   if (rr <= st->tol2 || st->iter >= st->maxit) st->need_check = 1;
 }
 
-__global__ void __launch_bounds__(256) k_update(long long N, double* __restrict__ U, const double* __restrict__ P,
+// Mixed forms: W = L P from the exact integer stencil of P_int.
+struct FieldInt {
+  using Raw = int;
+  const int* __restrict__ p;
+  __device__ __forceinline__ int load(unsigned i) const { return __ldg(p + i); }
+  __device__ __forceinline__ int convert(int v) const { return v; }
+};
+
+template <bool ZG>  // ZG: the first update of a zero initial guess writes U = alpha P
+struct OpUpdateInt {
+  struct Pre {
+    double r, u;
+  };
+  __device__ __forceinline__ Pre load(unsigned i) const { return Pre{R[i], ZG ? 0.0 : U[i]}; }
+  double* __restrict__ U;
+  double* __restrict__ R;
+  LowPrec lp;
+  SolveState* st;
+  double alpha, na0, na1, na2;  // -alpha / h^2 per axis
+  int kp, shift, uniform;
+  float rr, sR;
+  unsigned long long um;
+  __device__ __forceinline__ void operator()(unsigned i, int, int, int, Pre pre, int c, int xl, int xr, int yl,
+                                             int yr, int zl, int zr) {
+    const int dx = 2 * c - xl - xr, dy = 2 * c - yl - yr, dz = 2 * c - zl - zr;
+    double r = pre.r;
+    if (uniform) {
+      r = fma(na0, i32_to_f64_scaled(dx + dy + dz, -kp), r);
+    } else {
+      r = fma(na0, i32_to_f64_scaled(dx, -kp), r);
+      r = fma(na1, i32_to_f64_scaled(dy, -kp), r);
+      if (dz) r = fma(na2, i32_to_f64_scaled(dz, -kp), r);
+    }
+    R[i] = r;
+    const float r32 = f64_to_f32_odd(r, shift);
+    store_lp(lp, i, r, r32);
+    rr = fmaf(r32, r32, rr);
+    sR += r32;
+    const double pv = i32_to_f64_scaled(c, -kp);
+    const double u = ZG ? alpha * pv : fma(alpha, pv, pre.u);
+    U[i] = u;
+    const unsigned long long ub = mag_key(u);
+    um = ub > um ? ub : um;
+  }
+  __device__ __forceinline__ void flush(double (&acc)[2]) {
+    acc[0] = f32_to_f64_int(rr);
+    acc[1] = f32_to_f64_int(sR);
+    fold_umax(st, um);
+  }
+};
+
+template <bool ZG>
+__global__ void __launch_bounds__(TX* TY, 4) k_update_int(Geom g, double* __restrict__ U,
+                                                          const int* __restrict__ P, double* __restrict__ R,
+                                                          LowPrec lp, SolveState* st, double* partials) {
+  if (st->done) return;
+  const double alpha = st->alpha;
+  const int shift = st->lp_shift;
+  FieldInt f{P};
+  OpUpdateInt<ZG> op{U,      R,     lp,        st,   alpha, st->nah[0], st->nah[1], st->nah[2],
+                     st->kp, shift, g.uniform, 0.0f, 0.0f,  0ull};
+  stencil_sweep_fx<int, 2>(g, f, op, partials, &st->tickets[kTkUpd],
+                           [st, shift, g](const double(&s)[2]) { fin_update(st, s, shift, g); });
+}
+
+// FP64 form: P and W = L P are stored by the direction kernel.
+__global__ void __launch_bounds__(256) k_update(Geom g, double* __restrict__ U, const double* __restrict__ P,
                                                 const double* __restrict__ W, double* __restrict__ R, LowPrec lp,
                                                 SolveState* st, double* partials) {
+  const long long N = g.N;
   if (st->done) return;
   const double alpha = st->alpha;
   const double nalpha = -alpha;
   const int zg = st->zero_guess;
   const int shift = st->lp_shift;
   float a0 = 0.0f, a1 = 0.0f;
+  unsigned long long um = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
     const double p = __ldg(P + i);
-    U[i] = zg ? alpha * p : fma(alpha, p, U[i]);
+    const double u = zg ? alpha * p : fma(alpha, p, U[i]);
+    U[i] = u;
+    const unsigned long long ub = mag_key(u);
+    um = ub > um ? ub : um;
     const double r = fma(nalpha, __ldg(W + i), R[i]);
     R[i] = r;
-    store_lp(lp, shift, i, r);
-    const float r32 = f64_to_f32_int(r, shift);
+    const float r32 = f64_to_f32_odd(r, shift);
+    store_lp(lp, i, r, r32);
     a0 = fmaf(r32, r32, a0);
     a1 += r32;
   }
-  double acc[2] = {(double)a0, (double)a1};
+  fold_umax(st, um);
+  double acc[2] = {f32_to_f64_int(a0), f32_to_f64_int(a1)};
   grid_reduce<2>(acc, partials, &st->tickets[kTkUpd], gridDim.x, blockIdx.x,
-                 [st, shift, N](const double(&s)[2]) { fin_update(st, s, shift, N); });
+                 [st, shift, g](const double(&s)[2]) { fin_update(st, s, shift, g); });
 }
 
-// R = eta_hat (zero initial guess: lines 3-4 with U_0 = 0).
+// ------------------------------------------------------------------ streaming kernels
+// R = eta_hat (zero initial guess: U_0 = 0 in Algorithm 1); ||eta_hat||^2 in
+// FP64 (it scales the tolerance and is reported), sum(R) in FP32 from
+// R * 2^lp_shift.
 __global__ void __launch_bounds__(256) k_init_zero(long long N, const double* __restrict__ eta,
                                                    double* __restrict__ R, LowPrec lp, SolveState* st,
                                                    double* partials) {
   const double mean = st->mean_eta;
   const int shift = st->lp_shift;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  double e2 = 0.0;
+  float a1 = 0.0f;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
     const double r = __ldg(eta + i) - mean;
     R[i] = r;
-    store_lp(lp, shift, i, r);
-    acc[0] = fma(r, r, acc[0]);
-    acc[1] += r;
+    const float r32 = f64_to_f32_odd(r, shift);
+    store_lp(lp, i, r, r32);
+    e2 = fma(r, r, e2);
+    a1 += r32;
   }
-  acc[2] = acc[0];
-  grid_reduce<4>(acc, partials, &st->tickets[kTkInit], gridDim.x, blockIdx.x,
-                 [st, N](const double(&s)[4]) { fin_init(st, s, N); });
+  double acc[2] = {e2, f32_to_f64_int(a1)};
+  grid_reduce<2>(acc, partials, &st->tickets[kTkInit], gridDim.x, blockIdx.x, [st, N, shift](const double(&s)[2]) {
+    const double v[3] = {s[0], ldexp(s[1], -shift), s[0]};
+    fin_init(st, v, N);
+  });
 }
 
 // sum(eta) and sum(eta^2): the mean removed by eq. (centering) when the
-// operator is singular, and the exponent of the first low-precision copy.
-__global__ void __launch_bounds__(256) k_eta_sum(long long N, const double* __restrict__ eta, SolveState* st,
-                                                 double* partials) {
+// operator is singular, and the exponent of the first low-precision copy;
+// with a given initial guess also max|U_0| for the fixed-point residual.
+__global__ void __launch_bounds__(256) k_eta_sum(Geom g, const double* __restrict__ eta,
+                                                 const double* __restrict__ U0, SolveState* st, double* partials) {
+  const long long N = g.N;
   double acc[2] = {0.0, 0.0};
+  unsigned long long um = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
     const double e = __ldg(eta + i);
     acc[0] += e;
     acc[1] = fma(e, e, acc[1]);
+    if (U0) {
+      const unsigned long long ub = mag_key(__ldg(U0 + i));
+      um = ub > um ? ub : um;
+    }
   }
-  grid_reduce<2>(acc, partials, &st->tickets[kTkEta], gridDim.x, blockIdx.x, [st, N](const double(&s)[2]) {
+  fold_umax(st, um);
+  grid_reduce<2>(acc, partials, &st->tickets[kTkEta], gridDim.x, blockIdx.x, [st, N, g](const double(&s)[2]) {
     const double mean = st->singular ? s[0] / (double)N : 0.0;
     st->mean_eta = mean;
     const double n2 = s[1] - mean * s[0];
+    st->eta_norm2 = n2 > 0.0 ? n2 : s[1];  // estimate; the initial residual kernel sets the exact value
     st->lp_shift = lp_shift_for(n2 > 0.0 ? n2 : s[1], N);
+    st->umax = __longlong_as_double((long long)atomicExch(&st->umax_bits, 0ull));
+    plan_residual_check(st, g);
   });
 }
 
@@ -519,7 +767,10 @@ __global__ void __launch_bounds__(256) k_to_lp(long long N, const double* __rest
                                                SolveState* st) {
   const int shift = st->lp_shift;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
-    store_lp(lp, shift, i, __ldg(r + i));
+  {
+    const double v = __ldg(r + i);
+    store_lp(lp, i, v, f64_to_f32_odd(v, shift));
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) st->lp_shift_applied = shift;
 }
 
@@ -535,11 +786,12 @@ __global__ void __launch_bounds__(256) k_f32_to_f64(long long N, const float* __
 __global__ void k_rhs_add_bc(Geom g, double* __restrict__ eta, double b0, double b1, double b2, double b3, double b4,
                              double b5) {
   const double bv[6] = {b0, b1, b2, b3, b4, b5};
-  const long long plane = (long long)g.nx * g.ny;
+  const unsigned plane = (unsigned)g.nx * (unsigned)g.ny;  // N <= 2^31: 32-bit index arithmetic
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N; i += (long long)gridDim.x * blockDim.x) {
-    const int k = (int)(i / plane);
-    const long long rem = i - (long long)k * plane;
-    const int y = (int)(rem / g.nx), x = (int)(rem - (long long)y * g.nx);
+    const unsigned ui = (unsigned)i;
+    const int k = (int)(ui / plane);
+    const unsigned rem = ui - (unsigned)k * plane;
+    const int y = (int)(rem / (unsigned)g.nx), x = (int)(rem - (unsigned)y * (unsigned)g.nx);
     const int pos[3] = {x, y, k};
     const int len[3] = {g.nx, g.ny, g.nz};
     double add = 0.0;
@@ -556,10 +808,26 @@ __global__ void k_rhs_add_bc(Geom g, double* __restrict__ eta, double b0, double
   }
 }
 
+
 // ------------------------------------------------------------------ host launchers
 void launch_apply_laplacian(const tpcg_plan* p, const Geom& g, const double* x, double* w) {
   LaunchScope ls(p, kKApply);
   k_apply_laplacian<<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, x, w);
+}
+// Persistent grids of the fixed-point sweeps: every SM holds as many blocks as
+// the kernel's resources allow (at most 8), no more blocks than (tile, plane)
+// pairs.
+int setup_fx_grids(tpcg_plan* p) {
+  const void* fns[kFxCount] = {(const void*)k_direction_int, (const void*)k_update_int<false>,
+                               (const void*)k_residual_fx<false>, (const void*)k_residual_fx<true>};
+  const long long T = (long long)((p->nx + TX - 1) / TX) * ((p->ny + TY - 1) / TY) * p->nz;
+  for (int i = 0; i < kFxCount; ++i) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[i], TX * TY, 0) != cudaSuccess) return -1;
+    per_sm = std::max(1, std::min(per_sm, 8));
+    p->fx_blocks[i] = (int)std::max(1LL, std::min<long long>(T, (long long)p->num_sms * per_sm));
+  }
+  return 0;
 }
 LowPrec lowprec(const tpcg_plan* p) { return LowPrec{p->d_Rlp, p->lp_kind, p->pitch16[0], p->nx}; }
 
@@ -568,37 +836,44 @@ void launch_init_residual(const tpcg_plan* p, const Geom& g, const double* eta, 
   if (zero_guess)
     k_init_zero<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, eta, p->d_R, lowprec(p), p->d_state, p->d_partials);
   else
-    k_init_residual<<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, eta, U, p->d_R, lowprec(p),
-                                                                p->d_state, p->d_partials);
+    k_residual_fx<true><<<p->fx_blocks[kFxInit], p->st_block, 0, p->stream>>>(g, eta, U, p->d_R, lowprec(p),
+                                                                               p->d_state, p->d_partials, 0);
 }
-void launch_eta_sum(const tpcg_plan* p, const Geom& g, const double* eta) {
+void launch_eta_sum(const tpcg_plan* p, const Geom& g, const double* eta, const double* U0) {
   LaunchScope ls(p, kKEtaSum);
-  k_eta_sum<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, eta, p->d_state, p->d_partials);
+  k_eta_sum<<<p->stream_blocks, 256, 0, p->stream>>>(g, eta, U0, p->d_state, p->d_partials);
 }
 void launch_norm_shift(const tpcg_plan* p, const Geom& g, const double* r) {
   LaunchScope ls(p, kKConvert);
   k_norm_shift<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, r, p->d_state, p->d_partials);
 }
+// P_k is written to d_P[k & 1]; P_{k-1} is read from the other buffer.
 void launch_direction(const tpcg_plan* p, const Geom& g, int k) {
   LaunchScope ls(p, kKDirection);
-  const double* pold = p->d_P[(k + 1) & 1];
-  double* pnew = p->d_P[k & 1];
   if (p->prec == TPCG_FP64)
-    k_direction<double><<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, (const double*)p->d_Z, pold, pnew,
-                                                                    p->d_W, p->d_state, p->d_partials);
+    k_direction<<<p->st_grid, p->st_block, 0, p->stream>>>(
+        g, p->st_zchunk, (const double*)p->d_Z, (const double*)p->d_P[(k + 1) & 1], (double*)p->d_P[k & 1], p->d_W,
+        p->d_state, p->d_partials);
   else
-    k_direction_fx<<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, (const float*)p->d_Z, pold, pnew,
-                                                               p->d_W, p->d_state, p->d_partials);
+    k_direction_int<<<p->fx_blocks[kFxDir], p->st_block, 0, p->stream>>>(
+        g, (const float*)p->d_Z, (const int*)p->d_P[(k + 1) & 1], (int*)p->d_P[k & 1], p->d_state, p->d_partials);
 }
-void launch_update(const tpcg_plan* p, const Geom& g, double* U, int k) {
+void launch_update(const tpcg_plan* p, const Geom& g, double* U, int k, bool zero_guess_first) {
   LaunchScope ls(p, kKUpdate);
-  k_update<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, U, p->d_P[k & 1], p->d_W, p->d_R, lowprec(p), p->d_state,
-                                                     p->d_partials);
+  if (p->prec == TPCG_FP64)
+    k_update<<<p->stream_blocks, 256, 0, p->stream>>>(g, U, (const double*)p->d_P[k & 1], p->d_W, p->d_R,
+                                                       lowprec(p), p->d_state, p->d_partials);
+  else if (zero_guess_first)  // first update of a zero initial guess: U = alpha P
+    k_update_int<true><<<p->fx_blocks[kFxUpd], p->st_block, 0, p->stream>>>(
+        g, U, (const int*)p->d_P[k & 1], p->d_R, lowprec(p), p->d_state, p->d_partials);
+  else
+    k_update_int<false><<<p->fx_blocks[kFxUpd], p->st_block, 0, p->stream>>>(
+        g, U, (const int*)p->d_P[k & 1], p->d_R, lowprec(p), p->d_state, p->d_partials);
 }
 void launch_true_residual(const tpcg_plan* p, const Geom& g, const double* eta, const double* U, bool force) {
   LaunchScope ls(p, kKTrueRes);
-  k_true_residual<<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, eta, U, p->d_R, lowprec(p), p->d_state,
-                                                              p->d_partials, force ? 1 : 0);
+  k_residual_fx<false><<<p->fx_blocks[kFxTrue], p->st_block, 0, p->stream>>>(g, eta, U, p->d_R, lowprec(p),
+                                                                              p->d_state, p->d_partials, force ? 1 : 0);
 }
 void launch_center_u(const tpcg_plan* p, const Geom& g, double* U) {
   LaunchScope ls(p, kKCenter);

@@ -1,7 +1,7 @@
 // FP64 form of the pseudoinverse preconditioner (Algorithm 7, Sec. 4.3.3):
 // six mode-product passes, each a GEMM that contracts the contiguous index of
 // its input against a dense l x l eigenbasis matrix, with the Hadamard
-// pseudoinverse G (Algorithm 5, lines 5-6) recomputed in the epilogue of the
+// pseudoinverse G (Algorithm 5) recomputed in the epilogue of the
 // last forward pass and the PCG reductions (<R, Z>, sum Z) fused into the
 // epilogue of the last backward pass.
 //

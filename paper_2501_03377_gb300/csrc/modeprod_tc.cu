@@ -9,11 +9,11 @@
 //               x 64-column K-tiles of the input through an NS-slot ring;
 //   warp 1      allocates TMEM; lane 0 issues tcgen05.mma (M = 128) and
 //               tcgen05.commit to release ring slots / publish accumulators;
-//   warps 2..5  epilogue: tcgen05.ld of the FP32 accumulator (one TMEM lane
+//   warps 2..9  epilogue: tcgen05.ld of the FP32 accumulator (one TMEM lane
 //               per thread), optional Hadamard scaling by G = 1/(lam_a +
-//               lam_b + lam_c) with the null index zeroed (Algorithm 5,
-//               lines 5-6), BF16 (or FP32) stores, and in the last pass the
-//               PCG reductions <R, Z> and sum Z.
+//               lam_b + lam_c) with the null index zeroed (Algorithm 5),
+//               FP16/BF16 (or FP32) stores, and in the last pass the PCG
+//               reductions <R, Z>, sum Z and max |Z|.
 // Two accumulator buffers in TMEM let the epilogue of tile i overlap the MMAs
 // of tile i+1.  Two operand forms keep the global stores coalesced:
 //   form 1: D[row][c'] = X[row][:] . W^T[c'][:]  (data = A, M = 128 rows,
@@ -261,9 +261,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = *tmem_holder;
   const int ntiles = (a.rows + kTileRows - 1) / kTileRows;
 
-  double red0 = 0.0;
-  float red1 = 0.0f;
+  // last pass: rho = <R, Z> from FP32 products of R * 2^shR (exact power-of-two scaling to unit RMS,
+  // one rounding) and Z, in compensated FP32 per thread; sum(Z) likewise; max |Z|
+  Acc32 red0, red1;
   float zmax = 0.0f;
+  const int shR = (FINAL && a.st) ? a.st->lp_shift_applied : 0;
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
@@ -372,7 +374,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           float v[16];
           tc_ld16(tacc + (uint32_t)c0, v);
           if (!valid) continue;
-          if (a.scale) {  // Algorithm 7 line 4: multiply by G = 1 / (lam_a + lam_b + lam_c)
+          if (a.scale) {  // Algorithm 7, Hadamard step: multiply by G = 1 / (lam_a + lam_b + lam_c)
             const float4* lc4 = reinterpret_cast<const float4*>(a.lamC + c0);
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
@@ -391,13 +393,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (vec && c0 + 16 <= a.Cout) {
             store16<OutT>(a.out, obase + c0, v);
             if (FINAL) {
+              float d0 = 0.0f, d1 = 0.0f;
 #pragma unroll
               for (int i = 0; i < 8; ++i) {
-                red0 = fma(rcur[i].x, f32_to_f64_int(v[2 * i]), red0);
-                red0 = fma(rcur[i].y, f32_to_f64_int(v[2 * i + 1]), red0);
-                red1 += v[2 * i] + v[2 * i + 1];
+                d0 = fmaf(f64_to_f32_int(rcur[i].x, shR), v[2 * i], d0);
+                d1 = fmaf(f64_to_f32_int(rcur[i].y, shR), v[2 * i + 1], d1);
                 zmax = fmaxf(zmax, fmaxf(fabsf(v[2 * i]), fabsf(v[2 * i + 1])));
               }
+              red0.add(d0 + d1);
+              red1.add(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) +
+                       (((v[8] + v[9]) + (v[10] + v[11])) + ((v[12] + v[13]) + (v[14] + v[15]))));
             }
           } else {
 #pragma unroll
@@ -407,8 +412,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const long long o = obase + (long long)c * a.oc;
                 store_out<OutT>(a.out, o, v[j]);
                 if (FINAL) {
-                  red0 = fma(__ldg(a.R + o), f32_to_f64_int(v[j]), red0);
-                  red1 += v[j];
+                  red0.add(f64_to_f32_int(__ldg(a.R + o), shR) * v[j]);
+                  red1.add(v[j]);
                   zmax = fmaxf(zmax, fabsf(v[j]));
                 }
               }
@@ -466,14 +471,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int w = 0; w < kThreads / 32; ++w) m = fmaxf(m, smax[w]);
       atomicMax(&a.st->zmax_bits, __float_as_uint(m));
     }
-    double acc[2] = {red0, (double)red1};
+    double acc[2] = {acc_value(red0), acc_value(red1)};
     SolveState* st = a.st;
     const long long N = a.N;
     grid_reduce<2>(acc, a.partials, &st->tickets[kTkPrec], gridDim.x, blockIdx.x,
-                   [st, N](const double(&s)[2]) {
-                     st->zfx_shift = fixed_shift_for(atomicExch(&st->zmax_bits, 0u));
-                     if (!st->timeout) fin_precond(st, N, s);
-                     else {
+                   [st, N, shR](const double(&s)[2]) {
+                     st->zmax = __uint_as_float(atomicExch(&st->zmax_bits, 0u));
+                     const double v[2] = {ldexp(s[0], -shR), s[1]};
+                     if (!st->timeout) {
+                       fin_precond(st, N, v);
+                       plan_next_direction(st);
+                     } else {
                        st->status = TPCG_ERR_TIMEOUT;
                        st->done = 1;
                      }

@@ -76,13 +76,14 @@ __global__ void __launch_bounds__(256) k_na_residual(Geom g, const double* __res
                                                      const double* __restrict__ ups, NoAllocScratch* s,
                                                      double* out) {
   const double mean = s->mean;
-  const long long plane = (long long)g.nx * g.ny;
+  const unsigned plane = (unsigned)g.nx * (unsigned)g.ny;  // N < 2^31: 32-bit index arithmetic
   const bool has_z = g.nz > 1;
   double acc[2] = {0.0, 0.0};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N; i += (long long)gridDim.x * blockDim.x) {
-    const int k = (int)(i / plane);
-    const long long rem = i - (long long)k * plane;
-    const int y = (int)(rem / g.nx), x = (int)(rem - (long long)y * g.nx);
+    const unsigned ui = (unsigned)i;
+    const int k = (int)(ui / plane);
+    const unsigned rem = ui - (unsigned)k * plane;
+    const int y = (int)(rem / (unsigned)g.nx), x = (int)(rem - (unsigned)y * (unsigned)g.nx);
     const double c = __ldg(ups + i);
     auto at = [&](int xx, int yy, int kk) {
       return (xx < 0 || yy < 0 || kk < 0) ? 0.0 : __ldg(ups + (long long)kk * plane + (long long)yy * g.nx + xx);
@@ -134,8 +135,11 @@ extern "C" int tpcg_residual_norms_noalloc(int nx, int ny, int nz, const int bc[
   for (int m = 0; m < 3; ++m) {
     g.bc[m] = (m < naxes) ? bc[m] : kBcN;
     g.ih2[m] = (m < naxes) ? 1.0 / (h[m] * h[m]) : 0.0;
+    g.ih2f[m] = (float)g.ih2[m];
+    g.nih2[m] = -g.ih2[m];
     if (m < naxes && !(bc[m] == kBcP || bc[m] == kBcN)) singular = false;
   }
+  g.uniform = (g.ih2[0] == g.ih2[1]) && (naxes == 2 || g.ih2[2] == g.ih2[0]);
   g.N = N;
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);

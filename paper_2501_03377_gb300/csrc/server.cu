@@ -140,7 +140,7 @@ void pinned_put(tpcg_server* s, size_t bytes, void* p) {
 size_t estimate_slot_bytes(const PlanKey& k) {
   const size_t N = (size_t)k.nx * k.ny * k.nz;
   const bool fp64 = (k.prec == TPCG_FP64);
-  size_t b = N * 8 * 4;                      // R, P[2], W
+  size_t b = N * 8 + (fp64 ? N * 8 * 3 : N * 4 * 2);  // R; P[2] and W (FP64) or P[2] in int32
   b += N * (fp64 ? 8 : 4);                   // Z
   b += fp64 ? 0 : N * 2 + (size_t)k.ny * k.nz * 16;  // low-precision copy of R (padded rows)
   b += 2 * N * (fp64 ? 8 : 2) + 2 * (size_t)(k.nx + k.ny + k.nz) * 64;  // mode-product intermediates

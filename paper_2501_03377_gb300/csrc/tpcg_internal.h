@@ -12,7 +12,7 @@ namespace tpcg {
 
 constexpr int kBcP = 0, kBcD = 1, kBcN = 2, kBcDN = 3, kBcND = 4;
 
-// FP64 eigenpairs of one axis (Algorithm 5, lines 2-4).  lam is divided by h^2.
+// FP64 eigenpairs of one axis (Algorithm 5).  lam is divided by h^2.
 struct AxisBasis {
   int len = 1;
   int bc = 0;
@@ -31,7 +31,7 @@ int build_axis(int len, int bc, double h, AxisBasis& ax);
 // One mode-product pass of Algorithm 7: for every row r = a*B + b of the
 // input (an A x B x C array with C contiguous, rows in_pitch elements apart)
 //     out[a*oa + b*ob + c'*oc] = sum_c X[r][c] * Wm[c][c']   (W = V or V^T),
-// optionally multiplied by the Hadamard pseudoinverse G (line 4).  The output
+// optionally multiplied by the Hadamard pseudoinverse G (Algorithm 7).  The output
 // strides place the next contraction index contiguously, so every pass
 // contracts a contiguous index.
 struct StageParams {
@@ -51,6 +51,9 @@ struct StageParams {
 struct SolveState;  // device-side scalars (tpcg_dev.cuh)
 
 // Kernel kinds for the launch counter and the optional event profiler.
+// Persistent fixed-point sweeps (grid size per kernel, from its occupancy).
+enum FxKernel { kFxDir = 0, kFxUpd, kFxTrue, kFxInit, kFxCount };
+
 enum KernelKind {
   kKEtaSum = 0, kKInit, kKDirection, kKUpdate, kKTrueRes, kKCenter, kKApply, kKModeF64, kKModeTC, kKConvert,
   kKindCount
@@ -69,7 +72,7 @@ struct Profiler {
 };
 
 // One PCG solve driven as a resumable job: job_start() enqueues the set-up
-// (Algorithm 1, lines 2-7) and the first chunk of iterations; whenever the
+// (Algorithm 1 set-up) and the first chunk of iterations; whenever the
 // plan's state event has completed, job_step() inspects the device state and
 // enqueues the next chunk or the exit work.  Many jobs on different plans (and
 // streams) can be driven by one host thread.
@@ -114,8 +117,8 @@ struct tpcg_plan {
 
   // device: PCG workspaces
   double* d_R = nullptr;
-  double* d_P[2] = {nullptr, nullptr};  // direction, ping-pong: the stencil of the new P reads the old one
-  double* d_W = nullptr;
+  void* d_P[2] = {nullptr, nullptr};  // direction, ping-pong (FP64, or int32 fixed point in the mixed forms)
+  double* d_W = nullptr;               // W = L P (FP64 form only)
   void* d_Z = nullptr;       // FP64 (FP64 form) or FP32 (mixed forms)
   void* d_Rlp = nullptr;     // BF16 / FP16 copy of R (mixed forms), row pitch pitch16[0]
   int lp_kind = 0;           // 0 none (FP64 form), 1 BF16, 2 FP16 scaled by 2^lp_shift
@@ -139,5 +142,6 @@ struct tpcg_plan {
   // launch configuration (fixed per plan so that reductions are reproducible)
   dim3 st_grid, st_block;   // stencil kernels
   int st_zchunk = 1;
+  int fx_blocks[4] = {1, 1, 1, 1};  // FxKernel -> blocks of the persistent fixed-point sweeps
   int stream_blocks = 0;    // streaming kernels
 };
