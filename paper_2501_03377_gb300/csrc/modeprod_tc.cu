@@ -38,13 +38,15 @@ namespace tpcg {
 
 namespace {
 
-constexpr int kThreads = 320;   // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
+constexpr int kThreads = 352;   // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue, warp 10 TMA of R (last pass)
 constexpr int kEpiThreads = 256;
+constexpr int kRSlots = 4;                 // R chunks in flight (last pass): two slots per epilogue half
+constexpr int kRBytes = 128 * 16 * 8;      // one chunk: 128 rows x 16 FP64 columns
 constexpr int kTileRows = 128;
 constexpr int kKTile = 64;                 // BF16 elements per 128-byte swizzle row
 constexpr int kStageBytes = kTileRows * 128;
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
-constexpr int kMaxSmem = 232448 - 2048;  // opt-in limit minus room for static shared memory
+constexpr int kMaxSmem = 232448 - 1024;  // opt-in limit minus room for static shared memory (560 B used)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -116,17 +118,23 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
+// TMEM -> registers, 16 columns of the thread's lane, in split form for
+// software pipelining: issue the load, do other work, then wait.  The wait names the destination registers as in/out
+// operands, so the compiler cannot read them before the load has landed.
+__device__ __forceinline__ void tc_ld16_issue(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
       "[%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
         "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tc_ld16_wait(uint32_t (&r)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
 }
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
@@ -153,6 +161,7 @@ struct TcArgs {
   long long oa, ob, oc;
   int scale, singular;
   int vec;   // 16-element runs of the output are contiguous and 16-byte aligned
+  int rtma;  // last pass: R arrives by TMA (rows of R share one pitch), else by global loads
   int last;  // last pass: output is Z (FP32), undo the FP16 scaling
   int sG;    // the Hadamard step is multiplied by 2^-sG (FP16 range), undone on Z
   float gscale;          // 2^-sG
@@ -213,7 +222,8 @@ __device__ __forceinline__ void store16(void* out, long long o, const float (&x)
 
 template <int FORM, class InT, class OutT, bool FINAL>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_modeprod_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW, TcArgs a) {
+    k_modeprod_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
+                  const __grid_constant__ CUtensorMap tmR, TcArgs a) {
   if (a.st && a.st->done) return;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -221,7 +231,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* sm = smem_raw + (base - raw);
   const uint32_t sV = base;
   const uint32_t sD = sV + (uint32_t)a.KT * a.VR * 128u;
-  uint8_t* barp = sm + (size_t)a.KT * a.VR * 128 + (size_t)a.NS * kStageBytes;
+  const bool rtma = FINAL && a.rtma;
+  const uint32_t sR = sD + (uint32_t)a.NS * kStageBytes;  // 1024-aligned: V and stages are multiples of 1 KB
+  uint8_t* barp = sm + (size_t)a.KT * a.VR * 128 + (size_t)a.NS * kStageBytes + (rtma ? (size_t)kRSlots * kRBytes : 0);
   const uint32_t bars = smem_u32(barp);
   const int NS = a.NS;
   auto full = [&](int s) { return bars + 8u * s; };
@@ -230,7 +242,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto tempty = [&](int b) { return bars + 8u * (2 * NS + 2 + b); };
   const uint32_t vbar = bars + 8u * (2 * NS + 4);
   const uint32_t drain = bars + 8u * (2 * NS + 5);
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(barp + 8 * (2 * NS + 6));
+  auto rfull = [&](int s) { return bars + 8u * (2 * NS + 6 + s); };
+  auto rempty = [&](int s) { return bars + 8u * (2 * NS + 6 + kRSlots + s); };
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(barp + 8 * (2 * NS + 6 + 2 * kRSlots));
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
   const Abort ab{abort_flag, a.err, a.st};
 
@@ -246,6 +260,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     mbar_init(vbar, 1);
     mbar_init(drain, 1);
+    for (int s = 0; s < kRSlots; ++s) {
+      mbar_init(rfull(s), 1);
+      mbar_init(rempty(s), kEpiThreads / 2);  // the four warps of one epilogue half
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -331,6 +349,36 @@ __global__ void __launch_bounds__(kThreads, 1)
     const unsigned long long t0 = gtimer();
     while (!mbar_try_wait(drain, 0) && gtimer() - t0 < kWaitLimitNs) {
     }
+  } else if (warp == 10) {
+    // ---------------- TMA of R (last pass): 16-column chunks of the tile's 128 rows.  Chunk ci belongs to
+    // epilogue half ci % 2, which consumes its chunks in order from its own two-slot ring (a ring shared
+    // by both halves would let one half run two phases ahead of a slot and read it early).
+    if (rtma && lane == 0) {
+      const int nchunk = (a.Np + 15) / 16;
+      const int Jh[2] = {(nchunk + 1) / 2, nchunk / 2};  // chunks per tile of each half
+      int issued[2] = {0, 0};
+      bool ok = true;
+      int tcnt = 0;
+      for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++tcnt) {
+        for (int ci = 0; ci < nchunk; ++ci) {
+          const int hh = ci & 1;
+          const int k = tcnt * Jh[hh] + (ci >> 1);
+          const int slot = 2 * hh + (k & 1);
+          if (!(ok = wait_bounded(rempty(slot), (uint32_t)(((k >> 1) & 1) ^ 1), ab))) break;
+          mbar_expect_tx(rfull(slot), kRBytes);
+          tma_load_2d(sR + (uint32_t)slot * kRBytes, &tmR, ci * 16, tile * kTileRows, rfull(slot));
+          issued[hh] = k + 1;
+        }
+      }
+      if (!ok) {  // every issued load completes before the CTA may exit
+        for (int hh = 0; hh < 2; ++hh)
+          for (int k = (issued[hh] > 2 ? issued[hh] - 2 : 0); k < issued[hh]; ++k) {
+            const unsigned long long t0 = gtimer();
+            while (!mbar_try_wait(rfull(2 * hh + (k & 1)), (uint32_t)((k >> 1) & 1)) && gtimer() - t0 < kWaitLimitNs) {
+            }
+          }
+      }
+    }
   } else if (warp >= 2) {
     // ---------------- epilogue: two warps per TMEM lane quadrant, each taking every other 16-column chunk
     const int q = warp & 3;          // TMEM lane quadrant this warp may access
@@ -343,7 +391,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t tacc = tmem + (uint32_t)(b * a.acc_cols) + ((uint32_t)(q * 32) << 16);
       const int row0 = tile * kTileRows;
       if (FORM == 1) {
-        // one thread per row; its 16 consecutive output columns are contiguous in memory (oc == 1)
+        // one thread per row; its 16 consecutive output columns are contiguous in memory (oc == 1).
+        // This warp takes the 16-column chunks c0 = h*16 + 32 j.  The TMEM load of chunk j+1 is
+        // issued before chunk j is processed; in the last pass the residual R of chunk j+2 is
+        // fetched while chunk j is processed.
         const int r = row0 + q * 32 + lane;
         const bool valid = r < a.rows;
         const int ia = valid ? r / a.B : 0;
@@ -353,27 +404,42 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool null_row = a.singular && ia == 0 && ib == 0;
         const float zs = (a.last && a.shift_src) ? ldexpf(1.0f, a.sG - *a.shift_src) : 1.0f;
         const bool vec = a.vec && valid;
-        // last pass: the residual R of the same 16 outputs is fetched one chunk ahead
-        double2 rnext[8];
-        if (FINAL && vec && h * 16 + 16 <= a.Cout) {
-          const double2* rp = reinterpret_cast<const double2*>(a.R + obase + h * 16);
+        const int J = (a.Np - h * 16 + 31) / 32;  // chunks of this warp (uniform across the warp)
+        auto col = [&](int j) { return h * 16 + 32 * j; };
+        const int trow = q * 32 + lane;  // row within the tile
+        // R chunk j of this warp staged by TMA: wait for it, read this row's 16 values (128-byte swizzle:
+        // 16-byte piece i of row r sits at piece i ^ (r % 8)), release the slot.
+        auto take_r = [&](int j, double2 (&rb)[8]) {
+          const int k = tcount * J + j;  // this half's chunk sequence number
+          const int slot = 2 * h + (k & 1);
+          if (!wait_bounded(rfull(slot), (uint32_t)((k >> 1) & 1), ab)) return false;
+          const uint32_t base = sR + (uint32_t)slot * kRBytes + (uint32_t)trow * 128u;
 #pragma unroll
-          for (int i = 0; i < 8; ++i) rnext[i] = __ldg(rp + i);
-        }
-        for (int c0 = h * 16; c0 < a.Np; c0 += 32) {
-          double2 rcur[8];
-          if (FINAL) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) rcur[i] = rnext[i];
-            if (vec && c0 + 48 <= a.Cout) {
-              const double2* rp = reinterpret_cast<const double2*>(a.R + obase + c0 + 32);
-#pragma unroll
-              for (int i = 0; i < 8; ++i) rnext[i] = __ldg(rp + i);
-            }
+          for (int i = 0; i < 8; ++i) {
+            double x, y;
+            asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];"
+                         : "=d"(x), "=d"(y)
+                         : "r"(base + (uint32_t)((i ^ (trow & 7)) << 4))
+                         : "memory");
+            rb[i] = make_double2(x, y);
           }
+          // the slot is next written by TMA (async proxy): order these generic-proxy reads before it
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          mbar_arrive(rempty(slot));
+          return true;
+        };
+        auto fetch_r = [&](int j, double2 (&rb)[8]) {
+          if (FINAL && !rtma && vec && j < J && col(j) + 16 <= a.Cout) {
+            const double2* rp = reinterpret_cast<const double2*>(a.R + obase + col(j));
+#pragma unroll
+            for (int i = 0; i < 8; ++i) rb[i] = __ldg(rp + i);
+          }
+        };
+        auto process = [&](int c0, const uint32_t (&t)[16], const double2 (&rcur)[8]) {
+          if (!valid) return;
           float v[16];
-          tc_ld16(tacc + (uint32_t)c0, v);
-          if (!valid) continue;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(t[i]);
           if (a.scale) {  // Algorithm 7, Hadamard step: multiply by G = 1 / (lam_a + lam_b + lam_c)
             const float4* lc4 = reinterpret_cast<const float4*>(a.lamC + c0);
 #pragma unroll
@@ -419,32 +485,83 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
             }
           }
+        };
+        uint32_t tA[16], tB[16];
+        double2 rA[8], rB[8];
+        if (rtma) {
+          bool ok = true;
+          for (int j = 0; ok && j < J; ++j) {
+            tc_ld16_issue(tacc + (uint32_t)col(j), tA);
+            ok = __all_sync(0xffffffffu, take_r(j, rA));  // warp-uniform: tcgen05.ld is .sync.aligned
+            tc_ld16_wait(tA);
+            if (ok) process(col(j), tA, rA);
+          }
+        } else {
+          if (J > 0) {
+            tc_ld16_issue(tacc + (uint32_t)col(0), tA);
+            fetch_r(0, rA);
+            fetch_r(1, rB);
+            tc_ld16_wait(tA);
+          }
+          for (int j = 0; j < J; j += 2) {
+            if (j + 1 < J) tc_ld16_issue(tacc + (uint32_t)col(j + 1), tB);
+            process(col(j), tA, rA);
+            fetch_r(j + 2, rA);
+            if (j + 1 < J) {
+              tc_ld16_wait(tB);
+              if (j + 2 < J) tc_ld16_issue(tacc + (uint32_t)col(j + 2), tA);
+              process(col(j + 1), tB, rB);
+              fetch_r(j + 3, rB);
+              if (j + 2 < J) tc_ld16_wait(tA);
+            }
+          }
         }
       } else {
-        // one thread per output index; its 16 consecutive rows are contiguous in memory (ob == 1)
-        for (int mb = 0; mb < a.MB; ++mb) {
+        // one thread per output index; its 16 consecutive rows are contiguous in memory (ob == 1).
+        // Chunks (M-block mb, rows c0 = h*16 + 32 j) in a fixed order, TMEM loads one chunk ahead.
+        const int per_mb = (kTileRows - h * 16 + 31) / 32;
+        const int J = a.MB * per_mb;
+        auto taddr = [&](int j) {
+          const int mb = j / per_mb, c0 = h * 16 + 32 * (j - mb * per_mb);
+          return tacc + (uint32_t)(mb * 128 + c0);
+        };
+        auto process = [&](int j, const uint32_t (&t)[16]) {
+          const int mb = j / per_mb, c0 = h * 16 + 32 * (j - mb * per_mb);
           const int c = mb * 128 + q * 32 + lane;
-          const bool cvalid = c < a.Cout;
-          for (int c0 = h * 16; c0 < kTileRows; c0 += 32) {
-            float v[16];
-            tc_ld16(tacc + (uint32_t)(mb * 128 + c0), v);
-            const int r0 = row0 + c0;
-            if (!cvalid || r0 >= a.rows) continue;
-            int ia = r0 / a.B;
-            int ib = r0 - ia * a.B;
-            if (a.vec && ib + 16 <= a.B && r0 + 16 <= a.rows) {
-              store16<OutT>(a.out, (long long)ia * a.oa + ib + (long long)c * a.oc, v);
-            } else {
+          const int r0 = row0 + c0;
+          if (c >= a.Cout || r0 >= a.rows) return;
+          float v[16];
 #pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                if (r0 + j < a.rows)
-                  store_out<OutT>(a.out, (long long)ia * a.oa + (long long)ib * a.ob + (long long)c * a.oc, v[j]);
-                if (++ib == a.B) {
-                  ib = 0;
-                  ++ia;
-                }
+          for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(t[i]);
+          int ia = r0 / a.B;
+          int ib = r0 - ia * a.B;
+          if (a.vec && ib + 16 <= a.B && r0 + 16 <= a.rows) {
+            store16<OutT>(a.out, (long long)ia * a.oa + ib + (long long)c * a.oc, v);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              if (r0 + i < a.rows)
+                store_out<OutT>(a.out, (long long)ia * a.oa + (long long)ib * a.ob + (long long)c * a.oc, v[i]);
+              if (++ib == a.B) {
+                ib = 0;
+                ++ia;
               }
             }
+          }
+        };
+        uint32_t tA[16], tB[16];
+        if (J > 0) {
+          tc_ld16_issue(taddr(0), tA);
+          tc_ld16_wait(tA);
+        }
+        for (int j = 0; j < J; j += 2) {
+          if (j + 1 < J) tc_ld16_issue(taddr(j + 1), tB);
+          process(j, tA);
+          if (j + 1 < J) {
+            tc_ld16_wait(tB);
+            if (j + 2 < J) tc_ld16_issue(taddr(j + 2), tA);
+            process(j + 1, tB);
+            if (j + 2 < J) tc_ld16_wait(tA);
           }
         }
       }
@@ -493,6 +610,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 struct TcStage {
   CUtensorMap tmX;
   CUtensorMap tmW;
+  CUtensorMap tmR;  // R (FP64) for the last pass of a solve; a copy of tmX when unused
   int form;
   TcArgs args;
   int grid;
@@ -519,6 +637,20 @@ EncodeTiledFn encoder() {
       fn = reinterpret_cast<EncodeTiledFn>(ptr);
   }
   return fn;
+}
+
+// FP64 rows of R, 16 x 128 boxes with the 128-byte swizzle (last pass).
+int encode_r(CUtensorMap* map, const double* gaddr, int inner, long long outer, long long pitch_elems) {
+  EncodeTiledFn cuTensorMapEncodeTiled = encoder();
+  if (!cuTensorMapEncodeTiled) return -1;
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+  cuuint64_t strides[1] = {(cuuint64_t)pitch_elems * 8};
+  cuuint32_t box[2] = {16, (cuuint32_t)kTileRows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = cuTensorMapEncodeTiled(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(gaddr), dims, strides,
+                                      box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : -1;
 }
 
 int encode_2d(CUtensorMap* map, const void* gaddr, int inner, long long outer, int pitch_elems, int box_inner,
@@ -556,7 +688,7 @@ int set_all_smem_attrs() {
 
 template <int FORM, class InT, class OutT, bool FINAL>
 void launch(const TcStage& s, const TcArgs& a, cudaStream_t stream) {
-  k_modeprod_tc<FORM, InT, OutT, FINAL><<<s.grid, kThreads, s.smem, stream>>>(s.tmX, s.tmW, a);
+  k_modeprod_tc<FORM, InT, OutT, FINAL><<<s.grid, kThreads, s.smem, stream>>>(s.tmX, s.tmW, s.tmR, a);
 }
 
 template <class InT>
@@ -649,11 +781,17 @@ int tc_plan_setup(tpcg_plan* p) {
     a.gscale = std::ldexp(1.0f, -sG);
     a.shift_src = tp->fp16 ? &p->d_state->lp_shift_applied : nullptr;
     const size_t vbytes = (size_t)a.KT * a.VR * 128;
-    const size_t fixed = 1024 + vbytes + 256;
+    size_t fixed = 1024 + vbytes + 256;
     if (a.tmem_cols > 512 || a.VR > 256 || fixed + 2 * kStageBytes > (size_t)kMaxSmem) {
       delete tp;
       return TPCG_ERR_UNSUPPORTED;
     }
+    // last pass of a solve: R by TMA when its rows share one pitch (16-byte multiple) and the ring fits
+    a.rtma = (sp.final_stage && st.form == 1 && sp.oa == (long long)sp.B * sp.ob && sp.ob % 2 == 0 &&
+              fixed + (size_t)kRSlots * kRBytes + 2 * kStageBytes <= (size_t)kMaxSmem)
+                 ? 1
+                 : 0;
+    if (a.rtma) fixed += (size_t)kRSlots * kRBytes;
     a.NS = (int)std::min<size_t>(8, (kMaxSmem - fixed) / kStageBytes);
     st.smem = fixed + (size_t)a.NS * kStageBytes;
     const int ntiles = (a.rows + kTileRows - 1) / kTileRows;
@@ -663,6 +801,11 @@ int tc_plan_setup(tpcg_plan* p) {
     const int wpitch = p->pitch16[sp.axis];
     if (encode_2d(&st.tmX, xin, sp.C, (long long)a.rows, sp.in_pitch, kKTile, kTileRows, tp->fp16) ||
         encode_2d(&st.tmW, p->d_Wt16[sp.axis][sp.dir], sp.C, sp.Cout, wpitch, kKTile, a.VR, tp->fp16)) {
+      delete tp;
+      return TPCG_ERR_CUDA;
+    }
+    st.tmR = st.tmX;
+    if (a.rtma && encode_r(&st.tmR, p->d_R, sp.Cout, (long long)a.rows, sp.ob)) {
       delete tp;
       return TPCG_ERR_CUDA;
     }
