@@ -225,6 +225,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_modeprod_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
                   const __grid_constant__ CUtensorMap tmR, TcArgs a) {
   if (a.st && a.st->done) return;
+  // Programmatic dependent launch: the next pass may start its prologue (barriers, TMEM, eigenbasis
+  // load) on SMs this grid frees; it waits (griddepcontrol.wait) before touching this pass's output.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -289,6 +292,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- TMA producer
     mbar_expect_tx(vbar, (uint32_t)a.KT * a.VR * 128u);
     for (int kt = 0; kt < a.KT; ++kt) tma_load_2d(sV + (uint32_t)kt * a.VR * 128u, &tmW, kt * kKTile, 0, vbar);
+    // the operand is the previous pass's output: wait until that grid has completed
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     int it = 0;
     for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
       for (int kt = 0; kt < a.KT; ++kt, ++it) {
@@ -354,6 +359,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // epilogue half ci % 2, which consumes its chunks in order from its own two-slot ring (a ring shared
     // by both halves would let one half run two phases ahead of a slot and read it early).
     if (rtma && lane == 0) {
+      asm volatile("griddepcontrol.wait;" ::: "memory");
       const int nchunk = (a.Np + 15) / 16;
       const int Jh[2] = {(nchunk + 1) / 2, nchunk / 2};  // chunks per tile of each half
       int issued[2] = {0, 0};
@@ -688,7 +694,17 @@ int set_all_smem_attrs() {
 
 template <int FORM, class InT, class OutT, bool FINAL>
 void launch(const TcStage& s, const TcArgs& a, cudaStream_t stream) {
-  k_modeprod_tc<FORM, InT, OutT, FINAL><<<s.grid, kThreads, s.smem, stream>>>(s.tmX, s.tmW, s.tmR, a);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)s.grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = s.smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // see griddepcontrol in the kernel
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_modeprod_tc<FORM, InT, OutT, FINAL>, s.tmX, s.tmW, s.tmR, a);
 }
 
 template <class InT>
