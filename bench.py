@@ -283,22 +283,53 @@ def run_batched(prec, torch):
             "mean_iters": float(np.mean([i["iters"] for i in infos]))}
 
 
-def kernel_work(kind, plan_prec, N, dims, iters_total, applies_total, ztype_bytes):
-    """Algorithmic work of one kernel kind over the timed region: (amount, unit, bound)."""
+def kernel_work(kind, plan_prec, N, dims, iters_total, applies_total, solves, checks_total):
+    """Algorithmic work of one kernel kind over the timed region: (amount, unit, bound).
+
+    Bytes are the data each kernel must move once per grid point (halo re-reads and
+    reduction scratch excluded); flops are the FP64 operations of the FP64 form."""
     n, q, t = dims
+    mixed = plan_prec != "fp64"
     if kind == "modeprod_f64":
         return applies_total * 4.0 * N * (n + q + t + 0.25) / 1e12, "TFLOP", "alu"
     if kind == "modeprod_tc":
-        # HBM bytes per application (3D): BF16 in + BF16 out for passes 1-5 (4N each), pass 6 reads
-        # BF16 (2N) and R in FP64 (8N) and writes Z in FP32 (4N)
+        # per application (3D): passes 1-5 read + write FP16/BF16 (4 B each); the last pass reads
+        # FP16 (2 B) and R in FP64 (8 B) and writes Z in FP32 (4 B)
         per_apply = (5 * 4 + 14) * N if t > 1 else (3 * 4 + 14) * N
         return applies_total * per_apply / 1e9, "GB", "hbm"
     if kind == "direction":
-        # FP64 flops per point: P = (Z - m) + beta P_old (3), 7-point stencil (7), <W, P> (2)
+        if mixed:  # Z (FP32) + P_old (int32) in, P (int32) out
+            return iters_total * 12.0 * N / 1e9, "GB", "hbm"
+        # FP64 form: FP64 flops per point: P = (Z - m) + beta P_old (3), 7-point stencil (7), <W, P> (2)
         return iters_total * 12.0 * N / 1e12, "TFLOP", "alu"
     if kind == "update":
-        return iters_total * (8 * 4 + 8 * 2 + (2 if plan_prec != "fp64" else 0)) * N / 1e9, "GB", "hbm"
+        # mixed: P (4) + R (8+8) + U (8+8) + FP16 copy of R (2); FP64 form: P and W (8+8) + R + U
+        per = (4 + 16 + 16 + 2) if mixed else (16 + 16 + 16)
+        return iters_total * per * N / 1e9, "GB", "hbm"
+    if kind == "true_residual":
+        # eta (8) + U (8) in, R (8) + FP16 copy (2, mixed) out
+        return checks_total * (24 + (2 if mixed else 0)) * N / 1e9, "GB", "hbm"
+    if kind == "eta_sum":
+        return solves * 8.0 * N / 1e9, "GB", "hbm"
+    if kind == "init_residual":  # zero initial guess: eta in, R (+ FP16 copy) out
+        return solves * (16 + (2 if mixed else 0)) * N / 1e9, "GB", "hbm"
+    if kind == "center":
+        return solves * 16.0 * N / 1e9, "GB", "hbm"
     return None, None, None
+
+
+def max_over_ranks(x, world, torch, device):
+    """Largest value of a per-rank float over all ranks (the whole-job clock is the slowest rank)."""
+    if world <= 1:
+        return float(x)
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps, seconds):
+    """Units all ranks processed per second of the slowest rank (weak scaling: `steps` per rank)."""
+    return world * steps / seconds
 
 
 def run_ours(args, rank, world, torch):
@@ -333,12 +364,8 @@ def run_ours(args, rank, world, torch):
     iters_total = sum(i["iters"] for (_, i) in infos)
     applies_total = sum(i["precond_applies"] for (_, i) in infos)
 
-    # max over ranks
-    if world > 1:
-        t = torch.tensor([dt], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dt = float(t.item())
-    value = world * args.steps / dt
+    dt = max_over_ranks(dt, world, torch, dev)
+    value = whole_job_rate(world, args.steps, dt)
 
     # instrumented pass (same steps): per-kernel device time with CUDA events on the plan's stream
     plan.profile_begin()
@@ -349,22 +376,31 @@ def run_ours(args, rank, world, torch):
     total_k = sum(v["total_ms"] for v in kstats.values()) or 1.0
     kernels = {k: {"launches": v["launches"], "ms": round(v["total_ms"], 4),
                    "share": round(v["total_ms"] / total_k, 4)} for k, v in sorted(kstats.items(), key=lambda kv: -kv[1]["total_ms"])}
+    p_checks = sum(i.get("checks", 0) for (_, i) in pinfos)
     dom = max(kstats, key=lambda k: kstats[k]["total_ms"])
-    amount, unit, bound = kernel_work(dom, prec, N, (nx, ny, nz), p_iters, p_applies, 4)
-    roofline = None
-    if amount is not None:
-        secs = kstats[dom]["total_ms"] / 1e3
+
+    def roof(kind):
+        amount, unit, bound = kernel_work(kind, prec, N, (nx, ny, nz), p_iters, p_applies, args.steps, p_checks)
+        if amount is None:
+            return None
+        secs = kstats[kind]["total_ms"] / 1e3
+        achieved = amount / secs
         if unit == "TFLOP":
-            achieved = amount / secs
             peak = FP64_PEAK_TFLOPS if bound == "alu" else bf16_sus
-            roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                        "frac": achieved / peak, "traffic": None,
-                        "peak_source": "derived FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz" if bound == "alu"
-                        else f"{peak_src} bf16 sustained"}
-        else:
-            achieved = amount / secs
-            roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                        "frac": achieved / hbm_peak, "traffic": None, "peak_source": f"{peak_src} hbm_gbs"}
+            return {"kernel": kind, "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "peak_source": "derived FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz" if bound == "alu"
+                    else f"{peak_src} bf16 sustained"}
+        return {"kernel": kind, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "peak_source": f"{peak_src} hbm_gbs"}
+
+    roofline = roof(dom)
+    for k in kernels:
+        r = roof(k)
+        if r is not None:
+            kernels[k]["achieved"] = round(r["achieved"], 2)
+            kernels[k]["unit"] = r["unit"]
+            kernels[k]["frac"] = round(r["frac"], 4)
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     eh = [torch.from_numpy(w["eta"].copy()).pin_memory() for w in ws]
@@ -381,11 +417,8 @@ def run_ours(args, rank, world, torch):
     e1.record()
     torch.cuda.synchronize()
     e2e_dt = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        t = torch.tensor([e2e_dt], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_dt = float(t.item())
-    e2e = {"value": world * args.steps / e2e_dt, "unit": "solves/s", "h2d_bytes_per_step": 8 * N,
+    e2e_dt = max_over_ranks(e2e_dt, world, torch, dev)
+    e2e = {"value": whole_job_rate(world, args.steps, e2e_dt), "unit": "solves/s", "h2d_bytes_per_step": 8 * N,
            "d2h_bytes_per_step": 8 * N}
 
     # the BF16 mixed form, same workload and timing rules
@@ -395,7 +428,8 @@ def run_ours(args, rank, world, torch):
         for s in range(args.warmup):
             pb.solve(etas[s % 4], ups, tol=args.tol, maxit=60, zero_guess=True)
         dtb, infb, _ = time_steps(pb, etas, ups, args.steps, args.tol, torch, barrier)
-        bf16_cmp = {"value": world * args.steps / dtb, "unit": "solves/s", "steps": args.steps,
+        dtb = max_over_ranks(dtb, world, torch, dev)
+        bf16_cmp = {"value": whole_job_rate(world, args.steps, dtb), "unit": "solves/s", "steps": args.steps,
                     "iters_per_solve": sum(i["iters"] for (_, i) in infb) / args.steps,
                     "worst_rel_res_true": max(i["rel_res_true"] for (_, i) in infb)}
         pb.close()
@@ -408,7 +442,8 @@ def run_ours(args, rank, world, torch):
             p64.solve(etas[s % 4], ups, tol=args.tol, maxit=60, zero_guess=True)
         k64 = max(3, min(args.steps, 6))
         dt64, inf64, _ = time_steps(p64, etas, ups, k64, args.tol, torch, barrier)
-        fp64_cmp = {"value": world * k64 / dt64, "unit": "solves/s", "steps": k64,
+        dt64 = max_over_ranks(dt64, world, torch, dev)
+        fp64_cmp = {"value": whole_job_rate(world, k64, dt64), "unit": "solves/s", "steps": k64,
                     "iters_per_solve": sum(i["iters"] for (_, i) in inf64) / k64,
                     "worst_rel_res_true": max(i["rel_res_true"] for (_, i) in inf64)}
         p64.close()

@@ -93,6 +93,8 @@ typedef struct {
   double eta_norm;          /* ||eta_hat||_2                                        */
   double removed_mean;      /* mean removed from eta (singular operators), else 0   */
   double null_component;    /* mean removed from ups at exit (singular), else 0     */
+  int    checks;            /* evaluations of the true residual (stop-test checks   */
+                            /* behind Remark stoppincrit, plus the exit report)     */
 } tpcg_info;
 
 /* Create a plan for an nx x ny x nz grid (eq. lap1d requires n >= 3 on every

@@ -51,6 +51,7 @@ class tpcg_info(ctypes.Structure):
         ("eta_norm", ctypes.c_double),
         ("removed_mean", ctypes.c_double),
         ("null_component", ctypes.c_double),
+        ("checks", ctypes.c_int),
     ]
 
     def as_dict(self):

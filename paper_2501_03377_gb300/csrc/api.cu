@@ -323,6 +323,7 @@ int job_step(SolveJob& j) {
     info.rel_res_recur = (en == 0.0) ? 0.0 : sqrt(hs->rr) / en;
     info.removed_mean = p->singular ? hs->mean_eta : 0.0;
     info.null_component = (p->singular && j.done_host != 2) ? hs->sumU / (double)p->N : 0.0;
+    info.checks = hs->checks;
     j.status = status;
     j.phase = 3;
   }

@@ -413,6 +413,7 @@ __global__ void __launch_bounds__(TX* TY) k_residual_fx(Geom g, const double* __
       [st, force, N, sr, ku, finite_u](const double(&s)[4]) {
         const double rr = finite_u ? ldexp(s[0], -2 * sr) : __longlong_as_double(0x7ff8000000000000ll);
         const double sumR = ldexp(s[1], -sr), sumU = ldexp(s[2], 8 - ku);
+        if (!INIT) st->checks += 1;
         if (INIT) {
           const double v[3] = {rr, sumR, s[3]};
           fin_init(st, v, N);

@@ -36,6 +36,7 @@ struct SolveState {
   int zero_guess;      // U_0 = 0: the first update writes U instead of adding
   int singular;
   int precond_applies;
+  int checks;          // true-residual evaluations
   int timeout;         // a bounded device wait gave up
   unsigned zmax_bits;  // max |Z| accumulator of the preconditioner output (FP32 bits; atomicMax)
   float zmax;          // max |Z| of the current preconditioner output
