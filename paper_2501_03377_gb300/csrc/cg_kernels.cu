@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(TX* TY) k_direction(Geom g, int zchunk, const 
 
 // ------------------------------------------------------------------ direction, mixed forms
 // Z arrives in FP32.  The direction is stored as exact fixed point
-//     P_s = 2^-kp P_int,   P_int = round((Z_s + beta_s P_{s-1}) 2^kp),  |P_int| <= 2^27,
+//     P_s = 2^-kp P_int,   P_int = round((Z_s + beta_s P_{s-1}) 2^kp),  |P_int| <= 2^20,
 // (Algorithm 1), with kp from the bound max|Z_s| + |beta_s| max|P_{s-1}|.
 // W_s = L P_s is never stored: it is an exact integer stencil of
 // P_int, recomputed where it is needed, so U += alpha P and R -= alpha W stay
@@ -479,83 +479,91 @@ __global__ void __launch_bounds__(TX* TY) k_direction(Geom g, int zchunk, const 
 // keeps the constant (null-space) component of Z: L annihilates it, so W and
 // <W, P> are those of the centred Z (Remark orthogonality), rho is corrected
 // by -mean(Z) sum(R), and the constant offset of U is removed at exit.
-struct FieldDirInt {
-  struct Raw {
-    float z;
-    int p;
-  };
-  const float* __restrict__ z;
-  const int* __restrict__ pold;
-  float bs;  // beta_s 2^-kp_{s-1} (0 for the first direction)
-  float sc;  // 2^kp_s
-  int kp, first;
-  __device__ __forceinline__ Raw load(unsigned i) const { return Raw{__ldg(z + i), first ? 0 : __ldg(pold + i)}; }
-  __device__ __forceinline__ int convert(Raw r) const {
-    const float v = fmaf(bs, i22_to_f32(r.p), r.z);
-    if (sc != 0.0f) return f32_to_i22(v, sc);
-    return f32_to_fixed(v, kp);  // 2^kp outside the FP32 range: integer path
+// Register-window streams.  Thread (tx, ty) of a 32 x 8 block owns the grid
+// column (x, y) of a tile and marches in z: its z neighbours stay in
+// registers, x neighbours come from the neighbouring lanes by warp shuffle
+// (lanes 0 and 31 fetch the tile's halo column themselves), y neighbours from
+// loads of the rows the other warps stream (cache hits).  No shared memory and
+// no block barrier per plane.  Blocks take balanced contiguous ranges of
+// (tile, plane) pairs, walked as runs of consecutive planes of one tile.
+// Ghosts: ghost_index() maps a neighbour across a boundary to the wrapped
+// index (P), the point itself (N: mirror) or -1 (D: the value 0).
+template <class Run>
+__device__ __forceinline__ void for_each_run(const Geom& g, Run run) {
+  const unsigned bxn = (unsigned)(g.nx + TX - 1) / TX, byn = (unsigned)(g.ny + TY - 1) / TY;
+  const unsigned T = bxn * byn * (unsigned)g.nz;
+  const unsigned G = gridDim.x, q = T / G, rm = T - q * G;
+  const unsigned t_begin = blockIdx.x * q + min(blockIdx.x, rm);
+  const unsigned t_end = t_begin + q + (blockIdx.x < rm ? 1u : 0u);
+  for (unsigned t = t_begin; t < t_end;) {
+    const unsigned tile = t / (unsigned)g.nz;
+    const int k0 = (int)(t - tile * (unsigned)g.nz);
+    const int k1 = (int)min((unsigned)g.nz, (unsigned)k0 + (t_end - t));
+    t += (unsigned)(k1 - k0);
+    const unsigned tyi = tile / bxn;
+    run((int)(tile - tyi * bxn) * TX, (int)tyi * TY, k0, k1);
   }
-};
-
-struct OpDirInt {
-  using Pre = NoPre;
-  __device__ __forceinline__ NoPre load(unsigned) const { return NoPre{}; }
-  int* __restrict__ P;
-  SolveState* st;
-  int nx1, ny1, nz1;     // last index per axis
-  int endx, endy, endz;  // the axis' end ghost is not periodic: its edge is counted here
-  float w0, w1, w2;      // 1/h^2 per axis
-  float e;
-  int pm;
-  __device__ __forceinline__ void operator()(unsigned i, int x, int y, int k, NoPre, int c, int xl, int xr, int yl,
-                                             int yr, int zl, int zr) {
-    P[i] = c;
-    pm = max(pm, abs(c));
-    const float dx = i22_to_f32(c - xl), dy = i22_to_f32(c - yl), dz = i22_to_f32(c - zl);
-    float tx = dx * dx, ty = dy * dy, tz = dz * dz;
-    if (endx && x == nx1) {
-      const float d = i22_to_f32(c - xr);
-      tx = fmaf(d, d, tx);
-    }
-    if (endy && y == ny1) {
-      const float d = i22_to_f32(c - yr);
-      ty = fmaf(d, d, ty);
-    }
-    if (endz && k == nz1) {
-      const float d = i22_to_f32(c - zr);
-      tz = fmaf(d, d, tz);
-    }
-    e = fmaf(w0, tx, fmaf(w1, ty, fmaf(w2, tz, e)));
-  }
-  __device__ __forceinline__ void flush(double (&acc)[1]) {
-    acc[0] = f32_to_f64_int(e);
-    const unsigned long long m = block_max_u64((unsigned long long)pm);
-    if (threadIdx.x + threadIdx.y == 0) atomicMax(&st->pmax_bits, (unsigned)m);
-  }
-};
+}
 
 __global__ void __launch_bounds__(TX* TY) k_direction_int(Geom g, const float* __restrict__ Z,
                                                           const int* __restrict__ Pold, int* __restrict__ P,
                                                           SolveState* st, double* partials) {
   if (st->done) return;
   const int kp = st->kp_next;
-  const float sc = (kp >= -126 && kp <= 127) ? __int_as_float((kp + 127) << 23) : 0.0f;
+  const float sc = (kp >= -126 && kp <= 127) ? __int_as_float((kp + 127) << 23) : 0.0f;  // 2^kp
+  const float bs = st->bs_next;  // beta_s 2^-kp_{s-1} (0 for the first direction)
+  const int first = st->first;
+  const unsigned nx = (unsigned)g.nx, plane = (unsigned)g.nx * (unsigned)g.ny;
   const bool has_z = g.nz > 1;
-  FieldDirInt f{Z, Pold, st->bs_next, sc, kp, st->first};
-  OpDirInt op{P,
-              st,
-              g.nx - 1,
-              g.ny - 1,
-              g.nz - 1,
-              g.bc[0] != kBcP,
-              g.bc[1] != kBcP,
-              has_z && g.bc[2] != kBcP,
-              g.ih2f[0],
-              g.ih2f[1],
-              g.ih2f[2],
-              0.0f,
-              0};
-  stencil_sweep_fx<int, 1>(g, f, op, partials, &st->tickets[kTkDir], [st, kp, g](const double(&s)[1]) {
+  // P_int at grid index i, formed from Z_s and P_{s-1}
+  auto form = [&](unsigned i) -> int {
+    const float v = fmaf(bs, i22_to_f32(first ? 0 : __ldg(Pold + i)), __ldg(Z + i));
+    return sc != 0.0f ? f32_to_i22(v, sc) : f32_to_fixed(v, kp);  // 2^kp outside the FP32 range: integer path
+  };
+  // the end edge of an axis counts only for a Dirichlet end (ghost 0; a Neumann ghost gives a zero edge)
+  const bool endx = g.bc[0] == kBcD || g.bc[0] == kBcND, endy = g.bc[1] == kBcD || g.bc[1] == kBcND;
+  const bool endz = has_z && (g.bc[2] == kBcD || g.bc[2] == kBcND);
+  const float w0 = g.ih2f[0], w1 = g.ih2f[1], w2 = g.ih2f[2];
+  const int lane = threadIdx.x;
+  float e = 0.0f;
+  int pm = 0;
+  for_each_run(g, [&](int bx0, int by0, int k0, int k1) {
+    const int x = bx0 + lane, y = by0 + threadIdx.y;
+    const bool active = x < g.nx && y < g.ny;
+    const int xg = ghost_index(x - 1, g.nx, g.bc[0]);  // used by lane 0 (the tile's left halo)
+    const int yg = ghost_index(y - 1, g.ny, g.bc[1]);
+    const unsigned col = (unsigned)y * nx + (unsigned)x;
+    int zprev = 0;
+    if (has_z && active) {
+      const int kz = ghost_index(k0 - 1, g.nz, g.bc[2]);
+      zprev = kz >= 0 ? form((unsigned)kz * plane + col) : 0;
+    }
+    for (int k = k0; k < k1; ++k) {
+      const unsigned base = (unsigned)k * plane;
+      const int c = active ? form(base + col) : 0;
+      int xl = __shfl_up_sync(0xffffffffu, c, 1);
+      if (lane == 0) xl = (active && xg >= 0) ? form(base + (unsigned)y * nx + (unsigned)xg) : 0;
+      const int yl = (active && yg >= 0) ? form(base + (unsigned)yg * nx + (unsigned)x) : 0;
+      const int zl = has_z ? zprev : c;
+      if (active) {
+        P[base + col] = c;
+        pm = max(pm, abs(c));
+        const float dx = i22_to_f32(c - xl), dy = i22_to_f32(c - yl), dz = i22_to_f32(c - zl);
+        float tx = dx * dx, ty = dy * dy, tz = dz * dz;
+        const float cf = i22_to_f32(c);
+        if (endx && x == g.nx - 1) tx = fmaf(cf, cf, tx);
+        if (endy && y == g.ny - 1) ty = fmaf(cf, cf, ty);
+        if (endz && k == g.nz - 1) tz = fmaf(cf, cf, tz);
+        e = fmaf(w0, tx, fmaf(w1, ty, fmaf(w2, tz, e)));
+      }
+      zprev = c;
+    }
+  });
+  double acc[1] = {f32_to_f64_int(e)};
+  const unsigned long long m = block_max_u64((unsigned long long)pm);
+  if (threadIdx.x + threadIdx.y == 0) atomicMax(&st->pmax_bits, (unsigned)m);
+  const int nblocks = gridDim.x;
+  grid_reduce<1>(acc, partials, &st->tickets[kTkDir], nblocks, blockIdx.x, [st, kp, g](const double(&s)[1]) {
     st->kp = kp;
     st->pmax = ldexp((double)atomicExch(&st->pmax_bits, 0u), -kp);
     const double v[1] = {ldexp(s[0], -2 * kp)};
@@ -587,69 +595,107 @@ __device__ void fin_update(SolveState* st, const double (&s)[2], int shift, cons
   if (rr <= st->tol2 || st->iter >= st->maxit) st->need_check = 1;
 }
 
-// Mixed forms: W = L P from the exact integer stencil of P_int.
-struct FieldInt {
-  using Raw = int;
-  const int* __restrict__ p;
-  __device__ __forceinline__ int load(unsigned i) const { return __ldg(p + i); }
-  __device__ __forceinline__ int convert(int v) const { return v; }
-};
-
-template <bool ZG>  // ZG: the first update of a zero initial guess writes U = alpha P
-struct OpUpdateInt {
-  struct Pre {
-    double r, u;
-  };
-  __device__ __forceinline__ Pre load(unsigned i) const { return Pre{R[i], ZG ? 0.0 : U[i]}; }
-  double* __restrict__ U;
-  double* __restrict__ R;
-  LowPrec lp;
-  SolveState* st;
-  double alpha, na0, na1, na2;  // -alpha / h^2 per axis
-  int kp, shift, uniform;
-  float rr, sR;
-  unsigned long long um;
-  __device__ __forceinline__ void operator()(unsigned i, int, int, int, Pre pre, int c, int xl, int xr, int yl,
-                                             int yr, int zl, int zr) {
-    const int dx = 2 * c - xl - xr, dy = 2 * c - yl - yr, dz = 2 * c - zl - zr;
-    double r = pre.r;
-    if (uniform) {
-      r = fma(na0, i32_to_f64_scaled(dx + dy + dz, -kp), r);
-    } else {
-      r = fma(na0, i32_to_f64_scaled(dx, -kp), r);
-      r = fma(na1, i32_to_f64_scaled(dy, -kp), r);
-      if (dz) r = fma(na2, i32_to_f64_scaled(dz, -kp), r);
-    }
-    R[i] = r;
-    const float r32 = f64_to_f32_odd(r, shift);
-    store_lp(lp, i, r, r32);
-    rr = fmaf(r32, r32, rr);
-    sR += r32;
-    const double pv = i32_to_f64_scaled(c, -kp);
-    const double u = ZG ? alpha * pv : fma(alpha, pv, pre.u);
-    U[i] = u;
-    const unsigned long long ub = mag_key(u);
-    um = ub > um ? ub : um;
-  }
-  __device__ __forceinline__ void flush(double (&acc)[2]) {
-    acc[0] = f32_to_f64_int(rr);
-    acc[1] = f32_to_f64_int(sR);
-    fold_umax(st, um);
-  }
-};
-
+// Mixed forms: W = L P from the exact integer stencil of P_int, in a
+// register-window stream (see k_direction_int).  The loads of plane k+1 (P
+// two planes ahead, the y neighbours, R and U) are issued before plane k is
+// processed.  ZG: the first update of a zero initial guess writes U = alpha P.
 template <bool ZG>
 __global__ void __launch_bounds__(TX* TY, 4) k_update_int(Geom g, double* __restrict__ U,
                                                           const int* __restrict__ P, double* __restrict__ R,
                                                           LowPrec lp, SolveState* st, double* partials) {
   if (st->done) return;
   const double alpha = st->alpha;
+  const double na0 = st->nah[0], na1 = st->nah[1], na2 = st->nah[2];  // -alpha / h^2 per axis
+  const int kp = st->kp;
   const int shift = st->lp_shift;
-  FieldInt f{P};
-  OpUpdateInt<ZG> op{U,      R,     lp,        st,   alpha, st->nah[0], st->nah[1], st->nah[2],
-                     st->kp, shift, g.uniform, 0.0f, 0.0f,  0ull};
-  stencil_sweep_fx<int, 2>(g, f, op, partials, &st->tickets[kTkUpd],
-                           [st, shift, g](const double(&s)[2]) { fin_update(st, s, shift, g); });
+  const unsigned nx = (unsigned)g.nx, plane = (unsigned)g.nx * (unsigned)g.ny;
+  const bool has_z = g.nz > 1;
+  const int lane = threadIdx.x;
+  float rr = 0.0f, sR = 0.0f;
+  unsigned long long um = 0;
+  for_each_run(g, [&](int bx0, int by0, int k0, int k1) {
+    const int x = bx0 + lane, y = by0 + threadIdx.y;
+    const bool active = x < g.nx && y < g.ny;
+    const unsigned col = (unsigned)y * nx + (unsigned)x;
+    const int xgl = ghost_index(x - 1, g.nx, g.bc[0]), xgr = ghost_index(x + 1, g.nx, g.bc[0]);
+    const int ygl = ghost_index(y - 1, g.ny, g.bc[1]), ygr = ghost_index(y + 1, g.ny, g.bc[1]);
+    const bool own_xl = lane == 0, own_xr = lane == TX - 1 || x == g.nx - 1;  // halo or boundary: load
+    auto ld = [&](unsigned k, int xx, int yy) -> int {
+      return (xx >= 0 && yy >= 0) ? __ldg(P + k * plane + (unsigned)yy * nx + (unsigned)xx) : 0;
+    };
+    auto ldz = [&](int kk) -> int {  // P at (x, y, kk), kk possibly a ghost plane
+      if (!has_z) return 0;
+      const int kz = ghost_index(kk, g.nz, g.bc[2]);
+      return (active && kz >= 0) ? __ldg(P + (unsigned)kz * plane + col) : 0;
+    };
+    struct Plane {
+      int c, yl, yr, xl, xr;
+      double r, u;
+    };
+    auto fetch = [&](int k, int c) {
+      Plane f;
+      f.c = c;
+      f.yl = f.yr = f.xl = f.xr = 0;
+      f.r = f.u = 0.0;
+      if (active) {
+        const unsigned kk = (unsigned)k;
+        f.yl = ld(kk, x, ygl);
+        f.yr = ld(kk, x, ygr);
+        if (own_xl) f.xl = ld(kk, xgl, y);
+        if (own_xr) f.xr = ld(kk, xgr, y);
+        f.r = R[kk * plane + col];
+        if (!ZG) f.u = U[kk * plane + col];
+      }
+      return f;
+    };
+    int zl = ldz(k0 - 1);
+    const int c0 = active ? __ldg(P + (unsigned)k0 * plane + col) : 0;
+    int zr = (k0 + 1 < g.nz) ? (active ? __ldg(P + (unsigned)(k0 + 1) * plane + col) : 0) : ldz(k0 + 1);
+    Plane cur = fetch(k0, c0);
+    for (int k = k0; k < k1; ++k) {
+      // loads for plane k+1 (and P two planes ahead) go out before plane k is processed
+      Plane nxt;
+      int zr2 = 0;
+      if (k + 1 < k1) {
+        nxt = fetch(k + 1, zr);
+        zr2 = (k + 2 < g.nz) ? (active ? __ldg(P + (unsigned)(k + 2) * plane + col) : 0) : ldz(k + 2);
+      }
+      const int c = cur.c;
+      int xl = __shfl_up_sync(0xffffffffu, c, 1), xr = __shfl_down_sync(0xffffffffu, c, 1);
+      if (own_xl) xl = cur.xl;
+      if (own_xr) xr = cur.xr;
+      const int zlv = has_z ? zl : c, zrv = has_z ? zr : c;
+      if (active) {
+        const int dx = 2 * c - xl - xr, dy = 2 * c - cur.yl - cur.yr, dz = 2 * c - zlv - zrv;
+        double r = cur.r;
+        if (g.uniform) {
+          r = fma(na0, i32_to_f64_scaled(dx + dy + dz, -kp), r);
+        } else {
+          r = fma(na0, i32_to_f64_scaled(dx, -kp), r);
+          r = fma(na1, i32_to_f64_scaled(dy, -kp), r);
+          if (dz) r = fma(na2, i32_to_f64_scaled(dz, -kp), r);
+        }
+        const unsigned i = (unsigned)k * plane + col;
+        R[i] = r;
+        const float r32 = f64_to_f32_odd(r, shift);
+        store_lp(lp, i, r, r32);
+        rr = fmaf(r32, r32, rr);
+        sR += r32;
+        const double pv = i32_to_f64_scaled(c, -kp);
+        const double u = ZG ? alpha * pv : fma(alpha, pv, cur.u);
+        U[i] = u;
+        const unsigned long long ub = mag_key(u);
+        um = ub > um ? ub : um;
+      }
+      zl = c;
+      zr = zr2;
+      if (k + 1 < k1) cur = nxt;
+    }
+  });
+  double acc[2] = {f32_to_f64_int(rr), f32_to_f64_int(sR)};
+  fold_umax(st, um);
+  grid_reduce<2>(acc, partials, &st->tickets[kTkUpd], gridDim.x, blockIdx.x,
+                 [st, shift, g](const double(&s)[2]) { fin_update(st, s, shift, g); });
 }
 
 // FP64 form: P and W = L P are stored by the direction kernel.
