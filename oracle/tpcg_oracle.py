@@ -18,17 +18,22 @@ Contents, each citing the passage it follows:
   apply_minus_laplacian   -- eq. (ourproblem), Sec. 3.3 (mode-product form)
   center                  -- eq. (centering), Sec. 3.4.1
   rhs_add_bc              -- Sec. 3.4.2
+  efield                  -- Sec. 2 (field from potential), ghosts of eq. (lap1d) / Sec. 3.4.2
   pinv_init               -- Algorithms 4/5 (MPPI init), Sec. 4.3.3, threshold 1e-13
   pinv_apply              -- Algorithms 6/7 (MPPI apply), Sec. 4.3.3
+  jacobi_init/apply       -- Algorithms 2/3, Sec. 4.3.1 (p steps of (weighted) Jacobi)
   pcg                     -- Algorithm 1 with Remark (orthogonality) centring of Z
   minnorm_dense           -- brute force: dense eigendecomposition of the assembled operator
   normalize_rhs           -- eq. (normalization), Sec. 5.2
 
-Readings of places where the paper is silent (listed again in the design doc):
+Readings of places where the paper is silent:
   * grid spacing: the paper has unit spacing; a spacing h divides L_l by h^2;
   * threshold: |eigenvalue sum| < 1e-13 * max_l(1/h_l^2) counts as zero;
   * stopping: true relative residual ||H - L U|| / ||H|| <= tol (H centred);
-  * centring: Z every iteration (Remark orthogonality), U once at exit.
+  * centring: Z every iteration (Remark orthogonality), U once at exit;
+  * field: the text writes the field as minus "nabla dot" of the scalar
+    potential; read as the gradient, discretised by central differences with
+    the Laplacian's ghost values at the faces.
 """
 from __future__ import annotations
 
@@ -213,6 +218,40 @@ def rhs_add_bc(H: np.ndarray, bcs, hs, bvals) -> np.ndarray:
     return H
 
 
+_FACE_KINDS = {"D": ("D", "D"), "N": ("N", "N"), "DN": ("D", "N"), "ND": ("N", "D")}
+
+
+def efield(U: np.ndarray, bcs, hs, bvals=None):
+    """epsilon = -grad(ups) (Sec. 2), one array per present axis.
+
+    Second-order central differences  -(u_{i+1} - u_{i-1}) / (2 h).  The neighbour
+    across a face is the ghost value that eq. (lap1d) and Sec. 3.4.2 imply:
+    periodic faces wrap; a Dirichlet face holds u_B; a Neumann face holds
+    u_boundary + h * e_B with e_B the outward normal derivative (so e_B = 0 is the
+    mirror value of the homogeneous problem).  ``bvals`` as in ``rhs_add_bc``
+    (None: homogeneous data).
+    """
+    U = np.asarray(U, dtype=np.float64)
+    out = []
+    for m in range(3):
+        ell = U.shape[m]
+        if ell == 1:
+            continue
+        bc, h = bcs[m], hs[m]
+        u = np.moveaxis(U, m, 0)
+        if bc == "P":
+            lo, hi = u[-1:], u[:1]
+        else:
+            sk, ek = _FACE_KINDS[bc]
+            vs = 0.0 if bvals is None else bvals[2 * m]
+            ve = 0.0 if bvals is None else bvals[2 * m + 1]
+            lo = np.full_like(u[:1], vs) if sk == "D" else u[:1] + h * vs
+            hi = np.full_like(u[-1:], ve) if ek == "D" else u[-1:] + h * ve
+        ext = np.concatenate([lo, u, hi], axis=0)
+        out.append(np.moveaxis(-(ext[2:] - ext[:-2]) / (2.0 * h), 0, m))
+    return out
+
+
 def normalize_rhs(H: np.ndarray) -> np.ndarray:
     """Scale so that ||vec(H)||_2 = 1 / (number of grid points) (eq. normalization)."""
     return H * ((1.0 / H.size) / np.linalg.norm(H.ravel()))
@@ -268,16 +307,44 @@ class PCGResult:
         self.null_component = null_component
 
 
-def pcg(shape, bcs, hs, H, U0=None, tol=1e-13, maxit=50, precond="pinv", L=None, pinv=None):
+def jacobi_init(shape, bcs, hs, omega):
+    """Precomputed parts of the Jacobi(p, omega) preconditioner (Sec. 4.3.1): the
+    splitting L_l = D_omega(L_l) + O_omega(L_l) with D_omega = omega * diag(L_l) and
+    O_omega = L_l - D_omega per axis, and the Hadamard inverse of the tensor of
+    summed diagonals times omega (eq. HadInv and its 3D analogue)."""
+    Ls = axis_matrices(shape, bcs, hs)
+    Os = [L - omega * np.diag(np.diag(L)) for L in Ls]
+    d = [np.diag(L) for L in Ls]
+    Dhat = omega * (d[0][:, None, None] + d[1][None, :, None] + d[2][None, None, :])
+    return Os, 1.0 / Dhat
+
+
+def jacobi_apply(R: np.ndarray, Os, Dinv: np.ndarray, p: int) -> np.ndarray:
+    """Algorithm 3: X_0 = 0; X_j = Dinv (Hadamard) (R - sum_l O_omega(L_l) x_l X_{j-1}); Z = X_p."""
+    X = np.zeros_like(R)
+    for _ in range(p):
+        F = R - sum(mode_product(Os[m], X, m) for m in range(3))
+        X = Dinv * F
+    return X
+
+
+def pcg(shape, bcs, hs, H, U0=None, tol=1e-13, maxit=50, precond="pinv", L=None, pinv=None, jacobi=(3, 1.3),
+        patience=None):
     """Algorithm 1 with the pseudoinverse preconditioner (Algorithm 7).
 
     The Laplacian is the assembled sparse Kronecker sum (not a stencil).  If
     the operator is singular, H is centred once (eq. centering) and Z_s every
     iteration (Remark orthogonality); U is centred at exit so that the
     zero-mean (minimum-norm) representative is returned.  ``precond`` is
-    ``"pinv"`` or ``"none"`` (M = I).  Stops when the true relative residual
-    is <= tol, at maxit, or on stagnation.
+    ``"pinv"``, ``"jacobi"`` (Algorithm 3 with ``jacobi = (p, omega)``) or
+    ``"none"`` (M = I).  Stops when the true relative residual is <= tol, at
+    maxit, or on stagnation: ``patience`` consecutive iterations without halving
+    the best true residual (default 3 for the pseudoinverse, whose residual
+    falls by orders of magnitude per step; 50 for the comparators, whose CG
+    residual is not monotone).
     """
+    if patience is None:
+        patience = 3 if precond == "pinv" else 50
     if L is None:
         L = kron_sum(shape, bcs, hs)
     singular = is_singular(shape, bcs)
@@ -286,6 +353,13 @@ def pcg(shape, bcs, hs, H, U0=None, tol=1e-13, maxit=50, precond="pinv", L=None,
 
         def M(R):
             Z = pinv_apply(R, Vs, G)
+            return center(Z) if singular else Z
+    elif precond == "jacobi":
+        jp, omega = jacobi
+        Os, Dinv = jacobi_init(shape, bcs, hs, omega)
+
+        def M(R):
+            Z = jacobi_apply(R, Os, Dinv, jp)
             return center(Z) if singular else Z
     else:
 
@@ -333,7 +407,7 @@ def pcg(shape, bcs, hs, H, U0=None, tol=1e-13, maxit=50, precond="pinv", L=None,
             best, stall = true_res[-1], 0
         else:
             stall += 1
-            if stall >= 3:
+            if stall >= patience:
                 break
     null_component = 0.0
     if singular:

@@ -268,3 +268,85 @@ def test_cost_model_counts_mode_products():
     n, q, t = 256, 256, 128
     per_direction = 2 * n * q * t * n + 2 * n * q * t * q + 2 * n * q * t * t
     assert o.pinv_apply_flops(n, q, t) == 2 * per_direction + n * q * t
+
+
+# ---------------------------------------------------------------- Sec. 2: field from potential
+def test_efield_periodic_sine_is_exact_discrete_cosine():
+    """Central difference of sin(2 pi j / n) is cos(2 pi j / n) sin(2 pi / n) / h exactly."""
+    n, q, t, h = 24, 5, 4, 0.5
+    j = np.arange(n)
+    U = np.sin(2 * np.pi * j / n)[:, None, None] * np.ones((n, q, t))
+    ex, ey, ez = o.efield(U, ("P", "N", "D"), (h, 1.0, 1.0))
+    want = -np.cos(2 * np.pi * j / n) * np.sin(2 * np.pi / n) / h
+    assert np.abs(ex - want[:, None, None]).max() < 1e-14
+    assert np.abs(ey).max() == 0.0  # U constant in y: Neumann ghosts mirror it
+
+
+@pytest.mark.parametrize("bc", ["D", "N", "DN", "ND"])
+def test_efield_linear_potential_with_consistent_face_data(bc):
+    """u = c + a x h on x = -1..n: with face data taken from u itself the field is -a everywhere."""
+    n, h, a, c = 9, 0.25, 1.7, -0.3
+    x = np.arange(n)
+    U = (c + a * x * h)[:, None, None] * np.ones((n, 3, 1))
+    sk, ek = {"D": ("D", "D"), "N": ("N", "N"), "DN": ("D", "N"), "ND": ("N", "D")}[bc]
+    start = c - a * h if sk == "D" else -a        # Dirichlet value at the ghost, or outward derivative (-x)
+    end = c + a * n * h if ek == "D" else a       # Dirichlet value at the ghost, or outward derivative (+x)
+    ex, ey = o.efield(U, (bc, "P", "P"), (h, 1.0, 1.0), bvals=[start, end, 0, 0, 0, 0])
+    assert np.abs(ex + a).max() < 1e-12
+    assert np.abs(ey).max() == 0.0
+
+
+def test_efield_second_order_against_analytic_gradient():
+    """Smooth periodic potential: the discrete field converges at second order."""
+    errs = []
+    for n in (16, 32, 64):
+        h = 2 * np.pi / n
+        xs = np.arange(n) * h
+        U = (np.sin(xs)[:, None] * np.cos(2 * xs)[None, :])[:, :, None]
+        ex, ey = o.efield(U, ("P", "P", "P"), (h, h, 1.0))
+        gx = -(np.cos(xs)[:, None] * np.cos(2 * xs)[None, :])[:, :, None]
+        gy = (2 * np.sin(xs)[:, None] * np.sin(2 * xs)[None, :])[:, :, None]
+        errs.append(max(np.abs(ex - gx).max(), np.abs(ey - gy).max()))
+    assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5
+
+
+# ---------------------------------------------------------------- Sec. 4.3.1: Jacobi(p, omega)
+def test_jacobi_one_step_is_scaled_residual():
+    """p = 1: Z = R / (omega * (diag L_n + diag L_q + diag L_t)), the corner entries included."""
+    shape, bcs, hs, om = (6, 5, 4), ("DN", "N", "P"), (0.5, 1.0, 2.0), 1.3
+    R = np.random.default_rng(3).standard_normal(shape)
+    Os, Dinv = o.jacobi_init(shape, bcs, hs, om)
+    d = np.diag(o.kron_sum(shape, bcs, hs).toarray())
+    want = o.unvec(o.vec(R) / (om * d), shape)
+    assert np.abs(o.jacobi_apply(R, Os, Dinv, 1) - want).max() < 1e-15 * np.abs(want).max()
+
+
+def test_jacobi_many_steps_converge_to_the_inverse():
+    """As p grows the stationary iteration from 0 converges to L^-1 R (nonsingular operator)."""
+    shape, bcs, hs = (5, 4, 3), ("D", "DN", "ND"), (1.0, 1.0, 1.0)
+    R = np.random.default_rng(4).standard_normal(shape)
+    Os, Dinv = o.jacobi_init(shape, bcs, hs, 1.3)
+    Z = o.jacobi_apply(R, Os, Dinv, 3000)
+    x = o.solve_sparse_direct(shape, bcs, hs, R)
+    assert np.abs(Z - x).max() < 1e-10 * np.abs(x).max()
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 5])
+def test_jacobi_preconditioner_is_symmetric(p):
+    """<M a, b> = <a, M b>: a dropped or transposed O_omega would break it."""
+    shape, bcs, hs = (6, 5, 4), ("P", "ND", "N"), (0.7, 1.0, 1.3)
+    rng = np.random.default_rng(5)
+    a, b = rng.standard_normal(shape), rng.standard_normal(shape)
+    Os, Dinv = o.jacobi_init(shape, bcs, hs, 1.3)
+    lhs = np.vdot(o.jacobi_apply(a, Os, Dinv, p), b)
+    rhs = np.vdot(a, o.jacobi_apply(b, Os, Dinv, p))
+    assert abs(lhs - rhs) < 1e-12 * max(abs(lhs), 1.0)
+
+
+def test_comparator_ordering_on_a_small_problem():
+    """Experiment 2's qualitative ordering: p-inv needs the fewest iterations, then Jacobi(3, 1.3), then CG."""
+    shape, bcs = (24, 16, 1), ("P", "P", None)
+    H = o.normalize_rhs(o.center(np.random.default_rng(6).standard_normal(shape)))
+    it = {k: o.pcg(shape, bcs, (1, 1, 1), H, tol=1e-10, maxit=2000, precond=k).iters
+          for k in ("pinv", "jacobi", "none")}
+    assert it["pinv"] < it["jacobi"] < it["none"]
