@@ -156,10 +156,24 @@ int tpcg_solve_host(tpcg_plan* plan, const double* eta_host, double* ups_host, d
 int tpcg_solve_batched(tpcg_plan* const* plans, int nsolves, const int* nrhs, const double* const* eta,
                        double* const* ups, const double* tol, int maxit, unsigned flags, tpcg_info* infos);
 
-/* z = M(r): one application of the preconditioner of Algorithm 7 in the
- * plan's precision form, without centring.  r, z: device pointers of
- * nz*ny*nx doubles (may not alias).  Enqueues only.                        */
+/* z = M(r): one application of the plan's preconditioner (Algorithm 7 in the
+ * plan's precision form, or the comparator chosen by tpcg_plan_set_precond),
+ * without centring.  r, z: device pointers of nz*ny*nx doubles (may not
+ * alias).  Enqueues only.                                                    */
 int tpcg_precond_apply(tpcg_plan* plan, const double* r, double* z);
+
+/* ---- comparator preconditioners (Sec. 4.3.1; Experiment 2, Sec. 5) ------ */
+#define TPCG_PRECOND_PINV    0  /* Moore-Penrose pseudoinverse, Algorithms 5/7 (the default)        */
+#define TPCG_PRECOND_NONE    1  /* M = I: unpreconditioned CG                                       */
+#define TPCG_PRECOND_JACOBI  2  /* p steps of (weighted) Jacobi from X_0 = 0, Algorithms 2/3:
+                                 * X_j = X_{j-1} + (R - L X_{j-1}) / (omega * d), d the Kronecker
+                                 * sum of the 1D diagonals (corner entries of eq. lap1d included)  */
+
+/* Select the preconditioner of an FP64 plan (TPCG_ERR_UNSUPPORTED for the
+ * mixed forms, whose tensor-core path is the pseudoinverse).  p (1..64) and
+ * omega (>= 1, the splitting parameter of Sec. 4.3.1) are used by
+ * TPCG_PRECOND_JACOBI only.  Takes effect for the next solve.              */
+int tpcg_plan_set_precond(tpcg_plan* plan, int kind, int p, double omega);
 
 /* w = L x: the 7-point (5-point in 2D) Kronecker-sum stencil of eq.
  * (ourproblem), FP64, per-axis corners of eq. (lap1d).  x, w: device
@@ -174,6 +188,18 @@ int tpcg_apply_laplacian(tpcg_plan* plan, const double* x, double* w);
  * sign reading of Problem 2, Sec. 5.1).  eta: device pointer (nz*ny*nx
  * doubles); bval: host pointer.  Enqueues only.                           */
 int tpcg_rhs_add_bc(tpcg_plan* plan, double* eta, const double bval[6]);
+
+/* The electric field of a potential, epsilon = -grad(ups) (Sec. 2; the text's
+ * "nabla dot" of the scalar potential is read as the gradient), by central
+ * differences  -(u_{i+1} - u_{i-1}) / (2 h)  per axis.  The neighbour across a
+ * face is the ghost value of the plan's boundary condition (eq. lap1d) with
+ * the face data of tpcg_rhs_add_bc: periodic faces wrap, a Dirichlet face
+ * holds u_B, a Neumann face holds u_boundary + h e_B (e_B the outward normal
+ * derivative).  bval: host pointer to 6 doubles laid out as for
+ * tpcg_rhs_add_bc, or NULL for homogeneous data.  ups, ex, ey, ez: device
+ * pointers of nz*ny*nx doubles (x, y, z components); ez is ignored (may be
+ * NULL) for a 2D plan; outputs may not alias ups.  Enqueues only.           */
+int tpcg_efield(tpcg_plan* plan, const double* ups, const double bval[6], double* ex, double* ey, double* ez);
 
 /* Copy the FP64 eigenpairs of axis (0 = x, 1 = y, 2 = z) to host memory:
  * lam[ell] (already divided by h^2) and V[ell*ell] row-major with column k

@@ -29,13 +29,17 @@ TPCG_PENDING = 10
 TPCG_ERR_UNKNOWN_TICKET = 11
 TPCG_ERR_CANCELLED = 12
 
-BC = {"P": 0, "D": 1, "N": 2, "DN": 3, "ND": 4}
+TPCG_BC_P, TPCG_BC_D, TPCG_BC_N, TPCG_BC_DN, TPCG_BC_ND = 0, 1, 2, 3, 4
+BC = {"P": TPCG_BC_P, "D": TPCG_BC_D, "N": TPCG_BC_N, "DN": TPCG_BC_DN, "ND": TPCG_BC_ND}
 TPCG_FP64 = 0
 TPCG_MIXED_TF32 = 1
 TPCG_MIXED_BF16 = 2
 TPCG_MIXED_FP16 = 3
 PREC = {"fp64": TPCG_FP64, "tf32": TPCG_MIXED_TF32, "bf16": TPCG_MIXED_BF16, "fp16": TPCG_MIXED_FP16}
 TPCG_ZERO_GUESS = 1
+TPCG_PRECOND_PINV = 0
+TPCG_PRECOND_NONE = 1
+TPCG_PRECOND_JACOBI = 2
 TPCG_REQ_BORROW_HOST = 1
 TPCG_REQ_BORROW_DEVICE = 2
 
@@ -94,6 +98,8 @@ _SIGS = {
     "tpcg_precond_apply": (_I, [_P, _P, _P]),
     "tpcg_apply_laplacian": (_I, [_P, _P, _P]),
     "tpcg_rhs_add_bc": (_I, [_P, _P, ctypes.POINTER(_D)]),
+    "tpcg_efield": (_I, [_P, _P, ctypes.POINTER(_D), _P, _P, _P]),
+    "tpcg_plan_set_precond": (_I, [_P, _I, _I, _D]),
     "tpcg_plan_eigenpairs": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "tpcg_plan_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "tpcg_profile_begin": (_I, [_P]),
@@ -189,6 +195,15 @@ def tpcg_precond_apply(plan, r_ptr, z_ptr):
 
 def tpcg_apply_laplacian(plan, x_ptr, w_ptr):
     return lib().tpcg_apply_laplacian(plan, _P(x_ptr), _P(w_ptr))
+
+
+def tpcg_plan_set_precond(plan, kind, p=3, omega=1.3):
+    return lib().tpcg_plan_set_precond(plan, int(kind), int(p), float(omega))
+
+
+def tpcg_efield(plan, ups_ptr, bval, ex_ptr, ey_ptr, ez_ptr):
+    arr = None if bval is None else (_D * 6)(*[float(v) for v in bval])
+    return lib().tpcg_efield(plan, _P(ups_ptr), arr, _P(ex_ptr), _P(ey_ptr), _P(ez_ptr))
 
 
 def tpcg_rhs_add_bc(plan, eta_ptr, bval):
@@ -404,6 +419,22 @@ class Plan:
         st = tpcg_apply_laplacian(self.handle, x.data_ptr(), w.data_ptr())
         if st != TPCG_OK:
             raise TpcgError(st, "tpcg_apply_laplacian")
+
+    def set_precond(self, kind, p=3, omega=1.3):
+        """Choose the preconditioner ("pinv", "none" or "jacobi"); see tpcg_plan_set_precond."""
+        code = {"pinv": TPCG_PRECOND_PINV, "none": TPCG_PRECOND_NONE, "jacobi": TPCG_PRECOND_JACOBI}[kind]
+        st = tpcg_plan_set_precond(self.handle, code, p, omega)
+        if st:
+            raise TpcgError(st, "tpcg_plan_set_precond")
+
+    def efield(self, ups, ex, ey, ez=None, bval=None):
+        """Electric field -grad(ups) into ex, ey (and ez in 3D); see tpcg_efield."""
+        for t in (ups, ex, ey) + ((ez,) if ez is not None else ()):
+            self._check(t)
+        st = tpcg_efield(self.handle, ups.data_ptr(), bval, ex.data_ptr(), ey.data_ptr(),
+                         ez.data_ptr() if ez is not None else 0)
+        if st:
+            raise TpcgError(st, "tpcg_efield")
 
     def rhs_add_bc(self, eta, bval):
         self._check(eta)

@@ -27,8 +27,11 @@ void launch_to_lp(const tpcg_plan* p, const Geom& g, const double* r);
 void launch_norm_shift(const tpcg_plan* p, const Geom& g, const double* r);
 void launch_f32_to_f64(const tpcg_plan* p, long long N, const float* a, double* b);
 void launch_rhs_add_bc(const tpcg_plan* p, const Geom& g, double* eta, const double* bv);
+void launch_efield(const tpcg_plan* p, const Geom& g, const double* U, const double* bval, double* ex, double* ey,
+                   double* ez);
 int setup_fx_grids(tpcg_plan* p);
 void run_precond_f64(const tpcg_plan* pl, const double* R, double* Z, SolveState* st);
+void run_precond_cmp(const tpcg_plan* p, const Geom& g, const double* R, double* Z, SolveState* st);
 int run_precond_tc(const tpcg_plan* pl, float* Z, SolveState* st);
 int tc_plan_setup(tpcg_plan* pl);
 void tc_plan_release(tpcg_plan* pl);
@@ -210,7 +213,8 @@ uint16_t host_f16(double x) {
 
 int run_precond(const tpcg_plan* p, const double* R, void* Z, SolveState* st) {
   if (p->prec == TPCG_FP64) {
-    run_precond_f64(p, R, (double*)Z, st);
+    if (p->pc_kind == TPCG_PRECOND_PINV) run_precond_f64(p, R, (double*)Z, st);
+    else run_precond_cmp(p, make_geom(p), R, (double*)Z, st);
     return TPCG_OK;
   }
   return run_precond_tc(p, (float*)Z, st);
@@ -669,7 +673,8 @@ int tpcg_precond_apply(tpcg_plan* plan, const double* r, double* z) {
   DeviceGuard dg(plan->device);
   int rc;
   if (plan->prec == TPCG_FP64) {
-    run_precond_f64(plan, r, z, nullptr);
+    if (plan->pc_kind == TPCG_PRECOND_PINV) run_precond_f64(plan, r, z, nullptr);
+    else run_precond_cmp(plan, make_geom(plan), r, z, nullptr);
     return last_cuda_error();
   }
   const Geom g = make_geom(plan);
@@ -691,6 +696,53 @@ int tpcg_rhs_add_bc(tpcg_plan* plan, double* eta, const double bval[6]) {
   if (!plan || !eta || !bval) return TPCG_ERR_INVALID_ARG;
   DeviceGuard dg(plan->device);
   launch_rhs_add_bc(plan, make_geom(plan), eta, bval);
+  return last_cuda_error();
+}
+
+int tpcg_plan_set_precond(tpcg_plan* plan, int kind, int p, double omega) {
+  if (!plan) return TPCG_ERR_INVALID_ARG;
+  if (kind != TPCG_PRECOND_PINV && kind != TPCG_PRECOND_NONE && kind != TPCG_PRECOND_JACOBI)
+    return TPCG_ERR_INVALID_ARG;
+  if (kind == TPCG_PRECOND_JACOBI && (p < 1 || p > 64 || !(omega >= 1.0) || !(omega < 1e300)))
+    return TPCG_ERR_INVALID_ARG;
+  if (kind != TPCG_PRECOND_PINV && plan->prec != TPCG_FP64) return TPCG_ERR_UNSUPPORTED;
+  plan->pc_kind = kind;
+  if (kind == TPCG_PRECOND_JACOBI) {
+    plan->jac_p = p;
+    plan->jac_omega = omega;
+    // diagonal of L per axis and boundary class: the corner entries (alpha, beta) of eq. (lap1d)
+    double dg[3][3];
+    const int len[3] = {plan->nx, plan->ny, plan->nz};
+    for (int m = 0; m < 3; ++m) {
+      const double ih2 = 1.0 / (plan->h[m] * plan->h[m]);
+      if (len[m] == 1) {
+        dg[m][0] = dg[m][1] = dg[m][2] = 0.0;  // absent z axis: L_t = [0]
+        continue;
+      }
+      double alpha = 2.0, beta = 2.0;
+      switch (plan->bc[m]) {
+        case TPCG_BC_N: alpha = 1.0; beta = 1.0; break;
+        case TPCG_BC_DN: beta = 1.0; break;
+        case TPCG_BC_ND: alpha = 1.0; break;
+        default: break;
+      }
+      dg[m][0] = alpha * ih2;
+      dg[m][1] = 2.0 * ih2;
+      dg[m][2] = beta * ih2;
+    }
+    for (int cz = 0; cz < 3; ++cz)
+      for (int cy = 0; cy < 3; ++cy)
+        for (int cx = 0; cx < 3; ++cx)
+          plan->jac_invd[cx + 3 * cy + 9 * cz] = 1.0 / (omega * (dg[0][cx] + dg[1][cy] + dg[2][cz]));
+  }
+  return TPCG_OK;
+}
+
+int tpcg_efield(tpcg_plan* plan, const double* ups, const double bval[6], double* ex, double* ey, double* ez) {
+  if (!plan || !ups || !ex || !ey || (plan->nz > 1 && !ez)) return TPCG_ERR_INVALID_ARG;
+  if (ex == ups || ey == ups || (ez && ez == ups)) return TPCG_ERR_INVALID_ARG;
+  DeviceGuard dg(plan->device);
+  launch_efield(plan, make_geom(plan), ups, bval, ex, ey, plan->nz > 1 ? ez : nullptr);
   return last_cuda_error();
 }
 

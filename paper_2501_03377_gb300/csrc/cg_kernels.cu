@@ -856,6 +856,105 @@ __global__ void k_rhs_add_bc(Geom g, double* __restrict__ eta, double b0, double
 }
 
 
+// ------------------------------------------------------------------ comparator preconditioners
+// Jacobi(p, omega), Algorithms 2/3 (Sec. 4.3.1): X_0 = 0, X_j = X_{j-1} + (R - L X_{j-1}) / (omega d)
+// -- the same iteration as F_j = R - O_omega X_{j-1}, X_j = F_j / (omega d), with O_omega = L - omega D.
+// d depends only on whether a point is the first, an interior or the last point of each axis.
+struct JacobiTable {
+  double invd[27];
+};
+
+__device__ __forceinline__ double jacobi_invd(const JacobiTable& t, const Geom& g, unsigned i) {
+  const unsigned plane = (unsigned)g.nx * (unsigned)g.ny;
+  const int k = (int)(i / plane);
+  const unsigned rem = i - (unsigned)k * plane;
+  const int y = (int)(rem / (unsigned)g.nx), x = (int)(rem - (unsigned)y * (unsigned)g.nx);
+  auto cls = [](int pos, int len) { return len == 1 ? 1 : (pos == 0 ? 0 : (pos == len - 1 ? 2 : 1)); };
+  return t.invd[cls(x, g.nx) + 3 * cls(y, g.ny) + 9 * cls(k, g.nz)];
+}
+
+__global__ void __launch_bounds__(256) k_jacobi_first(Geom g, const double* __restrict__ R, double* __restrict__ X,
+                                                      JacobiTable t) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.N; i += (long long)gridDim.x * blockDim.x)
+    X[i] = __ldg(R + i) * jacobi_invd(t, g, (unsigned)i);
+}
+
+struct OpJacobi {
+  const double* __restrict__ R;
+  double* __restrict__ Xnew;
+  JacobiTable t;
+  Geom g;
+  __device__ __forceinline__ void operator()(long long i, double c, double w, double (&)[1]) {
+    Xnew[i] = fma(__ldg(R + i) - w, jacobi_invd(t, g, (unsigned)i), c);
+  }
+};
+
+__global__ void __launch_bounds__(TX* TY) k_jacobi_sweep(Geom g, int zchunk, const double* __restrict__ Xold,
+                                                         double* __restrict__ Xnew, const double* __restrict__ R,
+                                                         JacobiTable t) {
+  FieldPlain f{Xold};
+  OpJacobi op{R, Xnew, t, g};
+  stencil_sweep<0>(g, zchunk, f, op, nullptr, nullptr, NoFin{});
+}
+
+// rho = <R, Z> and sum(Z) in FP64 (comparators); Z = R first when copy (M = I).
+__global__ void __launch_bounds__(256) k_dot_rz(long long N, const double* __restrict__ R, double* __restrict__ Z,
+                                                int copy, SolveState* st, double* partials) {
+  double acc[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const double r = __ldg(R + i);
+    const double z = copy ? r : Z[i];
+    if (copy) Z[i] = r;
+    acc[0] = fma(r, z, acc[0]);
+    acc[1] += z;
+  }
+  if (!st) return;
+  grid_reduce<2>(acc, partials, &st->tickets[kTkPrec], gridDim.x, blockIdx.x,
+                 [st, N](const double(&s)[2]) { fin_precond(st, N, s); });
+}
+
+// ------------------------------------------------------------------ electric field
+// epsilon = -grad(ups) (Sec. 2; the field of the computed potential) by central
+// differences -(u_{i+1} - u_{i-1}) / (2 h).  The neighbour across a face is the
+// ghost value of the Laplacian's boundary condition (eq. lap1d) with the face
+// data of Sec. 3.4.2: periodic faces wrap, a Dirichlet face holds u_B, a Neumann
+// face holds u_boundary + h e_B (e_B the outward normal derivative).
+struct FaceData {
+  double v[6];      // face data, start and end face per axis (0: homogeneous)
+  double h[3];      // spacing per axis
+  double inv2h[3];  // 1 / (2 h)
+};
+
+__global__ void __launch_bounds__(256) k_efield(Geom g, const double* __restrict__ U, FaceData fd,
+                                                double* __restrict__ ex, double* __restrict__ ey,
+                                                double* __restrict__ ez) {
+  const unsigned plane = (unsigned)g.nx * (unsigned)g.ny;  // N <= 2^31: 32-bit index arithmetic
+  const int naxes = g.nz > 1 ? 3 : 2;
+  for (long long ii = blockIdx.x * (long long)blockDim.x + threadIdx.x; ii < g.N;
+       ii += (long long)gridDim.x * blockDim.x) {
+    const unsigned i = (unsigned)ii;
+    const int k = (int)(i / plane);
+    const unsigned rem = i - (unsigned)k * plane;
+    const int y = (int)(rem / (unsigned)g.nx), x = (int)(rem - (unsigned)y * (unsigned)g.nx);
+    const int pos[3] = {x, y, k}, len[3] = {g.nx, g.ny, g.nz};
+    const unsigned stride[3] = {1u, (unsigned)g.nx, plane};
+    const double u0 = __ldg(U + i);
+    for (int m = 0; m < naxes; ++m) {
+      const int bc = g.bc[m];
+      const bool startD = bc == kBcD || bc == kBcDN, endD = bc == kBcD || bc == kBcND;
+      double lo, hi;
+      if (pos[m] > 0) lo = __ldg(U + i - stride[m]);
+      else if (bc == kBcP) lo = __ldg(U + i + (unsigned)(len[m] - 1) * stride[m]);
+      else lo = startD ? fd.v[2 * m] : fma(fd.h[m], fd.v[2 * m], u0);
+      if (pos[m] < len[m] - 1) hi = __ldg(U + i + stride[m]);
+      else if (bc == kBcP) hi = __ldg(U + i - (unsigned)(len[m] - 1) * stride[m]);
+      else hi = endD ? fd.v[2 * m + 1] : fma(fd.h[m], fd.v[2 * m + 1], u0);
+      double* out = m == 0 ? ex : (m == 1 ? ey : ez);
+      out[i] = (lo - hi) * fd.inv2h[m];
+    }
+  }
+}
+
 // ------------------------------------------------------------------ host launchers
 void launch_apply_laplacian(const tpcg_plan* p, const Geom& g, const double* x, double* w) {
   LaunchScope ls(p, kKApply);
@@ -938,6 +1037,40 @@ void launch_f32_to_f64(const tpcg_plan* p, long long N, const float* a, double* 
   LaunchScope ls(p, kKConvert);
   k_f32_to_f64<<<p->stream_blocks, 256, 0, p->stream>>>(N, a, b);
 }
+void launch_efield(const tpcg_plan* p, const Geom& g, const double* U, const double* bval, double* ex, double* ey,
+                   double* ez) {
+  LaunchScope ls(p, kKConvert);
+  FaceData fd{};
+  for (int m = 0; m < 6; ++m) fd.v[m] = bval ? bval[m] : 0.0;
+  for (int m = 0; m < 3; ++m) {
+    fd.h[m] = p->h[m];
+    fd.inv2h[m] = 0.5 / p->h[m];
+  }
+  k_efield<<<p->stream_blocks, 256, 0, p->stream>>>(g, U, fd, ex, ey, ez);
+}
+// Comparator preconditioner of the FP64 form: Z = M(R), then (with st) rho, sum(Z) and the finalize.
+void run_precond_cmp(const tpcg_plan* p, const Geom& g, const double* R, double* Z, SolveState* st) {
+  if (p->pc_kind == TPCG_PRECOND_JACOBI) {
+    JacobiTable t;
+    for (int c = 0; c < 27; ++c) t.invd[c] = p->jac_invd[c];
+    // X_j lands in Z when p - j is even, else in the W workspace, so that X_p is Z
+    auto buf = [&](int j) { return ((p->jac_p - j) % 2 == 0) ? Z : p->d_W; };
+    {
+      LaunchScope ls(p, kKModeF64);
+      k_jacobi_first<<<p->stream_blocks, 256, 0, p->stream>>>(g, R, buf(1), t);
+    }
+    for (int j = 2; j <= p->jac_p; ++j) {
+      LaunchScope ls(p, kKModeF64);
+      k_jacobi_sweep<<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, buf(j - 1), buf(j), R, t);
+    }
+  }
+  if (st || p->pc_kind == TPCG_PRECOND_NONE) {
+    LaunchScope ls(p, kKModeF64);
+    k_dot_rz<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, R, Z, p->pc_kind == TPCG_PRECOND_NONE ? 1 : 0, st,
+                                                        p->d_partials);
+  }
+}
+
 void launch_rhs_add_bc(const tpcg_plan* p, const Geom& g, double* eta, const double* bv) {
   LaunchScope ls(p, kKConvert);
   k_rhs_add_bc<<<p->stream_blocks, 256, 0, p->stream>>>(g, eta, bv[0], bv[1], bv[2], bv[3], bv[4], bv[5]);

@@ -143,5 +143,11 @@ struct tpcg_plan {
   dim3 st_grid, st_block;   // stencil kernels
   int st_zchunk = 1;
   int fx_blocks[4] = {1, 1, 1, 1};  // FxKernel -> blocks of the persistent fixed-point sweeps
+  // comparator preconditioner of the FP64 form (TPCG_PRECOND_*), Jacobi(p, omega) and its table of
+  // 1 / (omega d) indexed by the boundary class (start, interior, end) of x + 3 y + 9 z
+  int pc_kind = 0;
+  int jac_p = 3;
+  double jac_omega = 1.3;
+  double jac_invd[27] = {};
   int stream_blocks = 0;    // streaming kernels
 };

@@ -54,3 +54,23 @@ def test_strerror_and_argument_checks_without_gpu(libpath):
     assert b.tpcg_plan_create(8, 8, 8, "PPN", (1, 1, 1), 7, 0)[0] == b.TPCG_ERR_INVALID_ARG
     assert b.tpcg_plan_create(300, 8, 8, "PPN", (1, 1, 1), b.TPCG_MIXED_BF16, 0)[0] == b.TPCG_ERR_UNSUPPORTED
     assert b.lib().tpcg_plan_destroy(None) == b.TPCG_ERR_INVALID_ARG
+
+
+def test_binding_constants_match_header_defines():
+    """Every #define TPCG_* of the header has the same value in the binding."""
+    from paper_2501_03377_gb300 import binding as b
+
+    txt = open(os.path.join(ROOT, "include", "tpcg.h")).read()
+    defines = dict(re.findall(r"^#define\s+(TPCG_\w+)\s+(-?\d+)", txt, flags=re.M))
+    assert len(defines) > 20
+    missing = [k for k in defines if not hasattr(b, k)]
+    assert not missing, missing
+    wrong = {k: (v, getattr(b, k)) for k, v in defines.items() if getattr(b, k) != int(v)}
+    assert not wrong, wrong
+
+
+def test_new_entry_points_validate_before_any_cuda_call(libpath):
+    from paper_2501_03377_gb300 import binding as b
+
+    assert b.tpcg_plan_set_precond(None, b.TPCG_PRECOND_JACOBI, 3, 1.3) == b.TPCG_ERR_INVALID_ARG
+    assert b.tpcg_efield(None, 0, None, 0, 0, 0) == b.TPCG_ERR_INVALID_ARG

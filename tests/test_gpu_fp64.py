@@ -237,6 +237,64 @@ def test_rhs_add_bc_matches_oracle():
     assert np.abs(ed.cpu().numpy() - ref).max() <= 1e-14 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("nx,ny,nz,bcs,h,bv", [
+    (12, 9, 7, ("DN", "ND", "D"), (0.5, 2.0, 1.5), [0.3, -0.5, 1.25, 2.0, -1.0, 0.75]),
+    (33, 17, 9, ("P", "N", "P"), (1.0, 0.7, 1.3), None),
+    (40, 24, 1, ("D", "N", "P"), (1.0, 1.0, 1.0), [1.0, -2.0, 0.5, 0.25, 0.0, 0.0]),
+    (16, 16, 8, ("N", "N", "N"), (1.0, 1.0, 1.0), [0.1, 0.2, -0.3, 0.4, 0.5, -0.6]),
+])
+def test_efield_matches_oracle(nx, ny, nz, bcs, h, bv):
+    """epsilon = -grad(ups) (Sec. 2) with the face data of Sec. 3.4.2, every component."""
+    ups = synth.random_field(nx, ny, nz, seed=21)
+    pl = _plan(nx, ny, nz, bcs, h)
+    ud = _dev(ups)
+    ex, ey = torch.empty_like(ud), torch.empty_like(ud)
+    ez = torch.empty_like(ud) if nz > 1 else None
+    pl.efield(ud, ex, ey, ez, bval=bv)
+    torch.cuda.synchronize()
+    ref = o.efield(to_oracle(ups), oracle_bcs(bcs, nz), h, bv)
+    got = [ex, ey] + ([ez] if ez is not None else [])
+    assert len(ref) == len(got)
+    for g, r in zip(got, ref):
+        r = from_oracle(r)
+        assert np.abs(g.cpu().numpy() - r).max() <= 1e-14 * max(1.0, np.abs(r).max())
+
+
+def test_efield_of_solution_recovers_gauss_law():
+    """div(epsilon) of the computed potential reproduces eta_hat on a periodic grid (the discrete
+    divergence of the central-difference field is the wide-stencil Laplacian, so compare spectrally
+    smooth data): the field's divergence correlates with eta at the level of the discretisation."""
+    nx, ny, nz = 32, 32, 16
+    w = synth.defect_rhs(nx, ny, nz, ("P", "P", "P"), 6, 3.0, seed=22)
+    pl = _plan(nx, ny, nz, ("P", "P", "P"))
+    ed = _dev(w)
+    ud = torch.zeros_like(ed)
+    st, info = pl.solve(ed, ud, tol=1e-12, maxit=20, zero_guess=True)
+    assert st == 0, info
+    ex, ey, ez = (torch.empty_like(ud) for _ in range(3))
+    pl.efield(ud, ex, ey, ez)
+    torch.cuda.synchronize()
+    ref = o.efield(to_oracle(ud.cpu().numpy()), ("P", "P", "P"), (1.0, 1.0, 1.0))
+    for g, r in zip((ex, ey, ez), ref):
+        assert np.abs(g.cpu().numpy() - from_oracle(r)).max() <= 1e-14 * max(1.0, np.abs(r).max())
+    # discrete Gauss law: central divergence of the central-difference field = eta_hat to O(h^2)
+    div = sum(np.roll(f.cpu().numpy(), -1, axis=a) - np.roll(f.cpu().numpy(), 1, axis=a)
+              for f, a in ((ex, 2), (ey, 1), (ez, 0))) / 2.0
+    eta_hat = w - w.mean()
+    assert np.corrcoef(div.ravel(), eta_hat.ravel())[0, 1] > 0.9
+
+
+def test_efield_argument_errors():
+    from paper_2501_03377_gb300 import binding as b
+
+    pl = _plan(8, 8, 8, ("P", "P", "N"))
+    ud = _dev(np.zeros((8, 8, 8)))
+    e = torch.empty_like(ud)
+    assert b.tpcg_efield(pl.handle, ud.data_ptr(), None, e.data_ptr(), e.data_ptr(), 0) == b.TPCG_ERR_INVALID_ARG
+    assert b.tpcg_efield(pl.handle, ud.data_ptr(), None, ud.data_ptr(), e.data_ptr(), e.data_ptr()) == \
+        b.TPCG_ERR_INVALID_ARG
+
+
 def test_film_workload_fp64_full_size():
     """128x128x64 film, P/P/DN, FP64 form, tol 1e-10, against the oracle at full size."""
     w = synth.workload_film_128(seed=0)
@@ -249,3 +307,75 @@ def test_film_workload_fp64_full_size():
     ref = o.pcg(sh, w["bcs"], (1, 1, 1), to_oracle(w["eta"]), tol=1e-13)
     assert rel_err(ud.cpu().numpy(), from_oracle(ref.U)) <= 1e-9
     assert info["rel_res_true"] <= 1e-10
+
+
+# ---------------------------------------------------------------- comparators (Sec. 4.3.1, Experiment 2)
+@pytest.mark.parametrize("p,omega", [(1, 1.0), (2, 1.3), (3, 1.3), (4, 2.0)])
+@pytest.mark.parametrize("nx,ny,nz,bcs,h", [(12, 9, 7, ("DN", "ND", "D"), (0.5, 2.0, 1.5)),
+                                            (33, 17, 9, ("P", "N", "P"), (1.0, 1.0, 1.0)),
+                                            (40, 24, 1, ("D", "N", "P"), (1.0, 0.7, 1.0))])
+def test_jacobi_precond_apply_matches_oracle(p, omega, nx, ny, nz, bcs, h):
+    r = synth.random_field(nx, ny, nz, seed=23)
+    pl = _plan(nx, ny, nz, bcs, h)
+    pl.set_precond("jacobi", p, omega)
+    rd = _dev(r)
+    zd = torch.empty_like(rd)
+    pl.precond(rd, zd)
+    torch.cuda.synchronize()
+    ob = oracle_bcs(bcs, nz)
+    Os, Dinv = o.jacobi_init((nx, ny, nz), ob, h, omega)
+    ref = from_oracle(o.jacobi_apply(to_oracle(r), Os, Dinv, p))
+    assert np.abs(zd.cpu().numpy() - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_none_precond_is_identity():
+    r = synth.random_field(16, 12, 8, seed=24)
+    pl = _plan(16, 12, 8, ("P", "D", "N"))
+    pl.set_precond("none")
+    rd = _dev(r)
+    zd = torch.zeros_like(rd)
+    pl.precond(rd, zd)
+    torch.cuda.synchronize()
+    assert torch.equal(zd, rd)
+
+
+@pytest.mark.parametrize("kind", ["none", "jacobi"])
+@pytest.mark.parametrize("nx,ny,nz,bcs", [(24, 20, 12, ("P", "P", "N")), (20, 16, 1, ("D", "DN", "P"))])
+def test_comparator_solves_match_oracle(kind, nx, ny, nz, bcs):
+    eta = synth.defect_rhs(nx, ny, nz, bcs, 4, 2.0, seed=25)
+    pl = _plan(nx, ny, nz, bcs)
+    pl.set_precond(kind, 3, 1.3)
+    ed = _dev(eta)
+    ud = torch.zeros_like(ed)
+    st, info = pl.solve(ed, ud, tol=1e-10, maxit=2000, zero_guess=True)
+    assert st == 0, info
+    assert info["rel_res_true"] <= 1e-10
+    ref = o.pcg((nx, ny, nz), oracle_bcs(bcs, nz), (1, 1, 1), to_oracle(eta), tol=1e-13, maxit=4000, precond=kind)
+    assert rel_err(ud.cpu().numpy(), from_oracle(ref.U)) <= 1e-7
+
+
+def test_comparator_ordering_on_gpu():
+    """Experiment 2, qualitatively: p-inv needs the fewest iterations, then Jacobi(3, 1.3), then CG."""
+    nx, ny, nz, bcs = 100, 50, 1, ("P", "P", "P")
+    eta = synth.defect_rhs(nx, ny, nz, bcs, 10, 2.0, seed=26)
+    iters = {}
+    for kind in ("pinv", "jacobi", "none"):
+        pl = _plan(nx, ny, nz, bcs)
+        pl.set_precond(kind, 3, 1.3)
+        ud = torch.zeros((nz, ny, nx), dtype=torch.float64, device="cuda")
+        st, info = pl.solve(_dev(eta), ud, tol=1e-10, maxit=5000, zero_guess=True)
+        assert st == 0, (kind, info)
+        iters[kind] = info["iters"]
+    assert iters["pinv"] < iters["jacobi"] < iters["none"], iters
+
+
+def test_set_precond_argument_errors():
+    from paper_2501_03377_gb300 import Plan, binding as b
+
+    pl = _plan(8, 8, 8, ("P", "P", "N"))
+    assert b.tpcg_plan_set_precond(pl.handle, 7, 3, 1.3) == b.TPCG_ERR_INVALID_ARG
+    assert b.tpcg_plan_set_precond(pl.handle, b.TPCG_PRECOND_JACOBI, 0, 1.3) == b.TPCG_ERR_INVALID_ARG
+    assert b.tpcg_plan_set_precond(pl.handle, b.TPCG_PRECOND_JACOBI, 3, 0.5) == b.TPCG_ERR_INVALID_ARG
+    mixed = Plan(16, 16, 16, ("P", "P", "N"), prec="fp16")
+    assert b.tpcg_plan_set_precond(mixed.handle, b.TPCG_PRECOND_NONE, 3, 1.3) == b.TPCG_ERR_UNSUPPORTED
+    assert b.tpcg_plan_set_precond(mixed.handle, b.TPCG_PRECOND_PINV, 3, 1.3) == b.TPCG_OK
