@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--serving-requests", type=int, default=400)
     ap.add_argument("--serving-rate", type=float, default=200.0)
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-comparators", action="store_true")
     return ap.parse_args()
 
 
@@ -251,6 +252,52 @@ def run_serving(args, prec):
             "warmup_requests": len(sessions)}
 
 
+def run_comparators(torch, steps=3):
+    """Experiment 2 on synthetic data: PCG with M = I, Jacobi(3, 1.3) and the pseudoinverse (FP64 and
+    the mixed tensor-core form) on the 128x128x64 film (P/P/DN, 200 charged defects), tol 1e-10."""
+    from paper_2501_03377_gb300 import Plan
+    from inputs import synth
+
+    w = synth.workload_film_128(seed=0)
+    eta = torch.from_numpy(w["eta"]).cuda()
+    ups = torch.zeros_like(eta)
+    out = {"workload": w["name"], "tol": w["tol"]}
+    for name, prec, kind in (("cg", "fp64", "none"), ("jacobi_3_1.3", "fp64", "jacobi"),
+                             ("pinv_fp64", "fp64", "pinv"), ("pinv_fp16", "fp16", "pinv")):
+        pl = Plan(w["nx"], w["ny"], w["nz"], w["bcs"], prec=prec)
+        pl.set_precond(kind, 3, 1.3)
+        pl.solve(eta, ups, tol=w["tol"], maxit=5000, zero_guess=True)  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        infos = [pl.solve(eta, ups, tol=w["tol"], maxit=5000, zero_guess=True)[1] for _ in range(steps)]
+        e1.record()
+        torch.cuda.synchronize()
+        dt = e0.elapsed_time(e1) / 1e3
+        out[name] = {"solves_per_s": steps / dt, "ms_per_solve": 1e3 * dt / steps, "iters": infos[-1]["iters"],
+                     "rel_res_true": max(i["rel_res_true"] for i in infos),
+                     "status": max(i["status"] for i in infos)}
+        pl.close()
+    return out
+
+
+def run_efield(plan, ups, torch, reps=10):
+    """epsilon = -grad(ups) on the bench grid: algorithmic bytes 32 per point (ups in, three components out)."""
+    nz, ny, nx = ups.shape
+    ex, ey, ez = (torch.empty_like(ups) for _ in range(3))
+    plan.efield(ups, ex, ey, ez)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        plan.efield(ups, ex, ey, ez)
+    e1.record()
+    torch.cuda.synchronize()
+    dt = e0.elapsed_time(e1) / 1e3 / reps
+    return {"us_per_call": 1e6 * dt, "achieved_gbs": 32.0 * nx * ny * nz / dt / 1e9, "unit": "GB/s",
+            "bytes_per_point": 32}
+
+
 def run_batched(prec, torch):
     """48 independent solves, grids {64..160}^2 x {32..96}, random BCs, 1-8 right-hand sides each."""
     import numpy as np
@@ -283,39 +330,52 @@ def run_batched(prec, torch):
             "mean_iters": float(np.mean([i["iters"] for i in infos]))}
 
 
+# DRAM bytes (read + write) per launch measured by ncu on the 256x256x128 FP16 workload (one capture
+# per kernel; ncu flushes the caches before each launch).  Summaries and commands are under
+# profiles/.  Set an entry to None when its kernel changes.
+NCU_TRAFFIC_PER_LAUNCH = {
+    "modeprod_tc": 172.38e6 / 6,   # mean over the six passes of one application
+    "update": 297.88e6,
+    "direction": 84.75e6,
+    "true_residual": None,
+}
+
+
 def kernel_work(kind, plan_prec, N, dims, iters_total, applies_total, solves, checks_total):
-    """Algorithmic work of one kernel kind over the timed region: (amount, unit, bound).
+    """Algorithmic work of one kernel kind over the timed region: (amount, unit, bound, launches that did
+    the work).
 
     Bytes are the data each kernel must move once per grid point (halo re-reads and
     reduction scratch excluded); flops are the FP64 operations of the FP64 form."""
     n, q, t = dims
     mixed = plan_prec != "fp64"
     if kind == "modeprod_f64":
-        return applies_total * 4.0 * N * (n + q + t + 0.25) / 1e12, "TFLOP", "alu"
+        return applies_total * 4.0 * N * (n + q + t + 0.25) / 1e12, "TFLOP", "alu", applies_total * (6 if t > 1 else 4)
     if kind == "modeprod_tc":
         # per application (3D): passes 1-5 read + write FP16/BF16 (4 B each); the last pass reads
         # FP16 (2 B) and R in FP64 (8 B) and writes Z in FP32 (4 B)
-        per_apply = (5 * 4 + 14) * N if t > 1 else (3 * 4 + 14) * N
-        return applies_total * per_apply / 1e9, "GB", "hbm"
+        npass = 6 if t > 1 else 4
+        per_apply = ((npass - 1) * 4 + 14) * N
+        return applies_total * per_apply / 1e9, "GB", "hbm", applies_total * npass
     if kind == "direction":
         if mixed:  # Z (FP32) + P_old (int32) in, P (int32) out
-            return iters_total * 12.0 * N / 1e9, "GB", "hbm"
+            return iters_total * 12.0 * N / 1e9, "GB", "hbm", iters_total
         # FP64 form: FP64 flops per point: P = (Z - m) + beta P_old (3), 7-point stencil (7), <W, P> (2)
-        return iters_total * 12.0 * N / 1e12, "TFLOP", "alu"
+        return iters_total * 12.0 * N / 1e12, "TFLOP", "alu", iters_total
     if kind == "update":
         # mixed: P (4) + R (8+8) + U (8+8) + FP16 copy of R (2); FP64 form: P and W (8+8) + R + U
         per = (4 + 16 + 16 + 2) if mixed else (16 + 16 + 16)
-        return iters_total * per * N / 1e9, "GB", "hbm"
+        return iters_total * per * N / 1e9, "GB", "hbm", iters_total
     if kind == "true_residual":
         # eta (8) + U (8) in, R (8) + FP16 copy (2, mixed) out
-        return checks_total * (24 + (2 if mixed else 0)) * N / 1e9, "GB", "hbm"
+        return checks_total * (24 + (2 if mixed else 0)) * N / 1e9, "GB", "hbm", checks_total
     if kind == "eta_sum":
-        return solves * 8.0 * N / 1e9, "GB", "hbm"
+        return solves * 8.0 * N / 1e9, "GB", "hbm", solves
     if kind == "init_residual":  # zero initial guess: eta in, R (+ FP16 copy) out
-        return solves * (16 + (2 if mixed else 0)) * N / 1e9, "GB", "hbm"
+        return solves * (16 + (2 if mixed else 0)) * N / 1e9, "GB", "hbm", solves
     if kind == "center":
-        return solves * 16.0 * N / 1e9, "GB", "hbm"
-    return None, None, None
+        return solves * 16.0 * N / 1e9, "GB", "hbm", solves
+    return None, None, None, None
 
 
 def max_over_ranks(x, world, torch, device):
@@ -380,7 +440,8 @@ def run_ours(args, rank, world, torch):
     dom = max(kstats, key=lambda k: kstats[k]["total_ms"])
 
     def roof(kind):
-        amount, unit, bound = kernel_work(kind, prec, N, (nx, ny, nz), p_iters, p_applies, args.steps, p_checks)
+        amount, unit, bound, worked = kernel_work(kind, prec, N, (nx, ny, nz), p_iters, p_applies, args.steps,
+                                                  p_checks)
         if amount is None:
             return None
         secs = kstats[kind]["total_ms"] / 1e3
@@ -391,8 +452,12 @@ def run_ours(args, rank, world, torch):
                     "frac": achieved / peak, "traffic": None,
                     "peak_source": "derived FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz" if bound == "alu"
                     else f"{peak_src} bf16 sustained"}
+        traffic = NCU_TRAFFIC_PER_LAUNCH.get(kind) if prec == "fp16" and nz == 128 else None
         return {"kernel": kind, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None, "peak_source": f"{peak_src} hbm_gbs"}
+                "frac": achieved / hbm_peak, "traffic": traffic,
+                "traffic_unit": "DRAM bytes per launch (ncu, cold caches)" if traffic else None,
+                "algorithmic_bytes_per_launch": amount * 1e9 / worked if worked else None,
+                "peak_source": f"{peak_src} hbm_gbs"}
 
     roofline = roof(dom)
     for k in kernels:
@@ -448,12 +513,15 @@ def run_ours(args, rank, world, torch):
                     "worst_rel_res_true": max(i["rel_res_true"] for (_, i) in inf64)}
         p64.close()
 
-    serving = batched = None
+    serving = batched = comparators = efield = None
     if rank == 0 and world == 1 and prec != "fp64":
         if args.serving_requests > 0:
             serving = run_serving(args, prec)
         if not args.no_batched:
             batched = run_batched(prec, torch)
+        if not args.no_comparators:
+            comparators = run_comparators(torch)
+        efield = run_efield(plan, ups, torch)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -478,7 +546,7 @@ def run_ours(args, rank, world, torch):
             "gpu_launches": launches,
             "roofline": roofline, "kernels": kernels,
             "e2e": e2e, "cpu_baseline": cpu, "fp64_form": fp64_cmp, "bf16_form": bf16_cmp,
-            "serving": serving, "batched": batched, "clocks": clocks,
+            "serving": serving, "batched": batched, "comparators": comparators, "efield": efield, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     plan.close()
