@@ -515,9 +515,14 @@ __global__ void __launch_bounds__(TX* TY) k_direction_int(Geom g, const float* _
   const int first = st->first;
   const unsigned nx = (unsigned)g.nx, plane = (unsigned)g.nx * (unsigned)g.ny;
   const bool has_z = g.nz > 1;
-  // P_int at grid index i, formed from Z_s and P_{s-1}
-  auto form = [&](unsigned i) -> int {
-    const float v = fmaf(bs, i22_to_f32(first ? 0 : __ldg(Pold + i)), __ldg(Z + i));
+  // P_int formed from Z_s and P_{s-1} at one grid point
+  struct Raw {
+    float z;
+    int p;
+  };
+  auto load = [&](unsigned i) -> Raw { return Raw{__ldg(Z + i), first ? 0 : __ldg(Pold + i)}; };
+  auto form = [&](Raw r) -> int {
+    const float v = fmaf(bs, i22_to_f32(r.p), r.z);
     return sc != 0.0f ? f32_to_i22(v, sc) : f32_to_fixed(v, kp);  // 2^kp outside the FP32 range: integer path
   };
   // the end edge of an axis counts only for a Dirichlet end (ghost 0; a Neumann ghost gives a zero edge)
@@ -527,36 +532,53 @@ __global__ void __launch_bounds__(TX* TY) k_direction_int(Geom g, const float* _
   const int lane = threadIdx.x;
   float e = 0.0f;
   int pm = 0;
+  constexpr int UZ = 4;  // planes whose loads are issued together (memory-level parallelism)
   for_each_run(g, [&](int bx0, int by0, int k0, int k1) {
     const int x = bx0 + lane, y = by0 + threadIdx.y;
     const bool active = x < g.nx && y < g.ny;
     const int xg = ghost_index(x - 1, g.nx, g.bc[0]);  // used by lane 0 (the tile's left halo)
     const int yg = ghost_index(y - 1, g.ny, g.bc[1]);
-    const unsigned col = (unsigned)y * nx + (unsigned)x;
+    const bool has_xl = lane == 0 && active && xg >= 0, has_yl = active && yg >= 0;
+    // in-plane offsets; inactive or absent neighbours read a valid point and discard the value
+    const unsigned col = active ? (unsigned)y * nx + (unsigned)x : 0u;
+    const unsigned colx = has_xl ? (unsigned)y * nx + (unsigned)xg : col;
+    const unsigned coly = has_yl ? (unsigned)yg * nx + (unsigned)x : col;
     int zprev = 0;
     if (has_z && active) {
       const int kz = ghost_index(k0 - 1, g.nz, g.bc[2]);
-      zprev = kz >= 0 ? form((unsigned)kz * plane + col) : 0;
+      zprev = kz >= 0 ? form(load((unsigned)kz * plane + col)) : 0;
     }
-    for (int k = k0; k < k1; ++k) {
-      const unsigned base = (unsigned)k * plane;
-      const int c = active ? form(base + col) : 0;
-      int xl = __shfl_up_sync(0xffffffffu, c, 1);
-      if (lane == 0) xl = (active && xg >= 0) ? form(base + (unsigned)y * nx + (unsigned)xg) : 0;
-      const int yl = (active && yg >= 0) ? form(base + (unsigned)yg * nx + (unsigned)x) : 0;
-      const int zl = has_z ? zprev : c;
-      if (active) {
-        P[base + col] = c;
-        pm = max(pm, abs(c));
-        const float dx = i22_to_f32(c - xl), dy = i22_to_f32(c - yl), dz = i22_to_f32(c - zl);
-        float tx = dx * dx, ty = dy * dy, tz = dz * dz;
-        const float cf = i22_to_f32(c);
-        if (endx && x == g.nx - 1) tx = fmaf(cf, cf, tx);
-        if (endy && y == g.ny - 1) ty = fmaf(cf, cf, ty);
-        if (endz && k == g.nz - 1) tz = fmaf(cf, cf, tz);
-        e = fmaf(w0, tx, fmaf(w1, ty, fmaf(w2, tz, e)));
+    for (int kb = k0; kb < k1; kb += UZ) {
+      Raw own[UZ], up[UZ], left[UZ];
+#pragma unroll
+      for (int j = 0; j < UZ; ++j) {
+        const unsigned base = (unsigned)min(kb + j, k1 - 1) * plane;
+        own[j] = load(base + col);
+        up[j] = load(base + coly);
+        left[j] = load(base + colx);
       }
-      zprev = c;
+#pragma unroll
+      for (int j = 0; j < UZ; ++j) {
+        const int k = kb + j;
+        if (k >= k1) break;  // block-uniform
+        const int c = active ? form(own[j]) : 0;
+        int xl = __shfl_up_sync(0xffffffffu, c, 1);
+        if (lane == 0) xl = has_xl ? form(left[j]) : 0;
+        const int yl = has_yl ? form(up[j]) : 0;
+        const int zl = has_z ? zprev : c;
+        if (active) {
+          P[(unsigned)k * plane + col] = c;
+          pm = max(pm, abs(c));
+          const float dx = i22_to_f32(c - xl), dy = i22_to_f32(c - yl), dz = i22_to_f32(c - zl);
+          float tx = dx * dx, ty = dy * dy, tz = dz * dz;
+          const float cf = i22_to_f32(c);
+          if (endx && x == g.nx - 1) tx = fmaf(cf, cf, tx);
+          if (endy && y == g.ny - 1) ty = fmaf(cf, cf, ty);
+          if (endz && k == g.nz - 1) tz = fmaf(cf, cf, tz);
+          e = fmaf(w0, tx, fmaf(w1, ty, fmaf(w2, tz, e)));
+        }
+        zprev = c;
+      }
     }
   });
   double acc[1] = {f32_to_f64_int(e)};
