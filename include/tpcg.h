@@ -288,11 +288,12 @@ int tpcg_profile_end(tpcg_plan* plan, tpcg_kernel_stat* stats, int max_stats, in
 
 /* ---- allocation-free residual check ----------------------------------------
  * No counterpart in the paper.  For callers that must not allocate device
- * memory at the time they check a solution: work recorded while a stream is
- * being captured into a CUDA graph, time-stepping loops that cannot afford the
- * device synchronisation cudaMalloc/cudaFree may cause, or applications that
- * hand this library a fixed budget at start-up.  No plan is needed and nothing
- * is allocated (no cudaMalloc, no cudaFree, no allocating library call).
+ * memory at the time they check a solution: time-stepping loops that cannot
+ * afford the device synchronisation cudaMalloc/cudaFree may cause,
+ * applications that hand this library a fixed budget at start-up and own
+ * every allocation after it, or code running where allocating is not
+ * allowed.  No plan is needed and nothing is allocated (no cudaMalloc, no
+ * cudaFree, no allocating library call).
  *
  * Writes, on `stream`, out[0] = ||eta_hat - L ups||_2, out[1] = ||eta_hat||_2
  * and out[2] = the mean removed from eta (0 unless every present axis is P or

@@ -2,18 +2,19 @@
 // plan and without any device allocation.
 //
 // Who needs it: code that must not call cudaMalloc at the moment it checks a
-// solution -- for example work issued while a stream is being captured into a
-// CUDA graph, a time-stepping loop that cannot afford the implicit device
-// synchronisation cudaMalloc/cudaFree may cause, or a host application that
-// gives this library a fixed device budget at start-up.  Everything else in
-// this library allocates its scratch when a plan is created; this entry point
-// instead keeps its scratch (the per-block partial sums of two reductions and
-// their arrival counters) in one file-scope __device__ array.
+// solution -- a time-stepping loop that cannot afford the implicit device
+// synchronisation cudaMalloc/cudaFree may cause, a host application that
+// gives this library a fixed device budget at start-up and owns every
+// allocation after that, or code running where allocation is not permitted
+// at all.  Everything else in this library allocates its scratch when a plan
+// is created; this entry point instead keeps its scratch (the per-block
+// partial sums of two reductions and their arrival counters) in one
+// file-scope __device__ array.
 //
-// It is a variant of the true-residual kernel of the PCG driver (stencil of
-// eq. ourproblem plus a deterministic two-stage reduction): same arithmetic,
-// one grid point per thread with direct neighbour loads instead of the
-// shared-memory plane ring, and no residual vector is written.
+// It is a variant of the residual evaluation of the PCG driver: the FP64
+// 7-point stencil of eq. ourproblem with the same ghost values and a
+// deterministic two-stage reduction, one grid point per thread with direct
+// neighbour loads, and no residual vector is written.
 #include <mutex>
 
 #include "tpcg_dev.cuh"

@@ -1,8 +1,10 @@
 """The allocation-free residual check against the solver's own report.
 
 tpcg_residual_norms_noalloc is for callers that cannot allocate device memory
-when they verify a solution (e.g. while capturing a CUDA graph); it keeps its
-scratch in a static device array instead of a plan.  This file is collected
+when they verify a solution (a time-stepping loop that must not trigger the
+synchronisation an allocation can cause, or an application whose device
+memory budget is fixed at start-up); it keeps its scratch in a static device
+array instead of a plan.  This file is collected
 last so that a run stopping at the first failure has run every other test.
 It must pass alone in a fresh process and after the other tests.
 """
