@@ -171,6 +171,25 @@ __device__ __forceinline__ void store_lp(const LowPrec& lp, long long i, double 
       (lp.kind == 2) ? f32_to_f16_bits_rn(fminf(fmaxf(r32o, -65504.0f), 65504.0f)) : f64_to_bf16_bits(r);
 }
 
+// Two adjacent values (i even, row pitch even): one packed 4-byte store.
+__device__ __forceinline__ void store_lp_pair(const LowPrec& lp, long long i, double r0, double r1, float a32,
+                                              float b32) {
+  if (!lp.ptr) return;
+  long long j = i;
+  if (lp.pitch != lp.nx) {  // padded rows (mixed forms: N < 2^32, 32-bit division)
+    const unsigned row = (unsigned)i / (unsigned)lp.nx;
+    j = (long long)row * lp.pitch + ((unsigned)i - row * (unsigned)lp.nx);
+  }
+  uint32_t v;
+  if (lp.kind == 2) {
+    const __half2 h = __floats2half2_rn(fminf(fmaxf(a32, -65504.0f), 65504.0f), fminf(fmaxf(b32, -65504.0f), 65504.0f));
+    v = *reinterpret_cast<const uint32_t*>(&h);
+  } else {
+    v = (uint32_t)f64_to_bf16_bits(r0) | ((uint32_t)f64_to_bf16_bits(r1) << 16);
+  }
+  *reinterpret_cast<uint32_t*>(reinterpret_cast<uint16_t*>(lp.ptr) + j) = v;
+}
+
 // ------------------------------------------------------------------ fixed-point stencil driver
 // Same 32 x 8 tiles and 4-slot plane ring as stencil_sweep, for fields held as
 // exact integers (IT = int or long long), organised for memory-level
@@ -488,9 +507,9 @@ __global__ void __launch_bounds__(TX* TY) k_direction(Geom g, int zchunk, const 
 // (tile, plane) pairs, walked as runs of consecutive planes of one tile.
 // Ghosts: ghost_index() maps a neighbour across a boundary to the wrapped
 // index (P), the point itself (N: mirror) or -1 (D: the value 0).
-template <class Run>
+template <int TW = TX, class Run>
 __device__ __forceinline__ void for_each_run(const Geom& g, Run run) {
-  const unsigned bxn = (unsigned)(g.nx + TX - 1) / TX, byn = (unsigned)(g.ny + TY - 1) / TY;
+  const unsigned bxn = (unsigned)(g.nx + TW - 1) / TW, byn = (unsigned)(g.ny + TY - 1) / TY;
   const unsigned T = bxn * byn * (unsigned)g.nz;
   const unsigned G = gridDim.x, q = T / G, rm = T - q * G;
   const unsigned t_begin = blockIdx.x * q + min(blockIdx.x, rm);
@@ -501,7 +520,7 @@ __device__ __forceinline__ void for_each_run(const Geom& g, Run run) {
     const int k1 = (int)min((unsigned)g.nz, (unsigned)k0 + (t_end - t));
     t += (unsigned)(k1 - k0);
     const unsigned tyi = tile / bxn;
-    run((int)(tile - tyi * bxn) * TX, (int)tyi * TY, k0, k1);
+    run((int)(tile - tyi * bxn) * TW, (int)tyi * TY, k0, k1);
   }
 }
 
@@ -708,6 +727,116 @@ __global__ void __launch_bounds__(TX* TY, 4) k_update_int(Geom g, double* __rest
         U[i] = u;
         const unsigned long long ub = mag_key(u);
         um = ub > um ? ub : um;
+      }
+      zl = c;
+      zr = zr2;
+      if (k + 1 < k1) cur = nxt;
+    }
+  });
+  double acc[2] = {f32_to_f64_int(rr), f32_to_f64_int(sR)};
+  fold_umax(st, um);
+  grid_reduce<2>(acc, partials, &st->tickets[kTkUpd], gridDim.x, blockIdx.x,
+                 [st, shift, g](const double(&s)[2]) { fin_update(st, s, shift, g); });
+}
+
+// The same update with two adjacent x points per thread (even nx): R and U move
+// as 16-byte double2, P and its y neighbours as int2, the FP16 copy as one
+// packed pair; only the outer x neighbours of a pair come by warp shuffle.
+// A warp covers 64 consecutive x of one row.
+template <bool ZG>
+__global__ void __launch_bounds__(TX* TY, 3) k_update_pair(Geom g, double* __restrict__ U,
+                                                           const int* __restrict__ P, double* __restrict__ R,
+                                                           LowPrec lp, SolveState* st, double* partials) {
+  if (st->done) return;
+  const double alpha = st->alpha;
+  const double na0 = st->nah[0], na1 = st->nah[1], na2 = st->nah[2];  // -alpha / h^2 per axis
+  const int kp = st->kp;
+  const int shift = st->lp_shift;
+  const unsigned nx = (unsigned)g.nx, plane = (unsigned)g.nx * (unsigned)g.ny;
+  const bool has_z = g.nz > 1;
+  const int lane = threadIdx.x;
+  float rr = 0.0f, sR = 0.0f;
+  unsigned long long um = 0;
+  for_each_run<2 * TX>(g, [&](int bx0, int by0, int k0, int k1) {
+    const int x = bx0 + 2 * lane, y = by0 + threadIdx.y;  // points (x, y) and (x + 1, y)
+    const bool active = x < g.nx && y < g.ny;             // nx even: both points or neither
+    const unsigned col = active ? (unsigned)y * nx + (unsigned)x : 0u;
+    const int xgl = ghost_index(x - 1, g.nx, g.bc[0]), xgr = ghost_index(x + 2, g.nx, g.bc[0]);
+    const int ygl = ghost_index(y - 1, g.ny, g.bc[1]), ygr = ghost_index(y + 1, g.ny, g.bc[1]);
+    const bool own_xl = lane == 0, own_xr = lane == TX - 1 || x + 2 >= g.nx;  // halo or boundary
+    const unsigned coll = (unsigned)y * nx + (unsigned)max(xgl, 0), colr = (unsigned)y * nx + (unsigned)max(xgr, 0);
+    const unsigned colu = (unsigned)max(ygl, 0) * nx + (unsigned)x, cold = (unsigned)max(ygr, 0) * nx + (unsigned)x;
+    const bool has_yl = active && ygl >= 0, has_yr = active && ygr >= 0;
+    const bool has_xl = active && own_xl && xgl >= 0, has_xr = active && own_xr && xgr >= 0;
+    const int2 zero2 = make_int2(0, 0);
+    auto ld2 = [&](unsigned i) -> int2 { return __ldg(reinterpret_cast<const int2*>(P + i)); };
+    auto ldz = [&](int kk) -> int2 {  // P at (x.., y, kk), kk possibly a ghost plane
+      if (!has_z || !active) return zero2;
+      const int kz = ghost_index(kk, g.nz, g.bc[2]);
+      return kz >= 0 ? ld2((unsigned)kz * plane + col) : zero2;
+    };
+    struct Plane {
+      int2 c, yl, yr;
+      int xl, xr;
+      double2 r, u;
+    };
+    auto fetch = [&](int k, int2 c) {
+      Plane f;
+      const unsigned base = (unsigned)k * plane;
+      f.c = c;
+      f.yl = has_yl ? ld2(base + colu) : zero2;
+      f.yr = has_yr ? ld2(base + cold) : zero2;
+      f.xl = has_xl ? __ldg(P + base + coll) : 0;
+      f.xr = has_xr ? __ldg(P + base + colr) : 0;
+      f.r = active ? *reinterpret_cast<const double2*>(R + base + col) : make_double2(0.0, 0.0);
+      f.u = (active && !ZG) ? *reinterpret_cast<const double2*>(U + base + col) : make_double2(0.0, 0.0);
+      return f;
+    };
+    int2 zl = ldz(k0 - 1);
+    const int2 c0 = active ? ld2((unsigned)k0 * plane + col) : zero2;
+    int2 zr = (k0 + 1 < g.nz) ? (active ? ld2((unsigned)(k0 + 1) * plane + col) : zero2) : ldz(k0 + 1);
+    Plane cur = fetch(k0, c0);
+    for (int k = k0; k < k1; ++k) {
+      Plane nxt;
+      int2 zr2 = zero2;
+      if (k + 1 < k1) {  // loads of plane k+1 (and P two planes ahead) go out before plane k is processed
+        nxt = fetch(k + 1, zr);
+        zr2 = (k + 2 < g.nz) ? (active ? ld2((unsigned)(k + 2) * plane + col) : zero2) : ldz(k + 2);
+      }
+      const int2 c = cur.c;
+      int xl = __shfl_up_sync(0xffffffffu, c.y, 1), xr = __shfl_down_sync(0xffffffffu, c.x, 1);
+      if (own_xl) xl = cur.xl;
+      if (own_xr) xr = cur.xr;
+      const int2 zlv = has_z ? zl : c, zrv = has_z ? zr : c;
+      if (active) {
+        const int dx0 = 2 * c.x - xl - c.y, dx1 = 2 * c.y - c.x - xr;
+        const int dy0 = 2 * c.x - cur.yl.x - cur.yr.x, dy1 = 2 * c.y - cur.yl.y - cur.yr.y;
+        const int dz0 = 2 * c.x - zlv.x - zrv.x, dz1 = 2 * c.y - zlv.y - zrv.y;
+        double r0 = cur.r.x, r1 = cur.r.y;
+        if (g.uniform) {
+          r0 = fma(na0, i32_to_f64_scaled(dx0 + dy0 + dz0, -kp), r0);
+          r1 = fma(na0, i32_to_f64_scaled(dx1 + dy1 + dz1, -kp), r1);
+        } else {
+          r0 = fma(na0, i32_to_f64_scaled(dx0, -kp), r0);
+          r0 = fma(na1, i32_to_f64_scaled(dy0, -kp), r0);
+          if (dz0) r0 = fma(na2, i32_to_f64_scaled(dz0, -kp), r0);
+          r1 = fma(na0, i32_to_f64_scaled(dx1, -kp), r1);
+          r1 = fma(na1, i32_to_f64_scaled(dy1, -kp), r1);
+          if (dz1) r1 = fma(na2, i32_to_f64_scaled(dz1, -kp), r1);
+        }
+        const unsigned i = (unsigned)k * plane + col;
+        *reinterpret_cast<double2*>(R + i) = make_double2(r0, r1);
+        const float a32 = f64_to_f32_odd(r0, shift), b32 = f64_to_f32_odd(r1, shift);
+        store_lp_pair(lp, i, r0, r1, a32, b32);
+        rr = fmaf(a32, a32, fmaf(b32, b32, rr));
+        sR += a32 + b32;
+        const double p0 = i32_to_f64_scaled(c.x, -kp), p1 = i32_to_f64_scaled(c.y, -kp);
+        const double u0 = ZG ? alpha * p0 : fma(alpha, p0, cur.u.x);
+        const double u1 = ZG ? alpha * p1 : fma(alpha, p1, cur.u.y);
+        *reinterpret_cast<double2*>(U + i) = make_double2(u0, u1);
+        const unsigned long long k0b = mag_key(u0), k1b = mag_key(u1);
+        const unsigned long long kb = k0b > k1b ? k0b : k1b;
+        um = kb > um ? kb : um;
       }
       zl = c;
       zr = zr2;
@@ -986,10 +1115,13 @@ void launch_apply_laplacian(const tpcg_plan* p, const Geom& g, const double* x, 
 // the kernel's resources allow (at most 8), no more blocks than (tile, plane)
 // pairs.
 int setup_fx_grids(tpcg_plan* p) {
-  const void* fns[kFxCount] = {(const void*)k_direction_int, (const void*)k_update_int<false>,
+  const bool pair = p->nx % 2 == 0;  // the update kernel takes two x points per thread
+  const void* fns[kFxCount] = {(const void*)k_direction_int,
+                               pair ? (const void*)k_update_pair<false> : (const void*)k_update_int<false>,
                                (const void*)k_residual_fx<false>, (const void*)k_residual_fx<true>};
-  const long long T = (long long)((p->nx + TX - 1) / TX) * ((p->ny + TY - 1) / TY) * p->nz;
   for (int i = 0; i < kFxCount; ++i) {
+    const int tw = (i == kFxUpd && pair) ? 2 * TX : TX;
+    const long long T = (long long)((p->nx + tw - 1) / tw) * ((p->ny + TY - 1) / TY) * p->nz;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[i], TX * TY, 0) != cudaSuccess) return -1;
     per_sm = std::max(1, std::min(per_sm, 8));
@@ -1031,7 +1163,13 @@ void launch_update(const tpcg_plan* p, const Geom& g, double* U, int k, bool zer
   if (p->prec == TPCG_FP64)
     k_update<<<p->stream_blocks, 256, 0, p->stream>>>(g, U, (const double*)p->d_P[k & 1], p->d_W, p->d_R,
                                                        lowprec(p), p->d_state, p->d_partials);
-  else if (zero_guess_first)  // first update of a zero initial guess: U = alpha P
+  else if (g.nx % 2 == 0 && zero_guess_first)  // first update of a zero initial guess: U = alpha P
+    k_update_pair<true><<<p->fx_blocks[kFxUpd], p->st_block, 0, p->stream>>>(
+        g, U, (const int*)p->d_P[k & 1], p->d_R, lowprec(p), p->d_state, p->d_partials);
+  else if (g.nx % 2 == 0)
+    k_update_pair<false><<<p->fx_blocks[kFxUpd], p->st_block, 0, p->stream>>>(
+        g, U, (const int*)p->d_P[k & 1], p->d_R, lowprec(p), p->d_state, p->d_partials);
+  else if (zero_guess_first)
     k_update_int<true><<<p->fx_blocks[kFxUpd], p->st_block, 0, p->stream>>>(
         g, U, (const int*)p->d_P[k & 1], p->d_R, lowprec(p), p->d_state, p->d_partials);
   else
