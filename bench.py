@@ -336,7 +336,7 @@ def run_batched(prec, torch):
 NCU_TRAFFIC_PER_LAUNCH = {
     "modeprod_tc": 172.38e6 / 6,   # mean over the six passes of one application
     "update": None,  # changed since its capture (two x points per thread)
-    "direction": None,  # changed since its capture (loads of four planes issued together)
+    "direction": None,  # changed since its capture (two x points per thread)
     "true_residual": None,
 }
 
