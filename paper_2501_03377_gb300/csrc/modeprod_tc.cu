@@ -38,10 +38,20 @@ namespace tpcg {
 
 namespace {
 
-constexpr int kThreads = 352;   // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue, warp 10 TMA of R (last pass)
-constexpr int kEpiThreads = 256;
-constexpr int kRSlots = 4;                 // R chunks in flight (last pass): two slots per epilogue half
-constexpr int kRBytes = 128 * 16 * 8;      // one chunk: 128 rows x 16 FP64 columns
+// Warp roles: warp 0 TMA of the operand, warp 1 MMA, then the epilogue warps, one group of four per
+// share of the accumulator's 16-column chunks (a warp may only read its TMEM lane quadrant, warp % 4).
+// The plain passes use sixteen epilogue warps; the last pass of a solve keeps eight, plus one warp
+// that stages R by TMA.
+template <bool FINAL>
+struct TcWarps {
+  static constexpr int epi = FINAL ? 8 : 16;
+  static constexpr int groups = epi / 4;
+  static constexpr int threads = (2 + epi + (FINAL ? 1 : 0)) * 32;
+  static constexpr int rwarp = FINAL ? 2 + epi : -1;
+};
+constexpr int kRSlots = 16;                // R chunks in flight (last pass): eight slots per epilogue half
+constexpr int kRHalf = kRSlots / 2;
+constexpr int kRBytes = 128 * 16 * 2;      // one chunk: 128 rows x 16 FP16/BF16 columns
 constexpr int kTileRows = 128;
 constexpr int kKTile = 64;                 // BF16 elements per 128-byte swizzle row
 constexpr int kStageBytes = kTileRows * 128;
@@ -161,7 +171,7 @@ struct TcArgs {
   long long oa, ob, oc;
   int scale, singular;
   int vec;   // 16-element runs of the output are contiguous and 16-byte aligned
-  int rtma;  // last pass: R arrives by TMA (rows of R share one pitch), else by global loads
+  int rtma;  // last pass: R~ arrives by TMA, else by global loads
   int last;  // last pass: output is Z (FP32), undo the FP16 scaling
   int sG;    // the Hadamard step is multiplied by 2^-sG (FP16 range), undone on Z
   float gscale;          // 2^-sG
@@ -170,7 +180,8 @@ struct TcArgs {
   const float* lamB;
   const float* lamC;
   void* out;
-  const double* R;
+  const uint16_t* Rt;  // the tensor-core copy of R the first pass read (FP16 = R * 2^shR, or BF16 = R)
+  int rpitch;          // its row pitch (elements)
   SolveState* st;
   double* partials;
   long long N;
@@ -183,6 +194,17 @@ __device__ __forceinline__ float rcp_approx(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
+}
+
+// Two 16-bit elements packed in one word (low half first) as FP32; BF16 is the top half of an FP32.
+template <class InT>
+__device__ __forceinline__ float2 lp2_to_f32(uint32_t w) {
+  if constexpr (std::is_same<InT, __half>::value) {
+    __half2 h2 = *reinterpret_cast<__half2*>(&w);
+    return __half22float2(h2);
+  } else {
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+  }
 }
 
 template <class OutT>
@@ -221,7 +243,7 @@ __device__ __forceinline__ void store16(void* out, long long o, const float (&x)
 }
 
 template <int FORM, class InT, class OutT, bool FINAL>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
     k_modeprod_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
                   const __grid_constant__ CUtensorMap tmR, TcArgs a) {
   if (a.st && a.st->done) return;
@@ -259,13 +281,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull(b), 1);
-      mbar_init(tempty(b), kEpiThreads);
+      mbar_init(tempty(b), TcWarps<FINAL>::epi * 32);
     }
     mbar_init(vbar, 1);
     mbar_init(drain, 1);
     for (int s = 0; s < kRSlots; ++s) {
       mbar_init(rfull(s), 1);
-      mbar_init(rempty(s), kEpiThreads / 2);  // the four warps of one epilogue half
+      mbar_init(rempty(s), TcWarps<FINAL>::epi * 16);  // the warps of one epilogue half
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -282,11 +304,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tmem = *tmem_holder;
   const int ntiles = (a.rows + kTileRows - 1) / kTileRows;
 
-  // last pass: rho = <R, Z> from FP32 products of R * 2^shR (exact power-of-two scaling to unit RMS,
-  // one rounding) and Z, in compensated FP32 per thread; sum(Z) likewise; max |Z|
+  // last pass: rho = <R~, Z>, R~ the 16-bit copy of R the first pass consumed (FP16: R * 2^shR, BF16: R,
+  // brought to the same 2^shR scale), from FP32 products in compensated FP32 per thread; sum(Z)
+  // likewise; max |Z|
   Acc32 red0, red1;
   float zmax = 0.0f;
   const int shR = (FINAL && a.st) ? a.st->lp_shift_applied : 0;
+  const float rs = std::is_same<InT, __half>::value ? 1.0f : ldexpf(1.0f, shR);
 
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer
@@ -354,10 +378,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const unsigned long long t0 = gtimer();
     while (!mbar_try_wait(drain, 0) && gtimer() - t0 < kWaitLimitNs) {
     }
-  } else if (warp == 10) {
-    // ---------------- TMA of R (last pass): 16-column chunks of the tile's 128 rows.  Chunk ci belongs to
-    // epilogue half ci % 2, which consumes its chunks in order from its own two-slot ring (a ring shared
-    // by both halves would let one half run two phases ahead of a slot and read it early).
+  } else if (warp == TcWarps<FINAL>::rwarp) {
+    // ---------------- TMA of R~ (last pass): 16-column chunks of the tile's 128 rows.  Chunk ci belongs to
+    // epilogue half ci % 2, which consumes its chunks in order from its own ring of kRHalf slots (a ring
+    // shared by both halves would let one half run a phase ahead of a slot and read it early).
     if (rtma && lane == 0) {
       asm volatile("griddepcontrol.wait;" ::: "memory");
       const int nchunk = (a.Np + 15) / 16;
@@ -369,8 +393,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int ci = 0; ci < nchunk; ++ci) {
           const int hh = ci & 1;
           const int k = tcnt * Jh[hh] + (ci >> 1);
-          const int slot = 2 * hh + (k & 1);
-          if (!(ok = wait_bounded(rempty(slot), (uint32_t)(((k >> 1) & 1) ^ 1), ab))) break;
+          const int slot = hh * kRHalf + (k % kRHalf);
+          if (!(ok = wait_bounded(rempty(slot), (uint32_t)(((k / kRHalf) & 1) ^ 1), ab))) break;
           mbar_expect_tx(rfull(slot), kRBytes);
           tma_load_2d(sR + (uint32_t)slot * kRBytes, &tmR, ci * 16, tile * kTileRows, rfull(slot));
           issued[hh] = k + 1;
@@ -378,17 +402,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (!ok) {  // every issued load completes before the CTA may exit
         for (int hh = 0; hh < 2; ++hh)
-          for (int k = (issued[hh] > 2 ? issued[hh] - 2 : 0); k < issued[hh]; ++k) {
+          for (int k = (issued[hh] > kRHalf ? issued[hh] - kRHalf : 0); k < issued[hh]; ++k) {
             const unsigned long long t0 = gtimer();
-            while (!mbar_try_wait(rfull(2 * hh + (k & 1)), (uint32_t)((k >> 1) & 1)) && gtimer() - t0 < kWaitLimitNs) {
+            while (!mbar_try_wait(rfull(hh * kRHalf + (k % kRHalf)), (uint32_t)((k / kRHalf) & 1)) &&
+                   gtimer() - t0 < kWaitLimitNs) {
             }
           }
       }
     }
   } else if (warp >= 2) {
-    // ---------------- epilogue: two warps per TMEM lane quadrant, each taking every other 16-column chunk
+    // ---------------- epilogue: NG warps per TMEM lane quadrant, each taking every NG-th 16-column chunk
+    constexpr int NG = TcWarps<FINAL>::groups;
     const int q = warp & 3;          // TMEM lane quadrant this warp may access
-    const int h = (warp - 2) >> 2;   // which half of the column chunks
+    const int h = (warp - 2) >> 2;   // which share of the column chunks
     int tcount = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tcount) {
       const int b = tcount & 1;
@@ -398,7 +424,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int row0 = tile * kTileRows;
       if (FORM == 1) {
         // one thread per row; its 16 consecutive output columns are contiguous in memory (oc == 1).
-        // This warp takes the 16-column chunks c0 = h*16 + 32 j.  The TMEM load of chunk j+1 is
+        // This warp takes the 16-column chunks c0 = h*16 + 16*NG*j.  The TMEM load of chunk j+1 is
         // issued before chunk j is processed; in the last pass the residual R of chunk j+2 is
         // fetched while chunk j is processed.
         const int r = row0 + q * 32 + lane;
@@ -410,38 +436,38 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool null_row = a.singular && ia == 0 && ib == 0;
         const float zs = (a.last && a.shift_src) ? ldexpf(1.0f, a.sG - *a.shift_src) : 1.0f;
         const bool vec = a.vec && valid;
-        const int J = (a.Np - h * 16 + 31) / 32;  // chunks of this warp (uniform across the warp)
-        auto col = [&](int j) { return h * 16 + 32 * j; };
+        const int J = (a.Np - h * 16 + 16 * NG - 1) / (16 * NG);  // chunks of this warp (warp-uniform)
+        auto col = [&](int j) { return h * 16 + 16 * NG * j; };
         const int trow = q * 32 + lane;  // row within the tile
-        // R chunk j of this warp staged by TMA: wait for it, read this row's 16 values (128-byte swizzle:
-        // 16-byte piece i of row r sits at piece i ^ (r % 8)), release the slot.
-        auto take_r = [&](int j, double2 (&rb)[8]) {
+        // R~ chunk j of this warp staged by TMA: wait for it, read this row's 16 values (32-byte swizzle:
+        // 16-byte piece i of row r sits at piece i ^ ((r / 4) % 2)), release the slot.
+        auto take_r = [&](int j, uint4 (&rb)[2]) {
           const int k = tcount * J + j;  // this half's chunk sequence number
-          const int slot = 2 * h + (k & 1);
-          if (!wait_bounded(rfull(slot), (uint32_t)((k >> 1) & 1), ab)) return false;
-          const uint32_t base = sR + (uint32_t)slot * kRBytes + (uint32_t)trow * 128u;
+          const int slot = h * kRHalf + (k % kRHalf);
+          if (!wait_bounded(rfull(slot), (uint32_t)((k / kRHalf) & 1), ab)) return false;
+          const uint32_t base = sR + (uint32_t)slot * kRBytes + (uint32_t)trow * 32u;
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            double x, y;
-            asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];"
-                         : "=d"(x), "=d"(y)
-                         : "r"(base + (uint32_t)((i ^ (trow & 7)) << 4))
+          for (int i = 0; i < 2; ++i) {
+            uint4 w;
+            asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(w.x), "=r"(w.y), "=r"(w.z), "=r"(w.w)
+                         : "r"(base + (uint32_t)((i ^ ((trow >> 2) & 1)) << 4))
                          : "memory");
-            rb[i] = make_double2(x, y);
+            rb[i] = w;
           }
           // the slot is next written by TMA (async proxy): order these generic-proxy reads before it
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           mbar_arrive(rempty(slot));
           return true;
         };
-        auto fetch_r = [&](int j, double2 (&rb)[8]) {
+        auto fetch_r = [&](int j, uint4 (&rb)[2]) {
           if (FINAL && !rtma && vec && j < J && col(j) + 16 <= a.Cout) {
-            const double2* rp = reinterpret_cast<const double2*>(a.R + obase + col(j));
-#pragma unroll
-            for (int i = 0; i < 8; ++i) rb[i] = __ldg(rp + i);
+            const uint4* rp = reinterpret_cast<const uint4*>(a.Rt + (long long)r * a.rpitch + col(j));
+            rb[0] = __ldg(rp);
+            rb[1] = __ldg(rp + 1);
           }
         };
-        auto process = [&](int c0, const uint32_t (&t)[16], const double2 (&rcur)[8]) {
+        auto process = [&](int c0, const uint32_t (&t)[16], const uint4 (&rcur)[2]) {
           if (!valid) return;
           float v[16];
 #pragma unroll
@@ -465,11 +491,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (vec && c0 + 16 <= a.Cout) {
             store16<OutT>(a.out, obase + c0, v);
             if (FINAL) {
+              const uint32_t rw[8] = {rcur[0].x, rcur[0].y, rcur[0].z, rcur[0].w,
+                                      rcur[1].x, rcur[1].y, rcur[1].z, rcur[1].w};
               float d0 = 0.0f, d1 = 0.0f;
 #pragma unroll
               for (int i = 0; i < 8; ++i) {
-                d0 = fmaf(f64_to_f32_int(rcur[i].x, shR), v[2 * i], d0);
-                d1 = fmaf(f64_to_f32_int(rcur[i].y, shR), v[2 * i + 1], d1);
+                const float2 rr = lp2_to_f32<InT>(rw[i]);
+                d0 = fmaf(rr.x * rs, v[2 * i], d0);
+                d1 = fmaf(rr.y * rs, v[2 * i + 1], d1);
                 zmax = fmaxf(zmax, fmaxf(fabsf(v[2 * i]), fabsf(v[2 * i + 1])));
               }
               red0.add(d0 + d1);
@@ -484,7 +513,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const long long o = obase + (long long)c * a.oc;
                 store_out<OutT>(a.out, o, v[j]);
                 if (FINAL) {
-                  red0.add(f64_to_f32_int(__ldg(a.R + o), shR) * v[j]);
+                  const uint32_t rb16 = __ldg(a.Rt + (long long)r * a.rpitch + c);
+                  red0.add(lp2_to_f32<InT>(rb16).x * rs * v[j]);
                   red1.add(v[j]);
                   zmax = fmaxf(zmax, fabsf(v[j]));
                 }
@@ -493,7 +523,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         };
         uint32_t tA[16], tB[16];
-        double2 rA[8], rB[8];
+        uint4 rA[2], rB[2];
         if (rtma) {
           bool ok = true;
           for (int j = 0; ok && j < J; ++j) {
@@ -524,15 +554,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       } else {
         // one thread per output index; its 16 consecutive rows are contiguous in memory (ob == 1).
-        // Chunks (M-block mb, rows c0 = h*16 + 32 j) in a fixed order, TMEM loads one chunk ahead.
-        const int per_mb = (kTileRows - h * 16 + 31) / 32;
+        // Chunks (M-block mb, rows c0 = h*16 + 16*NG*j) in a fixed order, TMEM loads one chunk ahead.
+        const int per_mb = (kTileRows - h * 16 + 16 * NG - 1) / (16 * NG);
         const int J = a.MB * per_mb;
         auto taddr = [&](int j) {
-          const int mb = j / per_mb, c0 = h * 16 + 32 * (j - mb * per_mb);
+          const int mb = j / per_mb, c0 = h * 16 + 16 * NG * (j - mb * per_mb);
           return tacc + (uint32_t)(mb * 128 + c0);
         };
         auto process = [&](int j, const uint32_t (&t)[16]) {
-          const int mb = j / per_mb, c0 = h * 16 + 32 * (j - mb * per_mb);
+          const int mb = j / per_mb, c0 = h * 16 + 16 * NG * (j - mb * per_mb);
           const int c = mb * 128 + q * 32 + lane;
           const int r0 = row0 + c0;
           if (c >= a.Cout || r0 >= a.rows) return;
@@ -584,14 +614,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   if constexpr (FINAL) {
     // max |Z| of the block -> one atomicMax (order-independent, so deterministic)
-    __shared__ float smax[kThreads / 32];
+    __shared__ float smax[TcWarps<FINAL>::threads / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) zmax = fmaxf(zmax, __shfl_xor_sync(0xffffffffu, zmax, o));
     if (lane == 0) smax[warp] = zmax;
     __syncthreads();
     if (threadIdx.x == 0) {
       float m = 0.0f;
-      for (int w = 0; w < kThreads / 32; ++w) m = fmaxf(m, smax[w]);
+      for (int w = 0; w < TcWarps<FINAL>::threads / 32; ++w) m = fmaxf(m, smax[w]);
       atomicMax(&a.st->zmax_bits, __float_as_uint(m));
     }
     double acc[2] = {acc_value(red0), acc_value(red1)};
@@ -616,7 +646,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 struct TcStage {
   CUtensorMap tmX;
   CUtensorMap tmW;
-  CUtensorMap tmR;  // R (FP64) for the last pass of a solve; a copy of tmX when unused
+  CUtensorMap tmR;  // R~ (16-bit) for the last pass of a solve; a copy of tmX when unused
   int form;
   TcArgs args;
   int grid;
@@ -645,16 +675,17 @@ EncodeTiledFn encoder() {
   return fn;
 }
 
-// FP64 rows of R, 16 x 128 boxes with the 128-byte swizzle (last pass).
-int encode_r(CUtensorMap* map, const double* gaddr, int inner, long long outer, long long pitch_elems) {
+// Rows of the 16-bit copy of R, 16 x 128 boxes with the 32-byte swizzle (last pass).
+int encode_r(CUtensorMap* map, const void* gaddr, int inner, long long outer, long long pitch_elems, bool fp16) {
   EncodeTiledFn cuTensorMapEncodeTiled = encoder();
   if (!cuTensorMapEncodeTiled) return -1;
   cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
-  cuuint64_t strides[1] = {(cuuint64_t)pitch_elems * 8};
+  cuuint64_t strides[1] = {(cuuint64_t)pitch_elems * 2};
   cuuint32_t box[2] = {16, (cuuint32_t)kTileRows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = cuTensorMapEncodeTiled(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(gaddr), dims, strides,
-                                      box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+  CUresult r = cuTensorMapEncodeTiled(map, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                                      2, const_cast<void*>(gaddr), dims, strides,
+                                      box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
                                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : -1;
 }
@@ -696,7 +727,7 @@ template <int FORM, class InT, class OutT, bool FINAL>
 void launch(const TcStage& s, const TcArgs& a, cudaStream_t stream) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)s.grid);
-  cfg.blockDim = dim3(kThreads);
+  cfg.blockDim = dim3(TcWarps<FINAL>::threads);
   cfg.dynamicSmemBytes = s.smem;
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
@@ -797,14 +828,15 @@ int tc_plan_setup(tpcg_plan* p) {
     a.gscale = std::ldexp(1.0f, -sG);
     a.shift_src = tp->fp16 ? &p->d_state->lp_shift_applied : nullptr;
     const size_t vbytes = (size_t)a.KT * a.VR * 128;
-    size_t fixed = 1024 + vbytes + 256;
+    size_t fixed = 1024 + vbytes + 512;  // alignment, eigenbasis, barriers and the TMEM address
     if (a.tmem_cols > 512 || a.VR > 256 || fixed + 2 * kStageBytes > (size_t)kMaxSmem) {
       delete tp;
       return TPCG_ERR_UNSUPPORTED;
     }
-    // last pass of a solve: R by TMA when its rows share one pitch (16-byte multiple) and the ring fits
-    a.rtma = (sp.final_stage && st.form == 1 && sp.oa == (long long)sp.B * sp.ob && sp.ob % 2 == 0 &&
-              fixed + (size_t)kRSlots * kRBytes + 2 * kStageBytes <= (size_t)kMaxSmem)
+    // last pass of a solve: R~ (the first pass's input, rows of pitch pitch16[0], a multiple of 8
+    // elements) by TMA when the ring fits
+    a.rpitch = p->pitch16[0];
+    a.rtma = (sp.final_stage && st.form == 1 && fixed + (size_t)kRSlots * kRBytes + 2 * kStageBytes <= (size_t)kMaxSmem)
                  ? 1
                  : 0;
     if (a.rtma) fixed += (size_t)kRSlots * kRBytes;
@@ -821,7 +853,7 @@ int tc_plan_setup(tpcg_plan* p) {
       return TPCG_ERR_CUDA;
     }
     st.tmR = st.tmX;
-    if (a.rtma && encode_r(&st.tmR, p->d_R, sp.Cout, (long long)a.rows, sp.ob)) {
+    if (a.rtma && encode_r(&st.tmR, p->d_Rlp, sp.Cout, (long long)a.rows, a.rpitch, tp->fp16)) {
       delete tp;
       return TPCG_ERR_CUDA;
     }
@@ -853,7 +885,7 @@ int run_precond_tc(const tpcg_plan* p, float* Z, SolveState* st) {
     const bool last = (si == ns - 1);
     a.out = last ? (void*)Z : p->d_T[si & 1];
     a.st = st;
-    a.R = p->d_R;
+    a.Rt = reinterpret_cast<const uint16_t*>(p->d_Rlp);
     a.partials = p->d_partials;
     LaunchScope ls(p, kKModeTC);
     if (tp->fp16) launch_stage<__half>(s, a, last, st != nullptr, p->stream);
