@@ -114,6 +114,20 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// TMA store of one staged box (bulk async-group of the issuing thread).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int c0, int c1) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   (unsigned long long)map),
+               "r"(c0), "r"(c1), "r"(src)
+               : "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, uint32_t src, int c0, int c1, int c2) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                   (unsigned long long)map),
+               "r"(c0), "r"(c1), "r"(c2), "r"(src)
+               : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -172,6 +186,10 @@ struct TcArgs {
   int scale, singular;
   int vec;   // 16-element runs of the output are contiguous and 16-byte aligned
   int rtma;  // last pass: R~ arrives by TMA, else by global loads
+  int rhalf;   // R~ ring slots per epilogue half (last pass, rtma)
+  int tstore;  // outputs leave through shared memory by TMA stores (tmO), else by direct stores
+  int tperm;   // form 2 output map: dims {B, A, Cout} (1) or {B, Cout, A} (0)
+  int aux;     // bytes of shared memory after the stages: R~ ring (last pass) and output staging
   int last;  // last pass: output is Z (FP32), undo the FP16 scaling
   int sG;    // the Hadamard step is multiplied by 2^-sG (FP16 range), undone on Z
   float gscale;          // 2^-sG
@@ -204,6 +222,41 @@ __device__ __forceinline__ float2 lp2_to_f32(uint32_t w) {
     return __half22float2(h2);
   } else {
     return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+  }
+}
+
+// Row `lane` of a [32][16] output box staged for a TMA store: FP16/BF16 rows of 32 bytes under the
+// 32-byte swizzle (16-byte piece i at i ^ ((lane / 4) % 2)), FP32 rows of 64 bytes under the 64-byte
+// swizzle (piece i at i ^ ((lane / 2) % 4)); eight consecutive lanes then cover all 32 banks.
+template <class OutT>
+__device__ __forceinline__ void stage_row(uint32_t buf, int lane, const float (&x)[16]) {
+  if constexpr (sizeof(OutT) == 2) {
+    uint32_t pk[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if constexpr (std::is_same<OutT, __half>::value) {
+        __half2 h2 = __floats2half2_rn(x[2 * i], x[2 * i + 1]);
+        pk[i] = *reinterpret_cast<uint32_t*>(&h2);
+      } else {
+        __nv_bfloat162 h2 = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+        pk[i] = *reinterpret_cast<uint32_t*>(&h2);
+      }
+    }
+    const uint32_t row = buf + (uint32_t)lane * 32u;
+    const uint32_t sw = (uint32_t)((lane >> 2) & 1);
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+      asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(row + (((uint32_t)i ^ sw) << 4)), "r"(pk[4 * i]),
+                   "r"(pk[4 * i + 1]), "r"(pk[4 * i + 2]), "r"(pk[4 * i + 3])
+                   : "memory");
+  } else {
+    const uint32_t row = buf + (uint32_t)lane * 64u;
+    const uint32_t sw = (uint32_t)((lane >> 1) & 3);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(row + (((uint32_t)i ^ sw) << 4)), "f"(x[4 * i]),
+                   "f"(x[4 * i + 1]), "f"(x[4 * i + 2]), "f"(x[4 * i + 3])
+                   : "memory");
   }
 }
 
@@ -245,7 +298,7 @@ __device__ __forceinline__ void store16(void* out, long long o, const float (&x)
 template <int FORM, class InT, class OutT, bool FINAL>
 __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
     k_modeprod_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
-                  const __grid_constant__ CUtensorMap tmR, TcArgs a) {
+                  const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmO, TcArgs a) {
   if (a.st && a.st->done) return;
   // Programmatic dependent launch: the next pass may start its prologue (barriers, TMEM, eigenbasis
   // load) on SMs this grid frees; it waits (griddepcontrol.wait) before touching this pass's output.
@@ -258,7 +311,10 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
   const uint32_t sD = sV + (uint32_t)a.KT * a.VR * 128u;
   const bool rtma = FINAL && a.rtma;
   const uint32_t sR = sD + (uint32_t)a.NS * kStageBytes;  // 1024-aligned: V and stages are multiples of 1 KB
-  uint8_t* barp = sm + (size_t)a.KT * a.VR * 128 + (size_t)a.NS * kStageBytes + (rtma ? (size_t)kRSlots * kRBytes : 0);
+  // output staging: two [32][16] boxes per epilogue warp, after the R~ ring of the last pass
+  constexpr uint32_t kOBytes = 32u * 16u * (uint32_t)sizeof(OutT);
+  const uint32_t sO = sR + (rtma ? (uint32_t)(2 * a.rhalf * kRBytes) : 0u);
+  uint8_t* barp = sm + (size_t)a.KT * a.VR * 128 + (size_t)a.NS * kStageBytes + (size_t)a.aux;
   const uint32_t bars = smem_u32(barp);
   const int NS = a.NS;
   auto full = [&](int s) { return bars + 8u * s; };
@@ -381,7 +437,8 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
   } else if (warp == TcWarps<FINAL>::rwarp) {
     // ---------------- TMA of R~ (last pass): 16-column chunks of the tile's 128 rows.  Chunk ci belongs to
     // epilogue half ci % 2, which consumes its chunks in order from its own ring of kRHalf slots (a ring
-    // shared by both halves would let one half run a phase ahead of a slot and read it early).
+    // shared by both halves would let one half run a phase ahead of a slot and read it early).  Slot s of
+    // half hh is hh * kRHalf + s, s < a.rhalf; its bytes sit at ring position hh * a.rhalf + s.
     if (rtma && lane == 0) {
       asm volatile("griddepcontrol.wait;" ::: "memory");
       const int nchunk = (a.Np + 15) / 16;
@@ -393,18 +450,19 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
         for (int ci = 0; ci < nchunk; ++ci) {
           const int hh = ci & 1;
           const int k = tcnt * Jh[hh] + (ci >> 1);
-          const int slot = hh * kRHalf + (k % kRHalf);
-          if (!(ok = wait_bounded(rempty(slot), (uint32_t)(((k / kRHalf) & 1) ^ 1), ab))) break;
+          const int slot = hh * kRHalf + (k % a.rhalf);
+          if (!(ok = wait_bounded(rempty(slot), (uint32_t)(((k / a.rhalf) & 1) ^ 1), ab))) break;
           mbar_expect_tx(rfull(slot), kRBytes);
-          tma_load_2d(sR + (uint32_t)slot * kRBytes, &tmR, ci * 16, tile * kTileRows, rfull(slot));
+          tma_load_2d(sR + (uint32_t)(hh * a.rhalf + k % a.rhalf) * kRBytes, &tmR, ci * 16, tile * kTileRows,
+                      rfull(slot));
           issued[hh] = k + 1;
         }
       }
       if (!ok) {  // every issued load completes before the CTA may exit
         for (int hh = 0; hh < 2; ++hh)
-          for (int k = (issued[hh] > kRHalf ? issued[hh] - kRHalf : 0); k < issued[hh]; ++k) {
+          for (int k = (issued[hh] > a.rhalf ? issued[hh] - a.rhalf : 0); k < issued[hh]; ++k) {
             const unsigned long long t0 = gtimer();
-            while (!mbar_try_wait(rfull(hh * kRHalf + (k % kRHalf)), (uint32_t)((k / kRHalf) & 1)) &&
+            while (!mbar_try_wait(rfull(hh * kRHalf + (k % a.rhalf)), (uint32_t)((k / a.rhalf) & 1)) &&
                    gtimer() - t0 < kWaitLimitNs) {
             }
           }
@@ -415,6 +473,26 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
     constexpr int NG = TcWarps<FINAL>::groups;
     const int q = warp & 3;          // TMEM lane quadrant this warp may access
     const int h = (warp - 2) >> 2;   // which share of the column chunks
+    // TMA store of one [32][16] box from this warp's two staging buffers (used alternately; a buffer is
+    // rewritten once the store issued from it two boxes earlier has finished reading it)
+    const uint32_t sOw = sO + (uint32_t)(warp - 2) * 2u * kOBytes;
+    int ocnt = 0;
+    auto emit = [&](const float (&v)[16], int x0, int x1, int x2) {
+      const uint32_t buf = sOw + (uint32_t)(ocnt & 1) * kOBytes;
+      if (ocnt >= 2) {
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        __syncwarp();
+      }
+      stage_row<OutT>(buf, lane, v);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> async-proxy reads
+      __syncwarp();
+      if (lane == 0) {
+        if (FORM == 1) tma_store_2d(&tmO, buf, x0, x1);
+        else tma_store_3d(&tmO, buf, x0, x1, x2);
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      }
+      ++ocnt;
+    };
     int tcount = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tcount) {
       const int b = tcount & 1;
@@ -443,9 +521,9 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
         // 16-byte piece i of row r sits at piece i ^ ((r / 4) % 2)), release the slot.
         auto take_r = [&](int j, uint4 (&rb)[2]) {
           const int k = tcount * J + j;  // this half's chunk sequence number
-          const int slot = h * kRHalf + (k % kRHalf);
-          if (!wait_bounded(rfull(slot), (uint32_t)((k / kRHalf) & 1), ab)) return false;
-          const uint32_t base = sR + (uint32_t)slot * kRBytes + (uint32_t)trow * 32u;
+          const int slot = h * kRHalf + (k % a.rhalf);
+          if (!wait_bounded(rfull(slot), (uint32_t)((k / a.rhalf) & 1), ab)) return false;
+          const uint32_t base = sR + (uint32_t)(h * a.rhalf + k % a.rhalf) * kRBytes + (uint32_t)trow * 32u;
 #pragma unroll
           for (int i = 0; i < 2; ++i) {
             uint4 w;
@@ -468,7 +546,7 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
           }
         };
         auto process = [&](int c0, const uint32_t (&t)[16], const uint4 (&rcur)[2]) {
-          if (!valid) return;
+          if (!valid && !a.tstore) return;
           float v[16];
 #pragma unroll
           for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(t[i]);
@@ -488,8 +566,10 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] *= zs;
           }
+          if (a.tstore) emit(v, c0, row0 + q * 32, 0);  // rows past `rows`, columns past Cout: clipped
+          if (!valid) return;
           if (vec && c0 + 16 <= a.Cout) {
-            store16<OutT>(a.out, obase + c0, v);
+            if (!a.tstore) store16<OutT>(a.out, obase + c0, v);
             if (FINAL) {
               const uint32_t rw[8] = {rcur[0].x, rcur[0].y, rcur[0].z, rcur[0].w,
                                       rcur[1].x, rcur[1].y, rcur[1].z, rcur[1].w};
@@ -511,7 +591,7 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
               const int c = c0 + j;
               if (c < a.Cout) {
                 const long long o = obase + (long long)c * a.oc;
-                store_out<OutT>(a.out, o, v[j]);
+                if (!a.tstore) store_out<OutT>(a.out, o, v[j]);
                 if (FINAL) {
                   const uint32_t rb16 = __ldg(a.Rt + (long long)r * a.rpitch + c);
                   red0.add(lp2_to_f32<InT>(rb16).x * rs * v[j]);
@@ -563,14 +643,21 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
         };
         auto process = [&](int j, const uint32_t (&t)[16]) {
           const int mb = j / per_mb, c0 = h * 16 + 16 * NG * (j - mb * per_mb);
-          const int c = mb * 128 + q * 32 + lane;
+          const int cb = mb * 128 + q * 32;
+          const int c = cb + lane;
           const int r0 = row0 + c0;
-          if (c >= a.Cout || r0 >= a.rows) return;
+          if (r0 >= a.rows) return;  // warp-uniform
           float v[16];
 #pragma unroll
           for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(t[i]);
           int ia = r0 / a.B;
           int ib = r0 - ia * a.B;
+          if (a.tstore) {  // B % 16 == 0: the 16 rows share one a; output indices past Cout are clipped
+            if (a.tperm) emit(v, ib, ia, cb);
+            else emit(v, ib, cb, ia);
+            return;
+          }
+          if (c >= a.Cout) return;
           if (a.vec && ib + 16 <= a.B && r0 + 16 <= a.rows) {
             store16<OutT>(a.out, (long long)ia * a.oa + ib + (long long)c * a.oc, v);
           } else {
@@ -604,6 +691,8 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
       tc_fence_before();
       mbar_arrive(tempty(b));
     }
+    // this warp's TMA stores are complete before the CTA may exit
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   }
 
   __syncthreads();
@@ -647,6 +736,7 @@ struct TcStage {
   CUtensorMap tmX;
   CUtensorMap tmW;
   CUtensorMap tmR;  // R~ (16-bit) for the last pass of a solve; a copy of tmX when unused
+  CUtensorMap tmO;  // the pass's output for TMA stores (args.tstore); a copy of tmX when unused
   int form;
   TcArgs args;
   int grid;
@@ -687,6 +777,43 @@ int encode_r(CUtensorMap* map, const void* gaddr, int inner, long long outer, lo
                                       2, const_cast<void*>(gaddr), dims, strides,
                                       box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
                                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : -1;
+}
+
+// The output of a pass as boxes of 16 contiguous elements x 32 lanes (one epilogue warp's chunk).
+// Form 1 (lane = row, contiguous output index): 2D {Cout, rows}, rows of one pitch.  Form 2 (lane =
+// output index, contiguous rows): 3D {B, Cout, A} or, when A has the smaller stride, {B, A, Cout}.
+// Returns -1 when the layout does not fit these maps (the pass then stores directly).
+int encode_out(CUtensorMap* map, void* gaddr, int esize, bool fp16, int form, const TcArgs& a, int* tperm) {
+  EncodeTiledFn cuTensorMapEncodeTiled = encoder();
+  if (!cuTensorMapEncodeTiled) return -1;
+  const CUtensorMapDataType dt = (esize == 4) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                              : (fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+  const CUtensorMapSwizzle sw = (esize == 4) ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
+  CUresult r;
+  if (form == 1) {
+    if (!(a.B == 1 || a.oa == (long long)a.B * a.ob)) return -1;
+    const long long pitch = (a.B == 1) ? a.oa : a.ob;
+    if (pitch <= 0 || (pitch * esize) % 16 != 0) return -1;
+    cuuint64_t dims[2] = {(cuuint64_t)a.Cout, (cuuint64_t)a.rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(pitch * esize)};
+    cuuint32_t box[2] = {16, 32};
+    cuuint32_t estr[2] = {1, 1};
+    r = cuTensorMapEncodeTiled(map, dt, 2, gaddr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    *tperm = 0;
+  } else {
+    if (a.ob != 1 || a.B % 16 != 0 || (a.oc * esize) % 16 != 0 || (a.oa * esize) % 16 != 0) return -1;
+    const int A = a.rows / a.B;
+    const bool perm = a.oa < a.oc;
+    cuuint64_t dims[3] = {(cuuint64_t)a.B, (cuuint64_t)(perm ? A : a.Cout), (cuuint64_t)(perm ? a.Cout : A)};
+    cuuint64_t strides[2] = {(cuuint64_t)((perm ? a.oa : a.oc) * esize), (cuuint64_t)((perm ? a.oc : a.oa) * esize)};
+    cuuint32_t box[3] = {16, perm ? 1u : 32u, perm ? 32u : 1u};
+    cuuint32_t estr[3] = {1, 1, 1};
+    r = cuTensorMapEncodeTiled(map, dt, 3, gaddr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    *tperm = perm ? 1 : 0;
+  }
   return r == CUDA_SUCCESS ? 0 : -1;
 }
 
@@ -735,7 +862,7 @@ void launch(const TcStage& s, const TcArgs& a, cudaStream_t stream) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_modeprod_tc<FORM, InT, OutT, FINAL>, s.tmX, s.tmW, s.tmR, a);
+  cudaLaunchKernelEx(&cfg, k_modeprod_tc<FORM, InT, OutT, FINAL>, s.tmX, s.tmW, s.tmR, s.tmO, a);
 }
 
 template <class InT>
@@ -833,13 +960,33 @@ int tc_plan_setup(tpcg_plan* p) {
       delete tp;
       return TPCG_ERR_UNSUPPORTED;
     }
+    // outputs by TMA stores through per-warp staging when the layout allows (the last pass writes Z,
+    // FP32, to the plan's Z buffer)
+    const bool last = sp.final_stage != 0;
+    const int esz = last ? 4 : 2;
+    void* out_addr = last ? p->d_Z : p->d_T[si & 1];
+    st.tmO = st.tmX;
+    a.tstore = (encode_out(&st.tmO, out_addr, esz, tp->fp16, st.form, a, &a.tperm) == 0) ? 1 : 0;
+    // staging bytes: two [32][16] boxes per epilogue warp (sixteen warps; eight in the last pass of a solve)
+    const size_t stage_plain = a.tstore ? (size_t)TcWarps<false>::epi * 2 * 32 * 16 * esz : 0;
+    const size_t stage_final = (a.tstore && last) ? (size_t)TcWarps<true>::epi * 2 * 32 * 16 * esz : 0;
     // last pass of a solve: R~ (the first pass's input, rows of pitch pitch16[0], a multiple of 8
-    // elements) by TMA when the ring fits
+    // elements) by TMA through the largest ring (up to kRHalf slots per half) that leaves two stages
     a.rpitch = p->pitch16[0];
-    a.rtma = (sp.final_stage && st.form == 1 && fixed + (size_t)kRSlots * kRBytes + 2 * kStageBytes <= (size_t)kMaxSmem)
-                 ? 1
-                 : 0;
-    if (a.rtma) fixed += (size_t)kRSlots * kRBytes;
+    a.rhalf = 0;
+    if (last && st.form == 1) {
+      const size_t room = (size_t)kMaxSmem - fixed - 2 * kStageBytes;
+      const size_t rh = room > stage_final ? (room - stage_final) / (2 * (size_t)kRBytes) : 0;
+      a.rhalf = (int)std::min<size_t>(kRHalf, rh);
+    }
+    a.rtma = (a.rhalf >= 2) ? 1 : 0;
+    if (!a.rtma) a.rhalf = 0;
+    a.aux = (int)std::max(stage_plain, (size_t)(2 * a.rhalf * kRBytes) + stage_final);
+    if (fixed + (size_t)a.aux + 2 * kStageBytes > (size_t)kMaxSmem) {  // no room for staging: direct stores
+      a.tstore = 0;
+      a.aux = 2 * a.rhalf * kRBytes;
+    }
+    fixed += (size_t)a.aux;
     a.NS = (int)std::min<size_t>(8, (kMaxSmem - fixed) / kStageBytes);
     st.smem = fixed + (size_t)a.NS * kStageBytes;
     const int ntiles = (a.rows + kTileRows - 1) / kTileRows;
@@ -884,6 +1031,7 @@ int run_precond_tc(const tpcg_plan* p, float* Z, SolveState* st) {
     TcArgs a = s.args;
     const bool last = (si == ns - 1);
     a.out = last ? (void*)Z : p->d_T[si & 1];
+    if (last && (void*)Z != p->d_Z) a.tstore = 0;  // the output map names the plan's Z buffer
     a.st = st;
     a.Rt = reinterpret_cast<const uint16_t*>(p->d_Rlp);
     a.partials = p->d_partials;
