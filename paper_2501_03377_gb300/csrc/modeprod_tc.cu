@@ -399,6 +399,13 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
     // ---------------- MMA issuer
     constexpr uint32_t fmt = std::is_same<InT, __half>::value ? 0u : 1u;
     const uint32_t idesc = (FORM == 1) ? idesc_f16kind(128, a.Np, fmt) : idesc_f16kind(128, 128, fmt);
+    // Shared-memory descriptors: the address field holds address / 16 in its low 14 bits (shared memory
+    // is below 256 KB, so offsets add without a carry out of the field); a 16-element K step is +2.
+    // The issue loop is kept short: one thread issuing small MMAs is otherwise slower than the tensor
+    // pipe executing them.
+    const unsigned long long dX0 = sw128_desc(sD), dV0 = sw128_desc(sV);
+    const uint32_t vkt = (uint32_t)(a.VR * 128) >> 4;  // one 64-wide K tile of V
+    const bool two_mb = (FORM != 1) && a.MB > 1;       // second 128-row block of V (form 2)
     bool ok = wait_bounded(vbar, 0, ab);
     int it = 0, tcount = 0;
     for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++tcount) {
@@ -410,18 +417,20 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
         const int s = it % NS;
         if (!(ok = wait_bounded(full(s), (uint32_t)((it / NS) & 1), ab))) break;
         tc_fence_after();
-        const uint32_t xs = sD + (uint32_t)s * kStageBytes;
-        const uint32_t vs = sV + (uint32_t)kt * a.VR * 128u;
+        const unsigned long long xd = dX0 + (uint32_t)s * (uint32_t)(kStageBytes >> 4);
+        const unsigned long long vd = dV0 + (uint32_t)kt * vkt;
+        const int nk = min(4, (a.C - kt * kKTile + 15) >> 4);  // K steps of 16 inside C
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
-          if (kt * kKTile + kk * 16 >= a.C) break;
-          const uint32_t accum = (kt > 0 || kk > 0) ? 1u : 0u;
-          if (FORM == 1) {
-            tc_mma(dacc, sw128_desc(xs + kk * 32), sw128_desc(vs + kk * 32), idesc, accum);
-          } else {
-            for (int mb = 0; mb < a.MB; ++mb)
-              tc_mma(dacc + (uint32_t)(mb * 128), sw128_desc(vs + (uint32_t)mb * kStageBytes + kk * 32),
-                     sw128_desc(xs + kk * 32), idesc, accum);
+          if (kk < nk) {
+            const uint32_t accum = (kt > 0 || kk > 0) ? 1u : 0u;
+            if (FORM == 1) {
+              tc_mma(dacc, xd + 2u * kk, vd + 2u * kk, idesc, accum);
+            } else {
+              tc_mma(dacc, vd + 2u * kk, xd + 2u * kk, idesc, accum);
+              if (two_mb)
+                tc_mma(dacc + 128u, vd + (uint32_t)(kStageBytes >> 4) + 2u * kk, xd + 2u * kk, idesc, accum);
+            }
           }
         }
         tc_commit(empty(s));
