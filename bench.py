@@ -334,10 +334,13 @@ def run_batched(prec, torch):
 # per kernel; ncu flushes the caches before each launch).  Summaries and commands are under
 # profiles/.  Set an entry to None when its kernel changes.
 NCU_TRAFFIC_PER_LAUNCH = {
-    "modeprod_tc": 172.38e6 / 6,   # mean over the six passes of one application
-    "update": None,  # changed since its capture (two x points per thread)
-    "direction": None,  # changed since its capture (two x points per thread)
-    "true_residual": None,
+    # DRAM bytes (read + write) per launch from the ncu captures summarised under profiles/ (cold caches)
+    # tensor-core passes: mean over the six passes of one application; passes 1-3 and 6 captured
+    # (17.0, 17.0, 16.8, 34.8 MB), passes 4 and 5 (the same FP16-in / FP16-out shape) taken as pass 1
+    "modeprod_tc": (4 * 17.0e6 + 16.8e6 + 34.8e6) / 6,
+    "update": 286.3e6,
+    "direction": 77.4e6,
+    "true_residual": 197.4e6,  # a launch that checks (the others return at once)
 }
 
 
@@ -352,10 +355,10 @@ def kernel_work(kind, plan_prec, N, dims, iters_total, applies_total, solves, ch
     if kind == "modeprod_f64":
         return applies_total * 4.0 * N * (n + q + t + 0.25) / 1e12, "TFLOP", "alu", applies_total * (6 if t > 1 else 4)
     if kind == "modeprod_tc":
-        # per application (3D): passes 1-5 read + write FP16/BF16 (4 B each); the last pass reads
-        # FP16 (2 B) and R in FP64 (8 B) and writes Z in FP32 (4 B)
+        # per application (3D): passes 1-5 read + write FP16/BF16 (2 + 2 B); the last pass reads its
+        # FP16 input (2 B) and the FP16 copy of R (2 B) and writes Z in FP32 (4 B)
         npass = 6 if t > 1 else 4
-        per_apply = ((npass - 1) * 4 + 14) * N
+        per_apply = ((npass - 1) * 4 + 8) * N
         return applies_total * per_apply / 1e9, "GB", "hbm", applies_total * npass
     if kind == "direction":
         if mixed:  # Z (FP32) + P_old (int32) in, P (int32) out
