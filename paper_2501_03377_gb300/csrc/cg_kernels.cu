@@ -713,6 +713,119 @@ __global__ void __launch_bounds__(TX* TY) k_direction_pair(Geom g, const float* 
   });
 }
 
+// The same direction with four adjacent x points per thread (nx a multiple of
+// 4): Z and P_old as 16-byte quads, P stored as int4; the left neighbour of a
+// quad's first point comes from the previous lane (lane 0: the tile's halo
+// column).  Loads, address arithmetic and loop control are shared by four
+// points instead of two.
+__global__ void __launch_bounds__(TX* TY) k_direction_quad(Geom g, const float* __restrict__ Z,
+                                                           const int* __restrict__ Pold, int* __restrict__ P,
+                                                           SolveState* st, double* partials) {
+  if (st->done) return;
+  const int kp = st->kp_next;
+  const float sc = (kp >= -126 && kp <= 127) ? __int_as_float((kp + 127) << 23) : 0.0f;  // 2^kp
+  const float bs = st->bs_next;  // beta_s 2^-kp_{s-1} (0 for the first direction)
+  const int first = st->first;
+  const unsigned nx = (unsigned)g.nx, plane = (unsigned)g.nx * (unsigned)g.ny;
+  const bool has_z = g.nz > 1;
+  struct Raw4 {
+    float4 z;
+    int4 p;
+  };
+  auto load4 = [&](unsigned i) -> Raw4 {
+    return Raw4{__ldg(reinterpret_cast<const float4*>(Z + i)),
+                first ? make_int4(0, 0, 0, 0) : __ldg(reinterpret_cast<const int4*>(Pold + i))};
+  };
+  auto form1 = [&](float z, int po) -> int {
+    const float v = fmaf(bs, i22_to_f32(po), z);
+    return sc != 0.0f ? f32_to_i22(v, sc) : f32_to_fixed(v, kp);  // 2^kp outside the FP32 range: integer path
+  };
+  auto form4 = [&](const Raw4& r) -> int4 {
+    return make_int4(form1(r.z.x, r.p.x), form1(r.z.y, r.p.y), form1(r.z.z, r.p.z), form1(r.z.w, r.p.w));
+  };
+  const bool endx = g.bc[0] == kBcD || g.bc[0] == kBcND, endy = g.bc[1] == kBcD || g.bc[1] == kBcND;
+  const bool endz = has_z && (g.bc[2] == kBcD || g.bc[2] == kBcND);
+  const float w0 = g.ih2f[0], w1 = g.ih2f[1], w2 = g.ih2f[2];
+  const int lane = threadIdx.x;
+  float e = 0.0f;
+  int pm = 0;
+  constexpr int UZ = 2;  // planes whose loads are issued together
+  for_each_run<4 * TX>(g, [&](int bx0, int by0, int k0, int k1) {
+    const int x = bx0 + 4 * lane, y = by0 + threadIdx.y;
+    const bool active = x < g.nx && y < g.ny;  // nx a multiple of 4: all four points or none
+    const int xg = ghost_index(x - 1, g.nx, g.bc[0]);
+    const int yg = ghost_index(y - 1, g.ny, g.bc[1]);
+    const bool has_xl = lane == 0 && active && xg >= 0, has_yl = active && yg >= 0;
+    const unsigned col = active ? (unsigned)y * nx + (unsigned)x : 0u;
+    const unsigned colx = has_xl ? (unsigned)y * nx + (unsigned)xg : col;
+    const unsigned coly = has_yl ? (unsigned)yg * nx + (unsigned)x : col;
+    const bool last_x = x + 3 == g.nx - 1;
+    int4 zprev = make_int4(0, 0, 0, 0);
+    if (has_z && active) {
+      const int kz = ghost_index(k0 - 1, g.nz, g.bc[2]);
+      if (kz >= 0) zprev = form4(load4((unsigned)kz * plane + col));
+    }
+    for (int kb = k0; kb < k1; kb += UZ) {
+      Raw4 own[UZ], up[UZ];
+      float lz[UZ];
+      int lp[UZ];
+#pragma unroll
+      for (int j = 0; j < UZ; ++j) {
+        const unsigned base = (unsigned)min(kb + j, k1 - 1) * plane;
+        own[j] = load4(base + col);
+        up[j] = load4(base + coly);
+        lz[j] = __ldg(Z + base + colx);
+        lp[j] = first ? 0 : __ldg(Pold + base + colx);
+      }
+#pragma unroll
+      for (int j = 0; j < UZ; ++j) {
+        const int k = kb + j;
+        if (k >= k1) break;  // block-uniform
+        int4 c = make_int4(0, 0, 0, 0);
+        if (active) c = form4(own[j]);
+        int xl = __shfl_up_sync(0xffffffffu, c.w, 1);
+        if (lane == 0) xl = has_xl ? form1(lz[j], lp[j]) : 0;
+        const int4 yl = has_yl ? form4(up[j]) : make_int4(0, 0, 0, 0);
+        const int4 zl = has_z ? zprev : c;
+        if (active) {
+          *reinterpret_cast<int4*>(P + (unsigned)k * plane + col) = c;
+          pm = max(pm, max(max(abs(c.x), abs(c.y)), max(abs(c.z), abs(c.w))));
+          const float dx0 = i22_to_f32(c.x - xl), dx1 = i22_to_f32(c.y - c.x), dx2 = i22_to_f32(c.z - c.y),
+                      dx3 = i22_to_f32(c.w - c.z);
+          const float dy0 = i22_to_f32(c.x - yl.x), dy1 = i22_to_f32(c.y - yl.y), dy2 = i22_to_f32(c.z - yl.z),
+                      dy3 = i22_to_f32(c.w - yl.w);
+          const float dz0 = i22_to_f32(c.x - zl.x), dz1 = i22_to_f32(c.y - zl.y), dz2 = i22_to_f32(c.z - zl.z),
+                      dz3 = i22_to_f32(c.w - zl.w);
+          float tx = fmaf(dx0, dx0, fmaf(dx1, dx1, fmaf(dx2, dx2, dx3 * dx3)));
+          float ty = fmaf(dy0, dy0, fmaf(dy1, dy1, fmaf(dy2, dy2, dy3 * dy3)));
+          float tz = fmaf(dz0, dz0, fmaf(dz1, dz1, fmaf(dz2, dz2, dz3 * dz3)));
+          if (endx && last_x) {
+            const float cf = i22_to_f32(c.w);
+            tx = fmaf(cf, cf, tx);
+          }
+          if ((endy && y == g.ny - 1) || (endz && k == g.nz - 1)) {
+            const float c0 = i22_to_f32(c.x), c1 = i22_to_f32(c.y), c2 = i22_to_f32(c.z), c3 = i22_to_f32(c.w);
+            const float sq = fmaf(c0, c0, fmaf(c1, c1, fmaf(c2, c2, c3 * c3)));
+            if (endy && y == g.ny - 1) ty += sq;
+            if (endz && k == g.nz - 1) tz += sq;
+          }
+          e = fmaf(w0, tx, fmaf(w1, ty, fmaf(w2, tz, e)));
+        }
+        zprev = c;
+      }
+    }
+  });
+  double acc[1] = {f32_to_f64_int(e)};
+  const unsigned long long m = block_max_u64((unsigned long long)pm);
+  if (threadIdx.x + threadIdx.y == 0) atomicMax(&st->pmax_bits, (unsigned)m);
+  grid_reduce<1>(acc, partials, &st->tickets[kTkDir], gridDim.x, blockIdx.x, [st, kp, g](const double(&s)[1]) {
+    st->kp = kp;
+    st->pmax = ldexp((double)atomicExch(&st->pmax_bits, 0u), -kp);
+    const double v[1] = {ldexp(s[0], -2 * kp)};
+    fin_direction(st, v, g);
+  });
+}
+
 // ------------------------------------------------------------------ update
 // U += alpha P and R -= alpha W (Algorithm 1), low-precision copy of R,
 // ||R||^2 and sum(R) for the stop test and the centring correction of rho,
@@ -1217,11 +1330,13 @@ void launch_apply_laplacian(const tpcg_plan* p, const Geom& g, const double* x, 
 // pairs.
 int setup_fx_grids(tpcg_plan* p) {
   const bool pair = p->nx % 2 == 0;  // direction and update take two x points per thread
-  const void* fns[kFxCount] = {pair ? (const void*)k_direction_pair : (const void*)k_direction_int,
+  const bool quad = p->nx % 4 == 0;  // direction takes four
+  const void* fns[kFxCount] = {quad ? (const void*)k_direction_quad
+                                    : (pair ? (const void*)k_direction_pair : (const void*)k_direction_int),
                                pair ? (const void*)k_update_pair<false> : (const void*)k_update_int<false>,
                                (const void*)k_residual_fx<false>, (const void*)k_residual_fx<true>};
   for (int i = 0; i < kFxCount; ++i) {
-    const int tw = ((i == kFxUpd || i == kFxDir) && pair) ? 2 * TX : TX;
+    const int tw = (i == kFxDir && quad) ? 4 * TX : (((i == kFxUpd || i == kFxDir) && pair) ? 2 * TX : TX);
     const long long T = (long long)((p->nx + tw - 1) / tw) * ((p->ny + TY - 1) / TY) * p->nz;
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[i], TX * TY, 0) != cudaSuccess) return -1;
@@ -1255,6 +1370,9 @@ void launch_direction(const tpcg_plan* p, const Geom& g, int k) {
     k_direction<<<p->st_grid, p->st_block, 0, p->stream>>>(
         g, p->st_zchunk, (const double*)p->d_Z, (const double*)p->d_P[(k + 1) & 1], (double*)p->d_P[k & 1], p->d_W,
         p->d_state, p->d_partials);
+  else if (g.nx % 4 == 0)
+    k_direction_quad<<<p->fx_blocks[kFxDir], p->st_block, 0, p->stream>>>(
+        g, (const float*)p->d_Z, (const int*)p->d_P[(k + 1) & 1], (int*)p->d_P[k & 1], p->d_state, p->d_partials);
   else if (g.nx % 2 == 0)
     k_direction_pair<<<p->fx_blocks[kFxDir], p->st_block, 0, p->stream>>>(
         g, (const float*)p->d_Z, (const int*)p->d_P[(k + 1) & 1], (int*)p->d_P[k & 1], p->d_state, p->d_partials);
