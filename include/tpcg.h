@@ -140,6 +140,23 @@ int tpcg_solve(tpcg_plan* plan, const double* eta, double* ups, double tol, int 
 int tpcg_solve_host(tpcg_plan* plan, const double* eta_host, double* ups_host, double tol, int maxit,
                     unsigned flags, tpcg_info* info);
 
+/* Solve L ups_host[i] = eta_host[i] for i = 0 .. nrhs-1 on one plan, every
+ * vector in HOST memory (pinned memory lets the copies overlap): the
+ * copy in of right-hand side i+1 and the copy out of solution i-1 run on
+ * plan-owned copy streams while solve i runs, through two plan-owned pairs of
+ * device buffers (allocated on first use; tpcg_plan_device_bytes counts
+ * them).  Each solve is the one tpcg_solve_host performs (same arguments
+ * tol, maxit, flags; Algorithm 1); ups_host[i] holds the initial guess unless
+ * flags has TPCG_ZERO_GUESS.  infos (host array of nrhs, may be NULL)
+ * receives one report per solve.  The solves have no counterpart in the
+ * paper beyond Algorithm 1 itself: this call only schedules their copies.
+ * Returns when every solution is in host memory: TPCG_OK, else the first
+ * per-solve status that was not TPCG_OK (every solve still runs), or
+ * TPCG_ERR_INVALID_ARG (nrhs < 0, a NULL array or entry, tol or maxit out of
+ * range: nothing runs), TPCG_ERR_OOM, TPCG_ERR_CUDA.                        */
+int tpcg_solve_host_stream(tpcg_plan* plan, int nrhs, const double* const* eta_host, double* const* ups_host,
+                           double tol, int maxit, unsigned flags, tpcg_info* infos);
+
 /* Many independent solves in one call (the batched form of tpcg_solve).
  * Solve s uses plans[s] and has nrhs[s] right-hand sides (nrhs == NULL: one
  * each) stored back to back: right-hand side r is eta[s] + r*N_s and its

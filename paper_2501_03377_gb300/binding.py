@@ -93,6 +93,8 @@ _SIGS = {
     "tpcg_plan_device_bytes": (_I, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     "tpcg_solve": (_I, [_P, _P, _P, _D, _I, ctypes.c_uint, ctypes.POINTER(tpcg_info)]),
     "tpcg_solve_host": (_I, [_P, _P, _P, _D, _I, ctypes.c_uint, ctypes.POINTER(tpcg_info)]),
+    "tpcg_solve_host_stream": (_I, [_P, _I, ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I, ctypes.c_uint,
+                                    ctypes.POINTER(tpcg_info)]),
     "tpcg_solve_batched": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_I), ctypes.POINTER(_P), ctypes.POINTER(_P),
                                 ctypes.POINTER(_D), _I, ctypes.c_uint, ctypes.POINTER(tpcg_info)]),
     "tpcg_precond_apply": (_I, [_P, _P, _P]),
@@ -178,6 +180,15 @@ def tpcg_solve_host(plan, eta_ptr, ups_ptr, tol, maxit, flags):
     info = tpcg_info()
     st = lib().tpcg_solve_host(plan, _P(eta_ptr), _P(ups_ptr), float(tol), int(maxit), int(flags), ctypes.byref(info))
     return st, info
+
+
+def tpcg_solve_host_stream(plan, eta_ptrs, ups_ptrs, tol, maxit, flags):
+    n = len(eta_ptrs)
+    infos = (tpcg_info * max(1, n))()
+    ea = (_P * max(1, n))(*[_P(x) for x in eta_ptrs])
+    ua = (_P * max(1, n))(*[_P(x) for x in ups_ptrs])
+    st = lib().tpcg_solve_host_stream(plan, n, ea, ua, float(tol), int(maxit), int(flags), infos)
+    return st, [infos[i] for i in range(n)]
 
 
 def tpcg_solve_batched(plans, nrhs, eta_ptrs, ups_ptrs, tols, maxit, flags):
@@ -405,6 +416,20 @@ class Plan:
         st, info = tpcg_solve_host(self.handle, eta_host.data_ptr(), ups_host.data_ptr(), tol, maxit,
                                    TPCG_ZERO_GUESS if zero_guess else 0)
         return st, info.as_dict()
+
+    def solve_host_stream(self, etas_host, ups_host, tol=1e-10, maxit=100, zero_guess=False):
+        """Solve for a list of host right-hand sides with the copies overlapping the solves."""
+        if len(etas_host) != len(ups_host):
+            raise ValueError("one solution buffer per right-hand side")
+        import torch
+
+        for t in list(etas_host) + list(ups_host):
+            if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous() or tuple(t.shape) != self.shape:
+                raise ValueError(f"expected contiguous float64 CPU tensors of shape {self.shape}")
+        st, infos = tpcg_solve_host_stream(self.handle, [t.data_ptr() for t in etas_host],
+                                           [t.data_ptr() for t in ups_host], tol, maxit,
+                                           TPCG_ZERO_GUESS if zero_guess else 0)
+        return st, [i.as_dict() for i in infos]
 
     def precond(self, r, z):
         self._check(r)

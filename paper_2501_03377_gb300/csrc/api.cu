@@ -161,6 +161,15 @@ void free_plan(tpcg_plan* p) {
   cudaFree(p->d_T[1]);
   cudaFree(p->d_eta_h);
   cudaFree(p->d_ups_h);
+  cudaFree(p->d_eta_h2);
+  cudaFree(p->d_ups_h2);
+  for (int i = 0; i < 2; ++i) {
+    if (p->ev_in[i]) cudaEventDestroy(p->ev_in[i]);
+    if (p->ev_solved[i]) cudaEventDestroy(p->ev_solved[i]);
+    if (p->ev_out[i]) cudaEventDestroy(p->ev_out[i]);
+  }
+  if (p->s_in) cudaStreamDestroy(p->s_in);
+  if (p->s_out) cudaStreamDestroy(p->s_out);
   cudaFree(p->d_state);
   cudaFree(p->d_partials);
   cudaFree(p->d_err);
@@ -666,6 +675,77 @@ int tpcg_solve_host(tpcg_plan* plan, const double* eta_host, double* ups_host, d
     return TPCG_ERR_CUDA;
   if (cudaStreamSynchronize(plan->stream) != cudaSuccess) return TPCG_ERR_CUDA;
   return rc;
+}
+
+// Two slots: solve i uses slot i % 2.  The copy in of solve i+1 (stream s_in) waits until the copy out
+// of solve i-1, which used the same slot, has finished; the solve waits for its copy in; the copy out of
+// solve i (stream s_out) waits for the solve.  Copies in and out thereby overlap the neighbouring solves.
+int tpcg_solve_host_stream(tpcg_plan* plan, int nrhs, const double* const* eta_host, double* const* ups_host,
+                           double tol, int maxit, unsigned flags, tpcg_info* infos) {
+  if (!plan || nrhs < 0 || (nrhs > 0 && (!eta_host || !ups_host))) return TPCG_ERR_INVALID_ARG;
+  if (!(tol > 0.0) || !(tol < 1.0) || maxit < 1) return TPCG_ERR_INVALID_ARG;
+  for (int i = 0; i < nrhs; ++i)
+    if (!eta_host[i] || !ups_host[i]) return TPCG_ERR_INVALID_ARG;
+  if (nrhs == 0) return TPCG_OK;
+  DeviceGuard dg(plan->device);
+  if (!plan->d_eta_h && (dalloc(plan, &plan->d_eta_h, (size_t)plan->N) || dalloc(plan, &plan->d_ups_h, (size_t)plan->N)))
+    return TPCG_ERR_OOM;
+  if (!plan->d_eta_h2 &&
+      (dalloc(plan, &plan->d_eta_h2, (size_t)plan->N) || dalloc(plan, &plan->d_ups_h2, (size_t)plan->N)))
+    return TPCG_ERR_OOM;
+  if (!plan->s_in) {
+    if (cudaStreamCreateWithFlags(&plan->s_in, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&plan->s_out, cudaStreamNonBlocking) != cudaSuccess)
+      return TPCG_ERR_CUDA;
+    for (int i = 0; i < 2; ++i)
+      if (cudaEventCreateWithFlags(&plan->ev_in[i], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&plan->ev_solved[i], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&plan->ev_out[i], cudaEventDisableTiming) != cudaSuccess)
+        return TPCG_ERR_CUDA;
+  }
+  double* const de[2] = {plan->d_eta_h, plan->d_eta_h2};
+  double* const du[2] = {plan->d_ups_h, plan->d_ups_h2};
+  const size_t bytes = sizeof(double) * (size_t)plan->N;
+  const bool warm = !(flags & TPCG_ZERO_GUESS);
+  // earlier work on the plan's stream (a previous call's solve) precedes this call's copies
+  if (cudaEventRecord(plan->ev_solved[0], plan->stream) != cudaSuccess ||
+      cudaStreamWaitEvent(plan->s_in, plan->ev_solved[0], 0) != cudaSuccess)
+    return TPCG_ERR_CUDA;
+  auto copy_in = [&](int i) -> bool {
+    const int s = i & 1;
+    if (i >= 2 && cudaStreamWaitEvent(plan->s_in, plan->ev_out[s], 0) != cudaSuccess) return false;
+    if (cudaMemcpyAsync(de[s], eta_host[i], bytes, cudaMemcpyHostToDevice, plan->s_in) != cudaSuccess) return false;
+    if (warm && cudaMemcpyAsync(du[s], ups_host[i], bytes, cudaMemcpyHostToDevice, plan->s_in) != cudaSuccess)
+      return false;
+    return cudaEventRecord(plan->ev_in[s], plan->s_in) == cudaSuccess;
+  };
+  int result = TPCG_OK, rc = TPCG_OK;
+  if (!copy_in(0)) rc = TPCG_ERR_CUDA;
+  for (int i = 0; i < nrhs && !rc; ++i) {
+    const int s = i & 1;
+    if (i + 1 < nrhs && !copy_in(i + 1)) {
+      rc = TPCG_ERR_CUDA;
+      break;
+    }
+    if (cudaStreamWaitEvent(plan->stream, plan->ev_in[s], 0) != cudaSuccess) {
+      rc = TPCG_ERR_CUDA;
+      break;
+    }
+    const int st = solve_impl(plan, de[s], du[s], tol, maxit, flags, infos ? &infos[i] : nullptr);
+    if (st == TPCG_ERR_CUDA || st == TPCG_ERR_INVALID_ARG) {
+      rc = st;
+      break;
+    }
+    if (st != TPCG_OK && result == TPCG_OK) result = st;
+    if (cudaEventRecord(plan->ev_solved[s], plan->stream) != cudaSuccess ||
+        cudaStreamWaitEvent(plan->s_out, plan->ev_solved[s], 0) != cudaSuccess ||
+        cudaMemcpyAsync(ups_host[i], du[s], bytes, cudaMemcpyDeviceToHost, plan->s_out) != cudaSuccess ||
+        cudaEventRecord(plan->ev_out[s], plan->s_out) != cudaSuccess)
+      rc = TPCG_ERR_CUDA;
+  }
+  const bool synced = cudaStreamSynchronize(plan->s_in) == cudaSuccess && cudaStreamSynchronize(plan->s_out) == cudaSuccess;
+  if (rc) return rc;
+  return synced ? result : TPCG_ERR_CUDA;
 }
 
 int tpcg_precond_apply(tpcg_plan* plan, const double* r, double* z) {

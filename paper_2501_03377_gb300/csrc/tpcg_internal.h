@@ -126,6 +126,12 @@ struct tpcg_plan {
   size_t t_elems = 0;
   double* d_eta_h = nullptr;  // device copies for tpcg_solve_host
   double* d_ups_h = nullptr;
+  // tpcg_solve_host_stream: the second slot of its two-slot pipeline (the first is d_eta_h / d_ups_h),
+  // its copy streams and its per-slot events (all created on first use)
+  double* d_eta_h2 = nullptr;
+  double* d_ups_h2 = nullptr;
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_solved[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
   tpcg::SolveState* d_state = nullptr;
   tpcg::SolveState* h_state = nullptr;  // pinned
   cudaEvent_t ev_state = nullptr;        // recorded after each read-back of the device state

@@ -252,3 +252,46 @@ def test_cuboid_256_tc_full_size(prec):
     Vs, _, G = o.pinv_init(sh, w["bcs"])
     direct = o.center(o.pinv_apply(etah, Vs, G))
     assert rel_err(to_oracle(u), direct) <= 1e-9
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_host_stream_matches_host_solves(prec):
+    """tpcg_solve_host_stream overlaps the copies of neighbouring solves; every solution is bitwise the
+    one tpcg_solve_host returns for the same right-hand side (same plan, same launch configuration),
+    across more solves than its two buffer slots, with a zero and with a given initial guess."""
+    nx, ny, nz, bcs = 64, 48, 24, ("P", "P", "N")
+    pl = _plan(nx, ny, nz, bcs, prec=prec)
+    etas = [torch.from_numpy(synth.defect_rhs(nx, ny, nz, bcs, 20, 1.5, seed=40 + i).copy()).pin_memory()
+            for i in range(5)]
+    outs = [torch.zeros_like(e).pin_memory() for e in etas]
+    st, infos = pl.solve_host_stream(etas, outs, tol=1e-10, maxit=40, zero_guess=True)
+    assert st == 0 and len(infos) == 5
+    for e, u, info in zip(etas, outs, infos):
+        ref = torch.zeros_like(e).pin_memory()
+        st1, info1 = pl.solve_host(e, ref, tol=1e-10, maxit=40, zero_guess=True)
+        assert st1 == 0 and info["status"] == 0 and info["iters"] == info1["iters"]
+        assert info["rel_res_true"] <= 1e-10
+        assert torch.equal(u, ref)
+    # warm starts (half of each solution): the initial guesses are read from the output buffers
+    guesses = [(0.5 * u).pin_memory() for u in outs[:3]]
+    outs = [g.clone().pin_memory() for g in guesses]
+    st, infos = pl.solve_host_stream(etas[:3], outs, tol=1e-10, maxit=40)
+    assert st == 0
+    for e, g, u in zip(etas[:3], guesses, outs):
+        ref = g.clone().pin_memory()
+        st1, _ = pl.solve_host(e, ref, tol=1e-10, maxit=40)
+        assert st1 == 0
+        assert torch.equal(u, ref)
+
+
+def test_host_stream_rejects_bad_arguments():
+    pl = _plan(16, 16, 8, ("P", "P", "N"), prec="fp16")
+    e = torch.zeros(8, 16, 16, dtype=torch.float64).pin_memory()
+    u = torch.zeros_like(e).pin_memory()
+    from paper_2501_03377_gb300 import binding as b
+
+    assert pl.solve_host_stream([], [], tol=1e-10)[0] == 0
+    assert b.tpcg_solve_host_stream(pl.handle, [e.data_ptr()], [u.data_ptr()], 2.0, 10, 0)[0] == b.TPCG_ERR_INVALID_ARG
+    assert b.tpcg_solve_host_stream(pl.handle, [e.data_ptr()], [0], 1e-10, 10, 0)[0] == b.TPCG_ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        pl.solve_host_stream([e], [], tol=1e-10)
