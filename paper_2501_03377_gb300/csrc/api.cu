@@ -21,7 +21,7 @@ void launch_eta_sum(const tpcg_plan* p, const Geom& g, const double* eta, const 
 void launch_direction(const tpcg_plan* p, const Geom& g, int k);
 void launch_update(const tpcg_plan* p, const Geom& g, double* U, int k, bool zero_guess_first);
 void launch_true_residual(const tpcg_plan* p, const Geom& g, const double* eta, const double* U, bool force);
-void launch_center_u(const tpcg_plan* p, const Geom& g, double* U);
+void launch_center_u(const tpcg_plan* p, const Geom& g, double* U, int iter_lo);
 void launch_zero(const tpcg_plan* p, long long N, double* U);
 void launch_to_lp(const tpcg_plan* p, const Geom& g, const double* r);
 void launch_norm_shift(const tpcg_plan* p, const Geom& g, const double* r);
@@ -258,6 +258,8 @@ int enqueue_iterations(SolveJob& j, int count) {
     const int rc = run_precond(p, p->d_R, p->d_Z, p->d_state);  // Z = M R, rho, beta
     if (rc) return rc;
   }
+  // singular operators: centre U on the device if the stop test succeeded inside this chunk
+  if (p->singular) launch_center_u(p, g, j.ups, j.issued);
   j.issued += count;
   return TPCG_OK;
 }
@@ -287,7 +289,10 @@ int job_start(SolveJob& j) {
   int rc = run_precond(p, p->d_R, p->d_Z, p->d_state);
   if (rc) return rc;
   j.issued = 0;
-  j.chunk = (p->prec == TPCG_FP64) ? 2 : 4;
+  // first chunk: the iteration count of the plan's previous converged solve (similar problems repeat
+  // on a plan), so that one read-back usually finds the solve finished; later chunks are short
+  const int deflt = (p->prec == TPCG_FP64) ? 2 : 4;
+  j.chunk = p->last_iters > 0 ? std::min(std::min(p->last_iters, 12), j.maxit + 1) : deflt;
   if ((rc = enqueue_iterations(j, j.chunk))) return rc;
   j.chunk = (p->prec == TPCG_FP64) ? 1 : 2;
   j.phase = 1;
@@ -309,17 +314,22 @@ int job_step(SolveJob& j) {
     const Geom g = make_geom(p);
     j.status_host = hs->status;
     j.done_host = hs->done;
-    if (hs->done == 2) {
-      launch_zero(p, g.N, j.ups);  // eta_hat = 0: minimum-norm solution is 0
-    } else {
-      if (!hs->done || hs->status == TPCG_ERR_BREAKDOWN) {
-        launch_true_residual(p, g, j.eta, j.ups, true);  // report the true residual of the returned iterate
-        if (!hs->done) j.status_host = TPCG_ERR_NOT_CONVERGED;
-      }
-      if (p->singular) launch_center_u(p, g, j.ups);
-    }
     j.phase = 2;
-    return enqueue_state_readback(p);
+    // converged: U was centred on the device behind the chunk (singular operators), the state just
+    // read back is final
+    const bool finished = hs->done == 1 && hs->status == TPCG_OK;
+    if (!finished) {
+      if (hs->done == 2) {
+        launch_zero(p, g.N, j.ups);  // eta_hat = 0: minimum-norm solution is 0
+      } else {
+        if (!hs->done || hs->status == TPCG_ERR_BREAKDOWN) {
+          launch_true_residual(p, g, j.eta, j.ups, true);  // report the true residual of the returned iterate
+          if (!hs->done) j.status_host = TPCG_ERR_NOT_CONVERGED;
+        }
+        if (p->singular) launch_center_u(p, g, j.ups, -1);
+      }
+      return enqueue_state_readback(p);
+    }
   }
   if (j.phase == 2) {
     int status = hs->status;
@@ -339,6 +349,7 @@ int job_step(SolveJob& j) {
     info.checks = hs->checks;
     j.status = status;
     j.phase = 3;
+    if (status == TPCG_OK) p->last_iters = hs->iter;
   }
   return TPCG_OK;
 }

@@ -403,6 +403,7 @@ __device__ void fin_true(SolveState* st, const double (&s)[3], long long N) {
   if (s[0] <= st->tol2) {
     st->status = TPCG_OK;
     st->done = 1;
+    st->done_iter = st->iter;
   } else if (st->iter >= st->maxit) {
     st->status = TPCG_ERR_NOT_CONVERGED;
     st->done = 1;
@@ -1161,8 +1162,14 @@ __global__ void __launch_bounds__(256) k_norm_shift(long long N, const double* _
                  [st, N](const double(&s)[1]) { st->lp_shift = lp_shift_for(s[0], N); });
 }
 
-// U -= sum(U)/N: return the zero-mean (minimum-norm) representative.
-__global__ void __launch_bounds__(256) k_center_u(long long N, double* __restrict__ U, const SolveState* st) {
+// U -= sum(U)/N: return the zero-mean (minimum-norm) representative.  With
+// iter_lo >= 0 only when the solve converged in an iteration after iter_lo:
+// launched behind each chunk of iterations, it centres U in the chunk where
+// the stop test succeeded (every block takes the same decision: done_iter is
+// set once) and saves the host a round trip.
+__global__ void __launch_bounds__(256) k_center_u(long long N, double* __restrict__ U, const SolveState* st,
+                                                  int iter_lo) {
+  if (iter_lo >= 0 && !(st->done == 1 && st->status == TPCG_OK && st->done_iter > iter_lo)) return;
   const double m = st->sumU / (double)N;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
     U[i] -= m;
@@ -1403,9 +1410,9 @@ void launch_true_residual(const tpcg_plan* p, const Geom& g, const double* eta, 
   k_residual_fx<false><<<p->fx_blocks[kFxTrue], p->st_block, 0, p->stream>>>(g, eta, U, p->d_R, lowprec(p),
                                                                               p->d_state, p->d_partials, force ? 1 : 0);
 }
-void launch_center_u(const tpcg_plan* p, const Geom& g, double* U) {
+void launch_center_u(const tpcg_plan* p, const Geom& g, double* U, int iter_lo) {
   LaunchScope ls(p, kKCenter);
-  k_center_u<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, U, p->d_state);
+  k_center_u<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, U, p->d_state, iter_lo);
 }
 void launch_zero(const tpcg_plan* p, long long N, double* U) {
   LaunchScope ls(p, kKConvert);

@@ -37,6 +37,7 @@ struct SolveState {
   int singular;
   int precond_applies;
   int checks;          // true-residual evaluations
+  int done_iter;       // iteration whose true-residual check met the tolerance (0: none)
   int timeout;         // a bounded device wait gave up
   unsigned zmax_bits;  // max |Z| accumulator of the preconditioner output (FP32 bits; atomicMax)
   float zmax;          // max |Z| of the current preconditioner output

@@ -156,4 +156,5 @@ struct tpcg_plan {
   double jac_omega = 1.3;
   double jac_invd[27] = {};
   int stream_blocks = 0;    // streaming kernels
+  int last_iters = 0;      // iterations of the plan's previous converged solve (first chunk of the next)
 };
