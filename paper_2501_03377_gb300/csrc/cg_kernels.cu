@@ -1150,6 +1150,63 @@ __global__ void __launch_bounds__(256) k_eta_sum(Geom g, const double* __restric
   });
 }
 
+// k_init_zero and k_eta_sum with two adjacent points per thread (N even and
+// below 2^32; nx even when there is a low-precision copy, so a pair never
+// straddles a padded row): 16-byte loads and stores and 32-bit indices.
+__global__ void __launch_bounds__(256) k_init_zero2(unsigned npair, long long N, const double* __restrict__ eta,
+                                                    double* __restrict__ R, LowPrec lp, SolveState* st,
+                                                    double* partials) {
+  const double mean = st->mean_eta;
+  const int shift = st->lp_shift;
+  double e2 = 0.0;
+  float a1 = 0.0f;
+  const unsigned stride = gridDim.x * blockDim.x;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < npair; t += stride) {
+    const double2 e = __ldg(reinterpret_cast<const double2*>(eta) + t);
+    const double r0 = e.x - mean, r1 = e.y - mean;
+    reinterpret_cast<double2*>(R)[t] = make_double2(r0, r1);
+    const float a32 = f64_to_f32_odd(r0, shift), b32 = f64_to_f32_odd(r1, shift);
+    store_lp_pair(lp, 2ll * t, r0, r1, a32, b32);
+    e2 = fma(r0, r0, fma(r1, r1, e2));
+    a1 += a32 + b32;
+  }
+  double acc[2] = {e2, f32_to_f64_int(a1)};
+  grid_reduce<2>(acc, partials, &st->tickets[kTkInit], gridDim.x, blockIdx.x, [st, N, shift](const double(&s)[2]) {
+    const double v[3] = {s[0], ldexp(s[1], -shift), s[0]};
+    fin_init(st, v, N);
+  });
+}
+
+__global__ void __launch_bounds__(256) k_eta_sum2(Geom g, unsigned npair, const double* __restrict__ eta,
+                                                  const double* __restrict__ U0, SolveState* st, double* partials) {
+  const long long N = g.N;
+  double acc[2] = {0.0, 0.0};
+  unsigned long long um = 0;
+  const unsigned stride = gridDim.x * blockDim.x;
+  for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < npair; t += stride) {
+    const double2 e = __ldg(reinterpret_cast<const double2*>(eta) + t);
+    acc[0] += e.x;
+    acc[0] += e.y;
+    acc[1] = fma(e.y, e.y, fma(e.x, e.x, acc[1]));
+    if (U0) {
+      const double2 u = __ldg(reinterpret_cast<const double2*>(U0) + t);
+      const unsigned long long a = mag_key(u.x), b = mag_key(u.y);
+      const unsigned long long ub = a > b ? a : b;
+      um = ub > um ? ub : um;
+    }
+  }
+  fold_umax(st, um);
+  grid_reduce<2>(acc, partials, &st->tickets[kTkEta], gridDim.x, blockIdx.x, [st, N, g](const double(&s)[2]) {
+    const double mean = st->singular ? s[0] / (double)N : 0.0;
+    st->mean_eta = mean;
+    const double n2 = s[1] - mean * s[0];
+    st->eta_norm2 = n2 > 0.0 ? n2 : s[1];  // estimate; the initial residual kernel sets the exact value
+    st->lp_shift = lp_shift_for(n2 > 0.0 ? n2 : s[1], N);
+    st->umax = __longlong_as_double((long long)atomicExch(&st->umax_bits, 0ull));
+    plan_residual_check(st, g);
+  });
+}
+
 // ||r||^2 -> exponent of the low-precision copy (tpcg_precond_apply).
 __global__ void __launch_bounds__(256) k_norm_shift(long long N, const double* __restrict__ r, SolveState* st,
                                                     double* partials) {
@@ -1354,9 +1411,17 @@ int setup_fx_grids(tpcg_plan* p) {
 }
 LowPrec lowprec(const tpcg_plan* p) { return LowPrec{p->d_Rlp, p->lp_kind, p->pitch16[0], p->nx}; }
 
+// two points per thread when the point count is even and below 2^32 and a pair never straddles a padded
+// row of the low-precision copy
+static bool pairs_ok(const tpcg_plan* p, const Geom& g) {
+  return g.N % 2 == 0 && g.N < (1ll << 32) && (p->d_Rlp == nullptr || g.nx % 2 == 0);
+}
 void launch_init_residual(const tpcg_plan* p, const Geom& g, const double* eta, const double* U, bool zero_guess) {
   LaunchScope ls(p, kKInit);
-  if (zero_guess)
+  if (zero_guess && pairs_ok(p, g))
+    k_init_zero2<<<p->stream_blocks, 256, 0, p->stream>>>((unsigned)(g.N / 2), g.N, eta, p->d_R, lowprec(p),
+                                                          p->d_state, p->d_partials);
+  else if (zero_guess)
     k_init_zero<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, eta, p->d_R, lowprec(p), p->d_state, p->d_partials);
   else
     k_residual_fx<true><<<p->fx_blocks[kFxInit], p->st_block, 0, p->stream>>>(g, eta, U, p->d_R, lowprec(p),
@@ -1364,7 +1429,10 @@ void launch_init_residual(const tpcg_plan* p, const Geom& g, const double* eta, 
 }
 void launch_eta_sum(const tpcg_plan* p, const Geom& g, const double* eta, const double* U0) {
   LaunchScope ls(p, kKEtaSum);
-  k_eta_sum<<<p->stream_blocks, 256, 0, p->stream>>>(g, eta, U0, p->d_state, p->d_partials);
+  if (pairs_ok(p, g))
+    k_eta_sum2<<<p->stream_blocks, 256, 0, p->stream>>>(g, (unsigned)(g.N / 2), eta, U0, p->d_state, p->d_partials);
+  else
+    k_eta_sum<<<p->stream_blocks, 256, 0, p->stream>>>(g, eta, U0, p->d_state, p->d_partials);
 }
 void launch_norm_shift(const tpcg_plan* p, const Geom& g, const double* r) {
   LaunchScope ls(p, kKConvert);
