@@ -1411,14 +1411,17 @@ int setup_fx_grids(tpcg_plan* p) {
 }
 LowPrec lowprec(const tpcg_plan* p) { return LowPrec{p->d_Rlp, p->lp_kind, p->pitch16[0], p->nx}; }
 
-// two points per thread when the point count is even and below 2^32 and a pair never straddles a padded
-// row of the low-precision copy
-static bool pairs_ok(const tpcg_plan* p, const Geom& g) {
-  return g.N % 2 == 0 && g.N < (1ll << 32) && (p->d_Rlp == nullptr || g.nx % 2 == 0);
+// The caller's arrays are device pointers to doubles: only 8-byte alignment is guaranteed, so the
+// kernels that move them as 16-byte pairs run only when the pointers allow it.
+static bool aligned16(const void* a) { return ((uintptr_t)a & 15) == 0; }
+// two points per thread when the point count is even and below 2^32, a pair never straddles a padded
+// row of the low-precision copy and the caller's arrays a, b (may be NULL) allow 16-byte accesses
+static bool pairs_ok(const tpcg_plan* p, const Geom& g, const void* a, const void* b) {
+  return g.N % 2 == 0 && g.N < (1ll << 32) && (p->d_Rlp == nullptr || g.nx % 2 == 0) && aligned16(a) && aligned16(b);
 }
 void launch_init_residual(const tpcg_plan* p, const Geom& g, const double* eta, const double* U, bool zero_guess) {
   LaunchScope ls(p, kKInit);
-  if (zero_guess && pairs_ok(p, g))
+  if (zero_guess && pairs_ok(p, g, eta, nullptr))
     k_init_zero2<<<p->stream_blocks, 256, 0, p->stream>>>((unsigned)(g.N / 2), g.N, eta, p->d_R, lowprec(p),
                                                           p->d_state, p->d_partials);
   else if (zero_guess)
@@ -1429,7 +1432,7 @@ void launch_init_residual(const tpcg_plan* p, const Geom& g, const double* eta, 
 }
 void launch_eta_sum(const tpcg_plan* p, const Geom& g, const double* eta, const double* U0) {
   LaunchScope ls(p, kKEtaSum);
-  if (pairs_ok(p, g))
+  if (pairs_ok(p, g, eta, U0))
     k_eta_sum2<<<p->stream_blocks, 256, 0, p->stream>>>(g, (unsigned)(g.N / 2), eta, U0, p->d_state, p->d_partials);
   else
     k_eta_sum<<<p->stream_blocks, 256, 0, p->stream>>>(g, eta, U0, p->d_state, p->d_partials);
@@ -1460,10 +1463,10 @@ void launch_update(const tpcg_plan* p, const Geom& g, double* U, int k, bool zer
   if (p->prec == TPCG_FP64)
     k_update<<<p->stream_blocks, 256, 0, p->stream>>>(g, U, (const double*)p->d_P[k & 1], p->d_W, p->d_R,
                                                        lowprec(p), p->d_state, p->d_partials);
-  else if (g.nx % 2 == 0 && zero_guess_first)  // first update of a zero initial guess: U = alpha P
+  else if (g.nx % 2 == 0 && aligned16(U) && zero_guess_first)  // first update of a zero guess: U = alpha P
     k_update_pair<true><<<p->fx_blocks[kFxUpd], p->st_block, 0, p->stream>>>(
         g, U, (const int*)p->d_P[k & 1], p->d_R, lowprec(p), p->d_state, p->d_partials);
-  else if (g.nx % 2 == 0)
+  else if (g.nx % 2 == 0 && aligned16(U))
     k_update_pair<false><<<p->fx_blocks[kFxUpd], p->st_block, 0, p->stream>>>(
         g, U, (const int*)p->d_P[k & 1], p->d_R, lowprec(p), p->d_state, p->d_partials);
   else if (zero_guess_first)

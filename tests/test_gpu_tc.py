@@ -295,3 +295,29 @@ def test_host_stream_rejects_bad_arguments():
     assert b.tpcg_solve_host_stream(pl.handle, [e.data_ptr()], [0], 1e-10, 10, 0)[0] == b.TPCG_ERR_INVALID_ARG
     with pytest.raises(ValueError):
         pl.solve_host_stream([e], [], tol=1e-10)
+
+
+def test_caller_arrays_need_only_8_byte_alignment():
+    """Device arrays of doubles are only guaranteed 8-byte alignment: the kernels that move the caller's
+    eta and U as 16-byte pairs must hand over to their one-point forms when a pointer does not allow it.
+    The solve from offset buffers must succeed and agree with the aligned solve."""
+    nx, ny, nz, bcs = 64, 48, 24, ("P", "P", "N")
+    pl = _plan(nx, ny, nz, bcs, prec="fp16")
+    eta = synth.defect_rhs(nx, ny, nz, bcs, 20, 1.5, seed=61)
+    ea = torch.from_numpy(eta.copy()).cuda()
+    ua = torch.zeros_like(ea)
+    st, _ = pl.solve(ea, ua, tol=1e-10, maxit=40, zero_guess=True)
+    assert st == 0
+    buf_e = torch.zeros(ea.numel() + 1, dtype=torch.float64, device="cuda")
+    buf_u = torch.zeros_like(buf_e)
+    eb = buf_e[1:].view(nz, ny, nx)
+    ub = buf_u[1:].view(nz, ny, nx)
+    eb.copy_(ea)
+    assert eb.data_ptr() % 16 == 8 and ub.data_ptr() % 16 == 8
+    st2, info2 = pl.solve(eb, ub, tol=1e-10, maxit=40, zero_guess=True)
+    assert st2 == 0 and info2["rel_res_true"] <= 1e-10
+    assert rel_err(ub.cpu().numpy(), ua.cpu().numpy()) <= 1e-9
+    ub.mul_(0.5)  # warm start from the offset buffer: the eta sum and the update read U
+    st3, info3 = pl.solve(eb, ub, tol=1e-10, maxit=40)
+    assert st3 == 0 and info3["rel_res_true"] <= 1e-10
+    assert rel_err(ub.cpu().numpy(), ua.cpu().numpy()) <= 1e-9
