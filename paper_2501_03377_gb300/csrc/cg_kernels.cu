@@ -959,7 +959,7 @@ __global__ void __launch_bounds__(TX* TY, 4) k_update_int(Geom g, double* __rest
 // packed pair; only the outer x neighbours of a pair come by warp shuffle.
 // A warp covers 64 consecutive x of one row.
 template <bool ZG>
-__global__ void __launch_bounds__(TX* TY, 3) k_update_pair(Geom g, double* __restrict__ U,
+__global__ void __launch_bounds__(TX* TY, 4) k_update_pair(Geom g, double* __restrict__ U,
                                                            const int* __restrict__ P, double* __restrict__ R,
                                                            LowPrec lp, SolveState* st, double* partials) {
   if (st->done) return;
