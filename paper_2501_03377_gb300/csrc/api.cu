@@ -21,6 +21,7 @@ void launch_eta_sum(const tpcg_plan* p, const Geom& g, const double* eta, const 
 void launch_direction(const tpcg_plan* p, const Geom& g, int k);
 void launch_update(const tpcg_plan* p, const Geom& g, double* U, int k, bool zero_guess_first);
 void launch_true_residual(const tpcg_plan* p, const Geom& g, const double* eta, const double* U, bool force);
+void launch_form_u(const tpcg_plan* p, const Geom& g, double* U, bool force);
 void launch_center_u(const tpcg_plan* p, const Geom& g, double* U, int iter_lo);
 void launch_zero(const tpcg_plan* p, long long N, double* U);
 void launch_to_lp(const tpcg_plan* p, const Geom& g, const double* r);
@@ -38,7 +39,8 @@ void tc_plan_release(tpcg_plan* pl);
 
 const char* kernel_kind_name(int kind) {
   static const char* names[kKindCount] = {"eta_sum", "init_residual", "direction", "update", "true_residual",
-                                          "center", "laplacian", "modeprod_f64", "modeprod_tc", "convert"};
+                                          "center", "laplacian", "modeprod_f64", "modeprod_tc", "convert",
+                                          "form_u"};
   return (kind >= 0 && kind < kKindCount) ? names[kind] : "unknown";
 }
 
@@ -153,7 +155,7 @@ void free_plan(tpcg_plan* p) {
   }
   cudaFree(p->d_R);
   cudaFree(p->d_P[0]);
-  cudaFree(p->d_P[1]);
+  if (p->prec == TPCG_FP64) cudaFree(p->d_P[1]);  // mixed forms: one allocation for the ring
   cudaFree(p->d_W);
   cudaFree(p->d_Z);
   cudaFree(p->d_Rlp);
@@ -254,6 +256,7 @@ int enqueue_iterations(SolveJob& j, int count) {
     const int k = j.issued + c;                         // P_k is written to d_P[k & 1], P_{k-1} read from the other
     launch_direction(p, g, k);                          // direction P, W = L P, alpha
     launch_update(p, g, j.ups, k, k == 0 && (j.flags & TPCG_ZERO_GUESS));  // U and R updates
+    if (p->prec != TPCG_FP64) launch_form_u(p, g, j.ups, false);  // deferred U updates, when a check is due
     launch_true_residual(p, g, j.eta, j.ups, false);    // stop test
     const int rc = run_precond(p, p->d_R, p->d_Z, p->d_state);  // Z = M R, rho, beta
     if (rc) return rc;
@@ -278,6 +281,7 @@ int job_start(SolveJob& j) {
   hs->tol2 = j.tol * j.tol;
   hs->first = 1;
   hs->zero_guess = zero_guess ? 1 : 0;
+  hs->u_valid = zero_guess ? 0 : 1;  // mixed forms: U holds the initial guess
   hs->singular = p->singular ? 1 : 0;
   hs->status = TPCG_OK;
   if (cudaMemcpyAsync(p->d_state, hs, sizeof(SolveState), cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
@@ -319,6 +323,7 @@ int job_step(SolveJob& j) {
     // read back is final
     const bool finished = hs->done == 1 && hs->status == TPCG_OK;
     if (!finished) {
+      if (p->prec != TPCG_FP64) launch_form_u(p, g, j.ups, true);  // apply any deferred U updates
       if (hs->done == 2) {
         launch_zero(p, g.N, j.ups);  // eta_hat = 0: minimum-norm solution is 0
       } else {
@@ -464,16 +469,16 @@ int tpcg_plan_create(int nx, int ny, int nz, const int bc[3], const double h[3],
   }
   // PCG workspaces
   if (!rc) rc = dalloc(p, &p->d_R, (size_t)N);
-  for (int b = 0; b < 2 && !rc; ++b) {
-    if (p->prec == TPCG_FP64) {
+  if (p->prec == TPCG_FP64) {
+    for (int b = 0; b < 2 && !rc; ++b) {
       double* d = nullptr;
       rc = dalloc(p, &d, (size_t)N);
       p->d_P[b] = d;
-    } else {
-      int* d = nullptr;
-      rc = dalloc(p, &d, (size_t)N);
-      p->d_P[b] = d;
     }
+  } else if (!rc) {  // ring of kPRing int32 directions (deferred U update)
+    int* d = nullptr;
+    rc = dalloc(p, &d, (size_t)N * kPRing);
+    for (int b = 0; b < kPRing && !rc; ++b) p->d_P[b] = d + (size_t)N * b;
   }
   if (!rc && p->prec == TPCG_FP64) rc = dalloc(p, &p->d_W, (size_t)N);
   if (!rc) {

@@ -834,14 +834,24 @@ __global__ void __launch_bounds__(TX* TY) k_direction_quad(Geom g, const float* 
 // accumulated per thread in FP32 from R * 2^lp_shift (exact
 // power-of-two scaling, unit RMS) and combined across threads in FP64: they
 // only steer the stop test, which the true residual confirms.
-__device__ void fin_update(SolveState* st, const double (&s)[2], int shift, const Geom& g) {
+// pslot >= 0 (mixed forms): U was not touched; record alpha_s, the exponent of P_s and its ring slot for
+// k_form_u.  pslot < 0 (FP64 form): U was updated; take max|U| for the residual check.
+__device__ void fin_update(SolveState* st, const double (&s)[2], int shift, const Geom& g, int pslot) {
   const double rr = ldexp(s[0], -2 * shift), sumR = ldexp(s[1], -shift);
   st->rr = rr;
   st->sumR = sumR;
   st->iter += 1;
   st->zero_guess = 0;
-  st->umax = __longlong_as_double((long long)atomicExch(&st->umax_bits, 0ull));
-  plan_residual_check(st, g);
+  if (pslot >= 0) {
+    const int n = st->n_pend;
+    st->pend_alpha[n] = st->alpha;
+    st->pend_kp[n] = st->kp;
+    st->pend_slot[n] = pslot;
+    st->n_pend = n + 1;
+  } else {
+    st->umax = __longlong_as_double((long long)atomicExch(&st->umax_bits, 0ull));
+    plan_residual_check(st, g);
+  }
   advance_shift(st, rr, g.N);
   if (!isfinite(rr)) {
     st->status = TPCG_ERR_BREAKDOWN;
@@ -851,16 +861,14 @@ __device__ void fin_update(SolveState* st, const double (&s)[2], int shift, cons
   if (rr <= st->tol2 || st->iter >= st->maxit) st->need_check = 1;
 }
 
-// Mixed forms: W = L P from the exact integer stencil of P_int, in a
+// Mixed forms: R -= alpha W with W = L P from the exact integer stencil of P_int, in a
 // register-window stream (see k_direction_int).  The loads of plane k+1 (P
-// two planes ahead, the y neighbours, R and U) are issued before plane k is
-// processed.  ZG: the first update of a zero initial guess writes U = alpha P.
-template <bool ZG>
-__global__ void __launch_bounds__(TX* TY, 4) k_update_int(Geom g, double* __restrict__ U,
-                                                          const int* __restrict__ P, double* __restrict__ R,
-                                                          LowPrec lp, SolveState* st, double* partials) {
+// two planes ahead, the y neighbours and R) are issued before plane k is
+// processed.  U += alpha P is deferred: the finalize records it for k_form_u
+// (P_s stays in ring slot pslot until then).
+__global__ void __launch_bounds__(TX* TY, 4) k_update_int(Geom g, const int* __restrict__ P, double* __restrict__ R,
+                                                          LowPrec lp, SolveState* st, double* partials, int pslot) {
   if (st->done) return;
-  const double alpha = st->alpha;
   const double na0 = st->nah[0], na1 = st->nah[1], na2 = st->nah[2];  // -alpha / h^2 per axis
   const int kp = st->kp;
   const int shift = st->lp_shift;
@@ -868,7 +876,6 @@ __global__ void __launch_bounds__(TX* TY, 4) k_update_int(Geom g, double* __rest
   const bool has_z = g.nz > 1;
   const int lane = threadIdx.x;
   float rr = 0.0f, sR = 0.0f;
-  unsigned long long um = 0;
   for_each_run(g, [&](int bx0, int by0, int k0, int k1) {
     const int x = bx0 + lane, y = by0 + threadIdx.y;
     const bool active = x < g.nx && y < g.ny;
@@ -886,13 +893,13 @@ __global__ void __launch_bounds__(TX* TY, 4) k_update_int(Geom g, double* __rest
     };
     struct Plane {
       int c, yl, yr, xl, xr;
-      double r, u;
+      double r;
     };
     auto fetch = [&](int k, int c) {
       Plane f;
       f.c = c;
       f.yl = f.yr = f.xl = f.xr = 0;
-      f.r = f.u = 0.0;
+      f.r = 0.0;
       if (active) {
         const unsigned kk = (unsigned)k;
         f.yl = ld(kk, x, ygl);
@@ -900,7 +907,6 @@ __global__ void __launch_bounds__(TX* TY, 4) k_update_int(Geom g, double* __rest
         if (own_xl) f.xl = ld(kk, xgl, y);
         if (own_xr) f.xr = ld(kk, xgr, y);
         f.r = R[kk * plane + col];
-        if (!ZG) f.u = U[kk * plane + col];
       }
       return f;
     };
@@ -937,11 +943,6 @@ __global__ void __launch_bounds__(TX* TY, 4) k_update_int(Geom g, double* __rest
         store_lp(lp, i, r, r32);
         rr = fmaf(r32, r32, rr);
         sR += r32;
-        const double pv = i32_to_f64_scaled(c, -kp);
-        const double u = ZG ? alpha * pv : fma(alpha, pv, cur.u);
-        U[i] = u;
-        const unsigned long long ub = mag_key(u);
-        um = ub > um ? ub : um;
       }
       zl = c;
       zr = zr2;
@@ -949,21 +950,17 @@ __global__ void __launch_bounds__(TX* TY, 4) k_update_int(Geom g, double* __rest
     }
   });
   double acc[2] = {f32_to_f64_int(rr), f32_to_f64_int(sR)};
-  fold_umax(st, um);
   grid_reduce<2>(acc, partials, &st->tickets[kTkUpd], gridDim.x, blockIdx.x,
-                 [st, shift, g](const double(&s)[2]) { fin_update(st, s, shift, g); });
+                 [st, shift, g, pslot](const double(&s)[2]) { fin_update(st, s, shift, g, pslot); });
 }
 
-// The same update with two adjacent x points per thread (even nx): R and U move
+// The same update with two adjacent x points per thread (even nx): R moves
 // as 16-byte double2, P and its y neighbours as int2, the FP16 copy as one
 // packed pair; only the outer x neighbours of a pair come by warp shuffle.
 // A warp covers 64 consecutive x of one row.
-template <bool ZG>
-__global__ void __launch_bounds__(TX* TY, 4) k_update_pair(Geom g, double* __restrict__ U,
-                                                           const int* __restrict__ P, double* __restrict__ R,
-                                                           LowPrec lp, SolveState* st, double* partials) {
+__global__ void __launch_bounds__(TX* TY, 4) k_update_pair(Geom g, const int* __restrict__ P, double* __restrict__ R,
+                                                           LowPrec lp, SolveState* st, double* partials, int pslot) {
   if (st->done) return;
-  const double alpha = st->alpha;
   const double na0 = st->nah[0], na1 = st->nah[1], na2 = st->nah[2];  // -alpha / h^2 per axis
   const int kp = st->kp;
   const int shift = st->lp_shift;
@@ -971,7 +968,6 @@ __global__ void __launch_bounds__(TX* TY, 4) k_update_pair(Geom g, double* __res
   const bool has_z = g.nz > 1;
   const int lane = threadIdx.x;
   float rr = 0.0f, sR = 0.0f;
-  unsigned long long um = 0;
   for_each_run<2 * TX>(g, [&](int bx0, int by0, int k0, int k1) {
     const int x = bx0 + 2 * lane, y = by0 + threadIdx.y;  // points (x, y) and (x + 1, y)
     const bool active = x < g.nx && y < g.ny;             // nx even: both points or neither
@@ -993,7 +989,7 @@ __global__ void __launch_bounds__(TX* TY, 4) k_update_pair(Geom g, double* __res
     struct Plane {
       int2 c, yl, yr;
       int xl, xr;
-      double2 r, u;
+      double2 r;
     };
     auto fetch = [&](int k, int2 c) {
       Plane f;
@@ -1004,7 +1000,6 @@ __global__ void __launch_bounds__(TX* TY, 4) k_update_pair(Geom g, double* __res
       f.xl = has_xl ? __ldg(P + base + coll) : 0;
       f.xr = has_xr ? __ldg(P + base + colr) : 0;
       f.r = active ? *reinterpret_cast<const double2*>(R + base + col) : make_double2(0.0, 0.0);
-      f.u = (active && !ZG) ? *reinterpret_cast<const double2*>(U + base + col) : make_double2(0.0, 0.0);
       return f;
     };
     int2 zl = ldz(k0 - 1);
@@ -1045,13 +1040,6 @@ __global__ void __launch_bounds__(TX* TY, 4) k_update_pair(Geom g, double* __res
         store_lp_pair(lp, i, r0, r1, a32, b32);
         rr = fmaf(a32, a32, fmaf(b32, b32, rr));
         sR += a32 + b32;
-        const double p0 = i32_to_f64_scaled(c.x, -kp), p1 = i32_to_f64_scaled(c.y, -kp);
-        const double u0 = ZG ? alpha * p0 : fma(alpha, p0, cur.u.x);
-        const double u1 = ZG ? alpha * p1 : fma(alpha, p1, cur.u.y);
-        *reinterpret_cast<double2*>(U + i) = make_double2(u0, u1);
-        const unsigned long long k0b = mag_key(u0), k1b = mag_key(u1);
-        const unsigned long long kb = k0b > k1b ? k0b : k1b;
-        um = kb > um ? kb : um;
       }
       zl = c;
       zr = zr2;
@@ -1059,9 +1047,8 @@ __global__ void __launch_bounds__(TX* TY, 4) k_update_pair(Geom g, double* __res
     }
   });
   double acc[2] = {f32_to_f64_int(rr), f32_to_f64_int(sR)};
-  fold_umax(st, um);
   grid_reduce<2>(acc, partials, &st->tickets[kTkUpd], gridDim.x, blockIdx.x,
-                 [st, shift, g](const double(&s)[2]) { fin_update(st, s, shift, g); });
+                 [st, shift, g, pslot](const double(&s)[2]) { fin_update(st, s, shift, g, pslot); });
 }
 
 // FP64 form: P and W = L P are stored by the direction kernel.
@@ -1092,7 +1079,7 @@ __global__ void __launch_bounds__(256) k_update(Geom g, double* __restrict__ U, 
   fold_umax(st, um);
   double acc[2] = {f32_to_f64_int(a0), f32_to_f64_int(a1)};
   grid_reduce<2>(acc, partials, &st->tickets[kTkUpd], gridDim.x, blockIdx.x,
-                 [st, shift, g](const double(&s)[2]) { fin_update(st, s, shift, g); });
+                 [st, shift, g](const double(&s)[2]) { fin_update(st, s, shift, g, -1); });
 }
 
 // ------------------------------------------------------------------ streaming kernels
@@ -1145,6 +1132,82 @@ __global__ void __launch_bounds__(256) k_eta_sum(Geom g, const double* __restric
     const double n2 = s[1] - mean * s[0];
     st->eta_norm2 = n2 > 0.0 ? n2 : s[1];  // estimate; the initial residual kernel sets the exact value
     st->lp_shift = lp_shift_for(n2 > 0.0 ? n2 : s[1], N);
+    st->umax = __longlong_as_double((long long)atomicExch(&st->umax_bits, 0ull));
+    plan_residual_check(st, g);
+  });
+}
+
+// Deferred U update of the mixed forms (Algorithm 1: U_{s+1} = U_s + alpha_s P_s).
+// The update kernel records alpha_s, the exponent of P_s = 2^-kp_s P_int,s and
+// its ring slot; this kernel applies the recorded updates in iteration order,
+// one FP64 FMA each -- the operations, in the order, of updating U every
+// iteration -- and takes max|U| for the fixed-point residual check.  It runs
+// when a true-residual check is due, when the ring of directions is about to
+// wrap, and (force) before the host reads an iterate.  Every block takes the
+// same decision from the state, which only the last block's finalize changes.
+// PAIR: two adjacent points per thread (N even, U 16-byte aligned).
+template <bool PAIR>
+__global__ void __launch_bounds__(256) k_form_u(Geom g, double* __restrict__ U, const int* __restrict__ Pring,
+                                                unsigned long long pstride, SolveState* st, double* partials,
+                                                int force) {
+  const int n = st->n_pend;
+  if (n == 0 || (!force && (st->done || (!st->need_check && n < kPRing - 1)))) return;
+  const bool valid = st->u_valid != 0;
+  double al[kPRing - 1];
+  int kpn[kPRing - 1];
+  const int* pp[kPRing - 1];
+#pragma unroll
+  for (int k = 0; k < kPRing - 1; ++k) {
+    const bool on = k < n;
+    al[k] = on ? st->pend_alpha[k] : 0.0;
+    kpn[k] = on ? -st->pend_kp[k] : 0;
+    pp[k] = Pring + (on ? (unsigned long long)st->pend_slot[k] * pstride : 0ull);
+  }
+  unsigned long long um = 0;
+  const unsigned long long N = (unsigned long long)g.N;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  if (PAIR) {
+    for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < N / 2; t += stride) {
+      const int2 q0 = __ldg(reinterpret_cast<const int2*>(pp[0]) + t);
+      double u0, u1;
+      if (valid) {
+        const double2 u = reinterpret_cast<const double2*>(U)[t];
+        u0 = fma(al[0], i32_to_f64_scaled(q0.x, kpn[0]), u.x);
+        u1 = fma(al[0], i32_to_f64_scaled(q0.y, kpn[0]), u.y);
+      } else {  // zero initial guess: the first update writes U = alpha_0 P_0
+        u0 = al[0] * i32_to_f64_scaled(q0.x, kpn[0]);
+        u1 = al[0] * i32_to_f64_scaled(q0.y, kpn[0]);
+      }
+#pragma unroll
+      for (int k = 1; k < kPRing - 1; ++k) {
+        if (k < n) {
+          const int2 q = __ldg(reinterpret_cast<const int2*>(pp[k]) + t);
+          u0 = fma(al[k], i32_to_f64_scaled(q.x, kpn[k]), u0);
+          u1 = fma(al[k], i32_to_f64_scaled(q.y, kpn[k]), u1);
+        }
+      }
+      reinterpret_cast<double2*>(U)[t] = make_double2(u0, u1);
+      const unsigned long long a = mag_key(u0), b = mag_key(u1);
+      const unsigned long long m = a > b ? a : b;
+      um = m > um ? m : um;
+    }
+  } else {
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < N; i += stride) {
+      const int q0 = __ldg(pp[0] + i);
+      double u = valid ? fma(al[0], i32_to_f64_scaled(q0, kpn[0]), U[i]) : al[0] * i32_to_f64_scaled(q0, kpn[0]);
+#pragma unroll
+      for (int k = 1; k < kPRing - 1; ++k)
+        if (k < n) u = fma(al[k], i32_to_f64_scaled(__ldg(pp[k] + i), kpn[k]), u);
+      U[i] = u;
+      const unsigned long long m = mag_key(u);
+      um = m > um ? m : um;
+    }
+  }
+  fold_umax(st, um);
+  double acc[1] = {0.0};
+  grid_reduce<1>(acc, partials, &st->tickets[kTkForm], gridDim.x, blockIdx.x, [st, g](const double(&)[1]) {
+    st->n_pend = 0;
+    st->u_valid = 1;
     st->umax = __longlong_as_double((long long)atomicExch(&st->umax_bits, 0ull));
     plan_residual_check(st, g);
   });
@@ -1397,7 +1460,7 @@ int setup_fx_grids(tpcg_plan* p) {
   const bool quad = p->nx % 4 == 0;  // direction takes four
   const void* fns[kFxCount] = {quad ? (const void*)k_direction_quad
                                     : (pair ? (const void*)k_direction_pair : (const void*)k_direction_int),
-                               pair ? (const void*)k_update_pair<false> : (const void*)k_update_int<false>,
+                               pair ? (const void*)k_update_pair : (const void*)k_update_int,
                                (const void*)k_residual_fx<false>, (const void*)k_residual_fx<true>};
   for (int i = 0; i < kFxCount; ++i) {
     const int tw = (i == kFxDir && quad) ? 4 * TX : (((i == kFxUpd || i == kFxDir) && pair) ? 2 * TX : TX);
@@ -1441,40 +1504,54 @@ void launch_norm_shift(const tpcg_plan* p, const Geom& g, const double* r) {
   LaunchScope ls(p, kKConvert);
   k_norm_shift<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, r, p->d_state, p->d_partials);
 }
-// P_k is written to d_P[k & 1]; P_{k-1} is read from the other buffer.
+// FP64 form: P_k is written to d_P[k & 1], P_{k-1} read from the other buffer.  Mixed forms: P_k goes to
+// ring slot k % kPRing (kept there until k_form_u has applied alpha_k P_k to U).
 void launch_direction(const tpcg_plan* p, const Geom& g, int k) {
   LaunchScope ls(p, kKDirection);
-  if (p->prec == TPCG_FP64)
+  if (p->prec == TPCG_FP64) {
     k_direction<<<p->st_grid, p->st_block, 0, p->stream>>>(
         g, p->st_zchunk, (const double*)p->d_Z, (const double*)p->d_P[(k + 1) & 1], (double*)p->d_P[k & 1], p->d_W,
         p->d_state, p->d_partials);
-  else if (g.nx % 4 == 0)
-    k_direction_quad<<<p->fx_blocks[kFxDir], p->st_block, 0, p->stream>>>(
-        g, (const float*)p->d_Z, (const int*)p->d_P[(k + 1) & 1], (int*)p->d_P[k & 1], p->d_state, p->d_partials);
+    return;
+  }
+  const int* Pold = (const int*)p->d_P[(k + kPRing - 1) % kPRing];
+  int* Pnew = (int*)p->d_P[k % kPRing];
+  if (g.nx % 4 == 0)
+    k_direction_quad<<<p->fx_blocks[kFxDir], p->st_block, 0, p->stream>>>(g, (const float*)p->d_Z, Pold, Pnew,
+                                                                           p->d_state, p->d_partials);
   else if (g.nx % 2 == 0)
-    k_direction_pair<<<p->fx_blocks[kFxDir], p->st_block, 0, p->stream>>>(
-        g, (const float*)p->d_Z, (const int*)p->d_P[(k + 1) & 1], (int*)p->d_P[k & 1], p->d_state, p->d_partials);
+    k_direction_pair<<<p->fx_blocks[kFxDir], p->st_block, 0, p->stream>>>(g, (const float*)p->d_Z, Pold, Pnew,
+                                                                           p->d_state, p->d_partials);
   else
-    k_direction_int<<<p->fx_blocks[kFxDir], p->st_block, 0, p->stream>>>(
-        g, (const float*)p->d_Z, (const int*)p->d_P[(k + 1) & 1], (int*)p->d_P[k & 1], p->d_state, p->d_partials);
+    k_direction_int<<<p->fx_blocks[kFxDir], p->st_block, 0, p->stream>>>(g, (const float*)p->d_Z, Pold, Pnew,
+                                                                          p->d_state, p->d_partials);
 }
 void launch_update(const tpcg_plan* p, const Geom& g, double* U, int k, bool zero_guess_first) {
+  (void)zero_guess_first;  // the FP64 kernel reads it from the state; the mixed forms defer U
   LaunchScope ls(p, kKUpdate);
-  if (p->prec == TPCG_FP64)
+  if (p->prec == TPCG_FP64) {
     k_update<<<p->stream_blocks, 256, 0, p->stream>>>(g, U, (const double*)p->d_P[k & 1], p->d_W, p->d_R,
                                                        lowprec(p), p->d_state, p->d_partials);
-  else if (g.nx % 2 == 0 && aligned16(U) && zero_guess_first)  // first update of a zero guess: U = alpha P
-    k_update_pair<true><<<p->fx_blocks[kFxUpd], p->st_block, 0, p->stream>>>(
-        g, U, (const int*)p->d_P[k & 1], p->d_R, lowprec(p), p->d_state, p->d_partials);
-  else if (g.nx % 2 == 0 && aligned16(U))
-    k_update_pair<false><<<p->fx_blocks[kFxUpd], p->st_block, 0, p->stream>>>(
-        g, U, (const int*)p->d_P[k & 1], p->d_R, lowprec(p), p->d_state, p->d_partials);
-  else if (zero_guess_first)
-    k_update_int<true><<<p->fx_blocks[kFxUpd], p->st_block, 0, p->stream>>>(
-        g, U, (const int*)p->d_P[k & 1], p->d_R, lowprec(p), p->d_state, p->d_partials);
+    return;
+  }
+  const int slot = k % kPRing;
+  if (g.nx % 2 == 0)
+    k_update_pair<<<p->fx_blocks[kFxUpd], p->st_block, 0, p->stream>>>(g, (const int*)p->d_P[slot], p->d_R,
+                                                                        lowprec(p), p->d_state, p->d_partials, slot);
   else
-    k_update_int<false><<<p->fx_blocks[kFxUpd], p->st_block, 0, p->stream>>>(
-        g, U, (const int*)p->d_P[k & 1], p->d_R, lowprec(p), p->d_state, p->d_partials);
+    k_update_int<<<p->fx_blocks[kFxUpd], p->st_block, 0, p->stream>>>(g, (const int*)p->d_P[slot], p->d_R,
+                                                                       lowprec(p), p->d_state, p->d_partials, slot);
+}
+// Mixed forms: apply the recorded updates to U (k_form_u) when a check is due, the ring is about to wrap,
+// or (force) unconditionally.
+void launch_form_u(const tpcg_plan* p, const Geom& g, double* U, bool force) {
+  LaunchScope ls(p, kKFormU);
+  if (g.N % 2 == 0 && aligned16(U))
+    k_form_u<true><<<p->stream_blocks, 256, 0, p->stream>>>(g, U, (const int*)p->d_P[0], (unsigned long long)g.N,
+                                                            p->d_state, p->d_partials, force ? 1 : 0);
+  else
+    k_form_u<false><<<p->stream_blocks, 256, 0, p->stream>>>(g, U, (const int*)p->d_P[0], (unsigned long long)g.N,
+                                                             p->d_state, p->d_partials, force ? 1 : 0);
 }
 void launch_true_residual(const tpcg_plan* p, const Geom& g, const double* eta, const double* U, bool force) {
   LaunchScope ls(p, kKTrueRes);

@@ -12,6 +12,9 @@ namespace tpcg {
 // Scalars of one PCG solve (Algorithm 1), kept in device memory so that the
 // iteration runs without host round trips.  Written only by the last block
 // of a reduction ("finalize"), read by every later kernel.
+// Mixed forms: the directions P_k kept in a ring for the deferred update of U (k_form_u).
+constexpr int kPRing = 8;
+
 struct SolveState {
   double mean_eta;     // mean removed from eta (eq. centering) when singular
   double eta_norm2;    // ||eta_hat||^2
@@ -53,9 +56,15 @@ struct SolveState {
   int lp_shift;        // power-of-two exponent applied when R is next converted to FP16
   int lp_shift_applied;  // exponent the current low-precision copy of R was converted with
   unsigned tickets[8]; // arrival counters of the last-block reductions
+  // mixed forms, deferred U += alpha_k P_k (k_form_u): alpha_k, the exponent of P_k and its ring slot
+  int n_pend;          // updates recorded and not yet applied to U
+  int u_valid;         // U holds an iterate (0: zero initial guess and no update applied yet)
+  double pend_alpha[kPRing];
+  int pend_kp[kPRing];
+  int pend_slot[kPRing];
 };
 
-enum Ticket { kTkEta = 0, kTkInit = 1, kTkDir = 2, kTkUpd = 3, kTkTrue = 4, kTkPrec = 5, kTkMisc = 6 };
+enum Ticket { kTkEta = 0, kTkInit = 1, kTkDir = 2, kTkUpd = 3, kTkTrue = 4, kTkPrec = 5, kTkMisc = 6, kTkForm = 7 };
 
 // Geometry of a grid and its stencil (eq. lap1d / eq. ourproblem).
 struct Geom {

@@ -55,7 +55,7 @@ struct SolveState;  // device-side scalars (tpcg_dev.cuh)
 enum FxKernel { kFxDir = 0, kFxUpd, kFxTrue, kFxInit, kFxCount };
 
 enum KernelKind {
-  kKEtaSum = 0, kKInit, kKDirection, kKUpdate, kKTrueRes, kKCenter, kKApply, kKModeF64, kKModeTC, kKConvert,
+  kKEtaSum = 0, kKInit, kKDirection, kKUpdate, kKTrueRes, kKCenter, kKApply, kKModeF64, kKModeTC, kKConvert, kKFormU,
   kKindCount
 };
 const char* kernel_kind_name(int kind);
@@ -117,7 +117,8 @@ struct tpcg_plan {
 
   // device: PCG workspaces
   double* d_R = nullptr;
-  void* d_P[2] = {nullptr, nullptr};  // direction, ping-pong (FP64, or int32 fixed point in the mixed forms)
+  void* d_P[8] = {};  // directions: FP64 ping-pong [0..1], or the mixed forms' ring of int32 fixed point [0..7]
+                     // (one allocation, d_P[0] its base)
   double* d_W = nullptr;               // W = L P (FP64 form only)
   void* d_Z = nullptr;       // FP64 (FP64 form) or FP32 (mixed forms)
   void* d_Rlp = nullptr;     // BF16 / FP16 copy of R (mixed forms), row pitch pitch16[0]
