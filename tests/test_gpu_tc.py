@@ -321,3 +321,23 @@ def test_caller_arrays_need_only_8_byte_alignment():
     st3, info3 = pl.solve(eb, ub, tol=1e-10, maxit=40)
     assert st3 == 0 and info3["rel_res_true"] <= 1e-10
     assert rel_err(ub.cpu().numpy(), ua.cpu().numpy()) <= 1e-9
+
+
+@pytest.mark.parametrize("maxit", [1, 2, 9])
+def test_unconverged_iterate_is_the_reported_one(maxit):
+    """A solve stopped by maxit returns an iterate with every recorded U += alpha P step applied (the mixed
+    forms apply them in one pass before the host reads U): the true residual of the returned U, computed
+    here with the operator, equals the reported one.  maxit = 9 also crosses the ring of recorded
+    directions (applied every seventh step)."""
+    nx, ny, nz, bcs = 40, 36, 20, ("P", "D", "N")
+    pl = _plan(nx, ny, nz, bcs, prec="bf16")
+    eta = synth.defect_rhs(nx, ny, nz, bcs, 12, 1.5, seed=71)
+    ed = torch.from_numpy(eta.copy()).cuda()
+    ud = torch.zeros_like(ed)
+    st, info = pl.solve(ed, ud, tol=1e-14, maxit=maxit, zero_guess=True)
+    assert st == 4 and info["iters"] == maxit  # TPCG_ERR_NOT_CONVERGED
+    w = torch.zeros_like(ed)
+    pl.laplacian(ud, w)
+    eta_hat = ed - info["removed_mean"]
+    res = torch.linalg.vector_norm(eta_hat - w).item() / torch.linalg.vector_norm(eta_hat).item()
+    assert abs(res - info["rel_res_true"]) <= 1e-6 * info["rel_res_true"] + 1e-15
