@@ -406,7 +406,7 @@ def whole_job_rate(world, steps, seconds):
 
 def run_ours(args, rank, world, torch):
     from paper_2501_03377_gb300 import Plan
-    from paper_2501_03377_gb300.binding import TPCG_ZERO_GUESS, tpcg_solve_batched
+    from paper_2501_03377_gb300.binding import TPCG_OPT_DEFER_U, TPCG_ZERO_GUESS, tpcg_solve_batched
 
     dev = torch.device("cuda", torch.cuda.current_device())
     prec = pick_prec(args)
@@ -440,6 +440,9 @@ def run_ours(args, rank, world, torch):
     conc = max(1, args.concurrency)
     cstreams = [torch.cuda.Stream() for _ in range(conc)]
     cplans = [Plan(nx, ny, nz, w0["bcs"], prec=prec, stream=cs.cuda_stream) for cs in cstreams]
+    if prec != "fp64" and conc > 1:  # several plans in flight: record U += alpha P and form U before each check
+        for cp in cplans:
+            cp.set_option(TPCG_OPT_DEFER_U, 1)
     counts = [args.steps // conc + (1 if q < args.steps % conc else 0) for q in range(conc)]
     firsts = [sum(counts[:q]) for q in range(conc)]
     E = [torch.stack([etas[(firsts[q] + r) % 4] for r in range(max(1, counts[q]))]).contiguous() for q in range(conc)]
@@ -609,7 +612,8 @@ def run_ours(args, rank, world, torch):
                        "l2": "every step its own 67 MB right-hand side (4 seeded ones in rotation) + ~0.3 GB "
                              "workspace per plan > 129 MB L2",
                        "parallelism": f"replicas x{world}",
-                       "concurrency": f"{conc} plans on {conc} streams (tpcg_solve_batched)"},
+                       "concurrency": f"{conc} plans on {conc} streams (tpcg_solve_batched)"
+                                      + (", TPCG_OPT_DEFER_U" if prec != "fp64" and conc > 1 else "")},
             "mpoints_per_s": value * N / 1e6,
             "iters_per_solve": iters_total / args.steps, "precond_applies_per_solve": applies_total / args.steps,
             "worst_rel_res_true": worst_res, "failed_solves": len(bad),

@@ -157,6 +157,22 @@ int tpcg_solve_host(tpcg_plan* plan, const double* eta_host, double* ups_host, d
 int tpcg_solve_host_stream(tpcg_plan* plan, int nrhs, const double* const* eta_host, double* const* ups_host,
                            double tol, int maxit, unsigned flags, tpcg_info* infos);
 
+/* Plan options (no counterpart in the paper: they choose how the library
+ * schedules the same arithmetic).
+ * TPCG_OPT_DEFER_U (mixed forms; 0 = off, the default): instead of updating
+ * U every iteration (Algorithm 1, U += alpha P), the update records alpha and
+ * the direction, which stays in a ring of eight, and U is formed with the same
+ * FP64 operations in the same order (bitwise the same U) before each
+ * true-residual check, every seventh step and before an unconverged iterate is
+ * returned.  It moves 16 bytes per grid point per iteration out of the
+ * iteration and adds one formation pass bound by the FP64 pipe: slower for one
+ * solve at a time, faster in total when several plans solve concurrently
+ * (e.g. tpcg_solve_batched over several plans).  Ignored for TPCG_FP64.
+ * Returns TPCG_OK or TPCG_ERR_INVALID_ARG (NULL plan, unknown option, value
+ * not 0 or 1).  Do not change an option while a solve of the plan runs.     */
+#define TPCG_OPT_DEFER_U 1
+int tpcg_plan_set_option(tpcg_plan* plan, int option, int value);
+
 /* Many independent solves in one call (the batched form of tpcg_solve).
  * Solve s uses plans[s] and has nrhs[s] right-hand sides (nrhs == NULL: one
  * each) stored back to back: right-hand side r is eta[s] + r*N_s and its

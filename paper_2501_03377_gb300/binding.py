@@ -40,6 +40,7 @@ TPCG_ZERO_GUESS = 1
 TPCG_PRECOND_PINV = 0
 TPCG_PRECOND_NONE = 1
 TPCG_PRECOND_JACOBI = 2
+TPCG_OPT_DEFER_U = 1
 TPCG_REQ_BORROW_HOST = 1
 TPCG_REQ_BORROW_DEVICE = 2
 
@@ -102,6 +103,7 @@ _SIGS = {
     "tpcg_rhs_add_bc": (_I, [_P, _P, ctypes.POINTER(_D)]),
     "tpcg_efield": (_I, [_P, _P, ctypes.POINTER(_D), _P, _P, _P]),
     "tpcg_plan_set_precond": (_I, [_P, _I, _I, _D]),
+    "tpcg_plan_set_option": (_I, [_P, _I, _I]),
     "tpcg_plan_eigenpairs": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "tpcg_plan_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "tpcg_profile_begin": (_I, [_P]),
@@ -206,6 +208,10 @@ def tpcg_precond_apply(plan, r_ptr, z_ptr):
 
 def tpcg_apply_laplacian(plan, x_ptr, w_ptr):
     return lib().tpcg_apply_laplacian(plan, _P(x_ptr), _P(w_ptr))
+
+
+def tpcg_plan_set_option(plan, option, value):
+    return lib().tpcg_plan_set_option(plan, int(option), int(value))
 
 
 def tpcg_plan_set_precond(plan, kind, p=3, omega=1.3):
@@ -444,6 +450,12 @@ class Plan:
         st = tpcg_apply_laplacian(self.handle, x.data_ptr(), w.data_ptr())
         if st != TPCG_OK:
             raise TpcgError(st, "tpcg_apply_laplacian")
+
+    def set_option(self, option, value):
+        """Plan option (TPCG_OPT_DEFER_U: 1 to record U += alpha P and form U before each check)."""
+        st = tpcg_plan_set_option(self.handle, option, value)
+        if st != TPCG_OK:
+            raise TpcgError(st, "tpcg_plan_set_option")
 
     def set_precond(self, kind, p=3, omega=1.3):
         """Choose the preconditioner ("pinv", "none" or "jacobi"); see tpcg_plan_set_precond."""

@@ -256,7 +256,7 @@ int enqueue_iterations(SolveJob& j, int count) {
     const int k = j.issued + c;                         // P_k is written to d_P[k & 1], P_{k-1} read from the other
     launch_direction(p, g, k);                          // direction P, W = L P, alpha
     launch_update(p, g, j.ups, k, k == 0 && (j.flags & TPCG_ZERO_GUESS));  // U and R updates
-    if (p->prec != TPCG_FP64) launch_form_u(p, g, j.ups, false);  // deferred U updates, when a check is due
+    if (p->defer_u) launch_form_u(p, g, j.ups, false);  // deferred U updates, when a check is due
     launch_true_residual(p, g, j.eta, j.ups, false);    // stop test
     const int rc = run_precond(p, p->d_R, p->d_Z, p->d_state);  // Z = M R, rho, beta
     if (rc) return rc;
@@ -323,7 +323,7 @@ int job_step(SolveJob& j) {
     // read back is final
     const bool finished = hs->done == 1 && hs->status == TPCG_OK;
     if (!finished) {
-      if (p->prec != TPCG_FP64) launch_form_u(p, g, j.ups, true);  // apply any deferred U updates
+      if (p->defer_u) launch_form_u(p, g, j.ups, true);  // apply any deferred U updates
       if (hs->done == 2) {
         launch_zero(p, g.N, j.ups);  // eta_hat = 0: minimum-norm solution is 0
       } else {
@@ -762,6 +762,15 @@ int tpcg_solve_host_stream(tpcg_plan* plan, int nrhs, const double* const* eta_h
   const bool synced = cudaStreamSynchronize(plan->s_in) == cudaSuccess && cudaStreamSynchronize(plan->s_out) == cudaSuccess;
   if (rc) return rc;
   return synced ? result : TPCG_ERR_CUDA;
+}
+
+int tpcg_plan_set_option(tpcg_plan* plan, int option, int value) {
+  if (!plan || (value != 0 && value != 1)) return TPCG_ERR_INVALID_ARG;
+  if (option == TPCG_OPT_DEFER_U) {
+    plan->defer_u = (plan->prec != TPCG_FP64) ? value : 0;  // the FP64 form always updates U in place
+    return TPCG_OK;
+  }
+  return TPCG_ERR_INVALID_ARG;
 }
 
 int tpcg_precond_apply(tpcg_plan* plan, const double* r, double* z) {

@@ -861,11 +861,10 @@ __device__ void fin_update(SolveState* st, const double (&s)[2], int shift, cons
   if (rr <= st->tol2 || st->iter >= st->maxit) st->need_check = 1;
 }
 
-// Mixed forms: R -= alpha W with W = L P from the exact integer stencil of P_int, in a
-// register-window stream (see k_direction_int).  The loads of plane k+1 (P
-// two planes ahead, the y neighbours and R) are issued before plane k is
-// processed.  U += alpha P is deferred: the finalize records it for k_form_u
-// (P_s stays in ring slot pslot until then).
+// Mixed forms with the deferred U update (TPCG_OPT_DEFER_U): R -= alpha W with W = L P from the exact
+// integer stencil of P_int, in a register-window stream (see k_direction_int).  The loads of plane k+1
+// (P two planes ahead, the y neighbours and R) are issued before plane k is processed.  U += alpha P is
+// not applied: the finalize records it for k_form_u (P_s stays in ring slot pslot until then).
 __global__ void __launch_bounds__(TX* TY, 4) k_update_int(Geom g, const int* __restrict__ P, double* __restrict__ R,
                                                           LowPrec lp, SolveState* st, double* partials, int pslot) {
   if (st->done) return;
@@ -1049,6 +1048,219 @@ __global__ void __launch_bounds__(TX* TY, 4) k_update_pair(Geom g, const int* __
   double acc[2] = {f32_to_f64_int(rr), f32_to_f64_int(sR)};
   grid_reduce<2>(acc, partials, &st->tickets[kTkUpd], gridDim.x, blockIdx.x,
                  [st, shift, g, pslot](const double(&s)[2]) { fin_update(st, s, shift, g, pslot); });
+}
+
+// Mixed forms, U updated in place (the default): U += alpha P and R -= alpha W with W = L P from the
+// exact integer stencil of P_int, in a register-window stream (see k_direction_int).  The loads of
+// plane k+1 (P two planes ahead, the y neighbours, R and U) are issued before plane k is processed.
+// ZG: the first update of a zero initial guess writes U = alpha P.
+template <bool ZG>
+__global__ void __launch_bounds__(TX* TY, 4) k_update_u_int(Geom g, double* __restrict__ U,
+                                                          const int* __restrict__ P, double* __restrict__ R,
+                                                          LowPrec lp, SolveState* st, double* partials) {
+  if (st->done) return;
+  const double alpha = st->alpha;
+  const double na0 = st->nah[0], na1 = st->nah[1], na2 = st->nah[2];  // -alpha / h^2 per axis
+  const int kp = st->kp;
+  const int shift = st->lp_shift;
+  const unsigned nx = (unsigned)g.nx, plane = (unsigned)g.nx * (unsigned)g.ny;
+  const bool has_z = g.nz > 1;
+  const int lane = threadIdx.x;
+  float rr = 0.0f, sR = 0.0f;
+  unsigned long long um = 0;
+  for_each_run(g, [&](int bx0, int by0, int k0, int k1) {
+    const int x = bx0 + lane, y = by0 + threadIdx.y;
+    const bool active = x < g.nx && y < g.ny;
+    const unsigned col = (unsigned)y * nx + (unsigned)x;
+    const int xgl = ghost_index(x - 1, g.nx, g.bc[0]), xgr = ghost_index(x + 1, g.nx, g.bc[0]);
+    const int ygl = ghost_index(y - 1, g.ny, g.bc[1]), ygr = ghost_index(y + 1, g.ny, g.bc[1]);
+    const bool own_xl = lane == 0, own_xr = lane == TX - 1 || x == g.nx - 1;  // halo or boundary: load
+    auto ld = [&](unsigned k, int xx, int yy) -> int {
+      return (xx >= 0 && yy >= 0) ? __ldg(P + k * plane + (unsigned)yy * nx + (unsigned)xx) : 0;
+    };
+    auto ldz = [&](int kk) -> int {  // P at (x, y, kk), kk possibly a ghost plane
+      if (!has_z) return 0;
+      const int kz = ghost_index(kk, g.nz, g.bc[2]);
+      return (active && kz >= 0) ? __ldg(P + (unsigned)kz * plane + col) : 0;
+    };
+    struct Plane {
+      int c, yl, yr, xl, xr;
+      double r, u;
+    };
+    auto fetch = [&](int k, int c) {
+      Plane f;
+      f.c = c;
+      f.yl = f.yr = f.xl = f.xr = 0;
+      f.r = f.u = 0.0;
+      if (active) {
+        const unsigned kk = (unsigned)k;
+        f.yl = ld(kk, x, ygl);
+        f.yr = ld(kk, x, ygr);
+        if (own_xl) f.xl = ld(kk, xgl, y);
+        if (own_xr) f.xr = ld(kk, xgr, y);
+        f.r = R[kk * plane + col];
+        if (!ZG) f.u = U[kk * plane + col];
+      }
+      return f;
+    };
+    int zl = ldz(k0 - 1);
+    const int c0 = active ? __ldg(P + (unsigned)k0 * plane + col) : 0;
+    int zr = (k0 + 1 < g.nz) ? (active ? __ldg(P + (unsigned)(k0 + 1) * plane + col) : 0) : ldz(k0 + 1);
+    Plane cur = fetch(k0, c0);
+    for (int k = k0; k < k1; ++k) {
+      // loads for plane k+1 (and P two planes ahead) go out before plane k is processed
+      Plane nxt;
+      int zr2 = 0;
+      if (k + 1 < k1) {
+        nxt = fetch(k + 1, zr);
+        zr2 = (k + 2 < g.nz) ? (active ? __ldg(P + (unsigned)(k + 2) * plane + col) : 0) : ldz(k + 2);
+      }
+      const int c = cur.c;
+      int xl = __shfl_up_sync(0xffffffffu, c, 1), xr = __shfl_down_sync(0xffffffffu, c, 1);
+      if (own_xl) xl = cur.xl;
+      if (own_xr) xr = cur.xr;
+      const int zlv = has_z ? zl : c, zrv = has_z ? zr : c;
+      if (active) {
+        const int dx = 2 * c - xl - xr, dy = 2 * c - cur.yl - cur.yr, dz = 2 * c - zlv - zrv;
+        double r = cur.r;
+        if (g.uniform) {
+          r = fma(na0, i32_to_f64_scaled(dx + dy + dz, -kp), r);
+        } else {
+          r = fma(na0, i32_to_f64_scaled(dx, -kp), r);
+          r = fma(na1, i32_to_f64_scaled(dy, -kp), r);
+          if (dz) r = fma(na2, i32_to_f64_scaled(dz, -kp), r);
+        }
+        const unsigned i = (unsigned)k * plane + col;
+        R[i] = r;
+        const float r32 = f64_to_f32_odd(r, shift);
+        store_lp(lp, i, r, r32);
+        rr = fmaf(r32, r32, rr);
+        sR += r32;
+        const double pv = i32_to_f64_scaled(c, -kp);
+        const double u = ZG ? alpha * pv : fma(alpha, pv, cur.u);
+        U[i] = u;
+        const unsigned long long ub = mag_key(u);
+        um = ub > um ? ub : um;
+      }
+      zl = c;
+      zr = zr2;
+      if (k + 1 < k1) cur = nxt;
+    }
+  });
+  double acc[2] = {f32_to_f64_int(rr), f32_to_f64_int(sR)};
+  fold_umax(st, um);
+  grid_reduce<2>(acc, partials, &st->tickets[kTkUpd], gridDim.x, blockIdx.x,
+                 [st, shift, g](const double(&s)[2]) { fin_update(st, s, shift, g, -1); });
+}
+
+// The same in-place update with two adjacent x points per thread (even nx): R and U move
+// as 16-byte double2, P and its y neighbours as int2, the FP16 copy as one
+// packed pair; only the outer x neighbours of a pair come by warp shuffle.
+// A warp covers 64 consecutive x of one row.
+template <bool ZG>
+__global__ void __launch_bounds__(TX* TY, 4) k_update_u_pair(Geom g, double* __restrict__ U,
+                                                           const int* __restrict__ P, double* __restrict__ R,
+                                                           LowPrec lp, SolveState* st, double* partials) {
+  if (st->done) return;
+  const double alpha = st->alpha;
+  const double na0 = st->nah[0], na1 = st->nah[1], na2 = st->nah[2];  // -alpha / h^2 per axis
+  const int kp = st->kp;
+  const int shift = st->lp_shift;
+  const unsigned nx = (unsigned)g.nx, plane = (unsigned)g.nx * (unsigned)g.ny;
+  const bool has_z = g.nz > 1;
+  const int lane = threadIdx.x;
+  float rr = 0.0f, sR = 0.0f;
+  unsigned long long um = 0;
+  for_each_run<2 * TX>(g, [&](int bx0, int by0, int k0, int k1) {
+    const int x = bx0 + 2 * lane, y = by0 + threadIdx.y;  // points (x, y) and (x + 1, y)
+    const bool active = x < g.nx && y < g.ny;             // nx even: both points or neither
+    const unsigned col = active ? (unsigned)y * nx + (unsigned)x : 0u;
+    const int xgl = ghost_index(x - 1, g.nx, g.bc[0]), xgr = ghost_index(x + 2, g.nx, g.bc[0]);
+    const int ygl = ghost_index(y - 1, g.ny, g.bc[1]), ygr = ghost_index(y + 1, g.ny, g.bc[1]);
+    const bool own_xl = lane == 0, own_xr = lane == TX - 1 || x + 2 >= g.nx;  // halo or boundary
+    const unsigned coll = (unsigned)y * nx + (unsigned)max(xgl, 0), colr = (unsigned)y * nx + (unsigned)max(xgr, 0);
+    const unsigned colu = (unsigned)max(ygl, 0) * nx + (unsigned)x, cold = (unsigned)max(ygr, 0) * nx + (unsigned)x;
+    const bool has_yl = active && ygl >= 0, has_yr = active && ygr >= 0;
+    const bool has_xl = active && own_xl && xgl >= 0, has_xr = active && own_xr && xgr >= 0;
+    const int2 zero2 = make_int2(0, 0);
+    auto ld2 = [&](unsigned i) -> int2 { return __ldg(reinterpret_cast<const int2*>(P + i)); };
+    auto ldz = [&](int kk) -> int2 {  // P at (x.., y, kk), kk possibly a ghost plane
+      if (!has_z || !active) return zero2;
+      const int kz = ghost_index(kk, g.nz, g.bc[2]);
+      return kz >= 0 ? ld2((unsigned)kz * plane + col) : zero2;
+    };
+    struct Plane {
+      int2 c, yl, yr;
+      int xl, xr;
+      double2 r, u;
+    };
+    auto fetch = [&](int k, int2 c) {
+      Plane f;
+      const unsigned base = (unsigned)k * plane;
+      f.c = c;
+      f.yl = has_yl ? ld2(base + colu) : zero2;
+      f.yr = has_yr ? ld2(base + cold) : zero2;
+      f.xl = has_xl ? __ldg(P + base + coll) : 0;
+      f.xr = has_xr ? __ldg(P + base + colr) : 0;
+      f.r = active ? *reinterpret_cast<const double2*>(R + base + col) : make_double2(0.0, 0.0);
+      f.u = (active && !ZG) ? *reinterpret_cast<const double2*>(U + base + col) : make_double2(0.0, 0.0);
+      return f;
+    };
+    int2 zl = ldz(k0 - 1);
+    const int2 c0 = active ? ld2((unsigned)k0 * plane + col) : zero2;
+    int2 zr = (k0 + 1 < g.nz) ? (active ? ld2((unsigned)(k0 + 1) * plane + col) : zero2) : ldz(k0 + 1);
+    Plane cur = fetch(k0, c0);
+    for (int k = k0; k < k1; ++k) {
+      Plane nxt;
+      int2 zr2 = zero2;
+      if (k + 1 < k1) {  // loads of plane k+1 (and P two planes ahead) go out before plane k is processed
+        nxt = fetch(k + 1, zr);
+        zr2 = (k + 2 < g.nz) ? (active ? ld2((unsigned)(k + 2) * plane + col) : zero2) : ldz(k + 2);
+      }
+      const int2 c = cur.c;
+      int xl = __shfl_up_sync(0xffffffffu, c.y, 1), xr = __shfl_down_sync(0xffffffffu, c.x, 1);
+      if (own_xl) xl = cur.xl;
+      if (own_xr) xr = cur.xr;
+      const int2 zlv = has_z ? zl : c, zrv = has_z ? zr : c;
+      if (active) {
+        const int dx0 = 2 * c.x - xl - c.y, dx1 = 2 * c.y - c.x - xr;
+        const int dy0 = 2 * c.x - cur.yl.x - cur.yr.x, dy1 = 2 * c.y - cur.yl.y - cur.yr.y;
+        const int dz0 = 2 * c.x - zlv.x - zrv.x, dz1 = 2 * c.y - zlv.y - zrv.y;
+        double r0 = cur.r.x, r1 = cur.r.y;
+        if (g.uniform) {
+          r0 = fma(na0, i32_to_f64_scaled(dx0 + dy0 + dz0, -kp), r0);
+          r1 = fma(na0, i32_to_f64_scaled(dx1 + dy1 + dz1, -kp), r1);
+        } else {
+          r0 = fma(na0, i32_to_f64_scaled(dx0, -kp), r0);
+          r0 = fma(na1, i32_to_f64_scaled(dy0, -kp), r0);
+          if (dz0) r0 = fma(na2, i32_to_f64_scaled(dz0, -kp), r0);
+          r1 = fma(na0, i32_to_f64_scaled(dx1, -kp), r1);
+          r1 = fma(na1, i32_to_f64_scaled(dy1, -kp), r1);
+          if (dz1) r1 = fma(na2, i32_to_f64_scaled(dz1, -kp), r1);
+        }
+        const unsigned i = (unsigned)k * plane + col;
+        *reinterpret_cast<double2*>(R + i) = make_double2(r0, r1);
+        const float a32 = f64_to_f32_odd(r0, shift), b32 = f64_to_f32_odd(r1, shift);
+        store_lp_pair(lp, i, r0, r1, a32, b32);
+        rr = fmaf(a32, a32, fmaf(b32, b32, rr));
+        sR += a32 + b32;
+        const double p0 = i32_to_f64_scaled(c.x, -kp), p1 = i32_to_f64_scaled(c.y, -kp);
+        const double u0 = ZG ? alpha * p0 : fma(alpha, p0, cur.u.x);
+        const double u1 = ZG ? alpha * p1 : fma(alpha, p1, cur.u.y);
+        *reinterpret_cast<double2*>(U + i) = make_double2(u0, u1);
+        const unsigned long long k0b = mag_key(u0), k1b = mag_key(u1);
+        const unsigned long long kb = k0b > k1b ? k0b : k1b;
+        um = kb > um ? kb : um;
+      }
+      zl = c;
+      zr = zr2;
+      if (k + 1 < k1) cur = nxt;
+    }
+  });
+  double acc[2] = {f32_to_f64_int(rr), f32_to_f64_int(sR)};
+  fold_umax(st, um);
+  grid_reduce<2>(acc, partials, &st->tickets[kTkUpd], gridDim.x, blockIdx.x,
+                 [st, shift, g](const double(&s)[2]) { fin_update(st, s, shift, g, -1); });
 }
 
 // FP64 form: P and W = L P are stored by the direction kernel.
@@ -1527,7 +1739,6 @@ void launch_direction(const tpcg_plan* p, const Geom& g, int k) {
                                                                           p->d_state, p->d_partials);
 }
 void launch_update(const tpcg_plan* p, const Geom& g, double* U, int k, bool zero_guess_first) {
-  (void)zero_guess_first;  // the FP64 kernel reads it from the state; the mixed forms defer U
   LaunchScope ls(p, kKUpdate);
   if (p->prec == TPCG_FP64) {
     k_update<<<p->stream_blocks, 256, 0, p->stream>>>(g, U, (const double*)p->d_P[k & 1], p->d_W, p->d_R,
@@ -1535,12 +1746,27 @@ void launch_update(const tpcg_plan* p, const Geom& g, double* U, int k, bool zer
     return;
   }
   const int slot = k % kPRing;
-  if (g.nx % 2 == 0)
-    k_update_pair<<<p->fx_blocks[kFxUpd], p->st_block, 0, p->stream>>>(g, (const int*)p->d_P[slot], p->d_R,
-                                                                        lowprec(p), p->d_state, p->d_partials, slot);
-  else
-    k_update_int<<<p->fx_blocks[kFxUpd], p->st_block, 0, p->stream>>>(g, (const int*)p->d_P[slot], p->d_R,
-                                                                       lowprec(p), p->d_state, p->d_partials, slot);
+  const int* P = (const int*)p->d_P[slot];
+  if (p->defer_u) {  // U += alpha P recorded for k_form_u
+    if (g.nx % 2 == 0)
+      k_update_pair<<<p->fx_blocks[kFxUpd], p->st_block, 0, p->stream>>>(g, P, p->d_R, lowprec(p), p->d_state,
+                                                                          p->d_partials, slot);
+    else
+      k_update_int<<<p->fx_blocks[kFxUpd], p->st_block, 0, p->stream>>>(g, P, p->d_R, lowprec(p), p->d_state,
+                                                                         p->d_partials, slot);
+  } else if (g.nx % 2 == 0 && aligned16(U) && zero_guess_first) {  // first update of a zero guess: U = alpha P
+    k_update_u_pair<true><<<p->fx_blocks[kFxUpd], p->st_block, 0, p->stream>>>(g, U, P, p->d_R, lowprec(p),
+                                                                                p->d_state, p->d_partials);
+  } else if (g.nx % 2 == 0 && aligned16(U)) {
+    k_update_u_pair<false><<<p->fx_blocks[kFxUpd], p->st_block, 0, p->stream>>>(g, U, P, p->d_R, lowprec(p),
+                                                                                 p->d_state, p->d_partials);
+  } else if (zero_guess_first) {
+    k_update_u_int<true><<<p->fx_blocks[kFxUpd], p->st_block, 0, p->stream>>>(g, U, P, p->d_R, lowprec(p),
+                                                                               p->d_state, p->d_partials);
+  } else {
+    k_update_u_int<false><<<p->fx_blocks[kFxUpd], p->st_block, 0, p->stream>>>(g, U, P, p->d_R, lowprec(p),
+                                                                                p->d_state, p->d_partials);
+  }
 }
 // Mixed forms: apply the recorded updates to U (k_form_u) when a check is due, the ring is about to wrap,
 // or (force) unconditionally.

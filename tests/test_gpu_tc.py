@@ -323,14 +323,18 @@ def test_caller_arrays_need_only_8_byte_alignment():
     assert rel_err(ub.cpu().numpy(), ua.cpu().numpy()) <= 1e-9
 
 
+@pytest.mark.parametrize("defer", [0, 1])
 @pytest.mark.parametrize("maxit", [1, 2, 9])
-def test_unconverged_iterate_is_the_reported_one(maxit):
+def test_unconverged_iterate_is_the_reported_one(maxit, defer):
     """A solve stopped by maxit returns an iterate with every recorded U += alpha P step applied (the mixed
     forms apply them in one pass before the host reads U): the true residual of the returned U, computed
     here with the operator, equals the reported one.  maxit = 9 also crosses the ring of recorded
     directions (applied every seventh step)."""
     nx, ny, nz, bcs = 40, 36, 20, ("P", "D", "N")
     pl = _plan(nx, ny, nz, bcs, prec="bf16")
+    from paper_2501_03377_gb300 import binding as b
+
+    pl.set_option(b.TPCG_OPT_DEFER_U, defer)
     eta = synth.defect_rhs(nx, ny, nz, bcs, 12, 1.5, seed=71)
     ed = torch.from_numpy(eta.copy()).cuda()
     ud = torch.zeros_like(ed)
@@ -341,3 +345,38 @@ def test_unconverged_iterate_is_the_reported_one(maxit):
     eta_hat = ed - info["removed_mean"]
     res = torch.linalg.vector_norm(eta_hat - w).item() / torch.linalg.vector_norm(eta_hat).item()
     assert abs(res - info["rel_res_true"]) <= 1e-6 * info["rel_res_true"] + 1e-15
+
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("case", [((64, 48, 24), ("P", "P", "N"), True), ((37, 9, 5), ("N", "N", "N"), True),
+                                  ((33, 7, 19), ("ND", "P", "D"), False)])
+def test_deferred_u_is_bitwise_the_in_place_update(prec, case):
+    """TPCG_OPT_DEFER_U records U += alpha P and forms U with the same FP64 operations in the same order:
+    the solution, the iteration count and the reported residual are bitwise those of the in-place update,
+    from a zero and from a given initial guess, for even and odd nx (both update kernels)."""
+    from paper_2501_03377_gb300 import binding as b
+
+    (nx, ny, nz), bcs, zero = case
+    eta = synth.defect_rhs(nx, ny, nz, bcs, 10, 1.5, seed=81)
+    ed = torch.from_numpy(eta.copy()).cuda()
+    outs = []
+    for defer in (0, 1):
+        pl = _plan(nx, ny, nz, bcs, prec=prec)
+        pl.set_option(b.TPCG_OPT_DEFER_U, defer)
+        ud = torch.zeros_like(ed) if zero else torch.from_numpy(0.1 * synth.random_field(nx, ny, nz, seed=82)).cuda()
+        st, info = pl.solve(ed, ud, tol=1e-11, maxit=60, zero_guess=zero)
+        assert st == 0
+        outs.append((ud.cpu().numpy(), info))
+    (u0, i0), (u1, i1) = outs
+    assert np.array_equal(u0, u1)
+    assert i0["iters"] == i1["iters"] and i0["rel_res_true"] == i1["rel_res_true"]
+
+
+def test_plan_option_rejects_bad_values():
+    from paper_2501_03377_gb300 import binding as b
+
+    pl = _plan(16, 16, 8, ("P", "P", "N"), prec="fp16")
+    assert b.tpcg_plan_set_option(pl.handle, b.TPCG_OPT_DEFER_U, 2) == b.TPCG_ERR_INVALID_ARG
+    assert b.tpcg_plan_set_option(pl.handle, 99, 1) == b.TPCG_ERR_INVALID_ARG
+    assert b.tpcg_plan_set_option(pl.handle, b.TPCG_OPT_DEFER_U, 1) == b.TPCG_OK
