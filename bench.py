@@ -343,8 +343,8 @@ NCU_TRAFFIC_PER_LAUNCH = {
     # tensor-core passes: mean over the six passes of one application; passes 1-3 and 6 captured
     # (17.0, 17.0, 16.8, 34.8 MB), passes 4 and 5 (the same FP16-in / FP16-out shape) taken as pass 1
     "modeprod_tc": (4 * 17.0e6 + 16.8e6 + 34.8e6) / 6,
-    "update": 134.7e6,
-    "form_u": 248.0e6,  # the formation before a check (six recorded directions)
+    "update": 276.1e6,  # the in-place update the instrumented (one-plan) pass runs
+    "form_u": 248.0e6,  # the formation before a check (six recorded directions; TPCG_OPT_DEFER_U)
     "direction": 76.6e6,
     "true_residual": 197.4e6,  # a launch that checks (the others return at once)
 }
@@ -372,8 +372,9 @@ def kernel_work(kind, plan_prec, N, dims, iters_total, applies_total, solves, ch
         # FP64 form: FP64 flops per point: P = (Z - m) + beta P_old (3), 7-point stencil (7), <W, P> (2)
         return iters_total * 12.0 * N / 1e12, "TFLOP", "alu", iters_total
     if kind == "update":
-        # mixed: P (4) + R (8+8) + FP16 copy of R (2), U deferred to form_u; FP64 form: P and W (8+8) + R + U
-        per = (4 + 16 + 2) if mixed else (16 + 16 + 16)
+        # the instrumented plan updates U in place: mixed P (4) + R (8+8) + U (8+8) + FP16 copy of R (2);
+        # FP64 form: P and W (8+8) + R + U
+        per = (4 + 16 + 16 + 2) if mixed else (16 + 16 + 16)
         return iters_total * per * N / 1e9, "GB", "hbm", iters_total
     if kind == "form_u":
         # mixed forms, zero initial guess: once per check, the recorded directions (4 B each) in and U (8) out
