@@ -737,13 +737,6 @@ __global__ void __launch_bounds__(TX* TY) k_direction_quad(Geom g, const float* 
     return Raw4{__ldg(reinterpret_cast<const float4*>(Z + i)),
                 first ? make_int4(0, 0, 0, 0) : __ldg(reinterpret_cast<const int4*>(Pold + i))};
   };
-  auto form1 = [&](float z, int po) -> int {
-    const float v = fmaf(bs, i22_to_f32(po), z);
-    return sc != 0.0f ? f32_to_i22(v, sc) : f32_to_fixed(v, kp);  // 2^kp outside the FP32 range: integer path
-  };
-  auto form4 = [&](const Raw4& r) -> int4 {
-    return make_int4(form1(r.z.x, r.p.x), form1(r.z.y, r.p.y), form1(r.z.z, r.p.z), form1(r.z.w, r.p.w));
-  };
   const bool endx = g.bc[0] == kBcD || g.bc[0] == kBcND, endy = g.bc[1] == kBcD || g.bc[1] == kBcND;
   const bool endz = has_z && (g.bc[2] == kBcD || g.bc[2] == kBcND);
   const float w0 = g.ih2f[0], w1 = g.ih2f[1], w2 = g.ih2f[2];
@@ -751,6 +744,18 @@ __global__ void __launch_bounds__(TX* TY) k_direction_quad(Geom g, const float* 
   float e = 0.0f;
   int pm = 0;
   constexpr int UZ = 2;  // planes whose loads are issued together
+  // the sweep, instantiated for 2^kp inside the FP32 range (one FMA per rounding) and outside it (integer
+  // path), so that the per-point code carries one of them only
+  auto sweep = [&](auto fast) {
+  constexpr bool kFast = decltype(fast)::value;
+  auto form1 = [&](float z, int po) -> int {
+    const float v = fmaf(bs, i22_to_f32(po), z);
+    if constexpr (kFast) return f32_to_i22(v, sc);
+    else return f32_to_fixed(v, kp);
+  };
+  auto form4 = [&](const Raw4& r) -> int4 {
+    return make_int4(form1(r.z.x, r.p.x), form1(r.z.y, r.p.y), form1(r.z.z, r.p.z), form1(r.z.w, r.p.w));
+  };
   for_each_run<4 * TX>(g, [&](int bx0, int by0, int k0, int k1) {
     const int x = bx0 + 4 * lane, y = by0 + threadIdx.y;
     const bool active = x < g.nx && y < g.ny;  // nx a multiple of 4: all four points or none
@@ -816,6 +821,9 @@ __global__ void __launch_bounds__(TX* TY) k_direction_quad(Geom g, const float* 
       }
     }
   });
+  };
+  if (sc != 0.0f) sweep(std::true_type{});
+  else sweep(std::false_type{});
   double acc[1] = {f32_to_f64_int(e)};
   const unsigned long long m = block_max_u64((unsigned long long)pm);
   if (threadIdx.x + threadIdx.y == 0) atomicMax(&st->pmax_bits, (unsigned)m);
