@@ -975,6 +975,9 @@ __global__ void __launch_bounds__(TX* TY, 4) k_update_pair(Geom g, const int* __
   const bool has_z = g.nz > 1;
   const int lane = threadIdx.x;
   float rr = 0.0f, sR = 0.0f;
+  // instantiated for equal and unequal spacings, so that the per-point code carries one stencil form
+  auto sweep = [&](auto uni) {
+  constexpr bool kUni = decltype(uni)::value;
   for_each_run<2 * TX>(g, [&](int bx0, int by0, int k0, int k1) {
     const int x = bx0 + 2 * lane, y = by0 + threadIdx.y;  // points (x, y) and (x + 1, y)
     const bool active = x < g.nx && y < g.ny;             // nx even: both points or neither
@@ -1030,7 +1033,7 @@ __global__ void __launch_bounds__(TX* TY, 4) k_update_pair(Geom g, const int* __
         const int dy0 = 2 * c.x - cur.yl.x - cur.yr.x, dy1 = 2 * c.y - cur.yl.y - cur.yr.y;
         const int dz0 = 2 * c.x - zlv.x - zrv.x, dz1 = 2 * c.y - zlv.y - zrv.y;
         double r0 = cur.r.x, r1 = cur.r.y;
-        if (g.uniform) {
+        if constexpr (kUni) {
           r0 = fma(na0, i32_to_f64_scaled(dx0 + dy0 + dz0, -kp), r0);
           r1 = fma(na0, i32_to_f64_scaled(dx1 + dy1 + dz1, -kp), r1);
         } else {
@@ -1053,6 +1056,9 @@ __global__ void __launch_bounds__(TX* TY, 4) k_update_pair(Geom g, const int* __
       if (k + 1 < k1) cur = nxt;
     }
   });
+  };
+  if (g.uniform) sweep(std::true_type{});
+  else sweep(std::false_type{});
   double acc[2] = {f32_to_f64_int(rr), f32_to_f64_int(sR)};
   grid_reduce<2>(acc, partials, &st->tickets[kTkUpd], gridDim.x, blockIdx.x,
                  [st, shift, g, pslot](const double(&s)[2]) { fin_update(st, s, shift, g, pslot); });
@@ -1179,6 +1185,9 @@ __global__ void __launch_bounds__(TX* TY, 4) k_update_u_pair(Geom g, double* __r
   const int lane = threadIdx.x;
   float rr = 0.0f, sR = 0.0f;
   unsigned long long um = 0;
+  // instantiated for equal and unequal spacings, so that the per-point code carries one stencil form
+  auto sweep = [&](auto uni) {
+  constexpr bool kUni = decltype(uni)::value;
   for_each_run<2 * TX>(g, [&](int bx0, int by0, int k0, int k1) {
     const int x = bx0 + 2 * lane, y = by0 + threadIdx.y;  // points (x, y) and (x + 1, y)
     const bool active = x < g.nx && y < g.ny;             // nx even: both points or neither
@@ -1235,7 +1244,7 @@ __global__ void __launch_bounds__(TX* TY, 4) k_update_u_pair(Geom g, double* __r
         const int dy0 = 2 * c.x - cur.yl.x - cur.yr.x, dy1 = 2 * c.y - cur.yl.y - cur.yr.y;
         const int dz0 = 2 * c.x - zlv.x - zrv.x, dz1 = 2 * c.y - zlv.y - zrv.y;
         double r0 = cur.r.x, r1 = cur.r.y;
-        if (g.uniform) {
+        if constexpr (kUni) {
           r0 = fma(na0, i32_to_f64_scaled(dx0 + dy0 + dz0, -kp), r0);
           r1 = fma(na0, i32_to_f64_scaled(dx1 + dy1 + dz1, -kp), r1);
         } else {
@@ -1265,6 +1274,9 @@ __global__ void __launch_bounds__(TX* TY, 4) k_update_u_pair(Geom g, double* __r
       if (k + 1 < k1) cur = nxt;
     }
   });
+  };
+  if (g.uniform) sweep(std::true_type{});
+  else sweep(std::false_type{});
   double acc[2] = {f32_to_f64_int(rr), f32_to_f64_int(sR)};
   fold_umax(st, um);
   grid_reduce<2>(acc, partials, &st->tickets[kTkUpd], gridDim.x, blockIdx.x,
