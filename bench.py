@@ -343,9 +343,9 @@ NCU_TRAFFIC_PER_LAUNCH = {
     # tensor-core passes: mean over the six passes of one application; passes 1-3 and 6 captured
     # (17.0, 17.0, 16.8, 34.8 MB), passes 4 and 5 (the same FP16-in / FP16-out shape) taken as pass 1
     "modeprod_tc": (4 * 17.0e6 + 16.8e6 + 34.8e6) / 6,
-    "update": 276.1e6,  # the in-place update the instrumented (one-plan) pass runs
+    "update": 275.0e6,  # the in-place update the instrumented (one-plan) pass runs
     "form_u": 248.0e6,  # the formation before a check (six recorded directions; TPCG_OPT_DEFER_U)
-    "direction": 76.6e6,
+    "direction": 76.2e6,
     "true_residual": 197.4e6,  # a launch that checks (the others return at once)
 }
 
