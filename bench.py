@@ -342,7 +342,7 @@ NCU_TRAFFIC_PER_LAUNCH = {
     # DRAM bytes (read + write) per launch from the ncu captures summarised under profiles/ (cold caches)
     # tensor-core passes: mean over the six passes of one application; passes 1-3 and 6 captured
     # (17.0, 17.0, 16.8, 34.8 MB), passes 4 and 5 (the same FP16-in / FP16-out shape) taken as pass 1
-    "modeprod_tc": (4 * 17.0e6 + 16.8e6 + 34.8e6) / 6,
+    "modeprod_tc": None,  # recaptured for the five-launch sequence (fused pair around G)
     "update": 275.0e6,  # the in-place update the instrumented (one-plan) pass runs
     "form_u": 248.0e6,  # the formation before a check (six recorded directions; TPCG_OPT_DEFER_U)
     "direction": 76.2e6,
@@ -350,7 +350,7 @@ NCU_TRAFFIC_PER_LAUNCH = {
 }
 
 
-def kernel_work(kind, plan_prec, N, dims, iters_total, applies_total, solves, checks_total):
+def kernel_work(kind, plan_prec, N, dims, iters_total, applies_total, solves, checks_total, launches=None):
     """Algorithmic work of one kernel kind over the timed region: (amount, unit, bound, launches that did
     the work).
 
@@ -361,9 +361,11 @@ def kernel_work(kind, plan_prec, N, dims, iters_total, applies_total, solves, ch
     if kind == "modeprod_f64":
         return applies_total * 4.0 * N * (n + q + t + 0.25) / 1e12, "TFLOP", "alu", applies_total * (6 if t > 1 else 4)
     if kind == "modeprod_tc":
-        # per application (3D): passes 1-5 read + write FP16/BF16 (2 + 2 B); the last pass reads its
-        # FP16 input (2 B) and the FP16 copy of R (2 B) and writes Z in FP32 (4 B)
-        npass = 6 if t > 1 else 4
+        # per application (3D): every launch but the last reads + writes FP16/BF16 (2 + 2 B); the last reads
+        # its FP16 input (2 B) and the FP16 copy of R (2 B) and writes Z in FP32 (4 B).  Six launches, or
+        # five when the pair of passes around G runs as one kernel (its intermediate stays on chip):
+        # `launches` is the plan's count per application.
+        npass = launches or (6 if t > 1 else 4)
         per_apply = ((npass - 1) * 4 + 8) * N
         return applies_total * per_apply / 1e9, "GB", "hbm", applies_total * npass
     if kind == "direction":
@@ -494,7 +496,7 @@ def run_ours(args, rank, world, torch):
 
     def roof(kind):
         amount, unit, bound, worked = kernel_work(kind, prec, N, (nx, ny, nz), p_iters, p_applies, args.steps,
-                                                  p_checks)
+                                                  p_checks, plan.precond_launches())
         if amount is None:
             return None
         secs = kstats[kind]["total_ms"] / 1e3

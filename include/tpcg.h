@@ -168,9 +168,18 @@ int tpcg_solve_host_stream(tpcg_plan* plan, int nrhs, const double* const* eta_h
  * iteration and adds one formation pass bound by the FP64 pipe: slower for one
  * solve at a time, faster in total when several plans solve concurrently
  * (e.g. tpcg_solve_batched over several plans).  Ignored for TPCG_FP64.
+ * TPCG_OPT_FUSE_G (mixed forms; 1 = on, the default): the forward and the
+ * backward mode product along the axis where the Hadamard step by G is
+ * applied (Algorithm 7) run as one kernel that keeps the scaled
+ * intermediate in shared memory: one launch and one round trip of the
+ * intermediate through memory fewer per preconditioner application, the same
+ * operations, bitwise the same Z.  0 runs one launch per mode product.  Used
+ * when the axis has at most 128 points, a multiple of 16, and the pass
+ * layouts allow it; ignored otherwise and for TPCG_FP64.
  * Returns TPCG_OK or TPCG_ERR_INVALID_ARG (NULL plan, unknown option, value
  * not 0 or 1).  Do not change an option while a solve of the plan runs.     */
 #define TPCG_OPT_DEFER_U 1
+#define TPCG_OPT_FUSE_G 2
 int tpcg_plan_set_option(tpcg_plan* plan, int option, int value);
 
 /* Many independent solves in one call (the batched form of tpcg_solve).
@@ -303,6 +312,12 @@ int tpcg_server_destroy(tpcg_server* server);
 /* ---- instrumentation ------------------------------------------------------
  * Number of CUDA kernels the plan has launched since it was created.       */
 int tpcg_plan_launch_count(const tpcg_plan* plan, unsigned long long* launches);
+
+/* Tensor-core kernel launches per preconditioner application of a mixed-form
+ * plan under its current options: one per mode product of Algorithm 7 (six
+ * in 3D, four in 2D), one fewer with TPCG_OPT_FUSE_G where it applies; 0 for
+ * TPCG_FP64.  TPCG_OK, or TPCG_ERR_INVALID_ARG for a NULL argument.         */
+int tpcg_plan_precond_launches(const tpcg_plan* plan, int* launches);
 
 /* Per-kernel-kind device time, measured with CUDA events recorded on the
  * plan's stream around every launch between tpcg_profile_begin() and

@@ -41,6 +41,7 @@ TPCG_PRECOND_PINV = 0
 TPCG_PRECOND_NONE = 1
 TPCG_PRECOND_JACOBI = 2
 TPCG_OPT_DEFER_U = 1
+TPCG_OPT_FUSE_G = 2
 TPCG_REQ_BORROW_HOST = 1
 TPCG_REQ_BORROW_DEVICE = 2
 
@@ -106,6 +107,7 @@ _SIGS = {
     "tpcg_plan_set_option": (_I, [_P, _I, _I]),
     "tpcg_plan_eigenpairs": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "tpcg_plan_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
+    "tpcg_plan_precond_launches": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
     "tpcg_profile_begin": (_I, [_P]),
     "tpcg_profile_end": (_I, [_P, ctypes.POINTER(tpcg_kernel_stat), _I, ctypes.POINTER(_I)]),
     "tpcg_residual_norms_noalloc": (_I, [_I, _I, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _P, _P, _P, _P]),
@@ -238,6 +240,12 @@ def tpcg_plan_eigenpairs(plan, axis, length):
 def tpcg_plan_launch_count(plan):
     v = ctypes.c_ulonglong()
     st = lib().tpcg_plan_launch_count(plan, ctypes.byref(v))
+    return st, v.value
+
+
+def tpcg_plan_precond_launches(plan):
+    v = ctypes.c_int()
+    st = lib().tpcg_plan_precond_launches(plan, ctypes.byref(v))
     return st, v.value
 
 
@@ -452,7 +460,8 @@ class Plan:
             raise TpcgError(st, "tpcg_apply_laplacian")
 
     def set_option(self, option, value):
-        """Plan option (TPCG_OPT_DEFER_U: 1 to record U += alpha P and form U before each check)."""
+        """Plan option: TPCG_OPT_DEFER_U (1: record U += alpha P and form U before each check) or
+        TPCG_OPT_FUSE_G (0: one launch per mode product instead of the fused pair around G)."""
         st = tpcg_plan_set_option(self.handle, option, value)
         if st != TPCG_OK:
             raise TpcgError(st, "tpcg_plan_set_option")
@@ -488,6 +497,10 @@ class Plan:
 
     def launch_count(self):
         return tpcg_plan_launch_count(self.handle)[1]
+
+    def precond_launches(self):
+        """Tensor-core launches per preconditioner application (0 for the FP64 form)."""
+        return tpcg_plan_precond_launches(self.handle)[1]
 
     def profile_begin(self):
         tpcg_profile_begin(self.handle)

@@ -36,6 +36,7 @@ void run_precond_cmp(const tpcg_plan* p, const Geom& g, const double* R, double*
 int run_precond_tc(const tpcg_plan* pl, float* Z, SolveState* st);
 int tc_plan_setup(tpcg_plan* pl);
 void tc_plan_release(tpcg_plan* pl);
+int tc_launches_per_apply(const tpcg_plan* pl);
 
 const char* kernel_kind_name(int kind) {
   static const char* names[kKindCount] = {"eta_sum", "init_residual", "direction", "update", "true_residual",
@@ -770,6 +771,10 @@ int tpcg_plan_set_option(tpcg_plan* plan, int option, int value) {
     plan->defer_u = (plan->prec != TPCG_FP64) ? value : 0;  // the FP64 form always updates U in place
     return TPCG_OK;
   }
+  if (option == TPCG_OPT_FUSE_G) {
+    plan->tc_fuse = value;
+    return TPCG_OK;
+  }
   return TPCG_ERR_INVALID_ARG;
 }
 
@@ -862,6 +867,12 @@ int tpcg_plan_eigenpairs(const tpcg_plan* plan, int axis, double* lam, double* V
 int tpcg_plan_launch_count(const tpcg_plan* plan, unsigned long long* launches) {
   if (!plan || !launches) return TPCG_ERR_INVALID_ARG;
   *launches = plan->launch_count;
+  return TPCG_OK;
+}
+
+int tpcg_plan_precond_launches(const tpcg_plan* plan, int* launches) {
+  if (!plan || !launches) return TPCG_ERR_INVALID_ARG;
+  *launches = (plan->prec == TPCG_FP64) ? 0 : tc_launches_per_apply(plan);
   return TPCG_OK;
 }
 

@@ -182,6 +182,7 @@ __host__ __device__ constexpr uint32_t idesc_f16kind(int M, int N, uint32_t fmt)
 struct TcArgs {
   int C, KT, Cout, VR, Np, MB, acc_cols, tmem_cols, NS;
   int rows, B;
+  int B1;  // fused pair: the row split (a, b) of the forward pass, for G
   long long oa, ob, oc;
   int scale, singular;
   int vec;   // 16-element runs of the output are contiguous and 16-byte aligned
@@ -740,20 +741,311 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
   }
 }
 
+// ------------------------------------------------------------------ fused pair of passes
+// In Algorithm 7 the Hadamard step by G sits between the forward and the
+// backward mode product along one axis.  When that axis is the contiguous
+// index of the forward pass's input, both products contract it over the same
+// 128-row tiles, so one kernel runs the two with the scaled intermediate of a
+// tile held in shared memory (it is neither written out nor read back):
+//   stage 1 (form 1): D1[row][c'] = X[row][:] . W1^T[c'][:], times G and the
+//            FP16 range factor, rounded to FP16/BF16 into T[row][c'] (K-major,
+//            128-byte swizzle: the layout TMA gives a loaded operand);
+//   stage 2 (form 2): D2[c][row] = W2^T[c][:] . T[row][:], stored in the
+//            backward pass's output layout.
+// Stage 1 issues the MMAs of the forward pass and stage 2 those of the
+// backward pass, in the same order, and the intermediate takes the same G
+// product and the same rounding: the output is bitwise that of the two passes.
+// Warps: 0 TMA, 1 MMA (stage 1 of tile i+1 is issued before stage 2 of tile
+// i), 2..17 epilogue (stage 1 then stage 2 of each tile).  TMEM: D1 and D2
+// double-buffered, 4 x 128 columns.  One T buffer: the epilogue writes T for
+// tile i+1 only after it has seen stage 2 of tile i complete.
+constexpr int kPairEpi = 16;
+constexpr int kPairThreads = (2 + kPairEpi) * 32;
+constexpr int kTBytes = kTileRows * 128;  // one 64-column K tile of T
+
+template <class InT>
+__global__ void __launch_bounds__(kPairThreads, 1)
+    k_modeprod_pair(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW1,
+                    const __grid_constant__ CUtensorMap tmW2, const __grid_constant__ CUtensorMap tmO, TcArgs a) {
+  if (a.st && a.st->done) return;
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* sm = smem_raw + (base - raw);
+  const int KT = a.KT, NS = a.NS;
+  const uint32_t sW1 = base;
+  const uint32_t sW2 = sW1 + (uint32_t)KT * a.VR * 128u;  // VR % 8 == 0: 1024-aligned
+  const uint32_t sT = sW2 + (uint32_t)KT * 128u * 128u;
+  const uint32_t sD = sT + (uint32_t)KT * kTBytes;
+  const uint32_t sO = sD + (uint32_t)NS * kStageBytes;
+  constexpr uint32_t kOBytes = 32u * 16u * (uint32_t)sizeof(InT);
+  uint8_t* barp = sm + (sO - base) + (size_t)kPairEpi * 2 * kOBytes;
+  const uint32_t bars = smem_u32(barp);
+  auto full = [&](int s) { return bars + 8u * s; };
+  auto empty = [&](int s) { return bars + 8u * (NS + s); };
+  auto d1full = [&](int b) { return bars + 8u * (2 * NS + b); };
+  auto d1empty = [&](int b) { return bars + 8u * (2 * NS + 2 + b); };
+  auto d2full = [&](int b) { return bars + 8u * (2 * NS + 4 + b); };
+  auto d2empty = [&](int b) { return bars + 8u * (2 * NS + 6 + b); };
+  const uint32_t tready = bars + 8u * (2 * NS + 8);
+  const uint32_t vbar = bars + 8u * (2 * NS + 9);
+  const uint32_t drain = bars + 8u * (2 * NS + 10);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(barp + 8 * (2 * NS + 11));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+  const Abort ab{abort_flag, a.err, a.st};
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(d1full(b), 1);
+      mbar_init(d1empty(b), kPairEpi * 32);
+      mbar_init(d2full(b), 1);
+      mbar_init(d2empty(b), kPairEpi * 32);
+    }
+    mbar_init(tready, kPairEpi * 32);
+    mbar_init(vbar, 1);
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                 "r"(512u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+  const int ntiles = (a.rows + kTileRows - 1) / kTileRows;
+  const int nmine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer: both eigenbases once, then the K tiles of every row tile
+    mbar_expect_tx(vbar, (uint32_t)KT * (uint32_t)(a.VR + 128) * 128u);
+    for (int kt = 0; kt < KT; ++kt) tma_load_2d(sW1 + (uint32_t)kt * a.VR * 128u, &tmW1, kt * kKTile, 0, vbar);
+    for (int kt = 0; kt < KT; ++kt) tma_load_2d(sW2 + (uint32_t)kt * 128u * 128u, &tmW2, kt * kKTile, 0, vbar);
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    int it = 0;
+    for (int i = 0; i < nmine && !*abort_flag; ++i) {
+      const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+      for (int kt = 0; kt < KT; ++kt, ++it) {
+        const int s = it % NS;
+        if (!wait_bounded(empty(s), (uint32_t)(((it / NS) & 1) ^ 1), ab)) break;
+        mbar_expect_tx(full(s), kStageBytes);
+        tma_load_2d(sD + (uint32_t)s * kStageBytes, &tmX, kt * kKTile, tile * kTileRows, full(s));
+      }
+    }
+    if (*abort_flag) {  // every issued load completes before the CTA may exit
+      for (int j = (it > NS ? it - NS : 0); j < it; ++j) {
+        const unsigned long long t0 = gtimer();
+        while (!mbar_try_wait(full(j % NS), (uint32_t)((j / NS) & 1)) && gtimer() - t0 < kWaitLimitNs) {
+        }
+      }
+      const unsigned long long t0 = gtimer();
+      while (!mbar_try_wait(vbar, 0) && gtimer() - t0 < kWaitLimitNs) {
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    constexpr uint32_t fmt = std::is_same<InT, __half>::value ? 0u : 1u;
+    const uint32_t idesc1 = idesc_f16kind(128, a.Np, fmt), idesc2 = idesc_f16kind(128, 128, fmt);
+    const unsigned long long dX0 = sw128_desc(sD), dW1 = sw128_desc(sW1), dW2 = sw128_desc(sW2), dT = sw128_desc(sT);
+    const uint32_t w1kt = (uint32_t)(a.VR * 128) >> 4, w2kt = (uint32_t)(128 * 128) >> 4,
+                   tkt = (uint32_t)kTBytes >> 4;
+    bool ok = wait_bounded(vbar, 0, ab);
+    int it = 0;
+    auto stage1 = [&](int i) {  // forward product of tile i into D1[i & 1]
+      const int b = i & 1;
+      if (!wait_bounded(d1empty(b), (uint32_t)(((i >> 1) & 1) ^ 1), ab)) return false;
+      tc_fence_after();
+      const uint32_t dacc = tmem + (uint32_t)(b * 128);
+      for (int kt = 0; kt < KT; ++kt, ++it) {
+        const int s = it % NS;
+        if (!wait_bounded(full(s), (uint32_t)((it / NS) & 1), ab)) return false;
+        tc_fence_after();
+        const unsigned long long xd = dX0 + (uint32_t)s * (uint32_t)(kStageBytes >> 4);
+        const unsigned long long wd = dW1 + (uint32_t)kt * w1kt;
+        const int nk = min(4, (a.C - kt * kKTile + 15) >> 4);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          if (kk < nk) tc_mma(dacc, xd + 2u * kk, wd + 2u * kk, idesc1, (kt > 0 || kk > 0) ? 1u : 0u);
+        tc_commit(empty(s));
+      }
+      tc_commit(d1full(b));
+      return true;
+    };
+    auto stage2 = [&](int i) {  // backward product of tile i (T in shared memory) into D2[i & 1]
+      const int b = i & 1;
+      if (!wait_bounded(tready, (uint32_t)(i & 1), ab)) return false;
+      if (!wait_bounded(d2empty(b), (uint32_t)(((i >> 1) & 1) ^ 1), ab)) return false;
+      tc_fence_after();
+      const uint32_t dacc = tmem + 256u + (uint32_t)(b * 128);
+      for (int kt = 0; kt < KT; ++kt) {
+        const unsigned long long wd = dW2 + (uint32_t)kt * w2kt, td = dT + (uint32_t)kt * tkt;
+        const int nk = min(4, (a.C - kt * kKTile + 15) >> 4);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          if (kk < nk) tc_mma(dacc, wd + 2u * kk, td + 2u * kk, idesc2, (kt > 0 || kk > 0) ? 1u : 0u);
+      }
+      tc_commit(d2full(b));
+      return true;
+    };
+    if (ok && nmine > 0) ok = stage1(0);
+    for (int i = 0; ok && i < nmine; ++i) {
+      if (i + 1 < nmine && !(ok = stage1(i + 1))) break;
+      ok = stage2(i);
+    }
+    tc_commit(drain);  // every MMA this thread issued is complete once `drain` fires
+    const unsigned long long t0 = gtimer();
+    while (!mbar_try_wait(drain, 0) && gtimer() - t0 < kWaitLimitNs) {
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue: four warps per TMEM lane quadrant, warp h of a quadrant taking the 16-column
+    // chunks h*16 + 64*j
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    const int trow = q * 32 + lane;
+    const uint32_t sOw = sO + (uint32_t)(warp - 2) * 2u * kOBytes;
+    int ocnt = 0;
+    auto emit = [&](const float (&v)[16], int x0, int x1, int x2) {  // as in k_modeprod_tc, form 2
+      const uint32_t buf = sOw + (uint32_t)(ocnt & 1) * kOBytes;
+      if (ocnt >= 2) {
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        __syncwarp();
+      }
+      stage_row<InT>(buf, lane, v);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        tma_store_3d(&tmO, buf, x0, x1, x2);
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      }
+      ++ocnt;
+    };
+    const int J1 = (a.Np - h * 16 + 63) / 64;  // stage-1 chunks of this warp (at most 2)
+    for (int i = 0; i < nmine; ++i) {
+      const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+      const int b = i & 1;
+      const int row0 = tile * kTileRows;
+      // stage 1: T[row][c'] = round(D1[row][c'] * G(row, c') * 2^-sG)
+      if (!__all_sync(0xffffffffu, wait_bounded(d1full(b), (uint32_t)((i >> 1) & 1), ab))) break;
+      tc_fence_after();
+      {
+        const uint32_t tacc = tmem + (uint32_t)(b * 128) + ((uint32_t)(q * 32) << 16);
+        const int r = row0 + trow;
+        const bool valid = r < a.rows;
+        const int ia = valid ? r / a.B1 : 0;
+        const int ib = valid ? r - ia * a.B1 : 0;
+        const float sab = valid ? a.lamA[ia] + a.lamB[ib] : 0.0f;
+        const bool null_row = a.singular && ia == 0 && ib == 0;
+        uint32_t t0[16], t1[16];
+        if (J1 > 0) tc_ld16_issue(tacc + (uint32_t)(h * 16), t0);
+        if (J1 > 1) tc_ld16_issue(tacc + (uint32_t)(h * 16 + 64), t1);
+        if (J1 > 0) tc_ld16_wait(t0);
+        if (J1 > 1) tc_ld16_wait(t1);
+        tc_fence_before();
+        mbar_arrive(d1empty(b));
+        auto put = [&](int c0, const uint32_t (&t)[16]) {
+          float v[16];
+#pragma unroll
+          for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(t[k]);
+          const float4* lc4 = reinterpret_cast<const float4*>(a.lamC + c0);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float4 l = __ldg(lc4 + k);
+            v[4 * k + 0] *= rcp_approx(sab + l.x) * a.gscale;
+            v[4 * k + 1] *= rcp_approx(sab + l.y) * a.gscale;
+            v[4 * k + 2] *= rcp_approx(sab + l.z) * a.gscale;
+            v[4 * k + 3] *= rcp_approx(sab + l.w) * a.gscale;
+          }
+          if (null_row && c0 == 0) v[0] = 0.0f;
+          uint32_t pk[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            if constexpr (std::is_same<InT, __half>::value) {
+              __half2 h2 = __floats2half2_rn(v[2 * k], v[2 * k + 1]);
+              pk[k] = valid ? *reinterpret_cast<uint32_t*>(&h2) : 0u;
+            } else {
+              __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+              pk[k] = valid ? *reinterpret_cast<uint32_t*>(&h2) : 0u;
+            }
+          }
+          // 128-byte swizzle: 16-byte piece p of row trow sits at piece p ^ (trow % 8)
+          const uint32_t rowa = sT + (uint32_t)(c0 >> 6) * (uint32_t)kTBytes + (uint32_t)trow * 128u;
+          const uint32_t p0 = (uint32_t)((c0 & 63) >> 3);
+#pragma unroll
+          for (int k = 0; k < 2; ++k)
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(rowa + (((p0 + k) ^ (uint32_t)(trow & 7)) << 4)),
+                         "r"(pk[4 * k]), "r"(pk[4 * k + 1]), "r"(pk[4 * k + 2]), "r"(pk[4 * k + 3])
+                         : "memory");
+        };
+        if (J1 > 0) put(h * 16, t0);
+        if (J1 > 1) put(h * 16 + 64, t1);
+        // generic-proxy writes of T -> the tensor core's (async-proxy) reads
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(tready);
+      }
+      // stage 2: thread = output index c = q*32 + lane, chunk = 16 consecutive rows
+      if (!__all_sync(0xffffffffu, wait_bounded(d2full(b), (uint32_t)((i >> 1) & 1), ab))) break;
+      tc_fence_after();
+      {
+        const uint32_t tacc = tmem + 256u + (uint32_t)(b * 128) + ((uint32_t)(q * 32) << 16);
+        uint32_t t0[16], t1[16];
+        tc_ld16_issue(tacc + (uint32_t)(h * 16), t0);
+        tc_ld16_issue(tacc + (uint32_t)(h * 16 + 64), t1);
+        tc_ld16_wait(t0);
+        tc_ld16_wait(t1);
+        tc_fence_before();
+        mbar_arrive(d2empty(b));
+        const int cb = q * 32;
+        auto out = [&](int c0, const uint32_t (&t)[16]) {
+          const int r0 = row0 + c0;
+          if (r0 >= a.rows || cb >= a.Cout) return;  // warp-uniform (rows % 16 == 0)
+          float v[16];
+#pragma unroll
+          for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(t[k]);
+          const int ia = r0 / a.B, ib = r0 - ia * a.B;
+          if (a.tperm) emit(v, ib, ia, cb);
+          else emit(v, ib, cb, ia);
+        };
+        out(h * 16, t0);
+        out(h * 16 + 64, t1);
+      }
+    }
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  }
+
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+  }
+}
+
 // ------------------------------------------------------------------ host side
 struct TcStage {
   CUtensorMap tmX;
   CUtensorMap tmW;
   CUtensorMap tmR;  // R~ (16-bit) for the last pass of a solve; a copy of tmX when unused
   CUtensorMap tmO;  // the pass's output for TMA stores (args.tstore); a copy of tmX when unused
+  CUtensorMap tmW2; // fused pair: the backward pass's eigenbasis; a copy of tmW otherwise
   int form;
+  int pair;  // 1: k_modeprod_pair runs this pass and the next one
   TcArgs args;
+  void* out;  // output buffer of a pass that is not the last
   int grid;
   size_t smem;
 };
 
 struct TcPlan {
-  std::vector<TcStage> stages;
+  std::vector<TcStage> stages;  // one launch per pass of Algorithm 7
+  std::vector<TcStage> fused;   // the same with the pass pair around G in one launch (empty when not possible)
   bool fp16 = false;
 };
 
@@ -856,6 +1148,10 @@ int set_all_smem_attrs() {
   bad |= set_smem_attr<2, InT, InT, false>(kMaxSmem);
   bad |= set_smem_attr<1, InT, float, false>(kMaxSmem);
   bad |= set_smem_attr<1, InT, float, true>(kMaxSmem);
+  bad |= cudaFuncSetAttribute(k_modeprod_pair<InT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) ==
+                 cudaSuccess
+             ? 0
+             : -1;
   return bad;
 }
 
@@ -875,8 +1171,25 @@ void launch(const TcStage& s, const TcArgs& a, cudaStream_t stream) {
 }
 
 template <class InT>
+void launch_pair(const TcStage& s, const TcArgs& a, cudaStream_t stream) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)s.grid);
+  cfg.blockDim = dim3(kPairThreads);
+  cfg.dynamicSmemBytes = s.smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_modeprod_pair<InT>, s.tmX, s.tmW, s.tmW2, s.tmO, a);
+}
+
+template <class InT>
 void launch_stage(const TcStage& s, const TcArgs& a, bool last, bool final_pcg, cudaStream_t stream) {
-  if (!last) {
+  if (s.pair) {
+    launch_pair<InT>(s, a, stream);
+  } else if (!last) {
     if (s.form == 1) launch<1, InT, InT, false>(s, a, stream);
     else launch<2, InT, InT, false>(s, a, stream);
   } else if (final_pcg) {
@@ -921,9 +1234,10 @@ int tc_plan_setup(tpcg_plan* p) {
     sG = std::max(0, (int)std::ceil(std::log2(bound / 16384.0)));
   }
   const int ns = (int)p->stages.size();
-  for (int si = 0; si < ns; ++si) {
+  // Launch parameters of pass si reading xin and writing out_addr (the plan's Z for the last pass).
+  auto build_one = [&](int si, const void* xin, void* out_addr, TcStage& st) -> int {
     const StageParams& sp = p->stages[si];
-    TcStage st{};
+    st = TcStage{};
     // form 1 (thread = row) when the output index is contiguous, form 2 (thread = output index)
     // when consecutive rows are: either way a thread owns 16 contiguous outputs
     st.form = (sp.oc == 1) ? 1 : 2;
@@ -941,14 +1255,12 @@ int tc_plan_setup(tpcg_plan* p) {
     a.tmem_cols = cols;
     a.rows = sp.A * sp.B;
     a.B = sp.B;
+    a.B1 = sp.B;
     a.oa = sp.oa;
     a.ob = sp.ob;
     a.oc = sp.oc;
     a.scale = sp.scale;
-    if (st.form == 2 && (sp.scale || sp.final_stage)) {  // scaling and PCG sums live in form-1 epilogues
-      delete tp;
-      return TPCG_ERR_UNSUPPORTED;
-    }
+    if (st.form == 2 && (sp.scale || sp.final_stage)) return TPCG_ERR_UNSUPPORTED;  // form-1 epilogues only
     if (st.form == 1)
       a.vec = (sp.final_stage ? (sp.oa % 4 == 0 && sp.ob % 4 == 0) : (sp.oa % 8 == 0 && sp.ob % 8 == 0)) ? 1 : 0;
     else
@@ -965,15 +1277,11 @@ int tc_plan_setup(tpcg_plan* p) {
     a.shift_src = tp->fp16 ? &p->d_state->lp_shift_applied : nullptr;
     const size_t vbytes = (size_t)a.KT * a.VR * 128;
     size_t fixed = 1024 + vbytes + 512;  // alignment, eigenbasis, barriers and the TMEM address
-    if (a.tmem_cols > 512 || a.VR > 256 || fixed + 2 * kStageBytes > (size_t)kMaxSmem) {
-      delete tp;
-      return TPCG_ERR_UNSUPPORTED;
-    }
-    // outputs by TMA stores through per-warp staging when the layout allows (the last pass writes Z,
-    // FP32, to the plan's Z buffer)
+    if (a.tmem_cols > 512 || a.VR > 256 || fixed + 2 * kStageBytes > (size_t)kMaxSmem) return TPCG_ERR_UNSUPPORTED;
+    // outputs by TMA stores through per-warp staging when the layout allows
     const bool last = sp.final_stage != 0;
     const int esz = last ? 4 : 2;
-    void* out_addr = last ? p->d_Z : p->d_T[si & 1];
+    st.out = out_addr;
     st.tmO = st.tmX;
     a.tstore = (encode_out(&st.tmO, out_addr, esz, tp->fp16, st.form, a, &a.tperm) == 0) ? 1 : 0;
     // staging bytes: two [32][16] boxes per epilogue warp (sixteen warps; eight in the last pass of a solve)
@@ -1000,20 +1308,87 @@ int tc_plan_setup(tpcg_plan* p) {
     st.smem = fixed + (size_t)a.NS * kStageBytes;
     const int ntiles = (a.rows + kTileRows - 1) / kTileRows;
     st.grid = std::max(1, std::min(ntiles, p->num_sms));
-    // operands: stage si reads the output of stage si-1 (R in BF16 for the first)
-    const void* xin = (si == 0) ? p->d_Rlp : p->d_T[(si - 1) & 1];
     const int wpitch = p->pitch16[sp.axis];
     if (encode_2d(&st.tmX, xin, sp.C, (long long)a.rows, sp.in_pitch, kKTile, kTileRows, tp->fp16) ||
-        encode_2d(&st.tmW, p->d_Wt16[sp.axis][sp.dir], sp.C, sp.Cout, wpitch, kKTile, a.VR, tp->fp16)) {
-      delete tp;
+        encode_2d(&st.tmW, p->d_Wt16[sp.axis][sp.dir], sp.C, sp.Cout, wpitch, kKTile, a.VR, tp->fp16))
       return TPCG_ERR_CUDA;
-    }
+    st.tmW2 = st.tmW;
     st.tmR = st.tmX;
-    if (a.rtma && encode_r(&st.tmR, p->d_Rlp, sp.Cout, (long long)a.rows, a.rpitch, tp->fp16)) {
-      delete tp;
+    if (a.rtma && encode_r(&st.tmR, p->d_Rlp, sp.Cout, (long long)a.rows, a.rpitch, tp->fp16)) return TPCG_ERR_CUDA;
+    return TPCG_OK;
+  };
+  // Passes si (forward, with G, form 1) and si + 1 (backward along the same axis, form 2) as one
+  // k_modeprod_pair launch; TPCG_ERR_UNSUPPORTED when the pair does not fit its layout rules.
+  auto build_pair = [&](int si, const void* xin, void* out_addr, TcStage& st) -> int {
+    if (si + 1 >= ns) return TPCG_ERR_UNSUPPORTED;
+    const StageParams& s1 = p->stages[si];
+    const StageParams& s2 = p->stages[si + 1];
+    const bool shape_ok = s1.scale && !s1.final_stage && s1.oc == 1 && !s2.final_stage && s2.oc != 1 &&
+                          s1.axis == s2.axis && s1.dir != s2.dir && s1.C == s1.Cout && s2.C == s1.C &&
+                          s2.Cout == s1.C && s1.C % 16 == 0 && s1.C <= 128 && s1.A * s1.B == s2.A * s2.B &&
+                          (s1.B == 1 || s1.oa == (long long)s1.B * s1.ob) &&
+                          ((s1.B == 1) ? s1.oa : s1.ob) == (long long)s2.in_pitch;  // row r of s1's output = row r of s2's input
+    if (!shape_ok) return TPCG_ERR_UNSUPPORTED;
+    TcStage f{}, b{};
+    int rc;
+    if ((rc = build_one(si, xin, out_addr, f)) || (rc = build_one(si + 1, xin, out_addr, b))) return rc;
+    if (f.form != 1 || b.form != 2 || !b.args.tstore || b.args.MB != 1 || b.args.B % 16 != 0)
+      return TPCG_ERR_UNSUPPORTED;
+    st = b;
+    st.pair = 1;
+    st.tmX = f.tmX;
+    st.tmW = f.tmW;  // W1: the forward eigenbasis, rows padded to a multiple of 8
+    if (encode_2d(&st.tmW2, p->d_Wt16[s2.axis][s2.dir], s2.C, s2.Cout, p->pitch16[s2.axis], kKTile, 128, tp->fp16))
       return TPCG_ERR_CUDA;
+    TcArgs& a = st.args;
+    a.Np = f.args.Np;
+    a.VR = f.args.VR;
+    a.B1 = s1.B;
+    a.scale = 1;
+    a.lamA = f.args.lamA;
+    a.lamB = f.args.lamB;
+    a.lamC = f.args.lamC;
+    // alignment, both eigenbases, T, the output staging (two FP16/BF16 [32][16] boxes per epilogue warp),
+    // barriers and the TMEM address
+    const size_t fixed = 1024 + (size_t)a.KT * (a.VR + 128) * 128 + (size_t)a.KT * kTBytes +
+                         (size_t)kPairEpi * 2 * 32 * 16 * 2 + 512;
+    if (fixed + 2 * (size_t)kStageBytes > (size_t)kMaxSmem) return TPCG_ERR_UNSUPPORTED;
+    a.NS = (int)std::min<size_t>(8, (kMaxSmem - fixed) / kStageBytes);
+    st.smem = fixed + (size_t)a.NS * kStageBytes;
+    return TPCG_OK;
+  };
+  int rc = TPCG_OK;
+  for (int si = 0; si < ns && rc == TPCG_OK; ++si) {
+    TcStage st{};
+    const bool last = (si == ns - 1);
+    rc = build_one(si, (si == 0) ? p->d_Rlp : p->d_T[(si - 1) & 1], last ? p->d_Z : p->d_T[si & 1], st);
+    if (rc == TPCG_OK) tp->stages.push_back(st);
+  }
+  // the fused launch sequence: launch li reads the previous launch's output and writes d_T[li % 2]
+  int sf = -1;
+  for (int si = 0; si + 1 < ns && sf < 0; ++si)
+    if (p->stages[si].scale) sf = si;
+  if (rc == TPCG_OK && sf >= 0) {
+    const void* prev = p->d_Rlp;
+    for (int si = 0, li = 0; si < ns; ++li) {
+      const bool pair = (si == sf);
+      const bool last = (si + (pair ? 1 : 0) == ns - 1);
+      void* outp = last ? p->d_Z : p->d_T[li & 1];
+      TcStage st{};
+      const int r = pair ? build_pair(si, prev, outp, st) : build_one(si, prev, outp, st);
+      if (r != TPCG_OK) {  // keep the one-launch-per-pass sequence only
+        tp->fused.clear();
+        if (r != TPCG_ERR_UNSUPPORTED) rc = r;
+        break;
+      }
+      tp->fused.push_back(st);
+      prev = outp;
+      si += pair ? 2 : 1;
     }
-    tp->stages.push_back(st);
+  }
+  if (rc != TPCG_OK) {
+    delete tp;
+    return rc;
   }
   const int bad = tp->fp16 ? set_all_smem_attrs<__half>() : set_all_smem_attrs<__nv_bfloat16>();
   if (bad) {
@@ -1022,6 +1397,12 @@ int tc_plan_setup(tpcg_plan* p) {
   }
   p->tc_state = tp;
   return TPCG_OK;
+}
+
+int tc_launches_per_apply(const tpcg_plan* p) {
+  const TcPlan* tp = reinterpret_cast<const TcPlan*>(p->tc_state);
+  if (!tp) return 0;
+  return (int)((p->tc_fuse && !tp->fused.empty()) ? tp->fused.size() : tp->stages.size());
 }
 
 void tc_plan_release(tpcg_plan* p) {
@@ -1034,12 +1415,13 @@ void tc_plan_release(tpcg_plan* p) {
 int run_precond_tc(const tpcg_plan* p, float* Z, SolveState* st) {
   const TcPlan* tp = reinterpret_cast<const TcPlan*>(p->tc_state);
   if (!tp) return TPCG_ERR_UNSUPPORTED;
-  const int ns = (int)tp->stages.size();
+  const std::vector<TcStage>& seq = (p->tc_fuse && !tp->fused.empty()) ? tp->fused : tp->stages;
+  const int ns = (int)seq.size();
   for (int si = 0; si < ns; ++si) {
-    const TcStage& s = tp->stages[si];
+    const TcStage& s = seq[si];
     TcArgs a = s.args;
     const bool last = (si == ns - 1);
-    a.out = last ? (void*)Z : p->d_T[si & 1];
+    a.out = last ? (void*)Z : s.out;
     if (last && (void*)Z != p->d_Z) a.tstore = 0;  // the output map names the plan's Z buffer
     a.st = st;
     a.Rt = reinterpret_cast<const uint16_t*>(p->d_Rlp);

@@ -158,5 +158,6 @@ struct tpcg_plan {
   double jac_invd[27] = {};
   int stream_blocks = 0;    // streaming kernels
   int defer_u = 0;          // mixed forms: TPCG_OPT_DEFER_U (U += alpha P recorded, applied by k_form_u)
+  int tc_fuse = 1;          // mixed forms: TPCG_OPT_FUSE_G (the two passes around G in one launch)
   int last_iters = 0;      // iterations of the plan's previous converged solve (first chunk of the next)
 };

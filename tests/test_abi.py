@@ -76,3 +76,5 @@ def test_new_entry_points_validate_before_any_cuda_call(libpath):
     assert b.tpcg_efield(None, 0, None, 0, 0, 0) == b.TPCG_ERR_INVALID_ARG
     assert b.tpcg_solve_host_stream(None, [], [], 1e-10, 10, 0)[0] == b.TPCG_ERR_INVALID_ARG
     assert b.tpcg_plan_set_option(None, b.TPCG_OPT_DEFER_U, 1) == b.TPCG_ERR_INVALID_ARG
+    assert b.tpcg_plan_set_option(None, b.TPCG_OPT_FUSE_G, 0) == b.TPCG_ERR_INVALID_ARG
+    assert b.tpcg_plan_precond_launches(None)[0] == b.TPCG_ERR_INVALID_ARG

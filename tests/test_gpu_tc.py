@@ -373,6 +373,63 @@ def test_deferred_u_is_bitwise_the_in_place_update(prec, case):
     assert i0["iters"] == i1["iters"] and i0["rel_res_true"] == i1["rel_res_true"]
 
 
+FUSE_CASES = [
+    ((16, 16, 16), ("P", "N", "P")),
+    ((64, 64, 32), ("P", "P", "N")),
+    ((9, 16, 48), ("P", "N", "D")),       # 144 rows: a ragged last tile; 48 columns: one partial K tile
+    ((96, 160, 96), ("N", "D", "P")),
+    ((64, 64, 1), ("D", "D", "D")),       # 2D: the pair runs along y
+    ((48, 80, 1), ("P", "N", "P")),
+    ((256, 256, 128), ("P", "P", "N")),
+    ((37, 9, 5), ("N", "N", "N")),        # not fusable: the option changes nothing
+]
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("shape,bcs", FUSE_CASES)
+def test_fused_pair_is_bitwise_the_two_passes(shape, bcs, prec):
+    """TPCG_OPT_FUSE_G runs the forward and the backward mode product around G in one kernel: the same
+    MMAs in the same order and the same rounding of the intermediate, so Z is bitwise that of one launch
+    per pass."""
+    from paper_2501_03377_gb300 import binding as b
+
+    nx, ny, nz = shape
+    r = synth.random_field(nx, ny, nz, seed=91)
+    rd = _dev(r)
+    outs = []
+    for fuse in (0, 1):
+        pl = _plan(nx, ny, nz, bcs, prec)
+        pl.set_option(b.TPCG_OPT_FUSE_G, fuse)
+        zd = torch.full_like(rd, float("nan"))
+        pl.precond(rd, zd)
+        torch.cuda.synchronize()
+        outs.append(zd.cpu().numpy())
+    assert np.isfinite(outs[1]).all()
+    assert np.array_equal(outs[0], outs[1])
+    fusable = shape != (37, 9, 5)
+    full = 6 if nz > 1 else 4
+    assert pl.precond_launches() == full - (1 if fusable else 0)
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_fused_pair_solve_is_bitwise(prec):
+    from paper_2501_03377_gb300 import binding as b
+
+    nx, ny, nz, bcs = 64, 48, 32, ("P", "P", "N")
+    eta = synth.defect_rhs(nx, ny, nz, bcs, 12, 1.5, seed=92)
+    ed = _dev(eta)
+    outs = []
+    for fuse in (0, 1):
+        pl = _plan(nx, ny, nz, bcs, prec)
+        pl.set_option(b.TPCG_OPT_FUSE_G, fuse)
+        ud = torch.zeros_like(ed)
+        st, info = pl.solve(ed, ud, tol=1e-10, maxit=60, zero_guess=True)
+        assert st == 0
+        outs.append((ud.cpu().numpy(), info["iters"], info["rel_res_true"]))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1:] == outs[1][1:]
+
+
 def test_plan_option_rejects_bad_values():
     from paper_2501_03377_gb300 import binding as b
 
@@ -380,3 +437,5 @@ def test_plan_option_rejects_bad_values():
     assert b.tpcg_plan_set_option(pl.handle, b.TPCG_OPT_DEFER_U, 2) == b.TPCG_ERR_INVALID_ARG
     assert b.tpcg_plan_set_option(pl.handle, 99, 1) == b.TPCG_ERR_INVALID_ARG
     assert b.tpcg_plan_set_option(pl.handle, b.TPCG_OPT_DEFER_U, 1) == b.TPCG_OK
+    assert b.tpcg_plan_set_option(pl.handle, b.TPCG_OPT_FUSE_G, 2) == b.TPCG_ERR_INVALID_ARG
+    assert b.tpcg_plan_set_option(pl.handle, b.TPCG_OPT_FUSE_G, 0) == b.TPCG_OK
