@@ -756,9 +756,11 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
 // backward pass, in the same order, and the intermediate takes the same G
 // product and the same rounding: the output is bitwise that of the two passes.
 // Warps: 0 TMA, 1 MMA (stage 1 of tile i+1 is issued before stage 2 of tile
-// i), 2..17 epilogue (stage 1 then stage 2 of each tile).  TMEM: D1 and D2
-// double-buffered, 4 x 128 columns.  One T buffer: the epilogue writes T for
-// tile i+1 only after it has seen stage 2 of tile i complete.
+// i), 2..17 epilogue, software-pipelined: stage 1 of tile i, then stage 2 of
+// tile i-1, so that the tensor core runs stage 2 of tile i-1 while the
+// epilogue scales tile i.  TMEM: D1 and D2 double-buffered, 4 x 128 columns;
+// T double-buffered: the epilogue writes T for tile i after it has seen stage
+// 2 of tile i-2 complete.
 constexpr int kPairEpi = 16;
 constexpr int kPairThreads = (2 + kPairEpi) * 32;
 constexpr int kTBytes = kTileRows * 128;  // one 64-column K tile of T
@@ -776,8 +778,8 @@ __global__ void __launch_bounds__(kPairThreads, 1)
   const int KT = a.KT, NS = a.NS;
   const uint32_t sW1 = base;
   const uint32_t sW2 = sW1 + (uint32_t)KT * a.VR * 128u;  // VR % 8 == 0: 1024-aligned
-  const uint32_t sT = sW2 + (uint32_t)KT * 128u * 128u;
-  const uint32_t sD = sT + (uint32_t)KT * kTBytes;
+  const uint32_t sT = sW2 + (uint32_t)KT * 128u * 128u;  // two buffers of KT K tiles
+  const uint32_t sD = sT + 2u * (uint32_t)KT * kTBytes;
   const uint32_t sO = sD + (uint32_t)NS * kStageBytes;
   constexpr uint32_t kOBytes = 32u * 16u * (uint32_t)sizeof(InT);
   uint8_t* barp = sm + (sO - base) + (size_t)kPairEpi * 2 * kOBytes;
@@ -788,10 +790,10 @@ __global__ void __launch_bounds__(kPairThreads, 1)
   auto d1empty = [&](int b) { return bars + 8u * (2 * NS + 2 + b); };
   auto d2full = [&](int b) { return bars + 8u * (2 * NS + 4 + b); };
   auto d2empty = [&](int b) { return bars + 8u * (2 * NS + 6 + b); };
-  const uint32_t tready = bars + 8u * (2 * NS + 8);
-  const uint32_t vbar = bars + 8u * (2 * NS + 9);
-  const uint32_t drain = bars + 8u * (2 * NS + 10);
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(barp + 8 * (2 * NS + 11));
+  auto tready = [&](int b) { return bars + 8u * (2 * NS + 8 + b); };
+  const uint32_t vbar = bars + 8u * (2 * NS + 10);
+  const uint32_t drain = bars + 8u * (2 * NS + 11);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(barp + 8 * (2 * NS + 12));
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
   const Abort ab{abort_flag, a.err, a.st};
 
@@ -806,8 +808,8 @@ __global__ void __launch_bounds__(kPairThreads, 1)
       mbar_init(d1empty(b), kPairEpi * 32);
       mbar_init(d2full(b), 1);
       mbar_init(d2empty(b), kPairEpi * 32);
+      mbar_init(tready(b), kPairEpi * 32);
     }
-    mbar_init(tready, kPairEpi * 32);
     mbar_init(vbar, 1);
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -883,12 +885,12 @@ __global__ void __launch_bounds__(kPairThreads, 1)
     };
     auto stage2 = [&](int i) {  // backward product of tile i (T in shared memory) into D2[i & 1]
       const int b = i & 1;
-      if (!wait_bounded(tready, (uint32_t)(i & 1), ab)) return false;
+      if (!wait_bounded(tready(b), (uint32_t)((i >> 1) & 1), ab)) return false;
       if (!wait_bounded(d2empty(b), (uint32_t)(((i >> 1) & 1) ^ 1), ab)) return false;
       tc_fence_after();
       const uint32_t dacc = tmem + 256u + (uint32_t)(b * 128);
       for (int kt = 0; kt < KT; ++kt) {
-        const unsigned long long wd = dW2 + (uint32_t)kt * w2kt, td = dT + (uint32_t)kt * tkt;
+        const unsigned long long wd = dW2 + (uint32_t)kt * w2kt, td = dT + (uint32_t)(b * KT + kt) * tkt;
         const int nk = min(4, (a.C - kt * kKTile + 15) >> 4);
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk)
@@ -929,95 +931,104 @@ __global__ void __launch_bounds__(kPairThreads, 1)
       ++ocnt;
     };
     const int J1 = (a.Np - h * 16 + 63) / 64;  // stage-1 chunks of this warp (at most 2)
-    for (int i = 0; i < nmine; ++i) {
+    // stage 1 of tile i: T[b][row][c'] = round(D1[row][c'] * G(row, c') * 2^-sG)
+    auto epi1 = [&](int i) {
+      const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+      const int b = i & 1;
+      const int r = tile * kTileRows + trow;
+      const bool valid = r < a.rows;
+      const int ia = valid ? r / a.B1 : 0;
+      const int ib = valid ? r - ia * a.B1 : 0;
+      const float sab = valid ? a.lamA[ia] + a.lamB[ib] : 0.0f;
+      const bool null_row = a.singular && ia == 0 && ib == 0;
+      if (!__all_sync(0xffffffffu, wait_bounded(d1full(b), (uint32_t)((i >> 1) & 1), ab))) return false;
+      tc_fence_after();
+      const uint32_t tacc = tmem + (uint32_t)(b * 128) + ((uint32_t)(q * 32) << 16);
+      uint32_t t0[16], t1[16];
+      if (J1 > 0) tc_ld16_issue(tacc + (uint32_t)(h * 16), t0);
+      if (J1 > 1) tc_ld16_issue(tacc + (uint32_t)(h * 16 + 64), t1);
+      if (J1 > 0) tc_ld16_wait(t0);
+      if (J1 > 1) tc_ld16_wait(t1);
+      tc_fence_before();
+      mbar_arrive(d1empty(b));
+      const uint32_t tb = sT + (uint32_t)(b * KT) * (uint32_t)kTBytes;
+      auto put = [&](int c0, const uint32_t (&t)[16]) {
+        float v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(t[k]);
+        const float4* lc4 = reinterpret_cast<const float4*>(a.lamC + c0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float4 l = __ldg(lc4 + k);
+          v[4 * k + 0] *= rcp_approx(sab + l.x) * a.gscale;
+          v[4 * k + 1] *= rcp_approx(sab + l.y) * a.gscale;
+          v[4 * k + 2] *= rcp_approx(sab + l.z) * a.gscale;
+          v[4 * k + 3] *= rcp_approx(sab + l.w) * a.gscale;
+        }
+        if (null_row && c0 == 0) v[0] = 0.0f;
+        uint32_t pk[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          if constexpr (std::is_same<InT, __half>::value) {
+            __half2 h2 = __floats2half2_rn(v[2 * k], v[2 * k + 1]);
+            pk[k] = valid ? *reinterpret_cast<uint32_t*>(&h2) : 0u;
+          } else {
+            __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+            pk[k] = valid ? *reinterpret_cast<uint32_t*>(&h2) : 0u;
+          }
+        }
+        // 128-byte swizzle: 16-byte piece p of row trow sits at piece p ^ (trow % 8)
+        const uint32_t rowa = tb + (uint32_t)(c0 >> 6) * (uint32_t)kTBytes + (uint32_t)trow * 128u;
+        const uint32_t p0 = (uint32_t)((c0 & 63) >> 3);
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(rowa + (((p0 + k) ^ (uint32_t)(trow & 7)) << 4)),
+                       "r"(pk[4 * k]), "r"(pk[4 * k + 1]), "r"(pk[4 * k + 2]), "r"(pk[4 * k + 3])
+                       : "memory");
+      };
+      if (J1 > 0) put(h * 16, t0);
+      if (J1 > 1) put(h * 16 + 64, t1);
+      // generic-proxy writes of T -> the tensor core's (async-proxy) reads
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(tready(b));
+      return true;
+    };
+    // stage 2 of tile i: thread = output index c = q*32 + lane, chunk = 16 consecutive rows
+    auto epi2 = [&](int i) {
       const int tile = (int)blockIdx.x + i * (int)gridDim.x;
       const int b = i & 1;
       const int row0 = tile * kTileRows;
-      // stage 1: T[row][c'] = round(D1[row][c'] * G(row, c') * 2^-sG)
-      if (!__all_sync(0xffffffffu, wait_bounded(d1full(b), (uint32_t)((i >> 1) & 1), ab))) break;
+      if (!__all_sync(0xffffffffu, wait_bounded(d2full(b), (uint32_t)((i >> 1) & 1), ab))) return false;
       tc_fence_after();
-      {
-        const uint32_t tacc = tmem + (uint32_t)(b * 128) + ((uint32_t)(q * 32) << 16);
-        const int r = row0 + trow;
-        const bool valid = r < a.rows;
-        const int ia = valid ? r / a.B1 : 0;
-        const int ib = valid ? r - ia * a.B1 : 0;
-        const float sab = valid ? a.lamA[ia] + a.lamB[ib] : 0.0f;
-        const bool null_row = a.singular && ia == 0 && ib == 0;
-        uint32_t t0[16], t1[16];
-        if (J1 > 0) tc_ld16_issue(tacc + (uint32_t)(h * 16), t0);
-        if (J1 > 1) tc_ld16_issue(tacc + (uint32_t)(h * 16 + 64), t1);
-        if (J1 > 0) tc_ld16_wait(t0);
-        if (J1 > 1) tc_ld16_wait(t1);
-        tc_fence_before();
-        mbar_arrive(d1empty(b));
-        auto put = [&](int c0, const uint32_t (&t)[16]) {
-          float v[16];
+      const uint32_t tacc = tmem + 256u + (uint32_t)(b * 128) + ((uint32_t)(q * 32) << 16);
+      uint32_t t0[16], t1[16];
+      tc_ld16_issue(tacc + (uint32_t)(h * 16), t0);
+      tc_ld16_issue(tacc + (uint32_t)(h * 16 + 64), t1);
+      tc_ld16_wait(t0);
+      tc_ld16_wait(t1);
+      tc_fence_before();
+      mbar_arrive(d2empty(b));
+      const int cb = q * 32;
+      auto out = [&](int c0, const uint32_t (&t)[16]) {
+        const int r0 = row0 + c0;
+        if (r0 >= a.rows || cb >= a.Cout) return;  // warp-uniform (rows % 16 == 0)
+        float v[16];
 #pragma unroll
-          for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(t[k]);
-          const float4* lc4 = reinterpret_cast<const float4*>(a.lamC + c0);
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const float4 l = __ldg(lc4 + k);
-            v[4 * k + 0] *= rcp_approx(sab + l.x) * a.gscale;
-            v[4 * k + 1] *= rcp_approx(sab + l.y) * a.gscale;
-            v[4 * k + 2] *= rcp_approx(sab + l.z) * a.gscale;
-            v[4 * k + 3] *= rcp_approx(sab + l.w) * a.gscale;
-          }
-          if (null_row && c0 == 0) v[0] = 0.0f;
-          uint32_t pk[8];
-#pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            if constexpr (std::is_same<InT, __half>::value) {
-              __half2 h2 = __floats2half2_rn(v[2 * k], v[2 * k + 1]);
-              pk[k] = valid ? *reinterpret_cast<uint32_t*>(&h2) : 0u;
-            } else {
-              __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
-              pk[k] = valid ? *reinterpret_cast<uint32_t*>(&h2) : 0u;
-            }
-          }
-          // 128-byte swizzle: 16-byte piece p of row trow sits at piece p ^ (trow % 8)
-          const uint32_t rowa = sT + (uint32_t)(c0 >> 6) * (uint32_t)kTBytes + (uint32_t)trow * 128u;
-          const uint32_t p0 = (uint32_t)((c0 & 63) >> 3);
-#pragma unroll
-          for (int k = 0; k < 2; ++k)
-            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(rowa + (((p0 + k) ^ (uint32_t)(trow & 7)) << 4)),
-                         "r"(pk[4 * k]), "r"(pk[4 * k + 1]), "r"(pk[4 * k + 2]), "r"(pk[4 * k + 3])
-                         : "memory");
-        };
-        if (J1 > 0) put(h * 16, t0);
-        if (J1 > 1) put(h * 16 + 64, t1);
-        // generic-proxy writes of T -> the tensor core's (async-proxy) reads
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(tready);
-      }
-      // stage 2: thread = output index c = q*32 + lane, chunk = 16 consecutive rows
-      if (!__all_sync(0xffffffffu, wait_bounded(d2full(b), (uint32_t)((i >> 1) & 1), ab))) break;
-      tc_fence_after();
-      {
-        const uint32_t tacc = tmem + 256u + (uint32_t)(b * 128) + ((uint32_t)(q * 32) << 16);
-        uint32_t t0[16], t1[16];
-        tc_ld16_issue(tacc + (uint32_t)(h * 16), t0);
-        tc_ld16_issue(tacc + (uint32_t)(h * 16 + 64), t1);
-        tc_ld16_wait(t0);
-        tc_ld16_wait(t1);
-        tc_fence_before();
-        mbar_arrive(d2empty(b));
-        const int cb = q * 32;
-        auto out = [&](int c0, const uint32_t (&t)[16]) {
-          const int r0 = row0 + c0;
-          if (r0 >= a.rows || cb >= a.Cout) return;  // warp-uniform (rows % 16 == 0)
-          float v[16];
-#pragma unroll
-          for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(t[k]);
-          const int ia = r0 / a.B, ib = r0 - ia * a.B;
-          if (a.tperm) emit(v, ib, ia, cb);
-          else emit(v, ib, cb, ia);
-        };
-        out(h * 16, t0);
-        out(h * 16 + 64, t1);
-      }
+        for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(t[k]);
+        const int ia = r0 / a.B, ib = r0 - ia * a.B;
+        if (a.tperm) emit(v, ib, ia, cb);
+        else emit(v, ib, cb, ia);
+      };
+      out(h * 16, t0);
+      out(h * 16 + 64, t1);
+      return true;
+    };
+    bool ok = true;
+    for (int i = 0; ok && i < nmine; ++i) {
+      ok = epi1(i);
+      if (ok && i > 0) ok = epi2(i - 1);
     }
+    if (ok && nmine > 0) epi2(nmine - 1);
     if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   }
 
@@ -1348,9 +1359,9 @@ int tc_plan_setup(tpcg_plan* p) {
     a.lamA = f.args.lamA;
     a.lamB = f.args.lamB;
     a.lamC = f.args.lamC;
-    // alignment, both eigenbases, T, the output staging (two FP16/BF16 [32][16] boxes per epilogue warp),
-    // barriers and the TMEM address
-    const size_t fixed = 1024 + (size_t)a.KT * (a.VR + 128) * 128 + (size_t)a.KT * kTBytes +
+    // alignment, both eigenbases, the two T buffers, the output staging (two FP16/BF16 [32][16] boxes per
+    // epilogue warp), barriers and the TMEM address
+    const size_t fixed = 1024 + (size_t)a.KT * (a.VR + 128) * 128 + 2 * (size_t)a.KT * kTBytes +
                          (size_t)kPairEpi * 2 * 32 * 16 * 2 + 512;
     if (fixed + 2 * (size_t)kStageBytes > (size_t)kMaxSmem) return TPCG_ERR_UNSUPPORTED;
     a.NS = (int)std::min<size_t>(8, (kMaxSmem - fixed) / kStageBytes);
