@@ -340,9 +340,9 @@ def run_batched(prec, torch):
 # profiles/.  Set an entry to None when its kernel changes.
 NCU_TRAFFIC_PER_LAUNCH = {
     # DRAM bytes (read + write) per launch from the ncu captures summarised under profiles/ (cold caches)
-    # tensor-core passes: mean over the six passes of one application; passes 1-3 and 6 captured
-    # (17.0, 17.0, 16.8, 34.8 MB), passes 4 and 5 (the same FP16-in / FP16-out shape) taken as pass 1
-    "modeprod_tc": None,  # recaptured for the five-launch sequence (fused pair around G)
+    # tensor-core launches: mean over the five launches of one application (3D, TPCG_OPT_FUSE_G): passes
+    # 1, 2 and 5 (17.0, 16.9, 17.0 MB), the fused pair of passes 3-4 (16.9 MB) and the last pass (34.7 MB)
+    "modeprod_tc": (17.0e6 + 16.9e6 + 17.0e6 + 16.9e6 + 34.7e6) / 5,
     "update": 275.0e6,  # the in-place update the instrumented (one-plan) pass runs
     "form_u": 248.0e6,  # the formation before a check (six recorded directions; TPCG_OPT_DEFER_U)
     "direction": 76.2e6,
