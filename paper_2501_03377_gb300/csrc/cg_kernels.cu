@@ -337,7 +337,7 @@ struct OpResidualFx {
     const double e = eta_i - mean;
     double r;
     if (uniform) {
-      r = fma(nih0, i64_to_f64_scaled(dx + dy + dz, -ku), e);
+      r = fma(nih0, i64_to_f64_scaled_hw(dx + dy + dz, -ku), e);
     } else {
       r = fma(nih0, i64_to_f64_scaled(dx, -ku), e);
       r = fma(nih1, i64_to_f64_scaled(dy, -ku), r);

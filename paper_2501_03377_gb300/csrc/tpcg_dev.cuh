@@ -410,6 +410,16 @@ __device__ __forceinline__ double i64_to_f64_scaled(long long v, int e) {
   return __longlong_as_double((long long)bits);
 }
 
+// The same value as i64_to_f64_scaled (one round-to-nearest-even step, then an
+// exact scaling by 2^e), with the hardware conversion: one operation on the
+// FP64 pipe instead of some thirty integer instructions, for kernels with
+// FP64-pipe headroom and an instruction-issue bound.  e is added to the
+// exponent field, so v * 2^e must be an FP64 normal number (or v == 0).
+__device__ __forceinline__ double i64_to_f64_scaled_hw(long long v, int e) {
+  const double x = __ll2double_rn(v);
+  return v ? __hiloint2double(__double2hiint(x) + (int)((unsigned)e << 20), __double2loint(x)) : 0.0;
+}
+
 // FP32 sum with Neumaier's compensation (the rounding error of every addition
 // is kept in c); the per-thread partial sums of the PCG scalars use it.
 struct Acc32 {
