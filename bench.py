@@ -346,7 +346,7 @@ NCU_TRAFFIC_PER_LAUNCH = {
     "update": 275.0e6,  # the in-place update the instrumented (one-plan) pass runs
     "form_u": 248.0e6,  # the formation before a check (six recorded directions; TPCG_OPT_DEFER_U)
     "direction": 76.2e6,
-    "true_residual": 197.4e6,  # a launch that checks (the others return at once)
+    "true_residual": 197.8e6,  # a launch that checks (the others return at once)
 }
 
 
