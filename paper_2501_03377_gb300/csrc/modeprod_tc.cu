@@ -1387,9 +1387,8 @@ int tc_plan_setup(tpcg_plan* p) {
       void* outp = last ? p->d_Z : p->d_T[li & 1];
       TcStage st{};
       const int r = pair ? build_pair(si, prev, outp, st) : build_one(si, prev, outp, st);
-      if (r != TPCG_OK) {  // keep the one-launch-per-pass sequence only
+      if (r != TPCG_OK) {  // the pair does not fit here: keep the one-launch-per-pass sequence only
         tp->fused.clear();
-        if (r != TPCG_ERR_UNSUPPORTED) rc = r;
         break;
       }
       tp->fused.push_back(st);
