@@ -61,3 +61,24 @@ def test_reference_arm_prints_only_on_rank_zero(capsys):
     args = types.SimpleNamespace(nz=128, warmup=0, steps=1, tol=1e-10, gpus=2)
     bench.run_reference(args, rank=1, world=2)
     assert capsys.readouterr().out == ""
+
+
+def test_kernel_work_counts_the_algorithmic_bytes():
+    """The roofline's numerator: per application, each tensor-core launch but the last moves 4 B per
+    point (FP16 in and out) and the last 8 (FP16 in, the FP16 copy of R, Z in FP32), so five launches
+    (the pair around G fused) move 24 B per point and six move 28; the stencil kernels' per-point
+    bytes are those of their operands."""
+    N, dims = 1000, (10, 10, 10)
+    amount, unit, bound, worked = bench.kernel_work("modeprod_tc", "fp16", N, dims, 6, 7, 1, 1, 5)
+    assert (unit, bound, worked) == ("GB", "hbm", 35)
+    assert amount * 1e9 == pytest.approx(7 * 24 * N)
+    amount, _, _, worked = bench.kernel_work("modeprod_tc", "fp16", N, dims, 6, 7, 1, 1, 6)
+    assert worked == 42 and amount * 1e9 == pytest.approx(7 * 28 * N)
+    amount, _, _, worked = bench.kernel_work("modeprod_tc", "bf16", N, (10, 10, 1), 6, 7, 1, 1, None)
+    assert worked == 28 and amount * 1e9 == pytest.approx(7 * 20 * N)  # 2D, four launches
+    amount, _, _, _ = bench.kernel_work("direction", "fp16", N, dims, 6, 7, 1, 1)
+    assert amount * 1e9 == pytest.approx(6 * 12 * N)  # Z 4 + P_old 4 in, P 4 out
+    amount, _, _, _ = bench.kernel_work("update", "fp16", N, dims, 6, 7, 1, 1)
+    assert amount * 1e9 == pytest.approx(6 * 38 * N)  # P 4, R 8+8, U 8+8, FP16 copy 2
+    amount, _, _, worked = bench.kernel_work("true_residual", "fp16", N, dims, 6, 7, 1, 2)
+    assert worked == 2 and amount * 1e9 == pytest.approx(2 * 26 * N)
