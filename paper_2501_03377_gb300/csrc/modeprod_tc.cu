@@ -3,7 +3,7 @@
 // a BF16 x BF16 -> FP32 tcgen05 GEMM that contracts the contiguous index of
 // its input against the l x l eigenbasis.
 //
-// One persistent, warp-specialised kernel serves every pass:
+// One persistent, warp-specialised kernel serves every single pass:
 //   warp 0      TMA producer: loads the whole BF16 eigenbasis W^T (K-major,
 //               128B-swizzled) into shared memory once, then streams 128-row
 //               x 64-column K-tiles of the input through an NS-slot ring;
@@ -20,6 +20,9 @@
 //           eigenbasis = B, N = Cout padded to 16); lanes walk the rows;
 //   form 2: D[c'][row] = W^T[c'][:] . X[row][:]  (eigenbasis = A in M-blocks
 //           of 128, data = B, N = 128); lanes walk the output index.
+// A second kernel, k_modeprod_pair, runs the forward and the backward pass
+// along the axis of the Hadamard step as one launch (see its comment); the
+// plan uses it where the layout allows and the option TPCG_OPT_FUSE_G is on.
 // Every wait on an mbarrier is bounded (globaltimer); on expiry the CTA sets
 // an error word, stops issuing, drains its own copies/MMAs with bounded waits,
 // frees TMEM and returns.
