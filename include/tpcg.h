@@ -167,7 +167,9 @@ int tpcg_solve_host_stream(tpcg_plan* plan, int nrhs, const double* const* eta_h
  * returned.  It moves 16 bytes per grid point per iteration out of the
  * iteration and adds one formation pass bound by the FP64 pipe: slower for one
  * solve at a time, faster in total when several plans solve concurrently
- * (e.g. tpcg_solve_batched over several plans).  Ignored for TPCG_FP64.
+ * (e.g. tpcg_solve_batched over several plans).  Setting it allocates the
+ * ring (six more int32 words per grid point than a plan that updates in place;
+ * TPCG_ERR_OOM if that fails, the plan unchanged).  Ignored for TPCG_FP64.
  * TPCG_OPT_FUSE_G (mixed forms; 1 = on, the default): the forward and the
  * backward mode product along the axis where the Hadamard step by G is
  * applied (Algorithm 7) run as one kernel that keeps the scaled
@@ -176,8 +178,9 @@ int tpcg_solve_host_stream(tpcg_plan* plan, int nrhs, const double* const* eta_h
  * operations, bitwise the same Z.  0 runs one launch per mode product.  Used
  * when the axis has at most 128 points, a multiple of 16, and the pass
  * layouts allow it; ignored otherwise and for TPCG_FP64.
- * Returns TPCG_OK or TPCG_ERR_INVALID_ARG (NULL plan, unknown option, value
- * not 0 or 1).  Do not change an option while a solve of the plan runs.     */
+ * Returns TPCG_OK, TPCG_ERR_OOM (above), or TPCG_ERR_INVALID_ARG (NULL plan,
+ * unknown option, value not 0 or 1).  Do not change an option while a solve
+ * of the plan runs.                                                         */
 #define TPCG_OPT_DEFER_U 1
 #define TPCG_OPT_FUSE_G 2
 int tpcg_plan_set_option(tpcg_plan* plan, int option, int value);

@@ -476,10 +476,11 @@ int tpcg_plan_create(int nx, int ny, int nz, const int bc[3], const double h[3],
       rc = dalloc(p, &d, (size_t)N);
       p->d_P[b] = d;
     }
-  } else if (!rc) {  // ring of kPRing int32 directions (deferred U update)
+  } else if (!rc) {  // int32 directions: two slots; the ring of kPRing is allocated with TPCG_OPT_DEFER_U
     int* d = nullptr;
-    rc = dalloc(p, &d, (size_t)N * kPRing);
-    for (int b = 0; b < kPRing && !rc; ++b) p->d_P[b] = d + (size_t)N * b;
+    rc = dalloc(p, &d, (size_t)N * 2);
+    for (int b = 0; b < 2 && !rc; ++b) p->d_P[b] = d + (size_t)N * b;
+    p->p_slots = 2;
   }
   if (!rc && p->prec == TPCG_FP64) rc = dalloc(p, &p->d_W, (size_t)N);
   if (!rc) {
@@ -768,7 +769,18 @@ int tpcg_solve_host_stream(tpcg_plan* plan, int nrhs, const double* const* eta_h
 int tpcg_plan_set_option(tpcg_plan* plan, int option, int value) {
   if (!plan || (value != 0 && value != 1)) return TPCG_ERR_INVALID_ARG;
   if (option == TPCG_OPT_DEFER_U) {
-    plan->defer_u = (plan->prec != TPCG_FP64) ? value : 0;  // the FP64 form always updates U in place
+    if (plan->prec == TPCG_FP64) return TPCG_OK;  // the FP64 form always updates U in place
+    if (value && plan->p_slots < kPRing) {  // the recorded directions need the whole ring
+      DeviceGuard dg(plan->device);
+      const size_t N = (size_t)plan->nx * plan->ny * plan->nz;
+      int* d = nullptr;
+      if (dalloc(plan, &d, N * kPRing) != TPCG_OK) return TPCG_ERR_OOM;
+      cudaFree(plan->d_P[0]);  // a solve's first direction does not read the previous slot
+      plan->device_bytes -= N * (size_t)plan->p_slots * sizeof(int);
+      for (int b = 0; b < kPRing; ++b) plan->d_P[b] = d + N * b;
+      plan->p_slots = kPRing;
+    }
+    plan->defer_u = value;
     return TPCG_OK;
   }
   if (option == TPCG_OPT_FUSE_G) {

@@ -1737,7 +1737,7 @@ void launch_norm_shift(const tpcg_plan* p, const Geom& g, const double* r) {
   k_norm_shift<<<p->stream_blocks, 256, 0, p->stream>>>(g.N, r, p->d_state, p->d_partials);
 }
 // FP64 form: P_k is written to d_P[k & 1], P_{k-1} read from the other buffer.  Mixed forms: P_k goes to
-// ring slot k % kPRing (kept there until k_form_u has applied alpha_k P_k to U).
+// ring slot k % p_slots (with TPCG_OPT_DEFER_U, kept there until k_form_u has applied alpha_k P_k to U).
 void launch_direction(const tpcg_plan* p, const Geom& g, int k) {
   LaunchScope ls(p, kKDirection);
   if (p->prec == TPCG_FP64) {
@@ -1746,8 +1746,9 @@ void launch_direction(const tpcg_plan* p, const Geom& g, int k) {
         p->d_state, p->d_partials);
     return;
   }
-  const int* Pold = (const int*)p->d_P[(k + kPRing - 1) % kPRing];
-  int* Pnew = (int*)p->d_P[k % kPRing];
+  const int ns = p->p_slots;
+  const int* Pold = (const int*)p->d_P[(k + ns - 1) % ns];
+  int* Pnew = (int*)p->d_P[k % ns];
   if (g.nx % 4 == 0)
     k_direction_quad<<<p->fx_blocks[kFxDir], p->st_block, 0, p->stream>>>(g, (const float*)p->d_Z, Pold, Pnew,
                                                                            p->d_state, p->d_partials);
@@ -1765,7 +1766,7 @@ void launch_update(const tpcg_plan* p, const Geom& g, double* U, int k, bool zer
                                                        lowprec(p), p->d_state, p->d_partials);
     return;
   }
-  const int slot = k % kPRing;
+  const int slot = k % p->p_slots;
   const int* P = (const int*)p->d_P[slot];
   if (p->defer_u) {  // U += alpha P recorded for k_form_u
     if (g.nx % 2 == 0)

@@ -117,8 +117,9 @@ struct tpcg_plan {
 
   // device: PCG workspaces
   double* d_R = nullptr;
-  void* d_P[8] = {};  // directions: FP64 ping-pong [0..1], or the mixed forms' ring of int32 fixed point [0..7]
-                     // (one allocation, d_P[0] its base)
+  void* d_P[8] = {};  // directions: FP64 ping-pong [0..1], or the mixed forms' ring of int32 fixed point
+                     // (one allocation, d_P[0] its base; p_slots slots)
+  int p_slots = 2;   // mixed forms: 2 (in-place update), kPRing once TPCG_OPT_DEFER_U has been set
   double* d_W = nullptr;               // W = L P (FP64 form only)
   void* d_Z = nullptr;       // FP64 (FP64 form) or FP32 (mixed forms)
   void* d_Rlp = nullptr;     // BF16 / FP16 copy of R (mixed forms), row pitch pitch16[0]
