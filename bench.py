@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--serving-rate", type=float, default=200.0)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-comparators", action="store_true")
+    ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-solves", type=int, default=10, help="oracle solves of the cpu_baseline (all cores)")
+    ap.add_argument("--no-cube", action="store_true", help="skip the 256x256x256 record")
     ap.add_argument("--concurrency", type=int, default=3,
                     help="plans (each on its own stream) the timed steps are spread over")
     return ap.parse_args()
@@ -124,17 +127,46 @@ def workload(nz, seeds):
     return [synth.workload_cuboid_256(seed=s, nz=nz) for s in seeds]
 
 
-def cpu_oracle_solve(w, tol):
-    """One oracle solve (operator and eigenbases built outside the timed part)."""
+def cpu_oracle_solves(w, tol, k):
+    """k oracle solves (operator and eigenbases built once, outside the timed part): (seconds, result)."""
     import oracle as o
 
     sh = (w["nx"], w["ny"], w["nz"])
     L = o.kron_sum(sh, w["bcs"])
     pinv = o.pinv_init(sh, w["bcs"])
     H = w["eta"].transpose(2, 1, 0)
-    t0 = time.perf_counter()
-    res = o.pcg(sh, w["bcs"], (1.0, 1.0, 1.0), H, tol=tol, L=L, pinv=pinv)
-    return time.perf_counter() - t0, res
+    total, res = 0.0, None
+    for _ in range(k):
+        t0 = time.perf_counter()
+        res = o.pcg(sh, w["bcs"], (1.0, 1.0, 1.0), H, tol=tol, L=L, pinv=pinv)
+        total += time.perf_counter() - t0
+    return total, res
+
+
+def cpu_oracle_solve(w, tol):
+    """One oracle solve (operator and eigenbases built outside the timed part)."""
+    return cpu_oracle_solves(w, tol, 1)
+
+
+def cpu_one_thread(nz, tol, k):
+    """The oracle on one host core: a child process with every BLAS/OpenMP pool limited to one thread
+    (the limits must be set before numpy loads).  Returns (solves/s, k) or None."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1", NUMEXPR_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", str(k), "--nz", str(nz), "--tol", str(tol)]
+    try:
+        out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+        d = json.loads(out.stdout.strip().splitlines()[-1])
+        return k / d["seconds"], k
+    except Exception:
+        return None
+
+
+def oracle_sample(args):
+    """--oracle-sample K: K oracle solves of the bench workload on this process's threads (JSON line)."""
+    w = workload(args.nz, [0])[0]
+    secs, res = cpu_oracle_solves(w, args.tol, args.oracle_sample)
+    print(json.dumps({"seconds": secs, "solves": args.oracle_sample, "iters": res.iters}), flush=True)
 
 
 def run_reference(args, rank, world):
@@ -393,6 +425,88 @@ def kernel_work(kind, plan_prec, N, dims, iters_total, applies_total, solves, ch
     return None, None, None, None
 
 
+def run_cube(args, prec, torch, hbm_peak, peak_src):
+    """The metric's 256^3 label: the 256x256x256 P/P/N cube (2000 defects), the mixed form on one plan and
+    on `concurrency` plans (tpcg_solve_batched, TPCG_OPT_DEFER_U), the FP64 form on one plan, and the
+    roofline of the tensor-core launches at this shape (CUDA events of an instrumented pass)."""
+    from paper_2501_03377_gb300 import Plan
+    from paper_2501_03377_gb300.binding import TPCG_OPT_DEFER_U, TPCG_ZERO_GUESS, tpcg_solve_batched
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ws = workload(256, [0, 1, 2, 3])
+    w0 = ws[0]
+    nx, ny, nz = w0["nx"], w0["ny"], w0["nz"]
+    N = nx * ny * nz
+    etas = [torch.from_numpy(w["eta"]).to(dev) for w in ws]
+    ups = torch.zeros_like(etas[0])
+    steps = max(4, min(args.steps, 12))
+    nobar = lambda: None  # noqa: E731
+    out = {"workload": w0["name"], "grid": [nx, ny, nz], "bcs": ",".join(w0["bcs"]), "tol": args.tol}
+    pl = Plan(nx, ny, nz, w0["bcs"], prec=prec)
+    for s in range(3):
+        pl.solve(etas[s % 4], ups, tol=args.tol, maxit=60, zero_guess=True)
+    dt, infos, _ = time_steps(pl, etas, ups, steps, args.tol, torch, nobar)
+    out[f"mixed_{prec}"] = {"value": steps / dt, "unit": "solves/s", "ms_per_solve": 1e3 * dt / steps, "steps": steps,
+                            "api": "tpcg_solve, one plan", "mpoints_per_s": steps * N / dt / 1e6,
+                            "iters_per_solve": sum(i["iters"] for (_, i) in infos) / steps,
+                            "worst_rel_res_true": max(i["rel_res_true"] for (_, i) in infos),
+                            "failed": sum(1 for (st, _) in infos if st != 0),
+                            "tc_launches_per_apply": pl.precond_launches()}
+    # tensor-core roofline at this shape
+    pl.profile_begin()
+    _, pinfos, _ = time_steps(pl, etas, ups, steps, args.tol, torch, nobar)
+    kst = pl.profile_end()
+    applies = sum(i["precond_applies"] for (_, i) in pinfos)
+    iters = sum(i["iters"] for (_, i) in pinfos)
+    checks = sum(i.get("checks", 0) for (_, i) in pinfos)
+    if "modeprod_tc" in kst:
+        amount, unit, bound, worked = kernel_work("modeprod_tc", prec, N, (nx, ny, nz), iters, applies, steps, checks,
+                                                  pl.precond_launches())
+        secs = kst["modeprod_tc"]["total_ms"] / 1e3
+        out["roofline_tc"] = {"kernel": "modeprod_tc", "bound": "hbm", "achieved": amount / secs, "peak": hbm_peak,
+                              "unit": "GB/s", "frac": amount / secs / hbm_peak, "peak_source": f"{peak_src} hbm_gbs",
+                              "us_per_apply": 1e6 * secs / max(1, applies),
+                              "algorithmic_bytes_per_apply": amount * 1e9 / max(1, applies)}
+    pl.close()
+    # several plans on their own streams (the headline's launch configuration)
+    conc = max(1, args.concurrency)
+    cs = [torch.cuda.Stream() for _ in range(conc)]
+    cps = [Plan(nx, ny, nz, w0["bcs"], prec=prec, stream=c.cuda_stream) for c in cs]
+    if conc > 1:
+        for cp in cps:
+            cp.set_option(TPCG_OPT_DEFER_U, 1)
+    counts = [steps // conc + (1 if q < steps % conc else 0) for q in range(conc)]
+    E = [torch.stack([etas[(sum(counts[:q]) + r) % 4] for r in range(max(1, counts[q]))]).contiguous()
+         for q in range(conc)]
+    Uc = [torch.zeros_like(e) for e in E]
+    bat = lambda ns: tpcg_solve_batched([cp.handle for cp in cps], ns, [e.data_ptr() for e in E],  # noqa: E731
+                                        [u.data_ptr() for u in Uc], [args.tol] * conc, 60, TPCG_ZERO_GUESS)
+    bat([1] * conc)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    st_b, binfos = bat(counts)
+    e1.record()
+    torch.cuda.synchronize()
+    dtb = e0.elapsed_time(e1) / 1e3
+    out[f"mixed_{prec}_{conc}_plans"] = {"value": steps / dtb, "unit": "solves/s", "steps": steps, "status": st_b,
+                                         "worst_rel_res_true": max(i["rel_res_true"] for i in binfos)}
+    for cp in cps:
+        cp.close()
+    del E, Uc
+    # the plain FP64 form
+    p64 = Plan(nx, ny, nz, w0["bcs"], prec="fp64")
+    p64.solve(etas[0], ups, tol=args.tol, maxit=60, zero_guess=True)
+    k64 = 3
+    dt64, inf64, _ = time_steps(p64, etas, ups, k64, args.tol, torch, nobar)
+    out["fp64"] = {"value": k64 / dt64, "unit": "solves/s", "steps": k64,
+                   "iters_per_solve": sum(i["iters"] for (_, i) in inf64) / k64,
+                   "worst_rel_res_true": max(i["rel_res_true"] for (_, i) in inf64)}
+    p64.close()
+    out["mixed_over_fp64"] = out[f"mixed_{prec}"]["value"] / out["fp64"]["value"]
+    return out
+
+
 def max_over_ranks(x, world, torch, device):
     """Largest value of a per-rank float over all ranks (the whole-job clock is the slowest rank)."""
     if world <= 1:
@@ -596,12 +710,21 @@ def run_ours(args, rank, world, torch):
         if not args.no_comparators:
             comparators = run_comparators(torch)
         efield = run_efield(plan, ups, torch)
+    cube = None
+    if rank == 0 and world == 1 and prec != "fp64" and nz == 128 and not args.no_cube:
+        cube = run_cube(args, prec, torch, hbm_peak, peak_src)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dtc, res = cpu_oracle_solve(ws[0], args.tol)
-        cpu = {"value": 1.0 / dtc, "unit": "solves/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-               "sample": f"1 full oracle solve of {w0['name']} (seed 0), operator prebuilt; {res.iters} PCG iteration(s)"}
+        k = max(1, args.cpu_solves)
+        dtc, res = cpu_oracle_solves(ws[0], args.tol, k)
+        one = cpu_one_thread(nz, args.tol, max(1, k // 5))
+        cpu = {"value": k / dtc, "unit": "solves/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+               "sample": f"{k} full oracle solves of {w0['name']} (seed 0), operator and eigenbases built once "
+                         f"outside the timing; {res.iters} PCG iteration(s) each; BLAS threads = all cores",
+               "one_thread": None if one is None else {
+                   "value": one[0], "unit": "solves/s", "cores": 1,
+                   "sample": f"{one[1]} oracle solves in a child process with BLAS/OpenMP limited to 1 thread"}}
 
     if rank == 0:
         line = {
@@ -623,7 +746,8 @@ def run_ours(args, rank, world, torch):
             "gpu_launches": launches, "single_plan": single,
             "roofline": roofline, "kernels": kernels,
             "e2e": e2e, "cpu_baseline": cpu, "fp64_form": fp64_cmp, "bf16_form": bf16_cmp,
-            "serving": serving, "batched": batched, "comparators": comparators, "efield": efield, "clocks": clocks,
+            "serving": serving, "batched": batched, "comparators": comparators, "efield": efield,
+            "cube_256": cube, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     plan.close()
@@ -631,6 +755,9 @@ def run_ours(args, rank, world, torch):
 
 def main():
     args = parse()
+    if args.oracle_sample:
+        oracle_sample(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":

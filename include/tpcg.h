@@ -178,11 +178,24 @@ int tpcg_solve_host_stream(tpcg_plan* plan, int nrhs, const double* const* eta_h
  * operations, bitwise the same Z.  0 runs one launch per mode product.  Used
  * when the axis has at most 128 points, a multiple of 16, and the pass
  * layouts allow it; ignored otherwise and for TPCG_FP64.
+ * TPCG_OPT_SLICES (mixed forms; 1 = on, the default): 3D grids with nx a
+ * multiple of 16 and every axis at most 256 points group the six mode products
+ * of Algorithm 7 by the data they touch: one launch applies the x and the y
+ * product to every z-plane (frontal slice) with the intermediate kept in
+ * shared memory, one launch applies the z products and the Hadamard step to
+ * the mode-3 fibres (two launches when the z axis exceeds 128 points or
+ * TPCG_OPT_FUSE_G is 0), one launch applies the backward x and y products
+ * per z-plane.  Same products, same precision; the rounding points of the
+ * intermediates differ (x before y in the backward products).  0 keeps one
+ * launch per mode product.
  * Returns TPCG_OK, TPCG_ERR_OOM (above), or TPCG_ERR_INVALID_ARG (NULL plan,
- * unknown option, value not 0 or 1).  Do not change an option while a solve
- * of the plan runs.                                                         */
+ * unknown option, value not 0 or 1).  Set options between solves only: not
+ * while another host thread, tpcg_solve_batched or a server request is using
+ * the plan.  Setting TPCG_OPT_DEFER_U first waits for the work already
+ * enqueued on the plan's stream, then replaces the direction storage.      */
 #define TPCG_OPT_DEFER_U 1
 #define TPCG_OPT_FUSE_G 2
+#define TPCG_OPT_SLICES 3
 int tpcg_plan_set_option(tpcg_plan* plan, int option, int value);
 
 /* Many independent solves in one call (the batched form of tpcg_solve).
@@ -246,6 +259,35 @@ int tpcg_rhs_add_bc(tpcg_plan* plan, double* eta, const double bval[6]);
  * NULL) for a 2D plan; outputs may not alias ups.  Enqueues only.           */
 int tpcg_efield(tpcg_plan* plan, const double* ups, const double bval[6], double* ex, double* ey, double* ez);
 
+/* ---- diagnostics of the CG recurrence (Algorithm 1, Sec. 4.1) ------------
+ * The scalars of the plan's most recent iteration, as the device computed
+ * them: for the last completed iteration s (0-based, iter = s + 1) alpha_s =
+ * rho_s / <W_s, P_s> with W_s = L P_s, beta_s (the coefficient that formed
+ * P_s = Z_s + beta_s P_{s-1}; 0 for the first direction), rho_s = <R_s, Z_s>
+ * with Z_s centred (Remark orthogonality), the recurrence's ||R_{s+1}||^2 and
+ * sum(R_{s+1}), and the mean of Z_s.  The mixed forms accumulate these per
+ * thread in FP32 and combine them in FP64, and take rho from the FP16/BF16
+ * copy of R the preconditioner read; the FP64 form computes them in FP64.
+ * Valid after a solve that stopped (e.g. maxit reached) until the next call
+ * that runs the plan.  Synchronises the plan's stream.                     */
+typedef struct {
+  int    iter;               /* iterations completed                                   */
+  double alpha, beta, rho;   /* alpha_s, beta_s, rho_s                                 */
+  double wp;                 /* <W_s, P_s> = <L P_s, P_s>                              */
+  double rr, sum_r;          /* ||R_{s+1}||^2 and sum(R_{s+1}) of the recurrence       */
+  double mean_z;             /* mean(Z_s) (singular operators; 0 otherwise)            */
+  int    lp_shift;           /* FP16 form: R_s entered the preconditioner as R_s*2^k   */
+  int    direction_exponent; /* mixed forms: P_s = P_int * 2^-k (int32 fixed point)   */
+} tpcg_cg_scalars;
+int tpcg_plan_cg_scalars(tpcg_plan* plan, tpcg_cg_scalars* out);
+
+/* FP64 copies of the plan's current CG vectors (device pointers of nz*ny*nx
+ * doubles, each may be NULL): R (the residual the last update or check
+ * wrote), Z (the last preconditioner output, exact conversion of the mixed
+ * forms' FP32 Z) and P_s (the last direction; the mixed forms' fixed point
+ * converted exactly).  Synchronises the plan's stream.                     */
+int tpcg_plan_cg_vectors(tpcg_plan* plan, double* R, double* Z, double* P);
+
 /* Copy the FP64 eigenpairs of axis (0 = x, 1 = y, 2 = z) to host memory:
  * lam[ell] (already divided by h^2) and V[ell*ell] row-major with column k
  * the eigenvector of lam[k] (eq. eig-svd-decomp).  ell is the axis length
@@ -307,6 +349,26 @@ int tpcg_server_poll(tpcg_server* server, unsigned long long ticket, double* ups
 int tpcg_server_wait(tpcg_server* server, unsigned long long ticket, double timeout_s, double* ups_out,
                      tpcg_info* info);
 int tpcg_server_get_stats(tpcg_server* server, tpcg_server_stats* stats);
+
+/* Where each finished request spent its latency (submit -> result in host
+ * memory), one record per request finished since the server was created or
+ * its statistics were last reset (at most 2^20 kept), in finishing order.
+ * queue_ms + build_ms + solve_ms + copy_ms = total_ms.  No counterpart in the
+ * paper: it explains the serving latency of Sec. 1's time-stepping use.     */
+typedef struct {
+  unsigned long long ticket, session;
+  int nx, ny, nz, prec;
+  int status, iters;
+  int plan_built;      /* 1: no idle cached plan of this key; one was created   */
+  double queue_ms;     /* submit -> admitted (slot and device memory free)      */
+  double build_ms;     /* admitted -> solve enqueued: plan creation (cache miss) */
+  double solve_ms;     /* copy of eta in, the PCG iterations, exit work          */
+  double copy_ms;      /* copy of the solution to host memory                    */
+  double total_ms;
+} tpcg_request_timing;
+/* Copies up to max_records records to out (host array) and their count to
+ * *n_records; max_records == 0 only reports how many are held.              */
+int tpcg_server_get_timings(tpcg_server* server, tpcg_request_timing* out, int max_records, int* n_records);
 /* Clear the counters and the latency record (e.g. after a warm-up phase).  */
 int tpcg_server_reset_stats(tpcg_server* server);
 /* Lets running requests finish, cancels queued ones, releases everything.  */
@@ -355,7 +417,12 @@ int tpcg_profile_end(tpcg_plan* plan, tpcg_kernel_stat* stats, int max_stats, in
  * loads it, held until the process exits) for the partial sums of at most
  * 2048 reduction blocks.  Grids of more than 2^31 - 1 points are rejected with
  * TPCG_ERR_UNSUPPORTED.  The first call on a device looks the array's address
- * up (cudaGetSymbolAddress); make that first call before any stream capture.
+ * up (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  A new context on the device (after
+ * cudaDeviceReset) moves the array; the next call notices the new context
+ * and looks the address up again (make that call outside a capture too).
+ * An error already pending in the calling thread (cudaPeekAtLastError) is
+ * left in place and reported as TPCG_ERR_CUDA before anything is enqueued.
  * Every call uses the same array: calls that may run concurrently on the GPU
  * (different streams, no ordering between them) race and must not be issued.
  * Each call clears the array's arrival counters before use.               */

@@ -42,6 +42,7 @@ TPCG_PRECOND_NONE = 1
 TPCG_PRECOND_JACOBI = 2
 TPCG_OPT_DEFER_U = 1
 TPCG_OPT_FUSE_G = 2
+TPCG_OPT_SLICES = 3
 TPCG_REQ_BORROW_HOST = 1
 TPCG_REQ_BORROW_DEVICE = 2
 
@@ -59,6 +60,16 @@ class tpcg_info(ctypes.Structure):
         ("null_component", ctypes.c_double),
         ("checks", ctypes.c_int),
     ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class tpcg_cg_scalars(ctypes.Structure):
+    _fields_ = [("iter", ctypes.c_int), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("rho", ctypes.c_double), ("wp", ctypes.c_double), ("rr", ctypes.c_double),
+                ("sum_r", ctypes.c_double), ("mean_z", ctypes.c_double), ("lp_shift", ctypes.c_int),
+                ("direction_exponent", ctypes.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -85,6 +96,17 @@ class tpcg_server_stats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class tpcg_request_timing(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_ulonglong), ("session", ctypes.c_ulonglong), ("nx", ctypes.c_int),
+                ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("prec", ctypes.c_int), ("status", ctypes.c_int),
+                ("iters", ctypes.c_int), ("plan_built", ctypes.c_int), ("queue_ms", ctypes.c_double),
+                ("build_ms", ctypes.c_double), ("solve_ms", ctypes.c_double), ("copy_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _P = ctypes.c_void_p
 _D = ctypes.c_double
 _I = ctypes.c_int
@@ -106,6 +128,8 @@ _SIGS = {
     "tpcg_plan_set_precond": (_I, [_P, _I, _I, _D]),
     "tpcg_plan_set_option": (_I, [_P, _I, _I]),
     "tpcg_plan_eigenpairs": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "tpcg_plan_cg_scalars": (_I, [_P, ctypes.POINTER(tpcg_cg_scalars)]),
+    "tpcg_plan_cg_vectors": (_I, [_P, _P, _P, _P]),
     "tpcg_plan_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "tpcg_plan_precond_launches": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
     "tpcg_profile_begin": (_I, [_P]),
@@ -116,6 +140,7 @@ _SIGS = {
     "tpcg_server_poll": (_I, [_P, ctypes.c_ulonglong, _P, ctypes.POINTER(tpcg_info)]),
     "tpcg_server_wait": (_I, [_P, ctypes.c_ulonglong, _D, _P, ctypes.POINTER(tpcg_info)]),
     "tpcg_server_get_stats": (_I, [_P, ctypes.POINTER(tpcg_server_stats)]),
+    "tpcg_server_get_timings": (_I, [_P, ctypes.POINTER(tpcg_request_timing), _I, ctypes.POINTER(_I)]),
     "tpcg_server_reset_stats": (_I, [_P]),
     "tpcg_server_destroy": (_I, [_P]),
     "tpcg_strerror": (ctypes.c_char_p, [_I]),
@@ -237,6 +262,16 @@ def tpcg_plan_eigenpairs(plan, axis, length):
     return st, list(lam), list(V)
 
 
+def tpcg_plan_cg_scalars(plan):
+    out = tpcg_cg_scalars()
+    st = lib().tpcg_plan_cg_scalars(plan, ctypes.byref(out))
+    return st, out.as_dict()
+
+
+def tpcg_plan_cg_vectors(plan, r_ptr, z_ptr, p_ptr):
+    return lib().tpcg_plan_cg_vectors(plan, _P(r_ptr), _P(z_ptr), _P(p_ptr))
+
+
 def tpcg_plan_launch_count(plan):
     v = ctypes.c_ulonglong()
     st = lib().tpcg_plan_launch_count(plan, ctypes.byref(v))
@@ -291,6 +326,16 @@ def tpcg_server_wait(server, ticket, timeout_s, ups_ptr):
     st = lib().tpcg_server_wait(server, ctypes.c_ulonglong(ticket), float(timeout_s), _P(ups_ptr),
                                 ctypes.byref(info))
     return st, info
+
+
+def tpcg_server_get_timings(server):
+    n = _I()
+    st = lib().tpcg_server_get_timings(server, None, 0, ctypes.byref(n))
+    if st != TPCG_OK or n.value == 0:
+        return st, []
+    arr = (tpcg_request_timing * n.value)()
+    st = lib().tpcg_server_get_timings(server, arr, n.value, ctypes.byref(n))
+    return st, [arr[i].as_dict() for i in range(n.value)]
 
 
 def tpcg_server_get_stats(server):
@@ -368,6 +413,10 @@ class Server:
     def stats(self):
         return tpcg_server_get_stats(self.handle)[1].as_dict()
 
+    def timings(self):
+        """Per-request latency breakdown (queue, plan build, solve, copy) of the finished requests."""
+        return tpcg_server_get_timings(self.handle)[1]
+
     def reset_stats(self):
         tpcg_server_reset_stats(self.handle)
 
@@ -394,6 +443,7 @@ class Plan:
             stream = torch.cuda.current_stream().cuda_stream
         self.shape = (nz, ny, nx)
         self.nx, self.ny, self.nz = nx, ny, nz
+        self.device = torch.device("cuda", torch.cuda.current_device())
         self.prec = PREC[prec] if isinstance(prec, str) else int(prec)
         st, handle = tpcg_plan_create(nx, ny, nz, bcs, h, self.prec, stream)
         if st != TPCG_OK:
@@ -460,8 +510,9 @@ class Plan:
             raise TpcgError(st, "tpcg_apply_laplacian")
 
     def set_option(self, option, value):
-        """Plan option: TPCG_OPT_DEFER_U (1: record U += alpha P and form U before each check) or
-        TPCG_OPT_FUSE_G (0: one launch per mode product instead of the fused pair around G)."""
+        """Plan option: TPCG_OPT_DEFER_U (1: record U += alpha P and form U before each check),
+        TPCG_OPT_FUSE_G (0: the products around G in separate launches) or TPCG_OPT_SLICES (0: one
+        launch per mode product instead of the frontal-slice launches)."""
         st = tpcg_plan_set_option(self.handle, option, value)
         if st != TPCG_OK:
             raise TpcgError(st, "tpcg_plan_set_option")
@@ -497,6 +548,24 @@ class Plan:
 
     def launch_count(self):
         return tpcg_plan_launch_count(self.handle)[1]
+
+    def cg_scalars(self):
+        """Device scalars of the most recent CG iteration (see tpcg_plan_cg_scalars)."""
+        st, d = tpcg_plan_cg_scalars(self.handle)
+        if st != TPCG_OK:
+            raise TpcgError(st, "tpcg_plan_cg_scalars")
+        return d
+
+    def cg_vectors(self):
+        """FP64 copies (torch tensors) of the plan's current R, Z and last direction P."""
+        import torch
+
+        shape = (self.nz, self.ny, self.nx)
+        R, Z, P = (torch.empty(shape, dtype=torch.float64, device=self.device) for _ in range(3))
+        st = tpcg_plan_cg_vectors(self.handle, R.data_ptr(), Z.data_ptr(), P.data_ptr())
+        if st != TPCG_OK:
+            raise TpcgError(st, "tpcg_plan_cg_vectors")
+        return R, Z, P
 
     def precond_launches(self):
         """Tensor-core launches per preconditioner application (0 for the FP64 form)."""

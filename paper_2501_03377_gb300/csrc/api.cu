@@ -27,6 +27,7 @@ void launch_zero(const tpcg_plan* p, long long N, double* U);
 void launch_to_lp(const tpcg_plan* p, const Geom& g, const double* r);
 void launch_norm_shift(const tpcg_plan* p, const Geom& g, const double* r);
 void launch_f32_to_f64(const tpcg_plan* p, long long N, const float* a, double* b);
+void launch_fixed_to_f64(const tpcg_plan* p, long long N, const int* a, int kp, double* b);
 void launch_rhs_add_bc(const tpcg_plan* p, const Geom& g, double* eta, const double* bv);
 void launch_efield(const tpcg_plan* p, const Geom& g, const double* U, const double* bval, double* ex, double* ey,
                    double* ez);
@@ -772,10 +773,13 @@ int tpcg_plan_set_option(tpcg_plan* plan, int option, int value) {
     if (plan->prec == TPCG_FP64) return TPCG_OK;  // the FP64 form always updates U in place
     if (value && plan->p_slots < kPRing) {  // the recorded directions need the whole ring
       DeviceGuard dg(plan->device);
+      // work already enqueued on the plan's stream may still read or write the two-slot block: let it
+      // finish before the block is replaced (a solve's first direction does not read the previous slot)
+      if (cudaStreamSynchronize(plan->stream) != cudaSuccess) return last_cuda_error() ? TPCG_ERR_CUDA : TPCG_ERR_CUDA;
       const size_t N = (size_t)plan->nx * plan->ny * plan->nz;
       int* d = nullptr;
       if (dalloc(plan, &d, N * kPRing) != TPCG_OK) return TPCG_ERR_OOM;
-      cudaFree(plan->d_P[0]);  // a solve's first direction does not read the previous slot
+      cudaFree(plan->d_P[0]);
       plan->device_bytes -= N * (size_t)plan->p_slots * sizeof(int);
       for (int b = 0; b < kPRing; ++b) plan->d_P[b] = d + N * b;
       plan->p_slots = kPRing;
@@ -785,6 +789,10 @@ int tpcg_plan_set_option(tpcg_plan* plan, int option, int value) {
   }
   if (option == TPCG_OPT_FUSE_G) {
     plan->tc_fuse = value;
+    return TPCG_OK;
+  }
+  if (option == TPCG_OPT_SLICES) {
+    plan->tc_slab = value;
     return TPCG_OK;
   }
   return TPCG_ERR_INVALID_ARG;
@@ -865,6 +873,52 @@ int tpcg_efield(tpcg_plan* plan, const double* ups, const double bval[6], double
   if (ex == ups || ey == ups || (ez && ez == ups)) return TPCG_ERR_INVALID_ARG;
   DeviceGuard dg(plan->device);
   launch_efield(plan, make_geom(plan), ups, bval, ex, ey, plan->nz > 1 ? ez : nullptr);
+  return last_cuda_error();
+}
+
+int tpcg_plan_cg_scalars(tpcg_plan* plan, tpcg_cg_scalars* out) {
+  if (!plan || !out) return TPCG_ERR_INVALID_ARG;
+  DeviceGuard dg(plan->device);
+  SolveState* hs = plan->h_state;
+  if (cudaMemcpyAsync(hs, plan->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, plan->stream) != cudaSuccess ||
+      cudaStreamSynchronize(plan->stream) != cudaSuccess)
+    return last_cuda_error() ? TPCG_ERR_CUDA : TPCG_ERR_CUDA;
+  std::memset(out, 0, sizeof(*out));
+  out->iter = hs->iter;
+  out->alpha = hs->alpha;
+  out->beta = hs->beta;
+  out->rho = hs->rho;
+  out->wp = hs->pWp;
+  out->rr = hs->rr;
+  out->sum_r = hs->sumR;
+  out->mean_z = hs->mZ;
+  out->lp_shift = (plan->lp_kind == 2) ? hs->lp_shift_applied : 0;
+  out->direction_exponent = (plan->prec == TPCG_FP64) ? 0 : hs->kp;
+  return TPCG_OK;
+}
+
+int tpcg_plan_cg_vectors(tpcg_plan* plan, double* R, double* Z, double* P) {
+  if (!plan) return TPCG_ERR_INVALID_ARG;
+  DeviceGuard dg(plan->device);
+  const long long N = plan->N;
+  SolveState* hs = plan->h_state;
+  if (cudaMemcpyAsync(hs, plan->d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, plan->stream) != cudaSuccess ||
+      cudaStreamSynchronize(plan->stream) != cudaSuccess)
+    return TPCG_ERR_CUDA;
+  const int k = hs->iter > 0 ? hs->iter - 1 : 0;  // index of the last direction formed
+  const size_t bytes = sizeof(double) * (size_t)N;
+  if (R && cudaMemcpyAsync(R, plan->d_R, bytes, cudaMemcpyDeviceToDevice, plan->stream) != cudaSuccess)
+    return TPCG_ERR_CUDA;
+  if (plan->prec == TPCG_FP64) {
+    if (Z && cudaMemcpyAsync(Z, plan->d_Z, bytes, cudaMemcpyDeviceToDevice, plan->stream) != cudaSuccess)
+      return TPCG_ERR_CUDA;
+    if (P && cudaMemcpyAsync(P, plan->d_P[k & 1], bytes, cudaMemcpyDeviceToDevice, plan->stream) != cudaSuccess)
+      return TPCG_ERR_CUDA;
+  } else {
+    if (Z) launch_f32_to_f64(plan, N, (const float*)plan->d_Z, Z);
+    if (P) launch_fixed_to_f64(plan, N, (const int*)plan->d_P[k % plan->p_slots], hs->kp, P);
+  }
+  if (cudaStreamSynchronize(plan->stream) != cudaSuccess) return TPCG_ERR_CUDA;
   return last_cuda_error();
 }
 

@@ -1551,6 +1551,13 @@ __global__ void __launch_bounds__(256) k_f32_to_f64(long long N, const float* __
     b[i] = f32_to_f64_int(__ldg(a + i));
 }
 
+// The mixed forms' fixed-point direction P = P_int * 2^-kp as FP64 (exact).
+__global__ void __launch_bounds__(256) k_fixed_to_f64(long long N, const int* __restrict__ a, int kp,
+                                                      double* __restrict__ b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
+    b[i] = i32_to_f64_scaled(__ldg(a + i), -kp);
+}
+
 // Sec. 3.4.2: fold constant boundary data into the right-hand side.  bval[2m]
 // at the start face of axis m, bval[2m+1] at the end face; Dirichlet adds
 // u/h^2 to the boundary layer, Neumann adds e/h (e: outward derivative).
@@ -1820,6 +1827,10 @@ void launch_to_lp(const tpcg_plan* p, const Geom& g, const double* r) {
 void launch_f32_to_f64(const tpcg_plan* p, long long N, const float* a, double* b) {
   LaunchScope ls(p, kKConvert);
   k_f32_to_f64<<<p->stream_blocks, 256, 0, p->stream>>>(N, a, b);
+}
+void launch_fixed_to_f64(const tpcg_plan* p, long long N, const int* a, int kp, double* b) {
+  LaunchScope ls(p, kKConvert);
+  k_fixed_to_f64<<<p->stream_blocks, 256, 0, p->stream>>>(N, a, kp, b);
 }
 void launch_efield(const tpcg_plan* p, const Geom& g, const double* U, const double* bval, double* ex, double* ey,
                    double* ez) {

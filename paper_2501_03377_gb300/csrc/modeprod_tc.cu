@@ -35,11 +35,12 @@
 #include <cstdio>
 #include <vector>
 
-#include "tpcg_dev.cuh"
+#include "tc_ptx.cuh"
 
 namespace tpcg {
 
 namespace {
+using namespace tcx;
 
 // Warp roles: warp 0 TMA of the operand, warp 1 MMA, then the epilogue warps, one group of four per
 // share of the accumulator's 16-column chunks (a warp may only read its TMEM lane quadrant, warp % 4).
@@ -58,129 +59,7 @@ constexpr int kRBytes = 128 * 16 * 2;      // one chunk: 128 rows x 16 FP16/BF16
 constexpr int kTileRows = 128;
 constexpr int kKTile = 64;                 // BF16 elements per 128-byte swizzle row
 constexpr int kStageBytes = kTileRows * 128;
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
-constexpr int kMaxSmem = 232448 - 1024;  // opt-in limit minus room for static shared memory (560 B used)
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-struct Abort {
-  volatile int* flag;  // shared
-  int* err;            // global error word
-  SolveState* st;
-};
-
-// Bounded wait for the phase of parity `parity` to complete.
-__device__ __forceinline__ bool wait_bounded(uint32_t bar, uint32_t parity, const Abort& ab) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = gtimer();
-  for (;;) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (*ab.flag) return false;
-    if (gtimer() - t0 > kWaitLimitNs) {
-      *ab.flag = 1;
-      if (ab.err) atomicExch(ab.err, 1);
-      if (ab.st) ab.st->timeout = 1;
-      return false;
-    }
-  }
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          dst),
-      "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(bar)
-      : "memory");
-}
-
-// TMA store of one staged box (bulk async-group of the issuing thread).
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int c0, int c1) {
-  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
-                   (unsigned long long)map),
-               "r"(c0), "r"(c1), "r"(src)
-               : "memory");
-}
-__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, uint32_t src, int c0, int c1, int c2) {
-  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
-                   (unsigned long long)map),
-               "r"(c0), "r"(c1), "r"(c2), "r"(src)
-               : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tc_mma(uint32_t d, unsigned long long a, unsigned long long b, uint32_t idesc,
-                                       uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-__device__ __forceinline__ void tc_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-// TMEM -> registers, 16 columns of the thread's lane, in split form for
-// software pipelining: issue the load, do other work, then wait.  The wait names the destination registers as in/out
-// operands, so the compiler cannot read them before the load has landed.
-__device__ __forceinline__ void tc_ld16_issue(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
-      "[%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-}
-__device__ __forceinline__ void tc_ld16_wait(uint32_t (&r)[16]) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;"
-               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
-               :
-               : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes, 8-row core groups 1024 bytes apart (tile base 1024-aligned).
-__device__ __forceinline__ unsigned long long sw128_desc(uint32_t saddr) {
-  unsigned long long d = 0;
-  d |= (unsigned long long)((saddr >> 4) & 0x3FFFu);
-  d |= (unsigned long long)1 << 16;             // leading-dimension byte offset (unused for swizzled K-major)
-  d |= (unsigned long long)(1024 >> 4) << 32;   // stride-dimension byte offset
-  d |= (unsigned long long)1 << 46;             // descriptor version
-  d |= (unsigned long long)2 << 61;             // 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptor of kind::f16: A and B both BF16 (fmt 1) or both FP16
-// (fmt 0), FP32 D, both K-major.
-__host__ __device__ constexpr uint32_t idesc_f16kind(int M, int N, uint32_t fmt) {
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
 
 struct TcArgs {
   int C, KT, Cout, VR, Np, MB, acc_cols, tmem_cols, NS;
@@ -211,59 +90,6 @@ struct TcArgs {
 };
 
 // FP32 reciprocal, hardware approximation (max error ~1 ulp): far below the
-// FP16/BF16 rounding of the value it scales.
-__device__ __forceinline__ float rcp_approx(float x) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-
-// Two 16-bit elements packed in one word (low half first) as FP32; BF16 is the top half of an FP32.
-template <class InT>
-__device__ __forceinline__ float2 lp2_to_f32(uint32_t w) {
-  if constexpr (std::is_same<InT, __half>::value) {
-    __half2 h2 = *reinterpret_cast<__half2*>(&w);
-    return __half22float2(h2);
-  } else {
-    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
-  }
-}
-
-// Row `lane` of a [32][16] output box staged for a TMA store: FP16/BF16 rows of 32 bytes under the
-// 32-byte swizzle (16-byte piece i at i ^ ((lane / 4) % 2)), FP32 rows of 64 bytes under the 64-byte
-// swizzle (piece i at i ^ ((lane / 2) % 4)); eight consecutive lanes then cover all 32 banks.
-template <class OutT>
-__device__ __forceinline__ void stage_row(uint32_t buf, int lane, const float (&x)[16]) {
-  if constexpr (sizeof(OutT) == 2) {
-    uint32_t pk[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      if constexpr (std::is_same<OutT, __half>::value) {
-        __half2 h2 = __floats2half2_rn(x[2 * i], x[2 * i + 1]);
-        pk[i] = *reinterpret_cast<uint32_t*>(&h2);
-      } else {
-        __nv_bfloat162 h2 = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
-        pk[i] = *reinterpret_cast<uint32_t*>(&h2);
-      }
-    }
-    const uint32_t row = buf + (uint32_t)lane * 32u;
-    const uint32_t sw = (uint32_t)((lane >> 2) & 1);
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-      asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(row + (((uint32_t)i ^ sw) << 4)), "r"(pk[4 * i]),
-                   "r"(pk[4 * i + 1]), "r"(pk[4 * i + 2]), "r"(pk[4 * i + 3])
-                   : "memory");
-  } else {
-    const uint32_t row = buf + (uint32_t)lane * 64u;
-    const uint32_t sw = (uint32_t)((lane >> 1) & 3);
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-      asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(row + (((uint32_t)i ^ sw) << 4)), "f"(x[4 * i]),
-                   "f"(x[4 * i + 1]), "f"(x[4 * i + 2]), "f"(x[4 * i + 3])
-                   : "memory");
-  }
-}
-
 template <class OutT>
 __device__ __forceinline__ void store_out(void* out, long long o, float v) {
   if constexpr (std::is_same<OutT, __half>::value)
@@ -1063,22 +889,7 @@ struct TcPlan {
   bool fp16 = false;
 };
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encoder() {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void* ptr = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(ptr);
-  }
-  return fn;
-}
+EncodeTiledFn encoder() { return tma_encoder(); }
 
 // Rows of the 16-bit copy of R, 16 x 128 boxes with the 32-byte swizzle (last pass).
 int encode_r(CUtensorMap* map, const void* gaddr, int inner, long long outer, long long pitch_elems, bool fp16) {
@@ -1234,6 +1045,21 @@ double smallest_positive_sum(const tpcg_plan* p) {
 
 }  // namespace
 
+// FP16 range: R enters at unit RMS, so intermediates of the forward products are bounded by sqrt(N);
+// after G they are bounded by sqrt(N) * max G, which 2^-sG brings under 2^14 (below the FP16 maximum
+// 65504).
+int tc_fp16_g_exponent(const tpcg_plan* p) {
+  const double smin = smallest_positive_sum(p);
+  const double bound = std::sqrt((double)p->N) / (smin > 0 ? smin : 1.0);
+  return std::max(0, (int)std::ceil(std::log2(bound / 16384.0)));
+}
+
+bool slab_applicable(const tpcg_plan* p);
+int slab_plan_setup(tpcg_plan* p);
+void slab_plan_release(tpcg_plan* p);
+int slab_launches_per_apply(const tpcg_plan* p);
+int run_precond_slab(const tpcg_plan* p, float* Z, SolveState* st);
+
 int tc_plan_setup(tpcg_plan* p) {
   if (p->prec != TPCG_MIXED_BF16 && p->prec != TPCG_MIXED_FP16) return TPCG_ERR_UNSUPPORTED;
   TcPlan* tp = new TcPlan();
@@ -1241,12 +1067,7 @@ int tc_plan_setup(tpcg_plan* p) {
   // FP16 range: R enters at unit RMS, so intermediates of the forward passes
   // are bounded by sqrt(N); after G they are bounded by sqrt(N) * max G,
   // which 2^-sG brings under 2^14 (below the FP16 maximum 65504).
-  int sG = 0;
-  if (tp->fp16) {
-    const double smin = smallest_positive_sum(p);
-    const double bound = std::sqrt((double)p->N) / (smin > 0 ? smin : 1.0);
-    sG = std::max(0, (int)std::ceil(std::log2(bound / 16384.0)));
-  }
+  const int sG = tp->fp16 ? tc_fp16_g_exponent(p) : 0;
   const int ns = (int)p->stages.size();
   // Launch parameters of pass si reading xin and writing out_addr (the plan's Z for the last pass).
   auto build_one = [&](int si, const void* xin, void* out_addr, TcStage& st) -> int {
@@ -1409,16 +1230,22 @@ int tc_plan_setup(tpcg_plan* p) {
     return TPCG_ERR_CUDA;
   }
   p->tc_state = tp;
+  if (slab_applicable(p)) {
+    const int r = slab_plan_setup(p);
+    if (r != TPCG_OK && r != TPCG_ERR_UNSUPPORTED) return r;
+  }
   return TPCG_OK;
 }
 
 int tc_launches_per_apply(const tpcg_plan* p) {
   const TcPlan* tp = reinterpret_cast<const TcPlan*>(p->tc_state);
   if (!tp) return 0;
+  if (p->tc_slab && p->slab_state) return slab_launches_per_apply(p);
   return (int)((p->tc_fuse && !tp->fused.empty()) ? tp->fused.size() : tp->stages.size());
 }
 
 void tc_plan_release(tpcg_plan* p) {
+  slab_plan_release(p);
   delete reinterpret_cast<TcPlan*>(p->tc_state);
   p->tc_state = nullptr;
 }
@@ -1428,6 +1255,7 @@ void tc_plan_release(tpcg_plan* p) {
 int run_precond_tc(const tpcg_plan* p, float* Z, SolveState* st) {
   const TcPlan* tp = reinterpret_cast<const TcPlan*>(p->tc_state);
   if (!tp) return TPCG_ERR_UNSUPPORTED;
+  if (p->tc_slab && p->slab_state && (void*)Z == p->d_Z) return run_precond_slab(p, Z, st);
   const std::vector<TcStage>& seq = (p->tc_fuse && !tp->fused.empty()) ? tp->fused : tp->stages;
   const int ns = (int)seq.size();
   for (int si = 0; si < ns; ++si) {

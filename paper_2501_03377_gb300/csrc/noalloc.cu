@@ -15,6 +15,7 @@
 // 7-point stencil of eq. ourproblem with the same ghost values and a
 // deterministic two-stage reduction, one grid point per thread with direct
 // neighbour loads, and no residual vector is written.
+#include <cmath>
 #include <mutex>
 
 #include "tpcg_dev.cuh"
@@ -35,24 +36,52 @@ struct NoAllocScratch {
 static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
 
 constexpr int kMaxDevices = 64;
-NoAllocScratch* g_scratch_addr[kMaxDevices] = {};
+// Per device: the context the address was looked up in and the address.  A new primary context (after
+// cudaDeviceReset) loads the module again and moves the array, so the address is looked up again
+// whenever the current context is not the one it was taken in.
+struct ScratchSlot {
+  void* ctx = nullptr;
+  NoAllocScratch* addr = nullptr;
+};
+ScratchSlot g_scratch_slot[kMaxDevices];
 std::mutex g_scratch_mutex;
 
-// Device address of the static scratch for the current device (looked up once
-// per device; cudaGetSymbolAddress allocates nothing).
-int scratch_for_current_device(NoAllocScratch** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TPCG_ERR_CUDA;
+typedef int (*CtxGetCurrentFn)(void**);  // cuCtxGetCurrent (CUresult, CUcontext*)
+
+// The driver's current context of this thread (looked up through the runtime: no driver library link).
+void* current_context() {
+  static CtxGetCurrentFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &ptr, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(ptr);
+    tried = true;
+  }
+  void* ctx = nullptr;
+  if (fn && fn(&ctx) != 0) ctx = nullptr;
+  return ctx;
+}
+
+// Device address of the static scratch for the current device, looked up with the device current the
+// first time it is used in a context (cudaGetSymbolAddress allocates nothing).
+int scratch_for_current_device(int dev, NoAllocScratch** out) {
+  if (dev < 0 || dev >= kMaxDevices) return TPCG_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_addr[dev]) {
+  ScratchSlot& slot = g_scratch_slot[dev];
+  void* ctx = current_context();
+  if (!slot.addr || slot.ctx != ctx) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
       return TPCG_ERR_CUDA;
     }
-    g_scratch_addr[dev] = reinterpret_cast<NoAllocScratch*>(p);
+    slot.addr = reinterpret_cast<NoAllocScratch*>(p);
+    slot.ctx = ctx;
   }
-  *out = g_scratch_addr[dev];
+  *out = slot.addr;
   return TPCG_OK;
 }
 
@@ -121,12 +150,18 @@ extern "C" int tpcg_residual_norms_noalloc(int nx, int ny, int nz, const int bc[
   const int naxes = (nz == 1) ? 2 : 3;
   for (int m = 0; m < naxes; ++m) {
     if (bc[m] < 0 || bc[m] > 4) return TPCG_ERR_INVALID_ARG;
-    if (!(h[m] > 0.0) || !(h[m] < 1e300)) return TPCG_ERR_INVALID_ARG;
+    if (!(h[m] > 0.0) || !std::isfinite(h[m])) return TPCG_ERR_INVALID_ARG;  // as tpcg_plan_create
   }
   const long long N = (long long)nx * ny * nz;
   if (N > 2147483647LL) return TPCG_ERR_UNSUPPORTED;  // beyond the supported grid size
+  // an error left pending by the caller's own work is theirs: report it without consuming it
+  if (cudaPeekAtLastError() != cudaSuccess) return TPCG_ERR_CUDA;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TPCG_ERR_CUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+    return TPCG_ERR_CUDA;
   NoAllocScratch* s = nullptr;
-  int rc = scratch_for_current_device(&s);
+  int rc = scratch_for_current_device(dev, &s);
   if (rc) return rc;
   Geom g{};
   g.nx = nx;
@@ -142,15 +177,13 @@ extern "C" int tpcg_residual_norms_noalloc(int nx, int ny, int nz, const int bc[
   }
   g.uniform = (g.ih2[0] == g.ih2[1]) && (naxes == 2 || g.ih2[2] == g.ih2[0]);
   g.N = N;
-  int dev = 0, sms = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long long want = (N + 255) / 256;
   const int blocks = (int)std::min<long long>(std::min<long long>(want, (long long)sms * 8), kNaMaxBlocks);
   cudaStream_t st = (cudaStream_t)stream;
   // the arrival counters must start at zero; an aborted earlier call may have left them set
   if (cudaMemsetAsync(s->tickets, 0, sizeof(s->tickets), st) != cudaSuccess) return TPCG_ERR_CUDA;
   k_na_eta_sum<<<blocks, 256, 0, st>>>(N, eta, s, singular ? 1 : 0);
+  if (cudaGetLastError() != cudaSuccess) return TPCG_ERR_CUDA;
   k_na_residual<<<blocks, 256, 0, st>>>(g, eta, ups, s, out);
   if (cudaGetLastError() != cudaSuccess) return TPCG_ERR_CUDA;
   return TPCG_OK;

@@ -60,6 +60,9 @@ struct Request {
   double* ups_host = nullptr;  // pinned result
   long long N = 0;
   Clock::time_point t_submit, t_done;
+  Clock::time_point t_admit, t_started, t_solved;  // admitted; plan ready and solve enqueued; solution on device
+  bool admitted = false, solved = false;
+  int plan_built = 0;  // the plan was created for this request (not found idle in the cache)
   int status = TPCG_PENDING;
   tpcg_info info{};
 };
@@ -106,6 +109,7 @@ struct tpcg_server {
   size_t used = 0;
   unsigned long long submitted = 0, completed = 0, failed = 0, rejected = 0;
   std::vector<double> latencies_ms;
+  std::vector<tpcg_request_timing> timings;  // one record per finished request since the last reset
   std::multimap<size_t, void*> pinned_pool;  // released pinned host buffers, by size
   tpcg::Clock::time_point t_first, t_last_done;
   bool have_first = false;
@@ -179,12 +183,40 @@ int running_slots(const tpcg_server* s) {
   return n;
 }
 
+double ms_between(Clock::time_point a, Clock::time_point b) {
+  return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+constexpr size_t kMaxTimingRecords = 1u << 20;
+
 void finish_request(tpcg_server* s, Request* r, int status) {
   r->status = status;
   r->t_done = Clock::now();
   s->t_last_done = r->t_done;
-  const double ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+  const double ms = ms_between(r->t_submit, r->t_done);
   s->latencies_ms.push_back(ms);
+  if (s->timings.size() < kMaxTimingRecords) {
+    tpcg_request_timing t;
+    std::memset(&t, 0, sizeof(t));
+    t.ticket = r->ticket;
+    t.session = r->req.session;
+    t.nx = r->req.nx;
+    t.ny = r->req.ny;
+    t.nz = r->req.nz;
+    t.prec = r->req.prec;
+    t.status = status;
+    t.iters = r->info.iters;
+    t.plan_built = r->plan_built;
+    const Clock::time_point ta = r->admitted ? r->t_admit : r->t_done;
+    const Clock::time_point tb = r->admitted ? r->t_started : r->t_done;
+    const Clock::time_point tc = r->solved ? r->t_solved : r->t_done;
+    t.queue_ms = ms_between(r->t_submit, ta);
+    t.build_ms = ms_between(ta, tb);
+    t.solve_ms = r->admitted ? ms_between(tb, tc) : 0.0;
+    t.copy_ms = r->solved ? ms_between(tc, r->t_done) : 0.0;
+    t.total_ms = ms;
+    s->timings.push_back(t);
+  }
   if (status == TPCG_OK) ++s->completed;
   else ++s->failed;
   if (r->req.session) {
@@ -227,6 +259,9 @@ bool try_admit(tpcg_server* s, Request* r, bool* reject) {
     unreserve();
     return false;
   }
+  r->t_admit = Clock::now();
+  r->admitted = true;
+  r->plan_built = 0;
   if (ses_need) {
     auto sit = s->sessions.find(r->req.session);
     if (sit != s->sessions.end()) {  // grid changed: drop the old solution
@@ -238,6 +273,7 @@ bool try_admit(tpcg_server* s, Request* r, bool* reject) {
     if (cudaMalloc((void**)&ns.d_ups, ses_need) != cudaSuccess) {
       cudaGetLastError();
       unreserve();
+      r->admitted = false;
       return false;
     }
     ns.N = r->N;
@@ -247,6 +283,7 @@ bool try_admit(tpcg_server* s, Request* r, bool* reject) {
     ses = &(s->sessions[r->req.session] = ns);
   }
   if (slot == s->slots.end()) {
+    r->plan_built = 1;
     Slot ns;
     ns.key = r->key;
     if (cudaStreamCreateWithFlags(&ns.stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -281,6 +318,7 @@ bool try_admit(tpcg_server* s, Request* r, bool* reject) {
     slot = std::prev(s->slots.end());
   }
   // start the solve
+  r->t_started = Clock::now();
   Slot& sl = *slot;
   sl.req = r;
   sl.last_used = Clock::now();
@@ -366,6 +404,8 @@ void worker_main(tpcg_server* s) {
         if (rc == TPCG_OK && sl.job.phase == 3) {
           Request* r = sl.req;
           r->info = sl.job.info;
+          r->t_solved = Clock::now();
+          r->solved = true;
           if (cudaMemcpyAsync(r->ups_host, sl.job.ups, (size_t)r->N * 8, cudaMemcpyDeviceToHost, sl.stream) !=
                   cudaSuccess ||
               cudaEventRecord(sl.ev, sl.stream) != cudaSuccess)
@@ -557,10 +597,20 @@ int tpcg_server_get_stats(tpcg_server* s, tpcg_server_stats* out) {
   return TPCG_OK;
 }
 
+int tpcg_server_get_timings(tpcg_server* s, tpcg_request_timing* out, int max_records, int* n_records) {
+  if (!s || !n_records || max_records < 0 || (max_records > 0 && !out)) return TPCG_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(s->mu);
+  const int n = (int)std::min<size_t>(s->timings.size(), (size_t)max_records);
+  if (n > 0) std::memcpy(out, s->timings.data(), sizeof(tpcg_request_timing) * (size_t)n);
+  *n_records = max_records == 0 ? (int)s->timings.size() : n;
+  return TPCG_OK;
+}
+
 int tpcg_server_reset_stats(tpcg_server* s) {
   if (!s) return TPCG_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lock(s->mu);
   s->latencies_ms.clear();
+  s->timings.clear();
   s->submitted = s->completed = s->failed = s->rejected = 0;
   s->have_first = false;
   return TPCG_OK;

@@ -143,6 +143,7 @@ struct tpcg_plan {
 
   std::vector<tpcg::StageParams> stages;
   void* tc_state = nullptr;   // tensor-core pass descriptors (tensor maps, launch shapes)
+  void* slab_state = nullptr; // frontal-slice launch descriptors (3D grids where they apply)
   mutable unsigned long long launch_count = 0;   // kernels launched by this plan
   mutable tpcg::Profiler prof;
   size_t device_bytes = 0;
@@ -160,5 +161,6 @@ struct tpcg_plan {
   int stream_blocks = 0;    // streaming kernels
   int defer_u = 0;          // mixed forms: TPCG_OPT_DEFER_U (U += alpha P recorded, applied by k_form_u)
   int tc_fuse = 1;          // mixed forms: TPCG_OPT_FUSE_G (the two passes around G in one launch)
+  int tc_slab = 1;          // mixed forms: TPCG_OPT_SLICES (frontal-slice launches where they apply)
   int last_iters = 0;      // iterations of the plan's previous converged solve (first chunk of the next)
 };

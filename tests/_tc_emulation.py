@@ -1,0 +1,96 @@
+"""Numpy emulation of the mixed tensor-core preconditioner (Algorithm 7) with the device's rounding points.
+
+Test infrastructure shared by the GPU parity tests and the CPU experiments on the precision readings:
+BF16 / FP16 rounding of FP64 and FP32 values (nearest even), mode products in FP32, the power-of-two
+scalings of the FP16 form, and the order in which each launch sequence rounds its intermediates.
+"""
+import numpy as np
+
+
+def bf16_from_f64(x):
+    """Round float64 -> bfloat16 (nearest-even) in one step; returned as float32."""
+    x = np.asarray(x, dtype=np.float64)
+    u = x.view(np.uint64)
+    sign = (u >> np.uint64(63)) << np.uint64(15)
+    e = ((u >> np.uint64(52)) & np.uint64(0x7FF)).astype(np.int64)
+    eb = e - 1023 + 127
+    mant = u & np.uint64(0xFFFFFFFFFFFFF)
+    top = (mant >> np.uint64(45)).astype(np.uint64)
+    rest = mant & np.uint64((1 << 45) - 1)
+    half = np.uint64(1 << 44)
+    bits = (np.clip(eb, 0, 255).astype(np.uint64) << np.uint64(7)) | top
+    up = (rest > half) | ((rest == half) & ((top & np.uint64(1)) == np.uint64(1)))
+    bits = bits + up.astype(np.uint64)
+    bits = np.where(eb <= 0, np.uint64(0), bits)
+    b16 = (sign | bits).astype(np.uint32)
+    return (b16 << np.uint32(16)).view(np.float32)
+
+
+def bf16_from_f32(x):
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    u = x.view(np.uint32).astype(np.uint64)
+    lsb = (u >> np.uint64(16)) & np.uint64(1)
+    u = (u + np.uint64(0x7FFF) + lsb) >> np.uint64(16)
+    return (u.astype(np.uint32) << np.uint32(16)).view(np.float32)
+
+
+def mode(M, X, m):
+    """M x_m X in float32 (float32 accumulation)."""
+    Y = np.tensordot(M.astype(np.float32), np.moveaxis(X, m, 0).astype(np.float32), axes=(1, 0))
+    return np.moveaxis(Y, 0, m).astype(np.float32)
+
+
+def f16_from_f32(x):
+    return np.asarray(x, dtype=np.float32).astype(np.float16).astype(np.float32)
+
+
+def f16_from_f64(x, shift=0):
+    """x * 2^shift rounded once to binary16 (nearest-even), returned as float32."""
+    return np.ldexp(np.asarray(x, dtype=np.float64), shift).astype(np.float16).astype(np.float32)
+
+
+def lp_shift(r):
+    rms = np.sqrt(np.mean(np.asarray(r, dtype=np.float64) ** 2))
+    return 0 if rms == 0 else int(np.clip(-np.floor(np.log2(rms)) - 1, -120, 120))
+
+
+def fp16_gscale_exponent(lams, N):
+    cands = [np.unique(np.asarray(l))[:2] for l in lams]
+    sums = [x + y + z for x in cands[0] for y in cands[1] for z in cands[2] if x + y + z > 1e-300]
+    bound = np.sqrt(N) / min(sums)
+    return max(0, int(np.ceil(np.log2(bound / 16384.0))))
+
+
+def emulate_precond(r_nqt, Vs, lams, singular, prec="bf16", slices=False):
+    """The tensor-core form of Algorithm 7 with its rounding points (BF16, or FP16 with the
+    power-of-two scalings that keep every intermediate in range).  slices: the frontal-slice launch
+    sequence, whose backward x product precedes the backward y product."""
+    three_d = r_nqt.shape[2] > 1
+    if prec == "bf16":
+        rin, rd, Vb = (lambda x: bf16_from_f64(x)), bf16_from_f32, [bf16_from_f64(V) for V in Vs]
+        s, sG = 0, 0
+    else:
+        s = lp_shift(r_nqt)
+        sG = fp16_gscale_exponent(lams, r_nqt.size)
+        rin, rd, Vb = (lambda x: f16_from_f64(x, s)), f16_from_f32, [f16_from_f64(V) for V in Vs]
+    F = rin(r_nqt)
+    F = rd(mode(Vb[0].T, F, 0))
+    F = mode(Vb[1].T, F, 1)
+    if three_d:
+        F = rd(F)
+        F = mode(Vb[2].T, F, 2)
+    la = [np.asarray(l, dtype=np.float32) for l in lams]
+    S = (la[0][:, None, None] + la[1][None, :, None]) + la[2][None, None, :]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        g = ((np.float32(1.0) / S).astype(np.float32) * np.float32(2.0 ** -sG)).astype(np.float32)
+        F = (F * g).astype(np.float32)
+    if singular:
+        F[0, 0, 0] = 0.0
+    F = rd(F)
+    if three_d:
+        F = rd(mode(Vb[2], F, 2))
+    if slices:
+        F = rd(mode(Vb[0], F, 0))
+        return (mode(Vb[1], F, 1) * np.float32(2.0 ** (sG - s))).astype(np.float32)
+    F = rd(mode(Vb[1], F, 1))
+    return (mode(Vb[0], F, 0) * np.float32(2.0 ** (sG - s))).astype(np.float32)

@@ -17,6 +17,7 @@ import pytest
 
 import oracle as o
 from inputs import synth
+from tests._tc_emulation import emulate_precond
 from tests._util import from_oracle, oracle_bcs, rel_err, to_oracle
 
 pytestmark = pytest.mark.gpu
@@ -42,89 +43,11 @@ def _dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", torch.float64)
 
 
-def bf16_from_f64(x):
-    """Round float64 -> bfloat16 (nearest-even) in one step; returned as float32."""
-    x = np.asarray(x, dtype=np.float64)
-    u = x.view(np.uint64)
-    sign = (u >> np.uint64(63)) << np.uint64(15)
-    e = ((u >> np.uint64(52)) & np.uint64(0x7FF)).astype(np.int64)
-    eb = e - 1023 + 127
-    mant = u & np.uint64(0xFFFFFFFFFFFFF)
-    top = (mant >> np.uint64(45)).astype(np.uint64)
-    rest = mant & np.uint64((1 << 45) - 1)
-    half = np.uint64(1 << 44)
-    bits = (np.clip(eb, 0, 255).astype(np.uint64) << np.uint64(7)) | top
-    up = (rest > half) | ((rest == half) & ((top & np.uint64(1)) == np.uint64(1)))
-    bits = bits + up.astype(np.uint64)
-    bits = np.where(eb <= 0, np.uint64(0), bits)
-    b16 = (sign | bits).astype(np.uint32)
-    return (b16 << np.uint32(16)).view(np.float32)
+def uses_slices(pl, nz):
+    """The plan applies its preconditioner by the frontal-slice launches (three, or four when the z
+    axis exceeds 128 points); one launch per mode product otherwise (five or six in 3D)."""
+    return nz > 1 and pl.precond_launches() <= 4
 
-
-def bf16_from_f32(x):
-    x = np.ascontiguousarray(x, dtype=np.float32)
-    u = x.view(np.uint32).astype(np.uint64)
-    lsb = (u >> np.uint64(16)) & np.uint64(1)
-    u = (u + np.uint64(0x7FFF) + lsb) >> np.uint64(16)
-    return (u.astype(np.uint32) << np.uint32(16)).view(np.float32)
-
-
-def mode(M, X, m):
-    """M x_m X in float32 (float32 accumulation)."""
-    Y = np.tensordot(M.astype(np.float32), np.moveaxis(X, m, 0).astype(np.float32), axes=(1, 0))
-    return np.moveaxis(Y, 0, m).astype(np.float32)
-
-
-def f16_from_f32(x):
-    return np.asarray(x, dtype=np.float32).astype(np.float16).astype(np.float32)
-
-
-def f16_from_f64(x, shift=0):
-    """x * 2^shift rounded once to binary16 (nearest-even), returned as float32."""
-    return np.ldexp(np.asarray(x, dtype=np.float64), shift).astype(np.float16).astype(np.float32)
-
-
-def lp_shift(r):
-    rms = np.sqrt(np.mean(np.asarray(r, dtype=np.float64) ** 2))
-    return 0 if rms == 0 else int(np.clip(-np.floor(np.log2(rms)) - 1, -120, 120))
-
-
-def fp16_gscale_exponent(lams, N):
-    cands = [np.unique(np.asarray(l))[:2] for l in lams]
-    sums = [x + y + z for x in cands[0] for y in cands[1] for z in cands[2] if x + y + z > 1e-300]
-    bound = np.sqrt(N) / min(sums)
-    return max(0, int(np.ceil(np.log2(bound / 16384.0))))
-
-
-def emulate_precond(r_nqt, Vs, lams, singular, prec="bf16"):
-    """The tensor-core form of Algorithm 7 with its rounding points (BF16, or FP16 with the
-    power-of-two scalings that keep every intermediate in range)."""
-    three_d = r_nqt.shape[2] > 1
-    if prec == "bf16":
-        rin, rd, Vb = (lambda x: bf16_from_f64(x)), bf16_from_f32, [bf16_from_f64(V) for V in Vs]
-        s, sG = 0, 0
-    else:
-        s = lp_shift(r_nqt)
-        sG = fp16_gscale_exponent(lams, r_nqt.size)
-        rin, rd, Vb = (lambda x: f16_from_f64(x, s)), f16_from_f32, [f16_from_f64(V) for V in Vs]
-    F = rin(r_nqt)
-    F = rd(mode(Vb[0].T, F, 0))
-    F = mode(Vb[1].T, F, 1)
-    if three_d:
-        F = rd(F)
-        F = mode(Vb[2].T, F, 2)
-    la = [np.asarray(l, dtype=np.float32) for l in lams]
-    S = (la[0][:, None, None] + la[1][None, :, None]) + la[2][None, None, :]
-    with np.errstate(divide="ignore"):
-        g = ((np.float32(1.0) / S).astype(np.float32) * np.float32(2.0 ** -sG)).astype(np.float32)
-        F = (F * g).astype(np.float32)
-    if singular:
-        F[0, 0, 0] = 0.0
-    F = rd(F)
-    if three_d:
-        F = rd(mode(Vb[2], F, 2))
-    F = rd(mode(Vb[1], F, 1))
-    return (mode(Vb[0], F, 0) * np.float32(2.0 ** (sG - s))).astype(np.float32)
 
 
 def emulate_bf16_precond(r_nqt, Vs, lams, singular):
@@ -152,15 +75,28 @@ CASES = [
     ((256, 256, 8), ("P", "P", "N")),
     ((96, 160, 96), ("N", "D", "P")),
     ((200, 40, 256), ("P", "N", "D")),
+    ((16, 3, 3), ("P", "D", "N")),        # frontal slices with a 3-point y axis: one padded N block
+    ((48, 40, 200), ("N", "P", "D")),     # z axis past 128: the tube products as two launches
+    ((256, 40, 200), ("DN", "N", "P")),
+    ((32, 256, 3), ("P", "P", "N")),
 ]
 
 
+@pytest.mark.parametrize("slices", [1, 0])
 @pytest.mark.parametrize("prec", ["bf16", "fp16"])
 @pytest.mark.parametrize("shape,bcs", CASES)
-def test_precond_tc_matches_emulation_and_oracle(shape, bcs, prec):
+def test_precond_tc_matches_emulation_and_oracle(shape, bcs, prec, slices):
+    from paper_2501_03377_gb300 import binding as b
+
     nx, ny, nz = shape
     r = synth.random_field(nx, ny, nz, seed=21)
     pl = _plan(nx, ny, nz, bcs, prec)
+    pl.set_option(b.TPCG_OPT_SLICES, slices)
+    sl = uses_slices(pl, nz)
+    if slices == 0:
+        assert not sl
+    elif nz > 1 and nx % 16 == 0:
+        assert sl
     rd = _dev(r)
     zd = torch.empty_like(rd)
     pl.precond(rd, zd)
@@ -169,12 +105,12 @@ def test_precond_tc_matches_emulation_and_oracle(shape, bcs, prec):
     sh = (nx, ny, nz)
     ob = oracle_bcs(bcs, nz)
     Vs, lams = plan_bases(pl, sh)
-    emu = from_oracle(emulate_precond(to_oracle(r), Vs, lams, o.is_singular(sh, ob), prec))
+    emu = from_oracle(emulate_precond(to_oracle(r), Vs, lams, o.is_singular(sh, ob), prec, slices=sl))
     e_emu = rel_err(z, emu)
     Vo, _, G = o.pinv_init(sh, ob)
     ref = from_oracle(o.pinv_apply(to_oracle(r), Vo, G))
     e_ref = rel_err(z, ref)
-    print(f"{prec} {shape} {bcs}: |z - emulation| = {e_emu:.2e}, |z - fp64 oracle| = {e_ref:.2e}")
+    print(f"{prec} {shape} {bcs} slices={int(sl)}: |z - emulation| = {e_emu:.2e}, |z - fp64 oracle| = {e_ref:.2e}")
     # one ulp: 2^-8 (BF16), 2^-11 (FP16); summation-order flips are rare
     assert e_emu <= (4e-3 if prec == "bf16" else 5e-4)
     assert e_ref <= (5e-2 if prec == "bf16" else 6e-3)
@@ -230,23 +166,25 @@ def test_tc_solve_deterministic(prec):
     assert np.array_equal(outs[0], outs[1])
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp16"])
-def test_cuboid_256_tc_full_size(prec):
-    """256x256x128 P/P/N cuboid (singular), mixed forms, tol 1e-10, in the bench's launch configuration.
+@pytest.mark.parametrize("prec,nz", [("bf16", 128), ("fp16", 128), ("fp16", 256)])
+def test_cuboid_256_tc_full_size(prec, nz):
+    """256x256x128 P/P/N cuboid (singular), mixed forms, tol 1e-10, in the bench's launch configuration,
+    and the 256x256x256 cube (the z axis past 128 points: the tube products as two launches).
     Checked by properties that hold at any size (true residual recomputed on the host with the
     assembled operator, zero mean) and against the oracle's direct pseudoinverse solution."""
-    w = synth.workload_cuboid_256(seed=0)
+    w = synth.workload_cuboid_256(seed=0, nz=nz)
     pl = _plan(w["nx"], w["ny"], w["nz"], w["bcs"], prec)
+    assert uses_slices(pl, nz) and pl.precond_launches() == (3 if nz <= 128 else 4)
     ed = _dev(w["eta"])
     ud = torch.zeros_like(ed)
     st, info = pl.solve(ed, ud, tol=1e-10, maxit=60, zero_guess=True)
     assert st == 0, info
     u = ud.cpu().numpy()
-    sh = (256, 256, 128)
+    sh = (256, 256, nz)
     L = o.kron_sum(sh, w["bcs"])
     etah = o.center(to_oracle(w["eta"]))
     true_res = np.linalg.norm(o.vec(etah) - L @ o.vec(to_oracle(u))) / np.linalg.norm(etah)
-    print(f"256x256x128 {prec}: iters={info['iters']} rel_res_true={true_res:.2e}")
+    print(f"256x256x{nz} {prec}: iters={info['iters']} rel_res_true={true_res:.2e}")
     assert true_res <= 1e-10
     assert abs(u.mean()) <= 1e-14 * np.abs(u).max()
     Vs, _, G = o.pinv_init(sh, w["bcs"])
@@ -385,12 +323,14 @@ FUSE_CASES = [
 ]
 
 
+@pytest.mark.parametrize("slices", [0, 1])
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
 @pytest.mark.parametrize("shape,bcs", FUSE_CASES)
-def test_fused_pair_is_bitwise_the_two_passes(shape, bcs, prec):
+def test_fused_pair_is_bitwise_the_two_passes(shape, bcs, prec, slices):
     """TPCG_OPT_FUSE_G runs the forward and the backward mode product around G in one kernel: the same
     MMAs in the same order and the same rounding of the intermediate, so Z is bitwise that of one launch
-    per pass."""
+    per pass.  With the frontal-slice launches the z products and G form one tube-pair launch instead of
+    two single tube passes, with the same guarantee."""
     from paper_2501_03377_gb300 import binding as b
 
     nx, ny, nz = shape
@@ -399,6 +339,7 @@ def test_fused_pair_is_bitwise_the_two_passes(shape, bcs, prec):
     outs = []
     for fuse in (0, 1):
         pl = _plan(nx, ny, nz, bcs, prec)
+        pl.set_option(b.TPCG_OPT_SLICES, slices)
         pl.set_option(b.TPCG_OPT_FUSE_G, fuse)
         zd = torch.full_like(rd, float("nan"))
         pl.precond(rd, zd)
@@ -406,9 +347,12 @@ def test_fused_pair_is_bitwise_the_two_passes(shape, bcs, prec):
         outs.append(zd.cpu().numpy())
     assert np.isfinite(outs[1]).all()
     assert np.array_equal(outs[0], outs[1])
-    fusable = shape != (37, 9, 5)
-    full = 6 if nz > 1 else 4
-    assert pl.precond_launches() == full - (1 if fusable else 0)
+    if slices and nz > 1 and nx % 16 == 0:
+        assert pl.precond_launches() == (3 if nz <= 128 else 4)
+    else:
+        fusable = shape != (37, 9, 5)
+        full = 6 if nz > 1 else 4
+        assert pl.precond_launches() == full - (1 if fusable else 0)
 
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
@@ -439,3 +383,34 @@ def test_plan_option_rejects_bad_values():
     assert b.tpcg_plan_set_option(pl.handle, b.TPCG_OPT_DEFER_U, 1) == b.TPCG_OK
     assert b.tpcg_plan_set_option(pl.handle, b.TPCG_OPT_FUSE_G, 2) == b.TPCG_ERR_INVALID_ARG
     assert b.tpcg_plan_set_option(pl.handle, b.TPCG_OPT_FUSE_G, 0) == b.TPCG_OK
+    assert b.tpcg_plan_set_option(pl.handle, b.TPCG_OPT_SLICES, 2) == b.TPCG_ERR_INVALID_ARG
+    assert b.tpcg_plan_set_option(pl.handle, b.TPCG_OPT_SLICES, 0) == b.TPCG_OK
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_defer_u_set_between_solves_is_bitwise(prec):
+    """TPCG_OPT_DEFER_U switched on between two solves of one plan (the direction storage is replaced
+    once the first solve's work has finished): the second solve equals, bitwise, the same solve on a
+    plan that had the option from the start, and the in-place update of a fresh plan."""
+    from paper_2501_03377_gb300 import binding as b
+
+    nx, ny, nz, bcs = 64, 48, 32, ("P", "P", "N")
+    e1 = _dev(synth.defect_rhs(nx, ny, nz, bcs, 12, 1.5, seed=93))
+    e2 = _dev(synth.defect_rhs(nx, ny, nz, bcs, 12, 1.5, seed=94))
+    pl = _plan(nx, ny, nz, bcs, prec)
+    u1 = torch.zeros_like(e1)
+    assert pl.solve(e1, u1, tol=1e-10, maxit=60, zero_guess=True)[0] == 0
+    pl.set_option(b.TPCG_OPT_DEFER_U, 1)
+    u2 = torch.zeros_like(e2)
+    st, info = pl.solve(e2, u2, tol=1e-10, maxit=60, zero_guess=True)
+    assert st == 0
+    outs = []
+    for defer in (1, 0):
+        q = _plan(nx, ny, nz, bcs, prec)
+        q.set_option(b.TPCG_OPT_DEFER_U, defer)
+        u = torch.zeros_like(e2)
+        stq, iq = q.solve(e2, u, tol=1e-10, maxit=60, zero_guess=True)
+        assert stq == 0 and iq["iters"] == info["iters"]
+        outs.append(u.cpu().numpy())
+    assert np.array_equal(u2.cpu().numpy(), outs[0])
+    assert np.array_equal(outs[0], outs[1])
