@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=400)
+    ap.add_argument("--serving-requests", type=int, default=2000)
     ap.add_argument("--serving-rate", type=float, default=200.0)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-comparators", action="store_true")
@@ -232,61 +232,116 @@ def time_steps(plan, etas, ups, steps, tol, torch, barrier, sampler=None):
     return dt, infos, clocks
 
 
-def run_serving(args, prec):
-    """Poisson request stream from 16 warm-started sessions (grids 64..256 x 64..256 x 32..192, random BCs)."""
+def _pct(v, p):
+    import numpy as np
+
+    return float(np.percentile(np.asarray(v, dtype=np.float64), p)) if len(v) else None
+
+
+def serving_stream(args, prec, torch):
+    """One request stream: Poisson arrivals at --serving-rate from 16 warm-started sessions (grids 64..256 x
+    64..256 x 32..192, random BCs); every request is the session's next time step, 1% of its defects moved
+    since the previous step.  Each session keeps two pinned right-hand-side buffers (lent to the server):
+    the buffer of step k held step k-2 and is brought to step k by the moves of steps k-1 and k, after step
+    k-2's request has finished.  The field is scaled to the paper's norm on the first step, and that scale
+    is kept (warm starts see a consistent time series)."""
     import numpy as np
 
     from inputs import synth
     from paper_2501_03377_gb300 import Server
 
-    import torch
-
     sessions = synth.serving_sessions(seed=0)
-    steps = 3
-    rhs = []
-    for ses in sessions:  # pinned host right-hand sides, lent to the server (no copy at submit)
-        per = []
-        for _ in range(steps):
-            per.append(torch.from_numpy(ses.rhs()).pin_memory())
-            ses.step()
-        rhs.append(per)
-    arrivals = synth.poisson_arrivals(args.serving_rate, args.serving_requests, seed=1)
-    order = np.random.default_rng(2).integers(0, len(sessions), size=args.serving_requests)
+    scales = [ses.paper_scale() for ses in sessions]
+    bufs = []
+    for ses, sc in zip(sessions, scales):
+        f = torch.from_numpy(sc * synth.gaussian_defects(
+            (ses.nz, ses.ny, ses.nx), tuple(b == "P" for b in ses.bcs), ses.centres,
+            np.full(len(ses.charges), ses.sigma), ses.charges, "charge")).pin_memory()
+        bufs.append([f, f.clone().pin_memory()])
+    state = [[0, 0] for _ in sessions]       # step each buffer holds
+    moves = [[None] for _ in sessions]       # moves[i][k]: the moves of step k (k >= 1)
+    pending = [[None, None] for _ in sessions]  # ticket of the request that borrowed each buffer
+    steps = [0] * len(sessions)
+    n = args.serving_requests
+    arrivals = synth.poisson_arrivals(args.serving_rate, n, seed=1)
+    order = np.random.default_rng(2).integers(0, len(sessions), size=n)
     srv = Server(max_slots=8)
-    # warm-up outside the measurement: one request per session builds its plan and session state
-    for i in range(len(sessions)):
-        srv.wait(srv.submit(rhs[i][0], sessions[i].bcs, prec=prec, session=i + 1, borrow=True), 120.0)
+    results = {}
+
+    def collect(t):
+        st, _, info = srv.wait(t, 600.0, want=False)
+        results[t] = (st, info)
+
+    # warm-up outside the measurement: one request per session builds its plan and session state (step 0)
+    for i, ses in enumerate(sessions):
+        collect(srv.submit(bufs[i][0], ses.bcs, prec=prec, session=i + 1, borrow=True))
     srv.reset_stats()
-    counters = [1] * len(sessions)
-    tickets = []
+    results.clear()
+    tickets, lag = [], []
     t0 = time.perf_counter()
-    for k in range(args.serving_requests):
+    for k in range(n):
+        i = int(order[k])
+        ses = sessions[i]
+        steps[i] += 1
+        step = steps[i]
+        moves[i].append(ses.step())
+        b = step % 2
+        if pending[i][b] is not None:  # the request of step - 2 still borrows this buffer
+            collect(pending[i][b])
+        buf = bufs[i][b]
+        a = buf.numpy()
+        for m in range(state[i][b] + 1, step + 1):
+            ses.apply_moves(a, moves[i][m], scales[i])
+        state[i][b] = step
         delay = t0 + arrivals[k] - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
-        i = int(order[k])
-        tickets.append(srv.submit(rhs[i][counters[i] % steps], sessions[i].bcs, prec=prec, session=i + 1,
-                                  borrow=True))
-        counters[i] += 1
-    worst, bad, iters = 0.0, 0, []
+        lag.append(max(0.0, -delay) * 1e3)
+        t = srv.submit(buf, ses.bcs, prec=prec, session=i + 1, borrow=True)
+        pending[i][b] = t
+        tickets.append(t)
     for t in tickets:
-        st, _, info = srv.wait(t, 300.0)
-        bad += st != 0
-        if info:
-            worst = max(worst, info["rel_res_true"])
-            iters.append(info["iters"])
-    t1 = time.perf_counter()
+        if t not in results:
+            collect(t)
     stats = srv.stats()
+    tim = srv.timings()
     srv.close()
-    # latency percentiles of the measured requests only
-    return {"requests": args.serving_requests, "rate_hz": args.serving_rate, "sessions": len(sessions),
-            "form": f"mixed-{prec}", "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"],
-            "mean_ms": stats["mean_ms"], "solves_per_s": stats["completed"] / stats["elapsed_s"],
-            "offered_span_s": float(arrivals[-1]),
-            "failed": bad, "worst_rel_res_true": worst, "mean_iters": float(np.mean(iters)) if iters else None,
-            "latency_note": "submit call -> solution in pinned host memory (H2D of the lent pinned eta, the "
-                            "solve, D2H); one warm-up request per session excluded",
-            "warmup_requests": len(sessions)}
+    ok = [results[t] for t in tickets]
+    worst = max((info["rel_res_true"] for st, info in ok if info), default=None)
+    iters = [info["iters"] for st, info in ok if info]
+    total = [r["total_ms"] for r in tim]
+    out = {"requests": n, "rate_hz": args.serving_rate, "sessions": len(sessions), "form": prec,
+           "p50_ms": stats["p50_ms"], "p99_ms": stats["p99_ms"], "mean_ms": stats["mean_ms"],
+           "solves_per_s": stats["completed"] / stats["elapsed_s"] if stats["elapsed_s"] else None,
+           "offered_span_s": float(arrivals[-1]), "failed": sum(1 for st, _ in ok if st != 0),
+           "worst_rel_res_true": worst, "mean_iters": float(np.mean(iters)) if iters else None,
+           "submit_lag_p99_ms": _pct(lag, 99),
+           "plan_builds": sum(r["plan_built"] for r in tim)}
+    # where the latency goes: mean of each cause overall, over the slowest 1 %, and per grid
+    causes = ("queue_ms", "build_ms", "solve_ms", "copy_ms")
+    out["mean_by_cause_ms"] = {c: float(np.mean([r[c] for r in tim])) for c in causes} if tim else None
+    if tim:
+        cut = _pct(total, 99)
+        tail = [r for r in tim if r["total_ms"] >= cut]
+        out["p99_tail_by_cause_ms"] = {c: float(np.mean([r[c] for r in tail])) for c in causes}
+        out["p99_tail_grids"] = sorted({f"{r['nx']}x{r['ny']}x{r['nz']}" for r in tail})
+        grids = {}
+        for r in tim:
+            grids.setdefault((r["nx"], r["ny"], r["nz"]), []).append(r)
+        out["by_grid"] = {f"{g[0]}x{g[1]}x{g[2]}": {
+            "requests": len(v), "p50_ms": _pct([r["total_ms"] for r in v], 50),
+            "p99_ms": _pct([r["total_ms"] for r in v], 99),
+            "solve_p50_ms": _pct([r["solve_ms"] for r in v], 50),
+            "queue_p50_ms": _pct([r["queue_ms"] for r in v], 50),
+            "mean_iters": float(np.mean([r["iters"] for r in v]))} for g, v in sorted(grids.items(), key=lambda kv: kv[0][0] * kv[0][1] * kv[0][2])}
+    out["latency_note"] = ("submit call -> solution in pinned host memory (H2D of the lent pinned eta, the solve, "
+                           "D2H); one warm-up request per session excluded; causes from tpcg_server_get_timings")
+    return out
+
+
+def run_serving(args, prec, torch):
+    """The serving record: the mixed form and the FP64 form on the same request stream."""
+    return {f"mixed_{prec}": serving_stream(args, prec, torch), "fp64": serving_stream(args, "fp64", torch)}
 
 
 def run_comparators(torch, steps=3):
@@ -372,9 +427,8 @@ def run_batched(prec, torch):
 # profiles/.  Set an entry to None when its kernel changes.
 NCU_TRAFFIC_PER_LAUNCH = {
     # DRAM bytes (read + write) per launch from the ncu captures summarised under profiles/ (cold caches)
-    # tensor-core launches: mean over the five launches of one application (3D, TPCG_OPT_FUSE_G): passes
-    # 1, 2 and 5 (17.0, 16.9, 17.0 MB), the fused pair of passes 3-4 (16.9 MB) and the last pass (34.7 MB)
-    "modeprod_tc": (17.0e6 + 16.9e6 + 17.0e6 + 16.9e6 + 34.7e6) / 5,
+    # tensor-core launches: None until the frontal-slice kernels have been captured again
+    "modeprod_tc": None,
     "update": 275.0e6,  # the in-place update the instrumented (one-plan) pass runs
     "form_u": 248.0e6,  # the formation before a check (six recorded directions; TPCG_OPT_DEFER_U)
     "direction": 76.2e6,
@@ -394,9 +448,10 @@ def kernel_work(kind, plan_prec, N, dims, iters_total, applies_total, solves, ch
         return applies_total * 4.0 * N * (n + q + t + 0.25) / 1e12, "TFLOP", "alu", applies_total * (6 if t > 1 else 4)
     if kind == "modeprod_tc":
         # per application (3D): every launch but the last reads + writes FP16/BF16 (2 + 2 B); the last reads
-        # its FP16 input (2 B) and the FP16 copy of R (2 B) and writes Z in FP32 (4 B).  Six launches, or
-        # five when the pair of passes around G runs as one kernel (its intermediate stays on chip):
-        # `launches` is the plan's count per application.
+        # its FP16 input (2 B) and the FP16 copy of R (2 B) and writes Z in FP32 (4 B).  `launches` is the
+        # plan's count per application: three with the frontal-slice launches (x-y pair per z-plane, the
+        # tube pair around G, the backward x-y pair: 16 B per point), four when the z products run as two
+        # launches (20 B), five or six with one launch per mode product (24 or 28 B).
         npass = launches or (6 if t > 1 else 4)
         per_apply = ((npass - 1) * 4 + 8) * N
         return applies_total * per_apply / 1e9, "GB", "hbm", applies_total * npass
@@ -704,7 +759,7 @@ def run_ours(args, rank, world, torch):
     serving = batched = comparators = efield = None
     if rank == 0 and world == 1 and prec != "fp64":
         if args.serving_requests > 0:
-            serving = run_serving(args, prec)
+            serving = run_serving(args, prec, torch)
         if not args.no_batched:
             batched = run_batched(prec, torch)
         if not args.no_comparators:

@@ -47,10 +47,9 @@ def _axis_profile(n: int, centre: float, sigma: float, periodic: bool):
     return idx[keep], w[keep]
 
 
-def gaussian_defects(shape_zyx, periodic_xyz, centres_xyz, sigmas, weights, mode: str) -> np.ndarray:
-    """Sum of separable Gaussian blobs on a (nz, ny, nx) grid."""
-    nz, ny, nx = shape_zyx
-    out = np.zeros((nz, ny, nx))
+def add_defects(out, periodic_xyz, centres_xyz, sigmas, weights, mode: str) -> np.ndarray:
+    """Add separable Gaussian blobs to a (nz, ny, nx) array in place (and return it)."""
+    nz, ny, nx = out.shape
     for c, s, wgt in zip(centres_xyz, sigmas, weights):
         ix, gx = _axis_profile(nx, c[0], s, periodic_xyz[0])
         iy, gy = _axis_profile(ny, c[1], s, periodic_xyz[1])
@@ -65,6 +64,11 @@ def gaussian_defects(shape_zyx, periodic_xyz, centres_xyz, sigmas, weights, mode
         blob = scale * gz[:, None, None] * gy[None, :, None] * gx[None, None, :]
         out[np.ix_(iz, iy, ix)] += blob
     return out
+
+
+def gaussian_defects(shape_zyx, periodic_xyz, centres_xyz, sigmas, weights, mode: str) -> np.ndarray:
+    """Sum of separable Gaussian blobs on a (nz, ny, nx) grid."""
+    return add_defects(np.zeros(shape_zyx), periodic_xyz, centres_xyz, sigmas, weights, mode)
 
 
 def scale_to_paper_norm(eta: np.ndarray) -> np.ndarray:
@@ -168,17 +172,38 @@ class ServingSession:
         self.charges = np.where(self.rng.random(n_defects) < 0.5, -1.0, 1.0)
 
     def step(self):
+        """Move 1% of the defects; returns (indices, old centres, new centres) of the moved ones."""
         k = max(1, len(self.charges) // 100)
         idx = self.rng.choice(len(self.charges), size=k, replace=False)
+        old = self.centres[idx].copy()
         dims = (self.nx, self.ny, self.nz)
         for d in range(3):
             self.centres[idx, d] = self.rng.uniform(0.0, dims[d], size=k)
+        return idx, old, self.centres[idx].copy()
 
     def rhs(self):
         periodic = tuple(b == "P" for b in self.bcs)
         eta = gaussian_defects((self.nz, self.ny, self.nx), periodic, self.centres,
                                np.full(len(self.charges), self.sigma), self.charges, "charge")
         return scale_to_paper_norm(eta)
+
+    def paper_scale(self):
+        """Factor that brings the current field to the paper's norm ||eta|| = 1/N (kept for later steps)."""
+        periodic = tuple(b == "P" for b in self.bcs)
+        eta = gaussian_defects((self.nz, self.ny, self.nx), periodic, self.centres,
+                               np.full(len(self.charges), self.sigma), self.charges, "charge")
+        nrm = np.linalg.norm(eta.ravel())
+        return (1.0 / eta.size) / nrm if nrm > 0 else 1.0
+
+    def apply_moves(self, buf, moves, scale):
+        """Update a field in place for the moves returned by step(): the moved defects' blobs are taken
+        away at their old centres and added at the new ones, with charges times `scale`."""
+        idx, old, new = moves
+        periodic = tuple(b == "P" for b in self.bcs)
+        sig = np.full(len(idx), self.sigma)
+        add_defects(buf, periodic, old, sig, -scale * self.charges[idx], "charge")
+        add_defects(buf, periodic, new, sig, scale * self.charges[idx], "charge")
+        return buf
 
 
 def serving_sessions(seed=0, count=16):

@@ -394,21 +394,22 @@ class Server:
         self.shapes[t] = tuple(eta.shape)
         return t
 
-    def _result(self, fn, ticket, *args):
+    def _result(self, fn, ticket, *args, want=True):
         import numpy as np
 
-        out = np.empty(self.shapes[ticket])
-        st, info = fn(self.handle, ticket, *args, out.ctypes.data)
+        out = np.empty(self.shapes[ticket]) if want else None
+        st, info = fn(self.handle, ticket, *args, out.ctypes.data if want else None)
         if st == TPCG_PENDING:
             return st, None, None
         self.shapes.pop(ticket, None)
         return st, out, info.as_dict()
 
-    def poll(self, ticket):
-        return self._result(tpcg_server_poll, ticket)
+    def poll(self, ticket, want=True):
+        """(status, solution or None while pending, info); want=False: report only, no copy of the solution."""
+        return self._result(tpcg_server_poll, ticket, want=want)
 
-    def wait(self, ticket, timeout_s=-1.0):
-        return self._result(tpcg_server_wait, ticket, timeout_s)
+    def wait(self, ticket, timeout_s=-1.0, want=True):
+        return self._result(tpcg_server_wait, ticket, timeout_s, want=want)
 
     def stats(self):
         return tpcg_server_get_stats(self.handle)[1].as_dict()

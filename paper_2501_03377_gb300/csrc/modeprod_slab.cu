@@ -34,7 +34,9 @@ namespace {
 using namespace tcx;
 
 constexpr int kSlabEpi = 16;
-constexpr int kSlabThreads = (2 + kSlabEpi) * 32;
+constexpr int kSlabThreads = (2 + kSlabEpi) * 32;       // tube pair: producer, MMA, epilogue
+constexpr int kFrontalThreads = (3 + kSlabEpi) * 32;    // frontal pair: + the producer of the step-2 ring
+constexpr int kFrontalRing2Warp = 2 + kSlabEpi;
 constexpr int kBlk = 16384;  // one 128-row x 64-element K tile of a K-major operand (128-byte rows)
 constexpr int kTubeCols = 128;  // columns of one tube tile (two MN-major atoms of 64)
 
@@ -47,7 +49,8 @@ struct SlabArgs {
   uint32_t reg1;           // bytes of the step-1 ring (the slice-T overlays it)
   int stg;                 // output staging boxes per epilogue warp (1 or 2)
   // tube pair
-  int MBz, KTz;            // 128-row blocks / K tiles of the z axis
+  int MBz, KTz;            // 128-row blocks / K tiles (64) of the z axis
+  int KS, KTs;             // K rows of one tube stage (64 or 128) and stages per column tile
   int ntiles;              // column tiles of q*n
   int NS;                  // ring stages
   int apply_g;             // single tube pass: multiply by G (forward) or not (backward)
@@ -130,7 +133,7 @@ __device__ __forceinline__ void pack16(const float (&v)[16], uint32_t (&pk)[8]) 
 // through a second ring.  TMEM: D1 blocks at columns b*N1, D2 blocks at b*N2
 // (D2 is written once D1 has been drained).
 template <class InT, class OutT, bool FINAL>
-__global__ void __launch_bounds__(kSlabThreads, 1)
+__global__ void __launch_bounds__(kFrontalThreads, 1)
     k_frontal_pair(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmA1,
                    const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmO, SlabArgs a) {
   if (a.st && a.st->done) return;
@@ -197,97 +200,122 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
   const int shR = (FINAL && a.st) ? a.st->lp_shift_applied : 0;
   const float rs = std::is_same<InT, __half>::value ? 1.0f : ldexpf(1.0f, shR);
 
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer
+  if (warp == 0) {
+    // ---------------- TMA producer of the step-1 ring: lane 0 waits for a free stage, then lanes 0 and 1
+    // issue the stage's two boxes (eigenbasis K tile, slice K tile) with one instruction
     asm volatile("griddepcontrol.wait;" ::: "memory");  // the slices are the previous launch's output
-    int it1 = 0, it2 = 0;
+    int it1 = 0;
     bool ok = true;
     for (int i = 0; ok && i < nmine; ++i) {
       const int p = (int)blockIdx.x + i * (int)gridDim.x;
       // the slice-T of the previous plane overlays the step-1 ring: wait until step 2 has read it
-      if (i > 0 && !(ok = wait_bounded(tfree, (uint32_t)((i - 1) & 1), ab))) break;
-      for (int kt = 0; ok && kt < a.KT1; ++kt, ++it1) {
-        const int s = it1 % NS1;
-        if (!(ok = wait_bounded(empty1(s), (uint32_t)(((it1 / NS1) & 1) ^ 1), ab))) break;
-        const uint32_t st = sR1 + (uint32_t)s * stage1;
-        mbar_expect_tx(full1(s), stage1);
-        for (int b = 0; b < MB1; ++b) tma_load_2d(st + (uint32_t)b * kBlk, &tmA1, kt * 64, b * 128, full1(s));
-        tma_load_3d(st + (uint32_t)MB1 * kBlk, &tmX, kt * 64, 0, p, full1(s));
+      if (i > 0) {
+        bool w = true;
+        if (lane == 0) w = wait_bounded(tfree, (uint32_t)((i - 1) & 1), ab);
+        if (!(ok = __shfl_sync(0xffffffffu, w, 0))) break;
       }
-      for (int b = 0; ok && b < MB2; ++b)
-        for (int kt = 0; ok && kt < a.KT2; ++kt, ++it2) {
-          const int s = it2 % NS2;
-          if (!(ok = wait_bounded(empty2(s), (uint32_t)(((it2 / NS2) & 1) ^ 1), ab))) break;
-          mbar_expect_tx(full2(s), kBlk);
-          tma_load_2d(sR2 + (uint32_t)s * kBlk, &tmA2, kt * 64, b * 128, full2(s));
+      for (int kt = 0; kt < a.KT1; ++kt, ++it1) {
+        const int s = it1 % NS1;
+        bool w = true;
+        if (lane == 0) {
+          w = wait_bounded(empty1(s), (uint32_t)(((it1 / NS1) & 1) ^ 1), ab);
+          if (w) mbar_expect_tx(full1(s), stage1);
         }
+        if (!(ok = __shfl_sync(0xffffffffu, w, 0))) break;
+        const uint32_t st = sR1 + (uint32_t)s * stage1;
+        if (lane < 2)
+          tma_load_3d(lane ? st + (uint32_t)MB1 * kBlk : st, lane ? &tmX : &tmA1, kt * 64, 0, lane ? p : 0,
+                      full1(s));
+      }
     }
-    if (!ok) {  // every issued load completes before the CTA may exit
+    if (!ok && lane == 0) {  // every issued load completes before the CTA may exit
       for (int j = (it1 > NS1 ? it1 - NS1 : 0); j < it1; ++j) {
         const unsigned long long t0 = gtimer();
         while (!mbar_try_wait(full1(j % NS1), (uint32_t)((j / NS1) & 1)) && gtimer() - t0 < kWaitLimitNs) {
         }
       }
-      for (int j = (it2 > NS2 ? it2 - NS2 : 0); j < it2; ++j) {
-        const unsigned long long t0 = gtimer();
-        while (!mbar_try_wait(full2(j % NS2), (uint32_t)((j / NS2) & 1)) && gtimer() - t0 < kWaitLimitNs) {
+    }
+    __syncwarp();
+  } else if (warp == kFrontalRing2Warp) {
+    // ---------------- TMA producer of the step-2 ring (the eigenbasis of step 2, one 128-row block per
+    // stage), running ahead of the step-1 producer
+    if (lane == 0) {
+      int it2 = 0;
+      bool ok = true;
+      for (int i = 0; ok && i < nmine; ++i)
+        for (int b = 0; ok && b < MB2; ++b)
+          for (int kt = 0; ok && kt < a.KT2; ++kt, ++it2) {
+            const int s = it2 % NS2;
+            if (!(ok = wait_bounded(empty2(s), (uint32_t)(((it2 / NS2) & 1) ^ 1), ab))) break;
+            mbar_expect_tx(full2(s), kBlk);
+            tma_load_2d(sR2 + (uint32_t)s * kBlk, &tmA2, kt * 64, b * 128, full2(s));
+          }
+      if (!ok) {
+        for (int j = (it2 > NS2 ? it2 - NS2 : 0); j < it2; ++j) {
+          const unsigned long long t0 = gtimer();
+          while (!mbar_try_wait(full2(j % NS2), (uint32_t)((j / NS2) & 1)) && gtimer() - t0 < kWaitLimitNs) {
+          }
         }
       }
     }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
-    constexpr uint32_t fmt = std::is_same<InT, __half>::value ? 0u : 1u;
-    const uint32_t idesc1 = idesc_f16kind(128, a.N1, fmt), idesc2 = idesc_f16kind(128, a.N2, fmt);
-    int it1 = 0, it2 = 0;
-    bool ok = true;
-    for (int i = 0; ok && i < nmine; ++i) {
-      if (i > 0 && !(ok = wait_bounded(d2empty, (uint32_t)((i - 1) & 1), ab))) break;
-      tc_fence_after();
-      // step 1: D1[b] = W1 block b . X^T over the K tiles of n
-      for (int kt = 0; ok && kt < a.KT1; ++kt, ++it1) {
-        const int s = it1 % NS1;
-        if (!(ok = wait_bounded(full1(s), (uint32_t)((it1 / NS1) & 1), ab))) break;
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      constexpr uint32_t fmt = std::is_same<InT, __half>::value ? 0u : 1u;
+      const uint32_t idesc1 = idesc_f16kind(128, a.N1, fmt), idesc2 = idesc_f16kind(128, a.N2, fmt);
+      int it1 = 0, it2 = 0;
+      bool ok = true;
+      for (int i = 0; ok && i < nmine; ++i) {
+        if (i > 0 && !(ok = wait_bounded(d2empty, (uint32_t)((i - 1) & 1), ab))) break;
         tc_fence_after();
-        const uint32_t st = sR1 + (uint32_t)s * stage1;
-        const unsigned long long xd = sw128_desc(st + (uint32_t)MB1 * kBlk);
-        const int nk = min(4, (a.n - kt * 64 + 15) >> 4);
-        for (int b = 0; b < MB1; ++b) {
-          const unsigned long long ad = sw128_desc(st + (uint32_t)b * kBlk);
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk)
-            if (kk < nk)
-              tc_mma(tmem + (uint32_t)(b * a.N1), ad + 2u * kk, xd + 2u * kk, idesc1, (kt > 0 || kk > 0) ? 1u : 0u);
-        }
-        tc_commit(empty1(s));
-      }
-      if (!ok) break;
-      tc_commit(d1full);
-      // step 2: D2[b] = W2 block b . T^T over the K tiles of q, T in shared memory
-      if (!(ok = wait_bounded(tready, (uint32_t)(i & 1), ab))) break;
-      tc_fence_after();
-      for (int b = 0; ok && b < MB2; ++b) {
-        for (int kt = 0; ok && kt < a.KT2; ++kt, ++it2) {
-          const int s = it2 % NS2;
-          if (!(ok = wait_bounded(full2(s), (uint32_t)((it2 / NS2) & 1), ab))) break;
+        // step 1: D1[b] = W1 block b . X^T over the K tiles of n
+        for (int kt = 0; ok && kt < a.KT1; ++kt, ++it1) {
+          const int s = it1 % NS1;
+          if (!(ok = wait_bounded(full1(s), (uint32_t)((it1 / NS1) & 1), ab))) break;
           tc_fence_after();
-          const unsigned long long ad = sw128_desc(sR2 + (uint32_t)s * kBlk);
-          const unsigned long long td = sw128_desc(sT + (uint32_t)kt * (uint32_t)MB1 * kBlk);
-          const int nk = min(4, (a.q - kt * 64 + 15) >> 4);
+          const uint32_t st = sR1 + (uint32_t)s * stage1;
+          const unsigned long long xd = sw128_desc(st + (uint32_t)MB1 * kBlk);
+          const int nk = min(4, (a.n - kt * 64 + 15) >> 4);
+          for (int b = 0; b < MB1; ++b) {
+            const unsigned long long ad = sw128_desc(st + (uint32_t)b * kBlk);
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk)
-            if (kk < nk)
-              tc_mma(tmem + (uint32_t)(b * a.N2), ad + 2u * kk, td + 2u * kk, idesc2, (kt > 0 || kk > 0) ? 1u : 0u);
-          tc_commit(empty2(s));
+            for (int kk = 0; kk < 4; ++kk)
+              if (kk < nk)
+                tc_mma(tmem + (uint32_t)(b * a.N1), ad + 2u * kk, xd + 2u * kk, idesc1, (kt > 0 || kk > 0) ? 1u : 0u);
+          }
+          tc_commit(empty1(s));
         }
-        if (ok) tc_commit(d2full0 + 8u * (uint32_t)b);
+        if (!ok) break;
+        tc_commit(d1full);
+        // step 2: D2[b] = W2 block b . T^T over the K tiles of q, T in shared memory
+        if (!(ok = wait_bounded(tready, (uint32_t)(i & 1), ab))) break;
+        tc_fence_after();
+        for (int b = 0; ok && b < MB2; ++b) {
+          for (int kt = 0; ok && kt < a.KT2; ++kt, ++it2) {
+            const int s = it2 % NS2;
+            if (!(ok = wait_bounded(full2(s), (uint32_t)((it2 / NS2) & 1), ab))) break;
+            tc_fence_after();
+            const unsigned long long ad = sw128_desc(sR2 + (uint32_t)s * kBlk);
+            const unsigned long long td = sw128_desc(sT + (uint32_t)kt * (uint32_t)MB1 * kBlk);
+            const int nk = min(4, (a.q - kt * 64 + 15) >> 4);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              if (kk < nk)
+                tc_mma(tmem + (uint32_t)(b * a.N2), ad + 2u * kk, td + 2u * kk, idesc2, (kt > 0 || kk > 0) ? 1u : 0u);
+            tc_commit(empty2(s));
+          }
+          if (ok) tc_commit(d2full0 + 8u * (uint32_t)b);
+        }
+        if (ok) tc_commit(tfree);
       }
-      if (ok) tc_commit(tfree);
+      tc_commit(drain);  // every MMA this thread issued is complete once `drain` fires
+      const unsigned long long t0 = gtimer();
+      while (!mbar_try_wait(drain, 0) && gtimer() - t0 < kWaitLimitNs) {
+      }
     }
-    tc_commit(drain);  // every MMA this thread issued is complete once `drain` fires
-    const unsigned long long t0 = gtimer();
-    while (!mbar_try_wait(drain, 0) && gtimer() - t0 < kWaitLimitNs) {
-    }
-  } else if (warp >= 2) {
+    __syncwarp();
+  } else {
     // ---------------- epilogue: warp (quadrant q4, share h) takes the 16-column chunks h*16 + 64 j
     const int q4 = warp & 3, h = (warp - 2) >> 2;
     BoxEmitter<OutT> em{sO + (uint32_t)(warp - 2) * (uint32_t)a.stg * kOB, a.stg};
@@ -331,49 +359,67 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // T (generic writes) -> tensor core reads
       tc_fence_before();
       mbar_arrive(tready);
-      // step-2 drain: output rows m = q' (or q), 16 consecutive columns per chunk
-      const int J2 = (a.N2 - h * 16 + 63) / 64;
+      // step-2 drain: output rows m = q' (or q), 16 consecutive columns per chunk.  The last launch of a
+      // solve reads R~ (this thread's row, its chunks of the block) into registers before it waits for
+      // the accumulator, so the loads overlap the MMAs.
+      const int J2 = (a.N2 - h * 16 + 63) / 64;  // chunks of this warp per block (at most 4)
+      uint4 rpre[4][2];
+      auto prefetch = [&](int b) {
+        if constexpr (FINAL) {
+          const int m = b * 128 + q4 * 32 + lane;
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (j < J2 && m < a.q) {
+              const uint4* rp =
+                  reinterpret_cast<const uint4*>(a.Rt + ((long long)p * a.q + m) * a.rpitch + h * 16 + 64 * j);
+              rpre[j][0] = __ldg(rp);
+              rpre[j][1] = __ldg(rp + 1);
+            }
+        }
+      };
       for (int b = 0; ok && b < MB2; ++b) {
+        prefetch(b);
         if (!(ok = __all_sync(0xffffffffu, wait_bounded(d2full0 + 8u * (uint32_t)b, (uint32_t)(i & 1), ab)))) break;
         tc_fence_after();
         const uint32_t tl = tmem + (uint32_t)(b * a.N2) + ((uint32_t)(q4 * 32) << 16);
         const int m0 = b * 128 + q4 * 32;
         const int m = m0 + lane;
-        for (int j = 0; j < J2; j += 2) {
-          uint32_t r0[16], r1[16];
-          const int c0 = h * 16 + 64 * j, c1 = c0 + 64;
-          tc_ld16_issue(tl + (uint32_t)c0, r0);
-          if (j + 1 < J2) tc_ld16_issue(tl + (uint32_t)c1, r1);
-          tc_ld16_wait(r0);
-          if (j + 1 < J2) tc_ld16_wait(r1);
+        auto process = [&](int c, const uint32_t (&r)[16], const uint4 (&rw4)[2]) {
+          float v[16];
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            if (u == 1 && j + 1 >= J2) break;
-            const int c = u ? c1 : c0;
-            float v[16];
+          for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+          if (a.last) {
 #pragma unroll
-            for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(u ? r1[k] : r0[k]);
-            if (a.last) {
+            for (int k = 0; k < 16; ++k) v[k] *= zs;
+          }
+          if (m0 < a.q) em.put3(&tmO, v, lane, c, m0, p);  // rows past q and columns past n are clipped
+          if (FINAL && m < a.q) {
+            const uint32_t rw[8] = {rw4[0].x, rw4[0].y, rw4[0].z, rw4[0].w, rw4[1].x, rw4[1].y, rw4[1].z, rw4[1].w};
+            float d0 = 0.0f, d1 = 0.0f;
 #pragma unroll
-              for (int k = 0; k < 16; ++k) v[k] *= zs;
+            for (int k = 0; k < 8; ++k) {
+              const float2 rr = lp2_to_f32<InT>(rw[k]);
+              d0 = fmaf(rr.x * rs, v[2 * k], d0);
+              d1 = fmaf(rr.y * rs, v[2 * k + 1], d1);
+              zmax = fmaxf(zmax, fmaxf(fabsf(v[2 * k]), fabsf(v[2 * k + 1])));
             }
-            if (m0 < a.q) em.put3(&tmO, v, lane, c, m0, p);  // rows past q and columns past n are clipped
-            if (FINAL && m < a.q && c < a.n) {
-              const uint4* rp = reinterpret_cast<const uint4*>(a.Rt + ((long long)p * a.q + m) * a.rpitch + c);
-              const uint4 w0 = __ldg(rp), w1 = __ldg(rp + 1);
-              const uint32_t rw[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-              float d0 = 0.0f, d1 = 0.0f;
+            red0.add(d0 + d1);
+            red1.add(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) +
+                     (((v[8] + v[9]) + (v[10] + v[11])) + ((v[12] + v[13]) + (v[14] + v[15]))));
+          }
+        };
 #pragma unroll
-              for (int k = 0; k < 8; ++k) {
-                const float2 rr = lp2_to_f32<InT>(rw[k]);
-                d0 = fmaf(rr.x * rs, v[2 * k], d0);
-                d1 = fmaf(rr.y * rs, v[2 * k + 1], d1);
-                zmax = fmaxf(zmax, fmaxf(fabsf(v[2 * k]), fabsf(v[2 * k + 1])));
-              }
-              red0.add(d0 + d1);
-              red1.add(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) +
-                       (((v[8] + v[9]) + (v[10] + v[11])) + ((v[12] + v[13]) + (v[14] + v[15]))));
-            }
+        for (int jp = 0; jp < 2; ++jp) {  // chunk pairs (2 jp, 2 jp + 1), TMEM loads of a pair issued together
+          const int ja = 2 * jp, jb = ja + 1;
+          if (ja < J2) {
+            uint32_t r0[16], r1[16];
+            const int c0 = h * 16 + 64 * ja, c1 = c0 + 64;
+            tc_ld16_issue(tl + (uint32_t)c0, r0);
+            if (jb < J2) tc_ld16_issue(tl + (uint32_t)c1, r1);
+            tc_ld16_wait(r0);
+            if (jb < J2) tc_ld16_wait(r1);
+            process(c0, r0, rpre[ja]);
+            if (jb < J2) process(c1, r1, rpre[jb]);
           }
         }
       }
@@ -390,14 +436,14 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
   }
   if constexpr (FINAL) {
-    __shared__ float smax[kSlabThreads / 32];
+    __shared__ float smax[kFrontalThreads / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) zmax = fmaxf(zmax, __shfl_xor_sync(0xffffffffu, zmax, o));
     if (lane == 0) smax[warp] = zmax;
     __syncthreads();
     if (threadIdx.x == 0) {
       float mx = 0.0f;
-      for (int w = 0; w < kSlabThreads / 32; ++w) mx = fmaxf(mx, smax[w]);
+      for (int w = 0; w < kFrontalThreads / 32; ++w) mx = fmaxf(mx, smax[w]);
       atomicMax(&a.st->zmax_bits, __float_as_uint(mx));
     }
     double acc[2] = {acc_value(red0), acc_value(red1)};
@@ -439,7 +485,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* sm = smem_raw + (base - raw);
   const int MBz = a.MBz, KTz = a.KTz, NS = a.NS;
-  constexpr uint32_t kStage = 64u * 128u * 2u;  // 64 K rows x 128 columns (two atoms)
+  const uint32_t kStage = (uint32_t)a.KS * 256u;  // KS rows of z x 128 columns (two MN-major atoms)
   constexpr uint32_t kAtomT = 128u * 128u;      // T: one 64-column atom of 128 K rows
   const uint32_t wbytes = (uint32_t)(MBz * KTz) * kBlk;
   const uint32_t sW1 = base;
@@ -493,28 +539,37 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
   const uint32_t tmem = *tmem_holder;
   const int nmine = a.ntiles > (int)blockIdx.x ? (a.ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
-  if (warp == 0 && lane == 0) {
+  if (warp == 0) {
     // ---------------- TMA producer: the eigenbases once (they do not depend on the previous launch),
-    // then the K tiles of every column tile
-    mbar_expect_tx(vbar, (PAIR ? 2u : 1u) * wbytes);
-    for (int kt = 0; kt < KTz; ++kt)
-      for (int b = 0; b < MBz; ++b) {
-        tma_load_2d(sW1 + (uint32_t)(kt * MBz + b) * kBlk, &tmW1, kt * 64, b * 128, vbar);
-        if (PAIR) tma_load_2d(sW2 + (uint32_t)(kt * MBz + b) * kBlk, &tmW2, kt * 64, b * 128, vbar);
-      }
+    // then the stages of every column tile (KS rows of z, two 64-column boxes issued together by lanes
+    // 0 and 1)
+    if (lane == 0) {
+      mbar_expect_tx(vbar, (PAIR ? 2u : 1u) * wbytes);
+      for (int kt = 0; kt < KTz; ++kt)
+        for (int b = 0; b < MBz; ++b) {
+          tma_load_2d(sW1 + (uint32_t)(kt * MBz + b) * kBlk, &tmW1, kt * 64, b * 128, vbar);
+          if (PAIR) tma_load_2d(sW2 + (uint32_t)(kt * MBz + b) * kBlk, &tmW2, kt * 64, b * 128, vbar);
+        }
+    }
     asm volatile("griddepcontrol.wait;" ::: "memory");
     int it = 0;
-    for (int i = 0; i < nmine && !*abort_flag; ++i) {
+    bool ok = true;
+    for (int i = 0; ok && i < nmine; ++i) {
       const int tile = (int)blockIdx.x + i * (int)gridDim.x;
-      for (int kt = 0; kt < KTz; ++kt, ++it) {
+      for (int ks = 0; ks < a.KTs; ++ks, ++it) {
         const int s = it % NS;
-        if (!wait_bounded(empty(s), (uint32_t)(((it / NS) & 1) ^ 1), ab)) break;
-        mbar_expect_tx(full(s), kStage);
-        tma_load_2d(sD + (uint32_t)s * kStage, &tmF, tile * kTubeCols, kt * 64, full(s));
-        tma_load_2d(sD + (uint32_t)s * kStage + kStage / 2, &tmF, tile * kTubeCols + 64, kt * 64, full(s));
+        bool w = true;
+        if (lane == 0) {
+          w = wait_bounded(empty(s), (uint32_t)(((it / NS) & 1) ^ 1), ab);
+          if (w) mbar_expect_tx(full(s), kStage);
+        }
+        if (!(ok = __shfl_sync(0xffffffffu, w, 0))) break;
+        if (lane < 2)
+          tma_load_2d(sD + (uint32_t)s * kStage + (uint32_t)lane * (kStage / 2), &tmF, tile * kTubeCols + 64 * lane,
+                      ks * a.KS, full(s));
       }
     }
-    if (*abort_flag) {
+    if (!ok && lane == 0) {  // every issued load completes before the CTA may exit
       for (int j = (it > NS ? it - NS : 0); j < it; ++j) {
         const unsigned long long t0 = gtimer();
         while (!mbar_try_wait(full(j % NS), (uint32_t)((j / NS) & 1)) && gtimer() - t0 < kWaitLimitNs) {
@@ -524,71 +579,77 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
       while (!mbar_try_wait(vbar, 0) && gtimer() - t0 < kWaitLimitNs) {
       }
     }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
-    constexpr uint32_t fmt = std::is_same<InT, __half>::value ? 0u : 1u;
-    const uint32_t idesc = idesc_f16kind_bmn(128, kTubeCols, fmt);
-    bool ok = wait_bounded(vbar, 0, ab);
-    int it = 0;
-    // stage 1 of tile i: D = W1 . F (data MN-major: K step of 16 rows = +2048 bytes; atoms 8 KB apart)
-    auto stage1 = [&](int i) {
-      const int b = i & 1;
-      if (!wait_bounded(d1empty(b), (uint32_t)(((i >> 1) & 1) ^ 1), ab)) return false;
-      tc_fence_after();
-      const uint32_t dacc = tmem + (PAIR ? (uint32_t)(b * 128) : (uint32_t)(b * 256));
-      for (int kt = 0; kt < KTz; ++kt, ++it) {
-        const int s = it % NS;
-        if (!wait_bounded(full(s), (uint32_t)((it / NS) & 1), ab)) return false;
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      constexpr uint32_t fmt = std::is_same<InT, __half>::value ? 0u : 1u;
+      const uint32_t idesc = idesc_f16kind_bmn(128, kTubeCols, fmt);
+      bool ok = wait_bounded(vbar, 0, ab);
+      int it = 0;
+      // stage 1 of tile i: D = W1 . F (data MN-major: K step of 16 rows = +2048 bytes; atoms KS rows apart)
+      auto stage1 = [&](int i) {
+        const int b = i & 1;
+        if (!wait_bounded(d1empty(b), (uint32_t)(((i >> 1) & 1) ^ 1), ab)) return false;
         tc_fence_after();
-        const uint32_t sd = sD + (uint32_t)s * kStage;
-        const int nk = min(4, (a.t - kt * 64 + 15) >> 4);
-        for (int mb = 0; mb < MBz; ++mb) {
-          const unsigned long long wd = sw128_desc(sW1 + (uint32_t)(kt * MBz + mb) * kBlk);
+        const uint32_t dacc = tmem + (PAIR ? (uint32_t)(b * 128) : (uint32_t)(b * 256));
+        for (int ks = 0; ks < a.KTs; ++ks, ++it) {
+          const int s = it % NS;
+          if (!wait_bounded(full(s), (uint32_t)((it / NS) & 1), ab)) return false;
+          tc_fence_after();
+          const uint32_t sd = sD + (uint32_t)s * kStage;
+          const int nk = min(a.KS >> 4, (a.t - ks * a.KS + 15) >> 4);
+          for (int mb = 0; mb < MBz; ++mb) {
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk)
+              if (kk < nk) {
+                const int kg = ks * (a.KS >> 4) + kk;  // K step of 16 rows; the eigenbasis K tiles hold 4 of them
+                const unsigned long long wd = sw128_desc(sW1 + (uint32_t)((kg >> 2) * MBz + mb) * kBlk) + 2u * (kg & 3);
+                tc_mma(dacc + (uint32_t)(mb * 128), wd, mn128_desc(sd + 2048u * kk, kStage / 2, 1024), idesc,
+                       (ks > 0 || kk > 0) ? 1u : 0u);
+              }
+          }
+          tc_commit(empty(s));
+        }
+        tc_commit(d1full(b));
+        return true;
+      };
+      // stage 2 of tile i (PAIR): D2 = W2 . T, T MN-major in shared memory (atoms 16 KB apart)
+      auto stage2 = [&](int i) {
+        const int b = i & 1;
+        if (!wait_bounded(tready(b), (uint32_t)((i >> 1) & 1), ab)) return false;
+        if (!wait_bounded(d2empty(b), (uint32_t)(((i >> 1) & 1) ^ 1), ab)) return false;
+        tc_fence_after();
+        const uint32_t dacc = tmem + 256u + (uint32_t)(b * 128);
+        const uint32_t tb = sT + (uint32_t)b * 2u * kAtomT;
+        for (int kt = 0; kt < KTz; ++kt) {
+          const unsigned long long wd = sw128_desc(sW2 + (uint32_t)kt * kBlk);
+          const int nk = min(4, (a.t - kt * 64 + 15) >> 4);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)
             if (kk < nk)
-              tc_mma(dacc + (uint32_t)(mb * 128), wd + 2u * kk, mn128_desc(sd + 2048u * kk, kStage / 2, 1024),
-                     idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+              tc_mma(dacc, wd + 2u * kk, mn128_desc(tb + (uint32_t)kt * 8192u + 2048u * kk, kAtomT, 1024), idesc,
+                     (kt > 0 || kk > 0) ? 1u : 0u);
         }
-        tc_commit(empty(s));
+        tc_commit(d2full(b));
+        return true;
+      };
+      if (PAIR) {
+        if (ok && nmine > 0) ok = stage1(0);
+        for (int i = 0; ok && i < nmine; ++i) {
+          if (i + 1 < nmine && !(ok = stage1(i + 1))) break;
+          ok = stage2(i);
+        }
+      } else {
+        for (int i = 0; ok && i < nmine; ++i) ok = stage1(i);
       }
-      tc_commit(d1full(b));
-      return true;
-    };
-    // stage 2 of tile i (PAIR): D2 = W2 . T, T MN-major in shared memory (atoms 16 KB apart)
-    auto stage2 = [&](int i) {
-      const int b = i & 1;
-      if (!wait_bounded(tready(b), (uint32_t)((i >> 1) & 1), ab)) return false;
-      if (!wait_bounded(d2empty(b), (uint32_t)(((i >> 1) & 1) ^ 1), ab)) return false;
-      tc_fence_after();
-      const uint32_t dacc = tmem + 256u + (uint32_t)(b * 128);
-      const uint32_t tb = sT + (uint32_t)b * 2u * kAtomT;
-      for (int kt = 0; kt < KTz; ++kt) {
-        const unsigned long long wd = sw128_desc(sW2 + (uint32_t)kt * kBlk);
-        const int nk = min(4, (a.t - kt * 64 + 15) >> 4);
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          if (kk < nk)
-            tc_mma(dacc, wd + 2u * kk, mn128_desc(tb + (uint32_t)kt * 8192u + 2048u * kk, kAtomT, 1024), idesc,
-                   (kt > 0 || kk > 0) ? 1u : 0u);
+      tc_commit(drain);
+      const unsigned long long t0 = gtimer();
+      while (!mbar_try_wait(drain, 0) && gtimer() - t0 < kWaitLimitNs) {
       }
-      tc_commit(d2full(b));
-      return true;
-    };
-    if (PAIR) {
-      if (ok && nmine > 0) ok = stage1(0);
-      for (int i = 0; ok && i < nmine; ++i) {
-        if (i + 1 < nmine && !(ok = stage1(i + 1))) break;
-        ok = stage2(i);
-      }
-    } else {
-      for (int i = 0; ok && i < nmine; ++i) ok = stage1(i);
     }
-    tc_commit(drain);
-    const unsigned long long t0 = gtimer();
-    while (!mbar_try_wait(drain, 0) && gtimer() - t0 < kWaitLimitNs) {
-    }
-  } else if (warp >= 2) {
+    __syncwarp();
+  } else {
     // ---------------- epilogue: lanes are z indices, 16 consecutive columns per chunk (one n'-run of one q')
     const int q4 = warp & 3, h = (warp - 2) >> 2;
     BoxEmitter<InT> em{sO + (uint32_t)(warp - 2) * 2u * kOB, 2};
@@ -751,7 +812,7 @@ template <class InT>
 void slab_launch(const SlabLaunch& L, const SlabArgs& a, bool final_pcg, cudaStream_t stream) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)L.grid);
-  cfg.blockDim = dim3(kSlabThreads);
+  cfg.blockDim = dim3(L.kind <= 1 ? kFrontalThreads : kSlabThreads);
   cfg.dynamicSmemBytes = L.smem;
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
@@ -824,15 +885,19 @@ int slab_plan_setup(tpcg_plan* p) {
     const size_t esz = dir ? 4 : 2;
     const uint32_t stage1 = (uint32_t)a.MB1 * kBlk + (uint32_t)a.N1 * 128u;
     const uint32_t tbytes = (uint32_t)a.KT2 * (uint32_t)a.MB1 * kBlk;
-    // largest rings that fit with two staging boxes per epilogue warp, else one
+    // ring depths and staging boxes that fit, best first: two step-1 stages, then up to four step-2
+    // stages, then two staging boxes per epilogue warp, then more step-1 stages
     const size_t barb = 8 * (2 * 4 + 2 * 4 + 7) + 16;
     bool found = false;
-    for (int stg = 2; stg >= 1 && !found; --stg)
-      for (int ns1 = std::min(a.KT1, 4); ns1 >= 1 && !found; --ns1) {
-        const uint32_t reg1 = std::max((uint32_t)ns1 * stage1, tbytes);
-        for (int ns2 = std::min(a.MB2 * a.KT2, 4); ns2 >= 1 && !found; --ns2) {
+    long best = -1;
+    for (int ns1 = 1; ns1 <= std::min(a.KT1, 4); ++ns1) {
+      const uint32_t reg1 = std::max((uint32_t)ns1 * stage1, tbytes);
+      for (int ns2 = 1; ns2 <= std::min(a.MB2 * a.KT2, 4); ++ns2)
+        for (int stg = 1; stg <= 2; ++stg) {
           const size_t total = 1024 + (size_t)reg1 + (size_t)ns2 * kBlk + (size_t)kSlabEpi * stg * 32 * 16 * esz + barb;
-          if (total <= (size_t)kMaxSmem && (ns2 >= 2 || a.MB2 * a.KT2 < 2)) {
+          const long key = std::min(ns1, 2) * 1000 + ns2 * 100 + stg * 10 + ns1;
+          if (total <= (size_t)kMaxSmem && key > best) {
+            best = key;
             a.NS1 = ns1;
             a.NS2 = ns2;
             a.reg1 = reg1;
@@ -841,20 +906,22 @@ int slab_plan_setup(tpcg_plan* p) {
             found = true;
           }
         }
-      }
+    }
     if (!found) return TPCG_ERR_UNSUPPORTED;
     const cuuint64_t dX[3] = {(cuuint64_t)n, (cuuint64_t)q, (cuuint64_t)t};
     const cuuint64_t sX[2] = {(cuuint64_t)in_pitch * 2, (cuuint64_t)in_pitch * 2 * q};
     const cuuint32_t bX[3] = {64, (cuuint32_t)a.N1, 1};
     const int lp0 = p->pitch16[0], lp1 = p->pitch16[1];
-    const cuuint64_t dA1[2] = {(cuuint64_t)n, (cuuint64_t)n}, sA1[1] = {(cuuint64_t)lp0 * 2};
+    const cuuint64_t dA1[3] = {(cuuint64_t)n, (cuuint64_t)n, 1};
+    const cuuint64_t sA1[2] = {(cuuint64_t)lp0 * 2, (cuuint64_t)lp0 * 2 * n};
+    const cuuint32_t bA1[3] = {64, (cuuint32_t)(a.MB1 * 128), 1};
     const cuuint64_t dA2[2] = {(cuuint64_t)q, (cuuint64_t)q}, sA2[1] = {(cuuint64_t)lp1 * 2};
     const cuuint32_t bA[2] = {64, 128};
     const cuuint64_t dO[3] = {(cuuint64_t)n, (cuuint64_t)q, (cuuint64_t)t};
     const cuuint64_t sO[2] = {(cuuint64_t)n * esz, (cuuint64_t)n * esz * q};
     const cuuint32_t bO[3] = {16, 32, 1};
     if (enc(&L.m0, dt, 3, in, dX, sX, bX, CU_TENSOR_MAP_SWIZZLE_128B) ||
-        enc(&L.m1, dt, 2, p->d_Wt16[0][dir], dA1, sA1, bA, CU_TENSOR_MAP_SWIZZLE_128B) ||
+        enc(&L.m1, dt, 3, p->d_Wt16[0][dir], dA1, sA1, bA1, CU_TENSOR_MAP_SWIZZLE_128B) ||
         enc(&L.m2, dt, 2, p->d_Wt16[1][dir], dA2, sA2, bA, CU_TENSOR_MAP_SWIZZLE_128B) ||
         enc(&L.m3, dir ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : dt, 3, out, dO, sO, bO,
             dir ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B))
@@ -868,6 +935,8 @@ int slab_plan_setup(tpcg_plan* p) {
     a = base;
     a.MBz = (t + 127) / 128;
     a.KTz = (t + 63) / 64;
+    a.KS = (t <= 64 || t > 128) ? 64 : 128;  // one stage per column tile up to 128 points of z
+    a.KTs = (t + a.KS - 1) / a.KS;
     a.ntiles = (int)((C + kTubeCols - 1) / kTubeCols);
     a.apply_g = (kind == 3 && dir == 0) ? 1 : 0;
     L.kind = kind;
@@ -876,12 +945,12 @@ int slab_plan_setup(tpcg_plan* p) {
     const size_t wbytes = (size_t)a.MBz * a.KTz * kBlk;
     const size_t fixed = 1024 + (pair ? 2 : 1) * wbytes + (pair ? 4 * 128 * 128 : 0) +
                          (size_t)kSlabEpi * 2 * 32 * 16 * 2 + 8 * (2 * 8 + 12) + 16;
-    const size_t kStage = 64 * 128 * 2;
+    const size_t kStage = (size_t)a.KS * 256;
     if (fixed + 2 * kStage > (size_t)kMaxSmem) return TPCG_ERR_UNSUPPORTED;
     a.NS = (int)std::min<size_t>(6, (kMaxSmem - fixed) / kStage);
     L.smem = fixed + (size_t)a.NS * kStage;
     const cuuint64_t dF[2] = {(cuuint64_t)C, (cuuint64_t)t}, sF[1] = {(cuuint64_t)C * 2};
-    const cuuint32_t bF[2] = {64, 64};
+    const cuuint32_t bF[2] = {64, (cuuint32_t)a.KS};
     const int lp2 = p->pitch16[2];
     const cuuint64_t dW[2] = {(cuuint64_t)t, (cuuint64_t)t}, sW[1] = {(cuuint64_t)lp2 * 2};
     const cuuint32_t bW[2] = {64, 128};

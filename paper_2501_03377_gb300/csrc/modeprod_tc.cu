@@ -198,81 +198,87 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
   const int shR = (FINAL && a.st) ? a.st->lp_shift_applied : 0;
   const float rs = std::is_same<InT, __half>::value ? 1.0f : ldexpf(1.0f, shR);
 
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer
-    mbar_expect_tx(vbar, (uint32_t)a.KT * a.VR * 128u);
-    for (int kt = 0; kt < a.KT; ++kt) tma_load_2d(sV + (uint32_t)kt * a.VR * 128u, &tmW, kt * kKTile, 0, vbar);
-    // the operand is the previous pass's output: wait until that grid has completed
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    int it = 0;
-    for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
-      for (int kt = 0; kt < a.KT; ++kt, ++it) {
-        const int s = it % NS;
-        const uint32_t ph = (uint32_t)((it / NS) & 1);
-        if (!wait_bounded(empty(s), ph ^ 1u, ab)) break;
-        mbar_expect_tx(full(s), kStageBytes);
-        tma_load_2d(sD + (uint32_t)s * kStageBytes, &tmX, kt * kKTile, tile * kTileRows, full(s));
-      }
-    }
-    // drain: every issued load has completed before the CTA may exit
-    if (*abort_flag) {
-      for (int j = (it > NS ? it - NS : 0); j < it; ++j) {
-        const unsigned long long t0 = gtimer();
-        while (!mbar_try_wait(full(j % NS), (uint32_t)((j / NS) & 1)) && gtimer() - t0 < kWaitLimitNs) {
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      mbar_expect_tx(vbar, (uint32_t)a.KT * a.VR * 128u);
+      for (int kt = 0; kt < a.KT; ++kt) tma_load_2d(sV + (uint32_t)kt * a.VR * 128u, &tmW, kt * kKTile, 0, vbar);
+      // the operand is the previous pass's output: wait until that grid has completed
+      asm volatile("griddepcontrol.wait;" ::: "memory");
+      int it = 0;
+      for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
+        for (int kt = 0; kt < a.KT; ++kt, ++it) {
+          const int s = it % NS;
+          const uint32_t ph = (uint32_t)((it / NS) & 1);
+          if (!wait_bounded(empty(s), ph ^ 1u, ab)) break;
+          mbar_expect_tx(full(s), kStageBytes);
+          tma_load_2d(sD + (uint32_t)s * kStageBytes, &tmX, kt * kKTile, tile * kTileRows, full(s));
         }
       }
-      const unsigned long long t0 = gtimer();
-      while (!mbar_try_wait(vbar, 0) && gtimer() - t0 < kWaitLimitNs) {
-      }
-    }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
-    constexpr uint32_t fmt = std::is_same<InT, __half>::value ? 0u : 1u;
-    const uint32_t idesc = (FORM == 1) ? idesc_f16kind(128, a.Np, fmt) : idesc_f16kind(128, 128, fmt);
-    // Shared-memory descriptors: the address field holds address / 16 in its low 14 bits (shared memory
-    // is below 256 KB, so offsets add without a carry out of the field); a 16-element K step is +2.
-    // The issue loop is kept short: one thread issuing small MMAs is otherwise slower than the tensor
-    // pipe executing them.
-    const unsigned long long dX0 = sw128_desc(sD), dV0 = sw128_desc(sV);
-    const uint32_t vkt = (uint32_t)(a.VR * 128) >> 4;  // one 64-wide K tile of V
-    const bool two_mb = (FORM != 1) && a.MB > 1;       // second 128-row block of V (form 2)
-    bool ok = wait_bounded(vbar, 0, ab);
-    int it = 0, tcount = 0;
-    for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++tcount) {
-      const int b = tcount & 1;
-      if (!(ok = wait_bounded(tempty(b), (uint32_t)(((tcount >> 1) & 1) ^ 1), ab))) break;
-      tc_fence_after();
-      const uint32_t dacc = tmem + (uint32_t)(b * a.acc_cols);
-      for (int kt = 0; kt < a.KT; ++kt, ++it) {
-        const int s = it % NS;
-        if (!(ok = wait_bounded(full(s), (uint32_t)((it / NS) & 1), ab))) break;
-        tc_fence_after();
-        const unsigned long long xd = dX0 + (uint32_t)s * (uint32_t)(kStageBytes >> 4);
-        const unsigned long long vd = dV0 + (uint32_t)kt * vkt;
-        const int nk = min(4, (a.C - kt * kKTile + 15) >> 4);  // K steps of 16 inside C
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          if (kk < nk) {
-            const uint32_t accum = (kt > 0 || kk > 0) ? 1u : 0u;
-            if (FORM == 1) {
-              tc_mma(dacc, xd + 2u * kk, vd + 2u * kk, idesc, accum);
-            } else {
-              tc_mma(dacc, vd + 2u * kk, xd + 2u * kk, idesc, accum);
-              if (two_mb)
-                tc_mma(dacc + 128u, vd + (uint32_t)(kStageBytes >> 4) + 2u * kk, xd + 2u * kk, idesc, accum);
-            }
+      // drain: every issued load has completed before the CTA may exit
+      if (*abort_flag) {
+        for (int j = (it > NS ? it - NS : 0); j < it; ++j) {
+          const unsigned long long t0 = gtimer();
+          while (!mbar_try_wait(full(j % NS), (uint32_t)((j / NS) & 1)) && gtimer() - t0 < kWaitLimitNs) {
           }
         }
-        tc_commit(empty(s));
+        const unsigned long long t0 = gtimer();
+        while (!mbar_try_wait(vbar, 0) && gtimer() - t0 < kWaitLimitNs) {
+        }
       }
-      if (!ok) break;
-      tc_commit(tfull(b));
     }
-    // all MMAs issued by this thread are complete once `drain` fires
-    tc_commit(drain);
-    const unsigned long long t0 = gtimer();
-    while (!mbar_try_wait(drain, 0) && gtimer() - t0 < kWaitLimitNs) {
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      constexpr uint32_t fmt = std::is_same<InT, __half>::value ? 0u : 1u;
+      const uint32_t idesc = (FORM == 1) ? idesc_f16kind(128, a.Np, fmt) : idesc_f16kind(128, 128, fmt);
+      // Shared-memory descriptors: the address field holds address / 16 in its low 14 bits (shared memory
+      // is below 256 KB, so offsets add without a carry out of the field); a 16-element K step is +2.
+      // The issue loop is kept short: one thread issuing small MMAs is otherwise slower than the tensor
+      // pipe executing them.
+      const unsigned long long dX0 = sw128_desc(sD), dV0 = sw128_desc(sV);
+      const uint32_t vkt = (uint32_t)(a.VR * 128) >> 4;  // one 64-wide K tile of V
+      const bool two_mb = (FORM != 1) && a.MB > 1;       // second 128-row block of V (form 2)
+      bool ok = wait_bounded(vbar, 0, ab);
+      int it = 0, tcount = 0;
+      for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++tcount) {
+        const int b = tcount & 1;
+        if (!(ok = wait_bounded(tempty(b), (uint32_t)(((tcount >> 1) & 1) ^ 1), ab))) break;
+        tc_fence_after();
+        const uint32_t dacc = tmem + (uint32_t)(b * a.acc_cols);
+        for (int kt = 0; kt < a.KT; ++kt, ++it) {
+          const int s = it % NS;
+          if (!(ok = wait_bounded(full(s), (uint32_t)((it / NS) & 1), ab))) break;
+          tc_fence_after();
+          const unsigned long long xd = dX0 + (uint32_t)s * (uint32_t)(kStageBytes >> 4);
+          const unsigned long long vd = dV0 + (uint32_t)kt * vkt;
+          const int nk = min(4, (a.C - kt * kKTile + 15) >> 4);  // K steps of 16 inside C
+  #pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            if (kk < nk) {
+              const uint32_t accum = (kt > 0 || kk > 0) ? 1u : 0u;
+              if (FORM == 1) {
+                tc_mma(dacc, xd + 2u * kk, vd + 2u * kk, idesc, accum);
+              } else {
+                tc_mma(dacc, vd + 2u * kk, xd + 2u * kk, idesc, accum);
+                if (two_mb)
+                  tc_mma(dacc + 128u, vd + (uint32_t)(kStageBytes >> 4) + 2u * kk, xd + 2u * kk, idesc, accum);
+              }
+            }
+          }
+          tc_commit(empty(s));
+        }
+        if (!ok) break;
+        tc_commit(tfull(b));
+      }
+      // all MMAs issued by this thread are complete once `drain` fires
+      tc_commit(drain);
+      const unsigned long long t0 = gtimer();
+      while (!mbar_try_wait(drain, 0) && gtimer() - t0 < kWaitLimitNs) {
+      }
     }
+    __syncwarp();
   } else if (warp == TcWarps<FINAL>::rwarp) {
     // ---------------- TMA of R~ (last pass): 16-column chunks of the tile's 128 rows.  Chunk ci belongs to
     // epilogue half ci % 2, which consumes its chunks in order from its own ring of kRHalf slots (a ring
@@ -307,6 +313,7 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
           }
       }
     }
+    __syncwarp();
   } else if (warp >= 2) {
     // ---------------- epilogue: NG warps per TMEM lane quadrant, each taking every NG-th 16-column chunk
     constexpr int NG = TcWarps<FINAL>::groups;
@@ -657,86 +664,92 @@ __global__ void __launch_bounds__(kPairThreads, 1)
   const int ntiles = (a.rows + kTileRows - 1) / kTileRows;
   const int nmine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer: both eigenbases once, then the K tiles of every row tile
-    mbar_expect_tx(vbar, (uint32_t)KT * (uint32_t)(a.VR + 128) * 128u);
-    for (int kt = 0; kt < KT; ++kt) tma_load_2d(sW1 + (uint32_t)kt * a.VR * 128u, &tmW1, kt * kKTile, 0, vbar);
-    for (int kt = 0; kt < KT; ++kt) tma_load_2d(sW2 + (uint32_t)kt * 128u * 128u, &tmW2, kt * kKTile, 0, vbar);
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    int it = 0;
-    for (int i = 0; i < nmine && !*abort_flag; ++i) {
-      const int tile = (int)blockIdx.x + i * (int)gridDim.x;
-      for (int kt = 0; kt < KT; ++kt, ++it) {
-        const int s = it % NS;
-        if (!wait_bounded(empty(s), (uint32_t)(((it / NS) & 1) ^ 1), ab)) break;
-        mbar_expect_tx(full(s), kStageBytes);
-        tma_load_2d(sD + (uint32_t)s * kStageBytes, &tmX, kt * kKTile, tile * kTileRows, full(s));
-      }
-    }
-    if (*abort_flag) {  // every issued load completes before the CTA may exit
-      for (int j = (it > NS ? it - NS : 0); j < it; ++j) {
-        const unsigned long long t0 = gtimer();
-        while (!mbar_try_wait(full(j % NS), (uint32_t)((j / NS) & 1)) && gtimer() - t0 < kWaitLimitNs) {
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer: both eigenbases once, then the K tiles of every row tile
+      mbar_expect_tx(vbar, (uint32_t)KT * (uint32_t)(a.VR + 128) * 128u);
+      for (int kt = 0; kt < KT; ++kt) tma_load_2d(sW1 + (uint32_t)kt * a.VR * 128u, &tmW1, kt * kKTile, 0, vbar);
+      for (int kt = 0; kt < KT; ++kt) tma_load_2d(sW2 + (uint32_t)kt * 128u * 128u, &tmW2, kt * kKTile, 0, vbar);
+      asm volatile("griddepcontrol.wait;" ::: "memory");
+      int it = 0;
+      for (int i = 0; i < nmine && !*abort_flag; ++i) {
+        const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+        for (int kt = 0; kt < KT; ++kt, ++it) {
+          const int s = it % NS;
+          if (!wait_bounded(empty(s), (uint32_t)(((it / NS) & 1) ^ 1), ab)) break;
+          mbar_expect_tx(full(s), kStageBytes);
+          tma_load_2d(sD + (uint32_t)s * kStageBytes, &tmX, kt * kKTile, tile * kTileRows, full(s));
         }
       }
-      const unsigned long long t0 = gtimer();
-      while (!mbar_try_wait(vbar, 0) && gtimer() - t0 < kWaitLimitNs) {
+      if (*abort_flag) {  // every issued load completes before the CTA may exit
+        for (int j = (it > NS ? it - NS : 0); j < it; ++j) {
+          const unsigned long long t0 = gtimer();
+          while (!mbar_try_wait(full(j % NS), (uint32_t)((j / NS) & 1)) && gtimer() - t0 < kWaitLimitNs) {
+          }
+        }
+        const unsigned long long t0 = gtimer();
+        while (!mbar_try_wait(vbar, 0) && gtimer() - t0 < kWaitLimitNs) {
+        }
       }
     }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
-    constexpr uint32_t fmt = std::is_same<InT, __half>::value ? 0u : 1u;
-    const uint32_t idesc1 = idesc_f16kind(128, a.Np, fmt), idesc2 = idesc_f16kind(128, 128, fmt);
-    const unsigned long long dX0 = sw128_desc(sD), dW1 = sw128_desc(sW1), dW2 = sw128_desc(sW2), dT = sw128_desc(sT);
-    const uint32_t w1kt = (uint32_t)(a.VR * 128) >> 4, w2kt = (uint32_t)(128 * 128) >> 4,
-                   tkt = (uint32_t)kTBytes >> 4;
-    bool ok = wait_bounded(vbar, 0, ab);
-    int it = 0;
-    auto stage1 = [&](int i) {  // forward product of tile i into D1[i & 1]
-      const int b = i & 1;
-      if (!wait_bounded(d1empty(b), (uint32_t)(((i >> 1) & 1) ^ 1), ab)) return false;
-      tc_fence_after();
-      const uint32_t dacc = tmem + (uint32_t)(b * 128);
-      for (int kt = 0; kt < KT; ++kt, ++it) {
-        const int s = it % NS;
-        if (!wait_bounded(full(s), (uint32_t)((it / NS) & 1), ab)) return false;
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      constexpr uint32_t fmt = std::is_same<InT, __half>::value ? 0u : 1u;
+      const uint32_t idesc1 = idesc_f16kind(128, a.Np, fmt), idesc2 = idesc_f16kind(128, 128, fmt);
+      const unsigned long long dX0 = sw128_desc(sD), dW1 = sw128_desc(sW1), dW2 = sw128_desc(sW2), dT = sw128_desc(sT);
+      const uint32_t w1kt = (uint32_t)(a.VR * 128) >> 4, w2kt = (uint32_t)(128 * 128) >> 4,
+                     tkt = (uint32_t)kTBytes >> 4;
+      bool ok = wait_bounded(vbar, 0, ab);
+      int it = 0;
+      auto stage1 = [&](int i) {  // forward product of tile i into D1[i & 1]
+        const int b = i & 1;
+        if (!wait_bounded(d1empty(b), (uint32_t)(((i >> 1) & 1) ^ 1), ab)) return false;
         tc_fence_after();
-        const unsigned long long xd = dX0 + (uint32_t)s * (uint32_t)(kStageBytes >> 4);
-        const unsigned long long wd = dW1 + (uint32_t)kt * w1kt;
-        const int nk = min(4, (a.C - kt * kKTile + 15) >> 4);
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          if (kk < nk) tc_mma(dacc, xd + 2u * kk, wd + 2u * kk, idesc1, (kt > 0 || kk > 0) ? 1u : 0u);
-        tc_commit(empty(s));
+        const uint32_t dacc = tmem + (uint32_t)(b * 128);
+        for (int kt = 0; kt < KT; ++kt, ++it) {
+          const int s = it % NS;
+          if (!wait_bounded(full(s), (uint32_t)((it / NS) & 1), ab)) return false;
+          tc_fence_after();
+          const unsigned long long xd = dX0 + (uint32_t)s * (uint32_t)(kStageBytes >> 4);
+          const unsigned long long wd = dW1 + (uint32_t)kt * w1kt;
+          const int nk = min(4, (a.C - kt * kKTile + 15) >> 4);
+  #pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            if (kk < nk) tc_mma(dacc, xd + 2u * kk, wd + 2u * kk, idesc1, (kt > 0 || kk > 0) ? 1u : 0u);
+          tc_commit(empty(s));
+        }
+        tc_commit(d1full(b));
+        return true;
+      };
+      auto stage2 = [&](int i) {  // backward product of tile i (T in shared memory) into D2[i & 1]
+        const int b = i & 1;
+        if (!wait_bounded(tready(b), (uint32_t)((i >> 1) & 1), ab)) return false;
+        if (!wait_bounded(d2empty(b), (uint32_t)(((i >> 1) & 1) ^ 1), ab)) return false;
+        tc_fence_after();
+        const uint32_t dacc = tmem + 256u + (uint32_t)(b * 128);
+        for (int kt = 0; kt < KT; ++kt) {
+          const unsigned long long wd = dW2 + (uint32_t)kt * w2kt, td = dT + (uint32_t)(b * KT + kt) * tkt;
+          const int nk = min(4, (a.C - kt * kKTile + 15) >> 4);
+  #pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            if (kk < nk) tc_mma(dacc, wd + 2u * kk, td + 2u * kk, idesc2, (kt > 0 || kk > 0) ? 1u : 0u);
+        }
+        tc_commit(d2full(b));
+        return true;
+      };
+      if (ok && nmine > 0) ok = stage1(0);
+      for (int i = 0; ok && i < nmine; ++i) {
+        if (i + 1 < nmine && !(ok = stage1(i + 1))) break;
+        ok = stage2(i);
       }
-      tc_commit(d1full(b));
-      return true;
-    };
-    auto stage2 = [&](int i) {  // backward product of tile i (T in shared memory) into D2[i & 1]
-      const int b = i & 1;
-      if (!wait_bounded(tready(b), (uint32_t)((i >> 1) & 1), ab)) return false;
-      if (!wait_bounded(d2empty(b), (uint32_t)(((i >> 1) & 1) ^ 1), ab)) return false;
-      tc_fence_after();
-      const uint32_t dacc = tmem + 256u + (uint32_t)(b * 128);
-      for (int kt = 0; kt < KT; ++kt) {
-        const unsigned long long wd = dW2 + (uint32_t)kt * w2kt, td = dT + (uint32_t)(b * KT + kt) * tkt;
-        const int nk = min(4, (a.C - kt * kKTile + 15) >> 4);
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          if (kk < nk) tc_mma(dacc, wd + 2u * kk, td + 2u * kk, idesc2, (kt > 0 || kk > 0) ? 1u : 0u);
+      tc_commit(drain);  // every MMA this thread issued is complete once `drain` fires
+      const unsigned long long t0 = gtimer();
+      while (!mbar_try_wait(drain, 0) && gtimer() - t0 < kWaitLimitNs) {
       }
-      tc_commit(d2full(b));
-      return true;
-    };
-    if (ok && nmine > 0) ok = stage1(0);
-    for (int i = 0; ok && i < nmine; ++i) {
-      if (i + 1 < nmine && !(ok = stage1(i + 1))) break;
-      ok = stage2(i);
     }
-    tc_commit(drain);  // every MMA this thread issued is complete once `drain` fires
-    const unsigned long long t0 = gtimer();
-    while (!mbar_try_wait(drain, 0) && gtimer() - t0 < kWaitLimitNs) {
-    }
+    __syncwarp();
   } else if (warp >= 2) {
     // ---------------- epilogue: four warps per TMEM lane quadrant, warp h of a quadrant taking the 16-column
     // chunks h*16 + 64*j

@@ -40,14 +40,14 @@ def _run(prec, shape, bcs, maxit, eta):
 
 
 def _fp64_scalars(L, R1, Z, P, alpha, singular):
-    """FP64 <L P, P> and rho_s = <R_s, Z_s'> of the vectors the device held (oracle ordering)."""
+    """FP64 <L P, P>, rho_s = <R_s, Z_s'> of the vectors the device held (oracle ordering), and ||R_s||."""
     p = o.vec(to_oracle(P))
     lp = L @ p
     wp = float(p @ lp)
     r_s = o.vec(to_oracle(R1)) + alpha * lp  # R_s from R_{s+1} = R_s - alpha_s L P_s
     z = o.vec(to_oracle(Z))
     rho = float(r_s @ z) - (float(z.mean()) * float(r_s.sum()) if singular else 0.0)
-    return wp, rho
+    return wp, rho, float(np.linalg.norm(r_s))
 
 
 CASES = [
@@ -71,7 +71,11 @@ def test_cg_scalars_match_fp64_dots(prec, shape, bcs):
         if info["iters"] < s:  # converged before s iterations
             break
         assert sc["iter"] == s
-        wp, rho = _fp64_scalars(L, R1, Z, P, sc["alpha"], singular)
+        wp, rho, rn = _fp64_scalars(L, R1, Z, P, sc["alpha"], singular)
+        if rn < 1e-9 * info["eta_norm"]:
+            # R_s is at the FP64 rounding floor (the FP64 form after one iteration): the host's
+            # reconstruction R_{s+1} + alpha L P cancels to noise, there is nothing left to compare
+            break
         e_wp = abs(sc["wp"] - wp) / wp
         e_rho = abs(sc["rho"] - rho) / rho
         e_alpha = abs(sc["alpha"] - rho / wp) / (rho / wp)
@@ -81,13 +85,13 @@ def test_cg_scalars_match_fp64_dots(prec, shape, bcs):
     print(f"\n{prec} {shape} {bcs}: iteration, rel. error of <W,P>, rho, alpha, beta vs FP64 dots")
     for r in rows:
         print("  s=%d  %.2e  %.2e  %.2e  %.2e" % r)
-    assert len(rows) >= 2
+    assert len(rows) >= (1 if prec == "fp64" else 3)
     N = nx * ny * nz
     if prec == "fp64":
         bound_wp = bound_rho = 1e-12
     else:
-        bound_wp = 1e-5  # FP32 partial sums per thread
-        # R~ rounding (uncorrelated with Z) plus FP32 partial sums
+        bound_wp = 1e-7  # FP32 partial sums per thread of exact integer differences (measured ~5e-9)
+        # R~ rounding (uncorrelated with Z) plus FP32 partial sums (measured 1e-7..3e-6 FP16, 5e-6..1e-5 BF16)
         ulp = 2.0 ** -11 if prec == "fp16" else 2.0 ** -8
         bound_rho = max(1e-5, 50 * ulp / np.sqrt(N))
     for s, e_wp, e_rho, e_alpha, e_beta in rows:

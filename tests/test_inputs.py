@@ -101,6 +101,26 @@ def test_serving_sessions_move_one_percent_of_their_defects():
     assert moved.sum() == max(1, len(ses.charges) // 100)
 
 
+def test_serving_incremental_update_equals_fresh_field():
+    """apply_moves on a field at step k-2 with the moves of steps k-1 and k gives the field of step k (the
+    bench's two-buffer scheme), at the scale fixed on the first step."""
+    ses = synth.ServingSession(7, 64, 32, 16, ("P", "D", "N"))
+    scale = ses.paper_scale()
+    periodic = tuple(b == "P" for b in ses.bcs)
+
+    def fresh():
+        return scale * synth.gaussian_defects((ses.nz, ses.ny, ses.nx), periodic, ses.centres,
+                                              np.full(len(ses.charges), ses.sigma), ses.charges, "charge")
+
+    buf = fresh()
+    np.testing.assert_allclose(np.linalg.norm(buf), 1.0 / buf.size, rtol=1e-12)
+    m1 = ses.step()
+    m2 = ses.step()
+    ses.apply_moves(buf, m1, scale)
+    ses.apply_moves(buf, m2, scale)
+    np.testing.assert_allclose(buf, fresh(), rtol=0, atol=1e-12 * np.abs(buf).max())
+
+
 def test_poisson_arrivals():
     t = synth.poisson_arrivals(200.0, 20000, seed=1)
     assert np.all(np.diff(t) > 0)
