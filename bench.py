@@ -427,8 +427,9 @@ def run_batched(prec, torch):
 # profiles/.  Set an entry to None when its kernel changes.
 NCU_TRAFFIC_PER_LAUNCH = {
     # DRAM bytes (read + write) per launch from the ncu captures summarised under profiles/ (cold caches)
-    # tensor-core launches: None until the frontal-slice kernels have been captured again
-    "modeprod_tc": None,
+    # tensor-core launches: mean over the three launches of one application (frontal-slice sequence): the
+    # forward x-y pair (17.1 MB), the tube pair (16.9 MB) and the backward x-y pair (34.7 MB)
+    "modeprod_tc": (17.1e6 + 16.9e6 + 34.7e6) / 3,
     "update": 275.0e6,  # the in-place update the instrumented (one-plan) pass runs
     "form_u": 248.0e6,  # the formation before a check (six recorded directions; TPCG_OPT_DEFER_U)
     "direction": 76.2e6,
