@@ -406,6 +406,18 @@ def run_batched(prec, torch):
         e = torch.from_numpy(np.stack([synth.batched_rhs(sp, r) for r in range(sp["nrhs"])])).cuda()
         etas.append(e)
         ups.append(torch.zeros_like(e))
+    # the launch sequence of every plan chosen by the autotuner (timed once per grid; the choices of this
+    # run are cached in a temporary file shared by plans of the same grid)
+    import tempfile
+
+    with tempfile.TemporaryDirectory() as td:
+        cache = os.path.join(td, "tpcg_tune.txt")
+        tunes = [pl.autotune(cache, applies=5) for pl in plans]
+    torch.cuda.synchronize()
+    chosen = {}
+    for tu in tunes:
+        k = f"slices={tu['slices']},fuse_g={tu['fuse_g']}"
+        chosen[k] = chosen.get(k, 0) + 1
     args = ([p.handle for p in plans], [sp["nrhs"] for sp in specs], [e.data_ptr() for e in etas],
             [u.data_ptr() for u in ups], [1e-10] * len(specs), 60, binding.TPCG_ZERO_GUESS)
     binding.tpcg_solve_batched(*args)  # warm-up
@@ -419,7 +431,8 @@ def run_batched(prec, torch):
     return {"solves": len(specs), "rhs": nrhs, "form": f"mixed-{prec}", "seconds": dt, "rhs_per_s": nrhs / dt,
             "mpoints_per_s": points / dt / 1e6, "status": st,
             "worst_rel_res_true": max(i["rel_res_true"] for i in infos),
-            "mean_iters": float(np.mean([i["iters"] for i in infos]))}
+            "mean_iters": float(np.mean([i["iters"] for i in infos])),
+            "autotuned_sequences": chosen, "autotune_timed": sum(t["candidates"] for t in tunes)}
 
 
 # DRAM bytes (read + write) per launch measured by ncu on the 256x256x128 FP16 workload (one capture
@@ -743,6 +756,20 @@ def run_ours(args, rank, world, torch):
                     "worst_rel_res_true": max(i["rel_res_true"] for (_, i) in infb)}
         pb.close()
 
+    # the TF32 mixed form (one launch per mode product, FP32 intermediates), same workload and timing rules
+    tf32_cmp = None
+    if prec == "fp16" and not args.no_bf16_compare:
+        pt = Plan(nx, ny, nz, w0["bcs"], prec="tf32")
+        for s in range(args.warmup):
+            pt.solve(etas[s % 4], ups, tol=args.tol, maxit=60, zero_guess=True)
+        dtt, inft, _ = time_steps(pt, etas, ups, args.steps, args.tol, torch, barrier)
+        dtt = max_over_ranks(dtt, world, torch, dev)
+        tf32_cmp = {"value": whole_job_rate(world, args.steps, dtt), "unit": "solves/s", "steps": args.steps,
+                    "iters_per_solve": sum(i["iters"] for (_, i) in inft) / args.steps,
+                    "worst_rel_res_true": max(i["rel_res_true"] for (_, i) in inft),
+                    "tc_launches_per_apply": pt.precond_launches()}
+        pt.close()
+
     # the plain FP64 form for comparison (fewer steps: it is ~100x slower)
     fp64_cmp = None
     if prec != "fp64" and not args.no_fp64_compare:
@@ -801,7 +828,7 @@ def run_ours(args, rank, world, torch):
             "worst_rel_res_true": worst_res, "failed_solves": len(bad),
             "gpu_launches": launches, "single_plan": single,
             "roofline": roofline, "kernels": kernels,
-            "e2e": e2e, "cpu_baseline": cpu, "fp64_form": fp64_cmp, "bf16_form": bf16_cmp,
+            "e2e": e2e, "cpu_baseline": cpu, "fp64_form": fp64_cmp, "bf16_form": bf16_cmp, "tf32_form": tf32_cmp,
             "serving": serving, "batched": batched, "comparators": comparators, "efield": efield,
             "cube_256": cube, "clocks": clocks,
         }

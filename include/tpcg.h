@@ -67,7 +67,11 @@ extern "C" {
  * beta, the solution update and the null-space (mean) projection are FP64;
  * only the three forward and three backward mode products change.        */
 #define TPCG_FP64         0  /* mode products in FP64 (CUDA cores)                   */
-#define TPCG_MIXED_TF32   1  /* reserved: TF32 tensor-core mode products             */
+#define TPCG_MIXED_TF32   1  /* TF32 tensor-core mode products (FP32 containers rounded
+                                to nearest even at the 10-bit TF32 mantissa), FP32
+                                accumulation and FP32 intermediates: FP32's range,
+                                no scaling; one launch per mode product, the
+                                eigenbasis streamed with the data                   */
 #define TPCG_MIXED_BF16   2  /* BF16 tensor-core mode products, FP32 accumulation    */
 #define TPCG_MIXED_FP16   3  /* FP16 tensor-core mode products, FP32 accumulation;
                                 R is scaled by a power of two to unit RMS before the
@@ -197,6 +201,30 @@ int tpcg_solve_host_stream(tpcg_plan* plan, int nrhs, const double* const* eta_h
 #define TPCG_OPT_FUSE_G 2
 #define TPCG_OPT_SLICES 3
 int tpcg_plan_set_option(tpcg_plan* plan, int option, int value);
+
+/* Autotuner of the preconditioner's launch sequence (no counterpart in the
+ * paper: it chooses how the library schedules the same products of
+ * Algorithm 7).  For a mixed-form plan it times every distinct sequence the
+ * plan offers -- frontal-slice launches or one launch per mode product
+ * (TPCG_OPT_SLICES), the products around G fused or not (TPCG_OPT_FUSE_G) --
+ * with `applies` preconditioner applications each (CUDA events on the plan's
+ * stream, a constant input in the plan's own buffers, nothing allocated),
+ * sets the fastest as the plan's options and reports it.  cache_path (host
+ * string, may be NULL): a text file of lines "nx ny nz prec slices fuse_g
+ * us_per_apply"; a line for this grid and precision is used without timing
+ * (from_cache = 1), a new result is appended.  The plan's workspace contents
+ * (R, its 16-bit copy, Z) are overwritten: call between solves.  FP64 plans
+ * have one sequence: TPCG_OK with candidates = 0.  Synchronises the plan's
+ * stream.  TPCG_ERR_INVALID_ARG (NULL plan or out, applies outside 1..1000),
+ * TPCG_ERR_CUDA.                                                            */
+typedef struct {
+  int slices;            /* TPCG_OPT_SLICES chosen                                 */
+  int fuse_g;            /* TPCG_OPT_FUSE_G chosen                                 */
+  double us_per_apply;   /* its time per preconditioner application (microseconds) */
+  int candidates;        /* sequences timed (0 when read from the cache)           */
+  int from_cache;        /* 1: taken from cache_path                               */
+} tpcg_tune_result;
+int tpcg_plan_autotune(tpcg_plan* plan, const char* cache_path, int applies, tpcg_tune_result* out);
 
 /* Many independent solves in one call (the batched form of tpcg_solve).
  * Solve s uses plans[s] and has nrhs[s] right-hand sides (nrhs == NULL: one

@@ -75,6 +75,14 @@ class tpcg_cg_scalars(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class tpcg_tune_result(ctypes.Structure):
+    _fields_ = [("slices", ctypes.c_int), ("fuse_g", ctypes.c_int), ("us_per_apply", ctypes.c_double),
+                ("candidates", ctypes.c_int), ("from_cache", ctypes.c_int)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 class tpcg_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_ulonglong), ("total_ms", ctypes.c_double)]
 
@@ -129,6 +137,7 @@ _SIGS = {
     "tpcg_plan_set_option": (_I, [_P, _I, _I]),
     "tpcg_plan_eigenpairs": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "tpcg_plan_cg_scalars": (_I, [_P, ctypes.POINTER(tpcg_cg_scalars)]),
+    "tpcg_plan_autotune": (_I, [_P, ctypes.c_char_p, _I, ctypes.POINTER(tpcg_tune_result)]),
     "tpcg_plan_cg_vectors": (_I, [_P, _P, _P, _P]),
     "tpcg_plan_launch_count": (_I, [_P, ctypes.POINTER(ctypes.c_ulonglong)]),
     "tpcg_plan_precond_launches": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
@@ -260,6 +269,12 @@ def tpcg_plan_eigenpairs(plan, axis, length):
     V = (_D * (length * length))()
     st = lib().tpcg_plan_eigenpairs(plan, int(axis), lam, V)
     return st, list(lam), list(V)
+
+
+def tpcg_plan_autotune(plan, cache_path=None, applies=5):
+    out = tpcg_tune_result()
+    st = lib().tpcg_plan_autotune(plan, cache_path.encode() if cache_path else None, int(applies), ctypes.byref(out))
+    return st, out.as_dict()
 
 
 def tpcg_plan_cg_scalars(plan):
@@ -549,6 +564,13 @@ class Plan:
 
     def launch_count(self):
         return tpcg_plan_launch_count(self.handle)[1]
+
+    def autotune(self, cache_path=None, applies=5):
+        """Time the preconditioner's launch sequences and keep the fastest (tpcg_plan_autotune)."""
+        st, d = tpcg_plan_autotune(self.handle, cache_path, applies)
+        if st != TPCG_OK:
+            raise TpcgError(st, "tpcg_plan_autotune")
+        return d
 
     def cg_scalars(self):
         """Device scalars of the most recent CG iteration (see tpcg_plan_cg_scalars)."""

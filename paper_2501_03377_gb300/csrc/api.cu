@@ -200,6 +200,25 @@ uint16_t host_bf16(double x) {
   return (uint16_t)(sign | bits);
 }
 
+// FP64 -> TF32 in an FP32 container: one round-to-nearest-even step at the 10-bit mantissa, on the FP64 bit
+// pattern (eigenbasis entries are finite, |x| <= 1, far inside the normal range).
+float host_tf32(double x) {
+  uint64_t u;
+  std::memcpy(&u, &x, 8);
+  const uint64_t sign = u >> 63;
+  const int e = (int)((u >> 52) & 0x7ff);
+  if (e == 0 || e - 1023 + 127 <= 0) return sign ? -0.0f : 0.0f;
+  const uint64_t mant = u & 0xfffffffffffffull;
+  uint64_t top = mant >> 42;                 // 10 kept bits
+  const uint64_t rest = mant & ((1ull << 42) - 1), half = 1ull << 41;
+  uint32_t bits = ((uint32_t)(e - 1023 + 127) << 23) | (uint32_t)(top << 13);
+  if (rest > half || (rest == half && (top & 1u))) bits += 1u << 13;  // carry may bump the exponent: correct
+  bits |= (uint32_t)sign << 31;
+  float f;
+  std::memcpy(&f, &bits, 4);
+  return f;
+}
+
 uint16_t host_f16(double x) {
   // FP64 -> FP16 (binary16), one round-to-nearest-even step, subnormals kept
   uint64_t u;
@@ -398,7 +417,6 @@ int tpcg_plan_create(int nx, int ny, int nz, const int bc[3], const double h[3],
   }
   if (prec != TPCG_FP64 && prec != TPCG_MIXED_BF16 && prec != TPCG_MIXED_TF32 && prec != TPCG_MIXED_FP16)
     return TPCG_ERR_INVALID_ARG;
-  if (prec == TPCG_MIXED_TF32) return TPCG_ERR_UNSUPPORTED;
   if (prec != TPCG_FP64 && (nx > 256 || ny > 256 || nz > 256)) return TPCG_ERR_UNSUPPORTED;
   const long long N = (long long)nx * ny * nz;
   if (N > (1LL << 31)) return TPCG_ERR_UNSUPPORTED;
@@ -411,7 +429,7 @@ int tpcg_plan_create(int nx, int ny, int nz, const int bc[3], const double h[3],
     p->h[m] = (m < naxes) ? h[m] : 1.0;
   }
   p->prec = prec;
-  p->lp_kind = (prec == TPCG_MIXED_BF16) ? 1 : (prec == TPCG_MIXED_FP16 ? 2 : 0);
+  p->lp_kind = (prec == TPCG_MIXED_BF16) ? 1 : (prec == TPCG_MIXED_FP16 ? 2 : (prec == TPCG_MIXED_TF32 ? 3 : 0));
   p->stream = (cudaStream_t)stream;
   p->is2d = (nz == 1);
   p->N = N;
@@ -450,7 +468,23 @@ int tpcg_plan_create(int nx, int ny, int nz, const int bc[3], const double h[3],
     cudaMemcpy(p->d_W64[m][1], VT.data(), sizeof(double) * l * l, cudaMemcpyHostToDevice);    // W = V^T
     cudaMemcpy(p->d_lam64[m], A.lam.data(), sizeof(double) * l, cudaMemcpyHostToDevice);
     cudaMemcpy(p->d_lam32[m], lam32.data(), sizeof(float) * lam32.size(), cudaMemcpyHostToDevice);
-    if (prec != TPCG_FP64) {
+    if (prec == TPCG_MIXED_TF32) {
+      // K-major W^T in TF32 (FP32 containers rounded to nearest even at the TF32 mantissa), as below
+      const int lp = p->pitch16[m];
+      std::vector<float> f0((size_t)l * lp, 0.0f), f1((size_t)l * lp, 0.0f);
+      for (int r = 0; r < l; ++r)
+        for (int c = 0; c < l; ++c) {
+          f0[(size_t)r * lp + c] = host_tf32(A.V[(size_t)c * l + r]);
+          f1[(size_t)r * lp + c] = host_tf32(A.V[(size_t)r * l + c]);
+        }
+      float *d0 = nullptr, *d1 = nullptr;
+      if ((rc = dalloc(p, &d0, f0.size()))) break;
+      p->d_Wt16[m][0] = d0;
+      if ((rc = dalloc(p, &d1, f1.size()))) break;
+      p->d_Wt16[m][1] = d1;
+      cudaMemcpy(d0, f0.data(), f0.size() * 4, cudaMemcpyHostToDevice);
+      cudaMemcpy(d1, f1.data(), f1.size() * 4, cudaMemcpyHostToDevice);
+    } else if (prec != TPCG_FP64) {
       // K-major W^T in BF16 / FP16: dir 0 (W = V) -> element [c'][c] = V[c][c']; dir 1 (W = V^T) -> V[c'][c].
       const int lp = p->pitch16[m];
       std::vector<uint16_t> b0((size_t)l * lp, 0), b1((size_t)l * lp, 0);
@@ -495,9 +529,10 @@ int tpcg_plan_create(int nx, int ny, int nz, const int bc[3], const double h[3],
       p->d_Z = z;
     }
   }
+  const size_t lp_elem = (prec == TPCG_MIXED_TF32) ? 2 : 1;  // 16-bit words per tensor-core operand
   if (!rc && prec != TPCG_FP64) {
     uint16_t* r = nullptr;
-    rc = dalloc(p, &r, (size_t)nz * ny * p->pitch16[0]);
+    rc = dalloc(p, &r, (size_t)nz * ny * p->pitch16[0] * lp_elem);
     p->d_Rlp = r;
   }
   for (int i = 0; i < 2 && !rc; ++i) {
@@ -507,9 +542,9 @@ int tpcg_plan_create(int nx, int ny, int nz, const int bc[3], const double h[3],
       p->d_T[i] = t;
     } else {
       uint16_t* t = nullptr;
-      rc = dalloc(p, &t, p->t_elems);
+      rc = dalloc(p, &t, p->t_elems * lp_elem);
       p->d_T[i] = t;
-      if (!rc) cudaMemset(t, 0, p->t_elems * 2);
+      if (!rc) cudaMemset(t, 0, p->t_elems * 2 * lp_elem);
     }
   }
   if (!rc) rc = dalloc(p, &p->d_state, 1);
@@ -874,6 +909,99 @@ int tpcg_efield(tpcg_plan* plan, const double* ups, const double bval[6], double
   DeviceGuard dg(plan->device);
   launch_efield(plan, make_geom(plan), ups, bval, ex, ey, plan->nz > 1 ? ez : nullptr);
   return last_cuda_error();
+}
+
+int tpcg_plan_autotune(tpcg_plan* plan, const char* cache_path, int applies, tpcg_tune_result* out) {
+  if (!plan || !out || applies < 1 || applies > 1000) return TPCG_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->slices = plan->tc_slab;
+  out->fuse_g = plan->tc_fuse;
+  if (plan->prec == TPCG_FP64) return TPCG_OK;  // one launch sequence only
+  DeviceGuard dg(plan->device);
+  char key[96];
+  std::snprintf(key, sizeof(key), "%d %d %d %d", plan->nx, plan->ny, plan->nz, plan->prec);
+  // a cached choice for this (grid, precision): "nx ny nz prec slices fuse_g us_per_apply" per line
+  if (cache_path) {
+    if (FILE* f = std::fopen(cache_path, "r")) {
+      char line[256];
+      while (std::fgets(line, sizeof(line), f)) {
+        int a[6];
+        double us = 0.0;
+        if (std::sscanf(line, "%d %d %d %d %d %d %lf", &a[0], &a[1], &a[2], &a[3], &a[4], &a[5], &us) == 7 &&
+            a[0] == plan->nx && a[1] == plan->ny && a[2] == plan->nz && a[3] == plan->prec && (a[4] == 0 || a[4] == 1) &&
+            (a[5] == 0 || a[5] == 1)) {
+          plan->tc_slab = a[4];
+          plan->tc_fuse = a[5];
+          out->slices = a[4];
+          out->fuse_g = a[5];
+          out->us_per_apply = us;
+          out->from_cache = 1;
+        }
+      }
+      std::fclose(f);
+      if (out->from_cache) return TPCG_OK;
+    }
+  }
+  // time every distinct launch sequence: the preconditioner alone, on a constant 16-bit input in the
+  // plan's own buffers (R~ in, Z out; nothing is allocated), events on the plan's stream
+  const int slab0 = plan->tc_slab, fuse0 = plan->tc_fuse;
+  const size_t lp_bytes = (size_t)plan->nz * plan->ny * plan->pitch16[0] * (plan->lp_kind == 3 ? 4 : 2);
+  if (cudaMemsetAsync(plan->d_Rlp, 0x3c, lp_bytes, plan->stream) != cudaSuccess) return TPCG_ERR_CUDA;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return TPCG_ERR_CUDA;
+  }
+  double best = -1.0;
+  int best_s = slab0, best_f = fuse0, rc = TPCG_OK;
+  std::vector<int> seen;  // launch counts per sequence, to skip options that change nothing
+  for (int sl = 1; sl >= 0 && !rc; --sl)
+    for (int fu = 1; fu >= 0 && !rc; --fu) {
+      plan->tc_slab = sl;
+      plan->tc_fuse = fu;
+      if (sl && !plan->slab_state) continue;
+      const int id = (sl && plan->slab_state ? 100 : 0) + tc_launches_per_apply(plan);
+      bool dup = false;
+      for (int v : seen) dup = dup || v == id;
+      if (dup) continue;
+      seen.push_back(id);
+      for (int w = 0; w < 2 && !rc; ++w) rc = run_precond_tc(plan, (float*)plan->d_Z, nullptr);
+      if (rc) break;
+      cudaEventRecord(e0, plan->stream);
+      for (int k = 0; k < applies && !rc; ++k) rc = run_precond_tc(plan, (float*)plan->d_Z, nullptr);
+      cudaEventRecord(e1, plan->stream);
+      float ms = 0.0f;
+      if (rc || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        rc = rc ? rc : TPCG_ERR_CUDA;
+        break;
+      }
+      const double us = 1e3 * (double)ms / applies;
+      ++out->candidates;
+      if (best < 0.0 || us < best) {
+        best = us;
+        best_s = sl;
+        best_f = fu;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  plan->tc_slab = rc ? slab0 : best_s;
+  plan->tc_fuse = rc ? fuse0 : best_f;
+  if (rc) {
+    last_cuda_error();
+    return rc;
+  }
+  if (last_cuda_error()) return TPCG_ERR_CUDA;
+  out->slices = best_s;
+  out->fuse_g = best_f;
+  out->us_per_apply = best;
+  if (cache_path) {
+    if (FILE* f = std::fopen(cache_path, "a")) {
+      std::fprintf(f, "%s %d %d %.3f\n", key, best_s, best_f, best);
+      std::fclose(f);
+    }
+  }
+  return TPCG_OK;
 }
 
 int tpcg_plan_cg_scalars(tpcg_plan* plan, tpcg_cg_scalars* out) {

@@ -154,9 +154,17 @@ __global__ void __launch_bounds__(TX* TY) k_apply_laplacian(Geom g, int zchunk, 
 // padded to `pitch` elements.  ptr == nullptr in the FP64 form.
 struct LowPrec {
   void* ptr;
-  int kind;  // 1 BF16, 2 FP16
+  int kind;  // 1 BF16, 2 FP16, 3 TF32 (FP32 containers, rounded to nearest even)
   int pitch, nx;
 };
+
+// r -> TF32 in an FP32 container: FP64 -> FP32 round-to-odd on the bit pattern, then round to nearest even
+// at the TF32 mantissa (round-to-odd keeps the sticky bit, so the two steps equal one correct rounding).
+__device__ __forceinline__ float f64_to_tf32(double r) {
+  const uint32_t b = __float_as_uint(f64_to_f32_odd(r, 0));
+  if ((b & 0x7f800000u) == 0x7f800000u) return __uint_as_float(b);
+  return __uint_as_float((b + 0xfffu + ((b >> 13) & 1u)) & 0xffffe000u);
+}
 
 // r32o = f64_to_f32_odd(r, shift): its RNE rounding to FP16 is the correctly
 // rounded r * 2^shift, saturated at the FP16 maximum.  BF16 takes r unscaled.
@@ -166,6 +174,10 @@ __device__ __forceinline__ void store_lp(const LowPrec& lp, long long i, double 
   if (lp.pitch != lp.nx) {  // padded rows (mixed forms: N < 2^32, 32-bit division)
     const unsigned row = (unsigned)i / (unsigned)lp.nx;
     j = (long long)row * lp.pitch + ((unsigned)i - row * (unsigned)lp.nx);
+  }
+  if (lp.kind == 3) {
+    reinterpret_cast<float*>(lp.ptr)[j] = f64_to_tf32(r);
+    return;
   }
   reinterpret_cast<uint16_t*>(lp.ptr)[j] =
       (lp.kind == 2) ? f32_to_f16_bits_rn(fminf(fmaxf(r32o, -65504.0f), 65504.0f)) : f64_to_bf16_bits(r);
@@ -179,6 +191,10 @@ __device__ __forceinline__ void store_lp_pair(const LowPrec& lp, long long i, do
   if (lp.pitch != lp.nx) {  // padded rows (mixed forms: N < 2^32, 32-bit division)
     const unsigned row = (unsigned)i / (unsigned)lp.nx;
     j = (long long)row * lp.pitch + ((unsigned)i - row * (unsigned)lp.nx);
+  }
+  if (lp.kind == 3) {
+    *reinterpret_cast<float2*>(reinterpret_cast<float*>(lp.ptr) + j) = make_float2(f64_to_tf32(r0), f64_to_tf32(r1));
+    return;
   }
   uint32_t v;
   if (lp.kind == 2) {

@@ -60,6 +60,13 @@ constexpr int kTileRows = 128;
 constexpr int kKTile = 64;                 // BF16 elements per 128-byte swizzle row
 constexpr int kStageBytes = kTileRows * 128;
 
+// Elements of InT per 128-byte swizzle row (one K tile) and per MMA K step.
+template <class InT>
+struct KShape {
+  static constexpr bool tf32 = sizeof(InT) == 4;
+  static constexpr int tile = 128 / (int)sizeof(InT);  // 64 (FP16/BF16) or 32 (TF32)
+  static constexpr int step = tf32 ? 8 : 16;
+};
 
 struct TcArgs {
   int C, KT, Cout, VR, Np, MB, acc_cols, tmem_cols, NS;
@@ -73,6 +80,8 @@ struct TcArgs {
   int tstore;  // outputs leave through shared memory by TMA stores (tmO), else by direct stores
   int tperm;   // form 2 output map: dims {B, A, Cout} (1) or {B, Cout, A} (0)
   int aux;     // bytes of shared memory after the stages: R~ ring (last pass) and output staging
+  int wstream;  // eigenbasis K tiles streamed with the data tiles (each stage holds both), else resident
+  int sbytes;   // bytes of one stage (data tile, plus the eigenbasis tile when streamed)
   int last;  // last pass: output is Z (FP32), undo the FP16 scaling
   int sG;    // the Hadamard step is multiplied by 2^-sG (FP16 range), undone on Z
   float gscale;          // 2^-sG
@@ -81,7 +90,8 @@ struct TcArgs {
   const float* lamB;
   const float* lamC;
   void* out;
-  const uint16_t* Rt;  // the tensor-core copy of R the first pass read (FP16 = R * 2^shR, or BF16 = R)
+  const uint16_t* Rt;  // the tensor-core copy of R the first pass read (FP16 = R * 2^shR, BF16 = R, or TF32 = R
+                       // in FP32 containers)
   int rpitch;          // its row pitch (elements)
   SolveState* st;
   double* partials;
@@ -89,7 +99,6 @@ struct TcArgs {
   int* err;
 };
 
-// FP32 reciprocal, hardware approximation (max error ~1 ulp): far below the
 template <class OutT>
 __device__ __forceinline__ void store_out(void* out, long long o, float v) {
   if constexpr (std::is_same<OutT, __half>::value)
@@ -137,14 +146,17 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* sm = smem_raw + (base - raw);
+  using KS = KShape<InT>;
   const uint32_t sV = base;
-  const uint32_t sD = sV + (uint32_t)a.KT * a.VR * 128u;
+  const uint32_t vres = a.wstream ? 0u : (uint32_t)a.KT * a.VR * 128u;  // resident eigenbasis
+  const uint32_t sD = sV + vres;
+  const uint32_t sbytes = (uint32_t)a.sbytes;
   const bool rtma = FINAL && a.rtma;
-  const uint32_t sR = sD + (uint32_t)a.NS * kStageBytes;  // 1024-aligned: V and stages are multiples of 1 KB
+  const uint32_t sR = sD + (uint32_t)a.NS * sbytes;  // 1024-aligned: V and stages are multiples of 1 KB
   // output staging: two [32][16] boxes per epilogue warp, after the R~ ring of the last pass
   constexpr uint32_t kOBytes = 32u * 16u * (uint32_t)sizeof(OutT);
   const uint32_t sO = sR + (rtma ? (uint32_t)(2 * a.rhalf * kRBytes) : 0u);
-  uint8_t* barp = sm + (size_t)a.KT * a.VR * 128 + (size_t)a.NS * kStageBytes + (size_t)a.aux;
+  uint8_t* barp = sm + (size_t)vres + (size_t)a.NS * sbytes + (size_t)a.aux;
   const uint32_t bars = smem_u32(barp);
   const int NS = a.NS;
   auto full = [&](int s) { return bars + 8u * s; };
@@ -201,8 +213,10 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer
-      mbar_expect_tx(vbar, (uint32_t)a.KT * a.VR * 128u);
-      for (int kt = 0; kt < a.KT; ++kt) tma_load_2d(sV + (uint32_t)kt * a.VR * 128u, &tmW, kt * kKTile, 0, vbar);
+      if (!a.wstream) {
+        mbar_expect_tx(vbar, (uint32_t)a.KT * a.VR * 128u);
+        for (int kt = 0; kt < a.KT; ++kt) tma_load_2d(sV + (uint32_t)kt * a.VR * 128u, &tmW, kt * KS::tile, 0, vbar);
+      }
       // the operand is the previous pass's output: wait until that grid has completed
       asm volatile("griddepcontrol.wait;" ::: "memory");
       int it = 0;
@@ -211,8 +225,9 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
           const int s = it % NS;
           const uint32_t ph = (uint32_t)((it / NS) & 1);
           if (!wait_bounded(empty(s), ph ^ 1u, ab)) break;
-          mbar_expect_tx(full(s), kStageBytes);
-          tma_load_2d(sD + (uint32_t)s * kStageBytes, &tmX, kt * kKTile, tile * kTileRows, full(s));
+          mbar_expect_tx(full(s), sbytes);
+          tma_load_2d(sD + (uint32_t)s * sbytes, &tmX, kt * KS::tile, tile * kTileRows, full(s));
+          if (a.wstream) tma_load_2d(sD + (uint32_t)s * sbytes + kStageBytes, &tmW, kt * KS::tile, 0, full(s));
         }
       }
       // drain: every issued load has completed before the CTA may exit
@@ -223,7 +238,7 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
           }
         }
         const unsigned long long t0 = gtimer();
-        while (!mbar_try_wait(vbar, 0) && gtimer() - t0 < kWaitLimitNs) {
+        while (!a.wstream && !mbar_try_wait(vbar, 0) && gtimer() - t0 < kWaitLimitNs) {
         }
       }
     }
@@ -231,7 +246,7 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer
-      constexpr uint32_t fmt = std::is_same<InT, __half>::value ? 0u : 1u;
+      constexpr uint32_t fmt = KS::tf32 ? 2u : (std::is_same<InT, __half>::value ? 0u : 1u);
       const uint32_t idesc = (FORM == 1) ? idesc_f16kind(128, a.Np, fmt) : idesc_f16kind(128, 128, fmt);
       // Shared-memory descriptors: the address field holds address / 16 in its low 14 bits (shared memory
       // is below 256 KB, so offsets add without a carry out of the field); a 16-element K step is +2.
@@ -240,7 +255,7 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
       const unsigned long long dX0 = sw128_desc(sD), dV0 = sw128_desc(sV);
       const uint32_t vkt = (uint32_t)(a.VR * 128) >> 4;  // one 64-wide K tile of V
       const bool two_mb = (FORM != 1) && a.MB > 1;       // second 128-row block of V (form 2)
-      bool ok = wait_bounded(vbar, 0, ab);
+      bool ok = a.wstream ? true : wait_bounded(vbar, 0, ab);
       int it = 0, tcount = 0;
       for (int tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x, ++tcount) {
         const int b = tcount & 1;
@@ -251,19 +266,23 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
           const int s = it % NS;
           if (!(ok = wait_bounded(full(s), (uint32_t)((it / NS) & 1), ab))) break;
           tc_fence_after();
-          const unsigned long long xd = dX0 + (uint32_t)s * (uint32_t)(kStageBytes >> 4);
-          const unsigned long long vd = dV0 + (uint32_t)kt * vkt;
-          const int nk = min(4, (a.C - kt * kKTile + 15) >> 4);  // K steps of 16 inside C
-  #pragma unroll
+          const unsigned long long xd = dX0 + (uint32_t)s * (sbytes >> 4);
+          const unsigned long long vd =
+              a.wstream ? dX0 + (uint32_t)s * (sbytes >> 4) + (uint32_t)(kStageBytes >> 4) : dV0 + (uint32_t)kt * vkt;
+          const int nk = min(4, (a.C - kt * KS::tile + KS::step - 1) / KS::step);  // K steps inside C
+          auto mma = [&](uint32_t d, unsigned long long ad, unsigned long long bd, uint32_t acc) {
+            if constexpr (KS::tf32) tc_mma_tf32(d, ad, bd, idesc, acc);
+            else tc_mma(d, ad, bd, idesc, acc);
+          };
+#pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             if (kk < nk) {
               const uint32_t accum = (kt > 0 || kk > 0) ? 1u : 0u;
               if (FORM == 1) {
-                tc_mma(dacc, xd + 2u * kk, vd + 2u * kk, idesc, accum);
+                mma(dacc, xd + 2u * kk, vd + 2u * kk, accum);
               } else {
-                tc_mma(dacc, vd + 2u * kk, xd + 2u * kk, idesc, accum);
-                if (two_mb)
-                  tc_mma(dacc + 128u, vd + (uint32_t)(kStageBytes >> 4) + 2u * kk, xd + 2u * kk, idesc, accum);
+                mma(dacc, vd + 2u * kk, xd + 2u * kk, accum);
+                if (two_mb) mma(dacc + 128u, vd + (uint32_t)(kStageBytes >> 4) + 2u * kk, xd + 2u * kk, accum);
               }
             }
           }
@@ -385,7 +404,7 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
           return true;
         };
         auto fetch_r = [&](int j, uint4 (&rb)[2]) {
-          if (FINAL && !rtma && vec && j < J && col(j) + 16 <= a.Cout) {
+          if (FINAL && !KS::tf32 && !rtma && vec && j < J && col(j) + 16 <= a.Cout) {
             const uint4* rp = reinterpret_cast<const uint4*>(a.Rt + (long long)r * a.rpitch + col(j));
             rb[0] = __ldg(rp);
             rb[1] = __ldg(rp + 1);
@@ -411,12 +430,30 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
           if (a.last) {
 #pragma unroll
             for (int j = 0; j < 16; ++j) v[j] *= zs;
+          } else if constexpr (KS::tf32) {  // intermediates: round to TF32 (nearest even) for the next pass
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = tf32_rn(v[j]);
           }
           if (a.tstore) emit(v, c0, row0 + q * 32, 0);  // rows past `rows`, columns past Cout: clipped
           if (!valid) return;
           if (vec && c0 + 16 <= a.Cout) {
             if (!a.tstore) store16<OutT>(a.out, obase + c0, v);
-            if (FINAL) {
+            if (FINAL && KS::tf32) {  // R~ in FP32 containers, 16 values of this row
+              const float4* rp =
+                  reinterpret_cast<const float4*>(reinterpret_cast<const float*>(a.Rt) + (long long)r * a.rpitch + c0);
+              float d0 = 0.0f, d1 = 0.0f;
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                const float4 rr = __ldg(rp + i);
+                d0 = fmaf(rr.x * rs, v[4 * i], fmaf(rr.y * rs, v[4 * i + 1], d0));
+                d1 = fmaf(rr.z * rs, v[4 * i + 2], fmaf(rr.w * rs, v[4 * i + 3], d1));
+                zmax = fmaxf(zmax, fmaxf(fmaxf(fabsf(v[4 * i]), fabsf(v[4 * i + 1])),
+                                         fmaxf(fabsf(v[4 * i + 2]), fabsf(v[4 * i + 3]))));
+              }
+              red0.add(d0 + d1);
+              red1.add(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) +
+                       (((v[8] + v[9]) + (v[10] + v[11])) + ((v[12] + v[13]) + (v[14] + v[15]))));
+            } else if (FINAL) {
               const uint32_t rw[8] = {rcur[0].x, rcur[0].y, rcur[0].z, rcur[0].w,
                                       rcur[1].x, rcur[1].y, rcur[1].z, rcur[1].w};
               float d0 = 0.0f, d1 = 0.0f;
@@ -439,8 +476,10 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
                 const long long o = obase + (long long)c * a.oc;
                 if (!a.tstore) store_out<OutT>(a.out, o, v[j]);
                 if (FINAL) {
-                  const uint32_t rb16 = __ldg(a.Rt + (long long)r * a.rpitch + c);
-                  red0.add(lp2_to_f32<InT>(rb16).x * rs * v[j]);
+                  float rv;
+                  if constexpr (KS::tf32) rv = __ldg(reinterpret_cast<const float*>(a.Rt) + (long long)r * a.rpitch + c);
+                  else rv = lp2_to_f32<InT>(__ldg(a.Rt + (long long)r * a.rpitch + c)).x;
+                  red0.add(rv * rs * v[j]);
                   red1.add(v[j]);
                   zmax = fmaxf(zmax, fabsf(v[j]));
                 }
@@ -495,7 +534,7 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
           if (r0 >= a.rows) return;  // warp-uniform
           float v[16];
 #pragma unroll
-          for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(t[i]);
+          for (int i = 0; i < 16; ++i) v[i] = KS::tf32 ? tf32_rn(__uint_as_float(t[i])) : __uint_as_float(t[i]);
           int ia = r0 / a.B;
           int ib = r0 - ia * a.B;
           if (a.tstore) {  // B % 16 == 0: the 16 rows share one a; output indices past Cout are clipped
@@ -715,7 +754,7 @@ __global__ void __launch_bounds__(kPairThreads, 1)
           const unsigned long long xd = dX0 + (uint32_t)s * (uint32_t)(kStageBytes >> 4);
           const unsigned long long wd = dW1 + (uint32_t)kt * w1kt;
           const int nk = min(4, (a.C - kt * kKTile + 15) >> 4);
-  #pragma unroll
+#pragma unroll
           for (int kk = 0; kk < 4; ++kk)
             if (kk < nk) tc_mma(dacc, xd + 2u * kk, wd + 2u * kk, idesc1, (kt > 0 || kk > 0) ? 1u : 0u);
           tc_commit(empty(s));
@@ -732,7 +771,7 @@ __global__ void __launch_bounds__(kPairThreads, 1)
         for (int kt = 0; kt < KT; ++kt) {
           const unsigned long long wd = dW2 + (uint32_t)kt * w2kt, td = dT + (uint32_t)(b * KT + kt) * tkt;
           const int nk = min(4, (a.C - kt * kKTile + 15) >> 4);
-  #pragma unroll
+#pragma unroll
           for (int kk = 0; kk < 4; ++kk)
             if (kk < nk) tc_mma(dacc, wd + 2u * kk, td + 2u * kk, idesc2, (kt > 0 || kk > 0) ? 1u : 0u);
         }
@@ -897,6 +936,7 @@ struct TcStage {
 };
 
 struct TcPlan {
+  bool tf32 = false;  // TF32 form: FP32 containers, eigenbasis streamed, one launch per pass
   std::vector<TcStage> stages;  // one launch per pass of Algorithm 7
   std::vector<TcStage> fused;   // the same with the pass pair around G in one launch (empty when not possible)
   bool fp16 = false;
@@ -956,16 +996,21 @@ int encode_out(CUtensorMap* map, void* gaddr, int esize, bool fp16, int form, co
   return r == CUDA_SUCCESS ? 0 : -1;
 }
 
+// Operands of the tensor core: FP16, BF16 or (TF32 form) FP32 containers.
+enum class OpType { kF16, kBF16, kF32 };
+
 int encode_2d(CUtensorMap* map, const void* gaddr, int inner, long long outer, int pitch_elems, int box_inner,
-              int box_outer, bool fp16) {
+              int box_outer, OpType ty) {
   EncodeTiledFn cuTensorMapEncodeTiled = encoder();
   if (!cuTensorMapEncodeTiled) return -1;
+  const int esz = (ty == OpType::kF32) ? 4 : 2;
   cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
-  cuuint64_t strides[1] = {(cuuint64_t)pitch_elems * 2};
+  cuuint64_t strides[1] = {(cuuint64_t)pitch_elems * esz};
   cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = cuTensorMapEncodeTiled(map, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
-                                      2, const_cast<void*>(gaddr), dims,
+  const CUtensorMapDataType dt = ty == OpType::kF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : (ty == OpType::kF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+  CUresult r = cuTensorMapEncodeTiled(map, dt, 2, const_cast<void*>(gaddr), dims,
                                       strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : -1;
@@ -990,6 +1035,14 @@ int set_all_smem_attrs() {
                  cudaSuccess
              ? 0
              : -1;
+  return bad;
+}
+
+int set_tf32_smem_attrs() {
+  int bad = 0;
+  bad |= set_smem_attr<1, float, float, false>(kMaxSmem);
+  bad |= set_smem_attr<2, float, float, false>(kMaxSmem);
+  bad |= set_smem_attr<1, float, float, true>(kMaxSmem);
   return bad;
 }
 
@@ -1026,7 +1079,7 @@ void launch_pair(const TcStage& s, const TcArgs& a, cudaStream_t stream) {
 template <class InT>
 void launch_stage(const TcStage& s, const TcArgs& a, bool last, bool final_pcg, cudaStream_t stream) {
   if (s.pair) {
-    launch_pair<InT>(s, a, stream);
+    if constexpr (sizeof(InT) == 2) launch_pair<InT>(s, a, stream);  // (no fused pair in the TF32 form)
   } else if (!last) {
     if (s.form == 1) launch<1, InT, InT, false>(s, a, stream);
     else launch<2, InT, InT, false>(s, a, stream);
@@ -1074,9 +1127,13 @@ int slab_launches_per_apply(const tpcg_plan* p);
 int run_precond_slab(const tpcg_plan* p, float* Z, SolveState* st);
 
 int tc_plan_setup(tpcg_plan* p) {
-  if (p->prec != TPCG_MIXED_BF16 && p->prec != TPCG_MIXED_FP16) return TPCG_ERR_UNSUPPORTED;
+  if (p->prec != TPCG_MIXED_BF16 && p->prec != TPCG_MIXED_FP16 && p->prec != TPCG_MIXED_TF32)
+    return TPCG_ERR_UNSUPPORTED;
   TcPlan* tp = new TcPlan();
   tp->fp16 = (p->prec == TPCG_MIXED_FP16);
+  tp->tf32 = (p->prec == TPCG_MIXED_TF32);
+  const OpType oty = tp->tf32 ? OpType::kF32 : (tp->fp16 ? OpType::kF16 : OpType::kBF16);
+  const int ktile = tp->tf32 ? 32 : kKTile;  // elements per 128-byte K tile
   // FP16 range: R enters at unit RMS, so intermediates of the forward passes
   // are bounded by sqrt(N); after G they are bounded by sqrt(N) * max G,
   // which 2^-sG brings under 2^14 (below the FP16 maximum 65504).
@@ -1091,7 +1148,7 @@ int tc_plan_setup(tpcg_plan* p) {
     st.form = (sp.oc == 1) ? 1 : 2;
     TcArgs& a = st.args;
     a.C = sp.C;
-    a.KT = (sp.C + kKTile - 1) / kKTile;
+    a.KT = (sp.C + ktile - 1) / ktile;
     a.Cout = sp.Cout;
     a.Np = ((sp.Cout + 15) / 16) * 16;
     a.MB = (sp.Cout + 127) / 128;
@@ -1123,12 +1180,17 @@ int tc_plan_setup(tpcg_plan* p) {
     a.sG = sG;
     a.gscale = std::ldexp(1.0f, -sG);
     a.shift_src = tp->fp16 ? &p->d_state->lp_shift_applied : nullptr;
-    const size_t vbytes = (size_t)a.KT * a.VR * 128;
+    // TF32: the eigenbasis (up to 256 x 256 FP32, 256 KB) does not fit next to the stages; each stage then
+    // carries its K tile of the eigenbasis with the data tile
+    a.wstream = tp->tf32 ? 1 : 0;
+    a.sbytes = kStageBytes + (a.wstream ? a.VR * 128 : 0);
+    const size_t sbytes = (size_t)a.sbytes;
+    const size_t vbytes = a.wstream ? 0 : (size_t)a.KT * a.VR * 128;
     size_t fixed = 1024 + vbytes + 512;  // alignment, eigenbasis, barriers and the TMEM address
-    if (a.tmem_cols > 512 || a.VR > 256 || fixed + 2 * kStageBytes > (size_t)kMaxSmem) return TPCG_ERR_UNSUPPORTED;
+    if (a.tmem_cols > 512 || a.VR > 256 || fixed + 2 * sbytes > (size_t)kMaxSmem) return TPCG_ERR_UNSUPPORTED;
     // outputs by TMA stores through per-warp staging when the layout allows
     const bool last = sp.final_stage != 0;
-    const int esz = last ? 4 : 2;
+    const int esz = (last || tp->tf32) ? 4 : 2;
     st.out = out_addr;
     st.tmO = st.tmX;
     a.tstore = (encode_out(&st.tmO, out_addr, esz, tp->fp16, st.form, a, &a.tperm) == 0) ? 1 : 0;
@@ -1139,26 +1201,26 @@ int tc_plan_setup(tpcg_plan* p) {
     // elements) by TMA through the largest ring (up to kRHalf slots per half) that leaves two stages
     a.rpitch = p->pitch16[0];
     a.rhalf = 0;
-    if (last && st.form == 1) {
-      const size_t room = (size_t)kMaxSmem - fixed - 2 * kStageBytes;
+    if (last && st.form == 1 && !tp->tf32) {  // (the TF32 form reads its FP32 R~ with global loads)
+      const size_t room = (size_t)kMaxSmem - fixed - 2 * sbytes;
       const size_t rh = room > stage_final ? (room - stage_final) / (2 * (size_t)kRBytes) : 0;
       a.rhalf = (int)std::min<size_t>(kRHalf, rh);
     }
     a.rtma = (a.rhalf >= 2) ? 1 : 0;
     if (!a.rtma) a.rhalf = 0;
     a.aux = (int)std::max(stage_plain, (size_t)(2 * a.rhalf * kRBytes) + stage_final);
-    if (fixed + (size_t)a.aux + 2 * kStageBytes > (size_t)kMaxSmem) {  // no room for staging: direct stores
+    if (fixed + (size_t)a.aux + 2 * sbytes > (size_t)kMaxSmem) {  // no room for staging: direct stores
       a.tstore = 0;
       a.aux = 2 * a.rhalf * kRBytes;
     }
     fixed += (size_t)a.aux;
-    a.NS = (int)std::min<size_t>(8, (kMaxSmem - fixed) / kStageBytes);
-    st.smem = fixed + (size_t)a.NS * kStageBytes;
+    a.NS = (int)std::min<size_t>(8, (kMaxSmem - fixed) / sbytes);
+    st.smem = fixed + (size_t)a.NS * sbytes;
     const int ntiles = (a.rows + kTileRows - 1) / kTileRows;
     st.grid = std::max(1, std::min(ntiles, p->num_sms));
     const int wpitch = p->pitch16[sp.axis];
-    if (encode_2d(&st.tmX, xin, sp.C, (long long)a.rows, sp.in_pitch, kKTile, kTileRows, tp->fp16) ||
-        encode_2d(&st.tmW, p->d_Wt16[sp.axis][sp.dir], sp.C, sp.Cout, wpitch, kKTile, a.VR, tp->fp16))
+    if (encode_2d(&st.tmX, xin, sp.C, (long long)a.rows, sp.in_pitch, ktile, kTileRows, oty) ||
+        encode_2d(&st.tmW, p->d_Wt16[sp.axis][sp.dir], sp.C, sp.Cout, wpitch, ktile, a.VR, oty))
       return TPCG_ERR_CUDA;
     st.tmW2 = st.tmW;
     st.tmR = st.tmX;
@@ -1168,7 +1230,7 @@ int tc_plan_setup(tpcg_plan* p) {
   // Passes si (forward, with G, form 1) and si + 1 (backward along the same axis, form 2) as one
   // k_modeprod_pair launch; TPCG_ERR_UNSUPPORTED when the pair does not fit its layout rules.
   auto build_pair = [&](int si, const void* xin, void* out_addr, TcStage& st) -> int {
-    if (si + 1 >= ns) return TPCG_ERR_UNSUPPORTED;
+    if (si + 1 >= ns || tp->tf32) return TPCG_ERR_UNSUPPORTED;
     const StageParams& s1 = p->stages[si];
     const StageParams& s2 = p->stages[si + 1];
     const bool shape_ok = s1.scale && !s1.final_stage && s1.oc == 1 && !s2.final_stage && s2.oc != 1 &&
@@ -1186,7 +1248,7 @@ int tc_plan_setup(tpcg_plan* p) {
     st.pair = 1;
     st.tmX = f.tmX;
     st.tmW = f.tmW;  // W1: the forward eigenbasis, rows padded to a multiple of 8
-    if (encode_2d(&st.tmW2, p->d_Wt16[s2.axis][s2.dir], s2.C, s2.Cout, p->pitch16[s2.axis], kKTile, 128, tp->fp16))
+    if (encode_2d(&st.tmW2, p->d_Wt16[s2.axis][s2.dir], s2.C, s2.Cout, p->pitch16[s2.axis], kKTile, 128, oty))
       return TPCG_ERR_CUDA;
     TcArgs& a = st.args;
     a.Np = f.args.Np;
@@ -1237,7 +1299,8 @@ int tc_plan_setup(tpcg_plan* p) {
     delete tp;
     return rc;
   }
-  const int bad = tp->fp16 ? set_all_smem_attrs<__half>() : set_all_smem_attrs<__nv_bfloat16>();
+  const int bad = tp->tf32 ? set_tf32_smem_attrs()
+                            : (tp->fp16 ? set_all_smem_attrs<__half>() : set_all_smem_attrs<__nv_bfloat16>());
   if (bad) {
     delete tp;
     return TPCG_ERR_CUDA;
@@ -1281,7 +1344,8 @@ int run_precond_tc(const tpcg_plan* p, float* Z, SolveState* st) {
     a.Rt = reinterpret_cast<const uint16_t*>(p->d_Rlp);
     a.partials = p->d_partials;
     LaunchScope ls(p, kKModeTC);
-    if (tp->fp16) launch_stage<__half>(s, a, last, st != nullptr, p->stream);
+    if (tp->tf32) launch_stage<float>(s, a, last, st != nullptr, p->stream);
+    else if (tp->fp16) launch_stage<__half>(s, a, last, st != nullptr, p->stream);
     else launch_stage<__nv_bfloat16>(s, a, last, st != nullptr, p->stream);
   }
   return TPCG_OK;

@@ -144,12 +144,13 @@ void pinned_put(tpcg_server* s, size_t bytes, void* p) {
 size_t estimate_slot_bytes(const PlanKey& k) {
   const size_t N = (size_t)k.nx * k.ny * k.nz;
   const bool fp64 = (k.prec == TPCG_FP64);
+  const size_t lpb = (k.prec == TPCG_MIXED_TF32) ? 4 : 2;  // bytes of a tensor-core operand
   size_t b = N * 8 + (fp64 ? N * 8 * 3 : N * 4 * 2);  // R; P[2] and W (FP64) or P[2] in int32
   b += N * (fp64 ? 8 : 4);                   // Z
-  b += fp64 ? 0 : N * 2 + (size_t)k.ny * k.nz * 16;  // low-precision copy of R (padded rows)
-  b += 2 * N * (fp64 ? 8 : 2) + 2 * (size_t)(k.nx + k.ny + k.nz) * 64;  // mode-product intermediates
+  b += fp64 ? 0 : N * lpb + (size_t)k.ny * k.nz * 8 * lpb;  // low-precision copy of R (padded rows)
+  b += 2 * N * (fp64 ? 8 : lpb) + 2 * (size_t)(k.nx + k.ny + k.nz) * 64;  // mode-product intermediates
   const size_t l2 = (size_t)k.nx * k.nx + (size_t)k.ny * k.ny + (size_t)k.nz * k.nz;
-  b += l2 * (16 + (fp64 ? 0 : 8));           // eigenbases
+  b += l2 * (16 + (fp64 ? 0 : 4 * lpb));     // eigenbases
   b += (1 << 20) + 16384 * 4 * 8;            // state, partial sums, slack
   b += N * 8 * 2;                            // slot's eta / ups buffers
   return b;

@@ -95,6 +95,24 @@ __device__ __forceinline__ void tc_mma(uint32_t d, unsigned long long a, unsigne
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
+// The same MMA with TF32 operands (32-bit containers, K = 8 per instruction), FP32 accumulation.
+__device__ __forceinline__ void tc_mma_tf32(uint32_t d, unsigned long long a, unsigned long long b, uint32_t idesc,
+                                            uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// FP32 -> TF32 (10-bit mantissa) with round-to-nearest-even on the bit pattern, kept in an FP32
+// container (the tensor core reads the top 19 bits); Inf/NaN unchanged, overflow to Inf.
+__device__ __forceinline__ float tf32_rn(float x) {
+  const uint32_t b = __float_as_uint(x);
+  if ((b & 0x7f800000u) == 0x7f800000u) return x;
+  const uint32_t r = b + 0xfffu + ((b >> 13) & 1u);
+  return __uint_as_float(r & 0xffffe000u);
+}
+
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -135,6 +153,8 @@ __device__ __forceinline__ unsigned long long sw128_desc(uint32_t saddr) {
 __host__ __device__ constexpr uint32_t idesc_f16kind(int M, int N, uint32_t fmt) {
   return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+
+// FP32 reciprocal, hardware approximation (max error ~1 ulp): far below the
 // FP16/BF16 rounding of the value it scales.
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;

@@ -49,6 +49,13 @@ def f16_from_f64(x, shift=0):
     return np.ldexp(np.asarray(x, dtype=np.float64), shift).astype(np.float16).astype(np.float32)
 
 
+def tf32_from(x):
+    """Round to TF32 (11 significant bits, FP32's exponent range), nearest even; returned as float32."""
+    x = np.asarray(x, dtype=np.float64)
+    m, e = np.frexp(x)
+    return np.ldexp(np.round(np.ldexp(m, 11)), e - 11).astype(np.float32)
+
+
 def lp_shift(r):
     rms = np.sqrt(np.mean(np.asarray(r, dtype=np.float64) ** 2))
     return 0 if rms == 0 else int(np.clip(-np.floor(np.log2(rms)) - 1, -120, 120))
@@ -68,6 +75,9 @@ def emulate_precond(r_nqt, Vs, lams, singular, prec="bf16", slices=False):
     three_d = r_nqt.shape[2] > 1
     if prec == "bf16":
         rin, rd, Vb = (lambda x: bf16_from_f64(x)), bf16_from_f32, [bf16_from_f64(V) for V in Vs]
+        s, sG = 0, 0
+    elif prec == "tf32":
+        rin, rd, Vb = tf32_from, tf32_from, [tf32_from(V) for V in Vs]
         s, sG = 0, 0
     else:
         s = lp_shift(r_nqt)

@@ -123,3 +123,14 @@ def test_batched_48_mixed_solves_fp16():
         assert torch.equal(us, ups[s][0])
         if o.is_singular((spec["nx"], spec["ny"], spec["nz"]), spec["bcs"]):
             assert abs(ups[s][0].mean().item()) <= 1e-14 * ups[s][0].abs().max().item()
+    # every spec: the true residual of its last right-hand side recomputed on the host with the oracle's
+    # assembled Kronecker sum (independent of the GPU's own residual check)
+    for spec, e, u in zip(specs, etas, ups):
+        sh = (spec["nx"], spec["ny"], spec["nz"])
+        L = o.kron_sum(sh, spec["bcs"])
+        r = spec["nrhs"] - 1
+        eh = to_oracle(e[r].cpu().numpy())
+        if o.is_singular(sh, spec["bcs"]):
+            eh = o.center(eh)
+        res = np.linalg.norm(o.vec(eh) - L @ o.vec(to_oracle(u[r].cpu().numpy()))) / np.linalg.norm(eh)
+        assert res <= 1e-10, (spec, res)

@@ -83,7 +83,7 @@ CASES = [
 
 
 @pytest.mark.parametrize("slices", [1, 0])
-@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "tf32"])
 @pytest.mark.parametrize("shape,bcs", CASES)
 def test_precond_tc_matches_emulation_and_oracle(shape, bcs, prec, slices):
     from paper_2501_03377_gb300 import binding as b
@@ -93,7 +93,7 @@ def test_precond_tc_matches_emulation_and_oracle(shape, bcs, prec, slices):
     pl = _plan(nx, ny, nz, bcs, prec)
     pl.set_option(b.TPCG_OPT_SLICES, slices)
     sl = uses_slices(pl, nz)
-    if slices == 0:
+    if slices == 0 or prec == "tf32":  # the TF32 form runs one launch per mode product
         assert not sl
     elif nz > 1 and nx % 16 == 0:
         assert sl
@@ -111,8 +111,8 @@ def test_precond_tc_matches_emulation_and_oracle(shape, bcs, prec, slices):
     ref = from_oracle(o.pinv_apply(to_oracle(r), Vo, G))
     e_ref = rel_err(z, ref)
     print(f"{prec} {shape} {bcs} slices={int(sl)}: |z - emulation| = {e_emu:.2e}, |z - fp64 oracle| = {e_ref:.2e}")
-    # one ulp: 2^-8 (BF16), 2^-11 (FP16); summation-order flips are rare
-    assert e_emu <= (4e-3 if prec == "bf16" else 5e-4)
+    # one ulp: 2^-8 (BF16), 2^-11 (FP16, TF32); summation-order flips are rare
+    assert e_emu <= {"bf16": 4e-3, "fp16": 5e-4, "tf32": 5e-4}[prec]
     assert e_ref <= (5e-2 if prec == "bf16" else 6e-3)
 
 
@@ -126,7 +126,7 @@ SOLVE_CASES = [
 ]
 
 
-@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "tf32"])
 @pytest.mark.parametrize("shape,bcs", SOLVE_CASES)
 def test_solve_tc_matches_oracle(shape, bcs, prec):
     nx, ny, nz = shape
@@ -166,7 +166,7 @@ def test_tc_solve_deterministic(prec):
     assert np.array_equal(outs[0], outs[1])
 
 
-@pytest.mark.parametrize("prec,nz", [("bf16", 128), ("fp16", 128), ("fp16", 256)])
+@pytest.mark.parametrize("prec,nz", [("bf16", 128), ("fp16", 128), ("fp16", 256), ("tf32", 128)])
 def test_cuboid_256_tc_full_size(prec, nz):
     """256x256x128 P/P/N cuboid (singular), mixed forms, tol 1e-10, in the bench's launch configuration,
     and the 256x256x256 cube (the z axis past 128 points: the tube products as two launches).
@@ -174,7 +174,10 @@ def test_cuboid_256_tc_full_size(prec, nz):
     assembled operator, zero mean) and against the oracle's direct pseudoinverse solution."""
     w = synth.workload_cuboid_256(seed=0, nz=nz)
     pl = _plan(w["nx"], w["ny"], w["nz"], w["bcs"], prec)
-    assert uses_slices(pl, nz) and pl.precond_launches() == (3 if nz <= 128 else 4)
+    if prec == "tf32":
+        assert pl.precond_launches() == 6
+    else:
+        assert uses_slices(pl, nz) and pl.precond_launches() == (3 if nz <= 128 else 4)
     ed = _dev(w["eta"])
     ud = torch.zeros_like(ed)
     st, info = pl.solve(ed, ud, tol=1e-10, maxit=60, zero_guess=True)
@@ -414,3 +417,30 @@ def test_defer_u_set_between_solves_is_bitwise(prec):
         outs.append(u.cpu().numpy())
     assert np.array_equal(u2.cpu().numpy(), outs[0])
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("shape,bcs", [((64, 64, 32), ("P", "P", "N")), ((37, 9, 5), ("N", "N", "N")),
+                                       ((96, 64, 160), ("D", "P", "N"))])
+def test_autotune_picks_a_sequence_caches_it_and_solves(shape, bcs, tmp_path):
+    """tpcg_plan_autotune times the distinct launch sequences, keeps the fastest, appends it to the cache
+    file; a second plan of the same grid takes it from the cache; solves after tuning still meet the bars."""
+    from paper_2501_03377_gb300 import binding as b
+
+    nx, ny, nz = shape
+    cache = str(tmp_path / "tune.txt")
+    pl = _plan(nx, ny, nz, bcs, "fp16")
+    r1 = pl.autotune(cache, applies=3)
+    assert r1["from_cache"] == 0 and r1["candidates"] >= 1 and r1["us_per_apply"] > 0
+    assert r1["candidates"] <= (4 if nx % 16 == 0 else 2)
+    q = _plan(nx, ny, nz, bcs, "fp16")
+    r2 = q.autotune(cache, applies=3)
+    assert r2["from_cache"] == 1 and (r2["slices"], r2["fuse_g"]) == (r1["slices"], r1["fuse_g"])
+    assert open(cache).read().count("\n") == 1
+    eta = synth.defect_rhs(nx, ny, nz, bcs, 8, 1.5, seed=95)
+    ed = _dev(eta)
+    ud = torch.zeros_like(ed)
+    st, info = q.solve(ed, ud, tol=1e-10, maxit=60, zero_guess=True)
+    assert st == 0 and info["rel_res_true"] <= 1e-10
+    f64 = _plan(nx, ny, nz, bcs, "fp64")
+    assert f64.autotune(None)["candidates"] == 0
+    assert b.tpcg_plan_autotune(pl.handle, None, 0)[0] == b.TPCG_ERR_INVALID_ARG
