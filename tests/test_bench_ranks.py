@@ -64,17 +64,22 @@ def test_reference_arm_prints_only_on_rank_zero(capsys):
 
 
 def test_kernel_work_counts_the_algorithmic_bytes():
-    """The roofline's numerator: per application, each tensor-core launch but the last moves 4 B per
-    point (FP16 in and out) and the last 8 (FP16 in, the FP16 copy of R, Z in FP32), so five launches
-    (the pair around G fused) move 24 B per point and six move 28; the stencil kernels' per-point
-    bytes are those of their operands."""
+    """The roofline's numerator.  The tensor-core preconditioner is counted at the scope table's 30 B per
+    point per application whatever the launch sequence; its design model beside it: each launch but the
+    last moves 4 B per point (FP16 in and out) and the last 8 (FP16 in, the FP16 copy of R, Z in FP32), so
+    three launches (frontal slices) move 16 B per point, five (the pair around G fused) 24 and six 28; the
+    stencil kernels' per-point bytes are those of their operands."""
     N, dims = 1000, (10, 10, 10)
-    amount, unit, bound, worked = bench.kernel_work("modeprod_tc", "fp16", N, dims, 6, 7, 1, 1, 5)
-    assert (unit, bound, worked) == ("GB", "hbm", 35)
-    assert amount * 1e9 == pytest.approx(7 * 24 * N)
-    amount, _, _, worked = bench.kernel_work("modeprod_tc", "fp16", N, dims, 6, 7, 1, 1, 6)
+    amount, unit, bound, worked = bench.kernel_work("modeprod_tc", "fp16", N, dims, 6, 7, 1, 1, 3)
+    assert (unit, bound, worked) == ("GB", "hbm", 21)
+    assert amount * 1e9 == pytest.approx(7 * 30 * N)
+    amount, _, _, worked = bench.kernel_work("modeprod_tc_design", "fp16", N, dims, 6, 7, 1, 1, 3)
+    assert worked == 21 and amount * 1e9 == pytest.approx(7 * 16 * N)
+    amount, _, _, worked = bench.kernel_work("modeprod_tc_design", "fp16", N, dims, 6, 7, 1, 1, 5)
+    assert worked == 35 and amount * 1e9 == pytest.approx(7 * 24 * N)
+    amount, _, _, worked = bench.kernel_work("modeprod_tc_design", "fp16", N, dims, 6, 7, 1, 1, 6)
     assert worked == 42 and amount * 1e9 == pytest.approx(7 * 28 * N)
-    amount, _, _, worked = bench.kernel_work("modeprod_tc", "bf16", N, (10, 10, 1), 6, 7, 1, 1, None)
+    amount, _, _, worked = bench.kernel_work("modeprod_tc_design", "bf16", N, (10, 10, 1), 6, 7, 1, 1, None)
     assert worked == 28 and amount * 1e9 == pytest.approx(7 * 20 * N)  # 2D, four launches
     amount, _, _, _ = bench.kernel_work("direction", "fp16", N, dims, 6, 7, 1, 1)
     assert amount * 1e9 == pytest.approx(6 * 12 * N)  # Z 4 + P_old 4 in, P 4 out
