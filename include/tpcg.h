@@ -78,6 +78,16 @@ extern "C" {
                                 conversion and the Hadamard step by 2^-s so every
                                 intermediate stays inside the FP16 range; the scale
                                 is undone exactly on Z                              */
+#define TPCG_MIXED_BF16X3 4  /* split BF16 tensor-core mode products: every operand x
+                                (R, the eigenbases, each intermediate) is carried as
+                                two BF16 words hi = bf16(x), lo = bf16(x - hi), and
+                                each K step issues three MMAs, hi.hi + lo.hi + hi.lo,
+                                into one FP32 accumulator (the lo.lo term, 2^-16
+                                relative, is dropped): mode products accurate to
+                                about 2^-16 instead of 2^-8, so CG needs fewer
+                                refinement iterations; one launch per mode product,
+                                the eigenbasis streamed with the data, intermediates
+                                4 B per point (hi and lo planes)                    */
 
 /* ---- tpcg_solve flags ---------------------------------------------------- */
 #define TPCG_ZERO_GUESS   1u  /* ignore ups on entry and start from ups = 0 */
@@ -181,8 +191,10 @@ int tpcg_solve_host_stream(tpcg_plan* plan, int nrhs, const double* const* eta_h
  * intermediate through memory fewer per preconditioner application, the same
  * operations, bitwise the same Z.  0 runs one launch per mode product.  Used
  * when the axis has at most 128 points, a multiple of 16, and the pass
- * layouts allow it; ignored otherwise and for TPCG_FP64.
- * TPCG_OPT_SLICES (mixed forms; 1 = on, the default): 3D grids with nx a
+ * layouts allow it; ignored otherwise and for TPCG_FP64, TPCG_MIXED_TF32 and
+ * TPCG_MIXED_BF16X3 (one launch per mode product).
+ * TPCG_OPT_SLICES (TPCG_MIXED_BF16 and TPCG_MIXED_FP16; 1 = on, the
+ * default; ignored for the other forms): 3D grids with nx a
  * multiple of 16 and every axis at most 256 points group the six mode products
  * of Algorithm 7 by the data they touch: one launch applies the x and the y
  * product to every z-plane (frontal slice) with the intermediate kept in

@@ -35,7 +35,9 @@ TPCG_FP64 = 0
 TPCG_MIXED_TF32 = 1
 TPCG_MIXED_BF16 = 2
 TPCG_MIXED_FP16 = 3
-PREC = {"fp64": TPCG_FP64, "tf32": TPCG_MIXED_TF32, "bf16": TPCG_MIXED_BF16, "fp16": TPCG_MIXED_FP16}
+TPCG_MIXED_BF16X3 = 4
+PREC = {"fp64": TPCG_FP64, "tf32": TPCG_MIXED_TF32, "bf16": TPCG_MIXED_BF16, "fp16": TPCG_MIXED_FP16,
+        "bf16x3": TPCG_MIXED_BF16X3}
 TPCG_ZERO_GUESS = 1
 TPCG_PRECOND_PINV = 0
 TPCG_PRECOND_NONE = 1

@@ -200,6 +200,14 @@ uint16_t host_bf16(double x) {
   return (uint16_t)(sign | bits);
 }
 
+// The value of a BF16 bit pattern (exact in FP64).
+double host_bf16_value(uint16_t b) {
+  const uint32_t u = (uint32_t)b << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return (double)f;
+}
+
 // FP64 -> TF32 in an FP32 container: one round-to-nearest-even step at the 10-bit mantissa, on the FP64 bit
 // pattern (eigenbasis entries are finite, |x| <= 1, far inside the normal range).
 float host_tf32(double x) {
@@ -415,7 +423,8 @@ int tpcg_plan_create(int nx, int ny, int nz, const int bc[3], const double h[3],
     if (bc[m] < 0 || bc[m] > 4) return TPCG_ERR_INVALID_ARG;
     if (!(h[m] > 0.0) || !std::isfinite(h[m])) return TPCG_ERR_INVALID_ARG;
   }
-  if (prec != TPCG_FP64 && prec != TPCG_MIXED_BF16 && prec != TPCG_MIXED_TF32 && prec != TPCG_MIXED_FP16)
+  if (prec != TPCG_FP64 && prec != TPCG_MIXED_BF16 && prec != TPCG_MIXED_TF32 && prec != TPCG_MIXED_FP16 &&
+      prec != TPCG_MIXED_BF16X3)
     return TPCG_ERR_INVALID_ARG;
   if (prec != TPCG_FP64 && (nx > 256 || ny > 256 || nz > 256)) return TPCG_ERR_UNSUPPORTED;
   const long long N = (long long)nx * ny * nz;
@@ -429,7 +438,11 @@ int tpcg_plan_create(int nx, int ny, int nz, const int bc[3], const double h[3],
     p->h[m] = (m < naxes) ? h[m] : 1.0;
   }
   p->prec = prec;
-  p->lp_kind = (prec == TPCG_MIXED_BF16) ? 1 : (prec == TPCG_MIXED_FP16 ? 2 : (prec == TPCG_MIXED_TF32 ? 3 : 0));
+  p->lp_kind = (prec == TPCG_MIXED_BF16)   ? 1
+               : (prec == TPCG_MIXED_FP16) ? 2
+               : (prec == TPCG_MIXED_TF32) ? 3
+               : (prec == TPCG_MIXED_BF16X3) ? 4
+                                             : 0;
   p->stream = (cudaStream_t)stream;
   p->is2d = (nz == 1);
   p->N = N;
@@ -486,13 +499,21 @@ int tpcg_plan_create(int nx, int ny, int nz, const int bc[3], const double h[3],
       cudaMemcpy(d1, f1.data(), f1.size() * 4, cudaMemcpyHostToDevice);
     } else if (prec != TPCG_FP64) {
       // K-major W^T in BF16 / FP16: dir 0 (W = V) -> element [c'][c] = V[c][c']; dir 1 (W = V^T) -> V[c'][c].
+      // The split form stores a second plane after the first: lo = bf16(v - hi), hi = bf16(v).
       const int lp = p->pitch16[m];
-      std::vector<uint16_t> b0((size_t)l * lp, 0), b1((size_t)l * lp, 0);
+      const size_t plane = (size_t)l * lp;
+      const bool split = (prec == TPCG_MIXED_BF16X3);
+      std::vector<uint16_t> b0(plane * (split ? 2 : 1), 0), b1(plane * (split ? 2 : 1), 0);
       for (int r = 0; r < l; ++r)
         for (int c = 0; c < l; ++c) {
           const double v0 = A.V[(size_t)c * l + r], v1 = A.V[(size_t)r * l + c];
-          b0[(size_t)r * lp + c] = (prec == TPCG_MIXED_FP16) ? host_f16(v0) : host_bf16(v0);
-          b1[(size_t)r * lp + c] = (prec == TPCG_MIXED_FP16) ? host_f16(v1) : host_bf16(v1);
+          const size_t o = (size_t)r * lp + c;
+          b0[o] = (prec == TPCG_MIXED_FP16) ? host_f16(v0) : host_bf16(v0);
+          b1[o] = (prec == TPCG_MIXED_FP16) ? host_f16(v1) : host_bf16(v1);
+          if (split) {
+            b0[plane + o] = host_bf16(v0 - host_bf16_value(b0[o]));
+            b1[plane + o] = host_bf16(v1 - host_bf16_value(b1[o]));
+          }
         }
       uint16_t *d0 = nullptr, *d1 = nullptr;
       if ((rc = dalloc(p, &d0, b0.size()))) break;
@@ -529,10 +550,16 @@ int tpcg_plan_create(int nx, int ny, int nz, const int bc[3], const double h[3],
       p->d_Z = z;
     }
   }
-  const size_t lp_elem = (prec == TPCG_MIXED_TF32) ? 2 : 1;  // 16-bit words per tensor-core operand
+  // 16-bit words per tensor-core operand: TF32 in FP32 containers; the split form in two planes of
+  // BF16 words (hi, then lo), each plane a multiple of 64 words so the lo plane starts 128-byte aligned
+  const size_t lp_elem = (prec == TPCG_MIXED_TF32 || prec == TPCG_MIXED_BF16X3) ? 2 : 1;
+  if (prec == TPCG_MIXED_BF16X3) {
+    p->lp_plane = (size_t)pad_to(nz * ny * p->pitch16[0], 64);
+    p->t_plane = (size_t)pad_to((int)p->t_elems, 64);
+  }
   if (!rc && prec != TPCG_FP64) {
     uint16_t* r = nullptr;
-    rc = dalloc(p, &r, (size_t)nz * ny * p->pitch16[0] * lp_elem);
+    rc = dalloc(p, &r, p->lp_plane ? 2 * p->lp_plane : (size_t)nz * ny * p->pitch16[0] * lp_elem);
     p->d_Rlp = r;
   }
   for (int i = 0; i < 2 && !rc; ++i) {
@@ -542,9 +569,10 @@ int tpcg_plan_create(int nx, int ny, int nz, const int bc[3], const double h[3],
       p->d_T[i] = t;
     } else {
       uint16_t* t = nullptr;
-      rc = dalloc(p, &t, p->t_elems * lp_elem);
+      const size_t words = p->t_plane ? 2 * p->t_plane : p->t_elems * lp_elem;
+      rc = dalloc(p, &t, words);
       p->d_T[i] = t;
-      if (!rc) cudaMemset(t, 0, p->t_elems * 2 * lp_elem);
+      if (!rc) cudaMemset(t, 0, words * 2);
     }
   }
   if (!rc) rc = dalloc(p, &p->d_state, 1);
@@ -945,7 +973,8 @@ int tpcg_plan_autotune(tpcg_plan* plan, const char* cache_path, int applies, tpc
   // time every distinct launch sequence: the preconditioner alone, on a constant 16-bit input in the
   // plan's own buffers (R~ in, Z out; nothing is allocated), events on the plan's stream
   const int slab0 = plan->tc_slab, fuse0 = plan->tc_fuse;
-  const size_t lp_bytes = (size_t)plan->nz * plan->ny * plan->pitch16[0] * (plan->lp_kind == 3 ? 4 : 2);
+  const size_t lp_bytes = plan->lp_plane ? 4 * plan->lp_plane
+                                         : (size_t)plan->nz * plan->ny * plan->pitch16[0] * (plan->lp_kind == 3 ? 4 : 2);
   if (cudaMemsetAsync(plan->d_Rlp, 0x3c, lp_bytes, plan->stream) != cudaSuccess) return TPCG_ERR_CUDA;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {

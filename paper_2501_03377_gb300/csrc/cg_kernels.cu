@@ -150,13 +150,25 @@ __global__ void __launch_bounds__(TX* TY) k_apply_laplacian(Geom g, int zchunk, 
 }
 
 // ------------------------------------------------------------------ low-precision copy of R
-// Input of the first tensor-core pass: BF16, or FP16 of R * 2^shift, rows
-// padded to `pitch` elements.  ptr == nullptr in the FP64 form.
+// Input of the first tensor-core pass: BF16, FP16 of R * 2^shift, TF32, or the
+// BF16 pair hi = bf16(R), lo = bf16(R - hi) in two planes; rows padded to
+// `pitch` elements.  ptr == nullptr in the FP64 form.
 struct LowPrec {
   void* ptr;
-  int kind;  // 1 BF16, 2 FP16, 3 TF32 (FP32 containers, rounded to nearest even)
+  int kind;  // 1 BF16, 2 FP16, 3 TF32 (FP32 containers, rounded to nearest even), 4 BF16 hi/lo planes
   int pitch, nx;
+  long long plane;  // kind 4: 16-bit words from the hi plane to the lo plane
 };
+
+// The value of a BF16 bit pattern, exactly.
+__device__ __forceinline__ double bf16_bits_to_f64(uint16_t b) { return (double)__uint_as_float((uint32_t)b << 16); }
+
+// r -> (hi, lo) = (bf16(r), bf16(r - hi)), each rounded once to nearest even from FP64 (r - hi is exact).
+__device__ __forceinline__ uint32_t f64_to_bf16_split(double r) {
+  const uint16_t hi = f64_to_bf16_bits(r);
+  const uint16_t lo = f64_to_bf16_bits(r - bf16_bits_to_f64(hi));
+  return (uint32_t)hi | ((uint32_t)lo << 16);
+}
 
 // r -> TF32 in an FP32 container: FP64 -> FP32 round-to-odd on the bit pattern, then round to nearest even
 // at the TF32 mantissa (round-to-odd keeps the sticky bit, so the two steps equal one correct rounding).
@@ -179,6 +191,12 @@ __device__ __forceinline__ void store_lp(const LowPrec& lp, long long i, double 
     reinterpret_cast<float*>(lp.ptr)[j] = f64_to_tf32(r);
     return;
   }
+  if (lp.kind == 4) {
+    const uint32_t hl = f64_to_bf16_split(r);
+    reinterpret_cast<uint16_t*>(lp.ptr)[j] = (uint16_t)hl;
+    reinterpret_cast<uint16_t*>(lp.ptr)[lp.plane + j] = (uint16_t)(hl >> 16);
+    return;
+  }
   reinterpret_cast<uint16_t*>(lp.ptr)[j] =
       (lp.kind == 2) ? f32_to_f16_bits_rn(fminf(fmaxf(r32o, -65504.0f), 65504.0f)) : f64_to_bf16_bits(r);
 }
@@ -194,6 +212,13 @@ __device__ __forceinline__ void store_lp_pair(const LowPrec& lp, long long i, do
   }
   if (lp.kind == 3) {
     *reinterpret_cast<float2*>(reinterpret_cast<float*>(lp.ptr) + j) = make_float2(f64_to_tf32(r0), f64_to_tf32(r1));
+    return;
+  }
+  if (lp.kind == 4) {
+    const uint32_t h0 = f64_to_bf16_split(r0), h1 = f64_to_bf16_split(r1);
+    uint16_t* q = reinterpret_cast<uint16_t*>(lp.ptr);
+    *reinterpret_cast<uint32_t*>(q + j) = (h0 & 0xffffu) | (h1 << 16);
+    *reinterpret_cast<uint32_t*>(q + lp.plane + j) = (h0 >> 16) | (h1 & 0xffff0000u);
     return;
   }
   uint32_t v;
@@ -1727,7 +1752,9 @@ int setup_fx_grids(tpcg_plan* p) {
   }
   return 0;
 }
-LowPrec lowprec(const tpcg_plan* p) { return LowPrec{p->d_Rlp, p->lp_kind, p->pitch16[0], p->nx}; }
+LowPrec lowprec(const tpcg_plan* p) {
+  return LowPrec{p->d_Rlp, p->lp_kind, p->pitch16[0], p->nx, (long long)p->lp_plane};
+}
 
 // The caller's arrays are device pointers to doubles: only 8-byte alignment is guaranteed, so the
 // kernels that move them as 16-byte pairs run only when the pointers allow it.

@@ -839,7 +839,8 @@ int tc_fp16_g_exponent(const tpcg_plan* p);
 // The frontal-slice sequence applies to the FP16 and BF16 forms on 3D grids with nx a multiple of 16
 // (every slice row and every 16-column chunk aligned), nx, ny, nz <= 256.
 bool slab_applicable(const tpcg_plan* p) {
-  return p->prec != TPCG_MIXED_TF32 && !p->is2d && p->nx % 16 == 0 && p->nx <= 256 && p->ny <= 256 && p->nz <= 256 && p->nx >= 16;
+  return (p->prec == TPCG_MIXED_FP16 || p->prec == TPCG_MIXED_BF16) && !p->is2d && p->nx % 16 == 0 && p->nx <= 256 &&
+         p->ny <= 256 && p->nz <= 256 && p->nx >= 16;
 }
 
 int slab_plan_setup(tpcg_plan* p) {

@@ -1,12 +1,15 @@
-// Mixed-precision form of the pseudoinverse preconditioner (Algorithm 7,
+// Mixed-precision forms of the pseudoinverse preconditioner (Algorithm 7,
 // Sec. 4.3.3) on the 5th-generation tensor cores: every mode-product pass is
-// a BF16 x BF16 -> FP32 tcgen05 GEMM that contracts the contiguous index of
-// its input against the l x l eigenbasis.
+// a tcgen05 GEMM (FP16, BF16, TF32, or split BF16 pairs; FP32 accumulation)
+// that contracts the contiguous index of its input against the l x l
+// eigenbasis.
 //
 // One persistent, warp-specialised kernel serves every single pass:
-//   warp 0      TMA producer: loads the whole BF16 eigenbasis W^T (K-major,
-//               128B-swizzled) into shared memory once, then streams 128-row
-//               x 64-column K-tiles of the input through an NS-slot ring;
+//   warp 0      TMA producer: loads the eigenbasis W^T (K-major, 128B-
+//               swizzled) into shared memory once, then streams 128-row x
+//               128-byte K-tiles of the input through an NS-slot ring (the
+//               4-byte forms -- TF32 and the split BF16 pairs -- stream the
+//               eigenbasis K-tile with each data K-tile instead);
 //   warp 1      allocates TMEM; lane 0 issues tcgen05.mma (M = 128) and
 //               tcgen05.commit to release ring slots / publish accumulators;
 //   warps 2..9  epilogue: tcgen05.ld of the FP32 accumulator (one TMEM lane
@@ -60,12 +63,25 @@ constexpr int kTileRows = 128;
 constexpr int kKTile = 64;                 // BF16 elements per 128-byte swizzle row
 constexpr int kStageBytes = kTileRows * 128;
 
+// The split form's operand type: x carried as two BF16 planes, hi = bf16(x) and lo = bf16(x - hi).  A stage
+// holds the hi tile and then the lo tile of the data (and of the eigenbasis), and every K step issues three
+// MMAs into one FP32 accumulator: hi.hi + lo.hi + hi.lo (the lo.lo term, 2^-16 relative, is dropped).
+struct Bf16Pair {};
+
 // Elements of InT per 128-byte swizzle row (one K tile) and per MMA K step.
 template <class InT>
 struct KShape {
   static constexpr bool tf32 = sizeof(InT) == 4;
+  static constexpr bool split = false;
   static constexpr int tile = 128 / (int)sizeof(InT);  // 64 (FP16/BF16) or 32 (TF32)
   static constexpr int step = tf32 ? 8 : 16;
+};
+template <>
+struct KShape<Bf16Pair> {
+  static constexpr bool tf32 = false;
+  static constexpr bool split = true;
+  static constexpr int tile = 64;
+  static constexpr int step = 16;
 };
 
 struct TcArgs {
@@ -81,7 +97,7 @@ struct TcArgs {
   int tperm;   // form 2 output map: dims {B, A, Cout} (1) or {B, Cout, A} (0)
   int aux;     // bytes of shared memory after the stages: R~ ring (last pass) and output staging
   int wstream;  // eigenbasis K tiles streamed with the data tiles (each stage holds both), else resident
-  int sbytes;   // bytes of one stage (data tile, plus the eigenbasis tile when streamed)
+  int sbytes;   // bytes of one stage (data tile, plus the eigenbasis tile when streamed; split: hi and lo of each)
   int last;  // last pass: output is Z (FP32), undo the FP16 scaling
   int sG;    // the Hadamard step is multiplied by 2^-sG (FP16 range), undone on Z
   float gscale;          // 2^-sG
@@ -90,18 +106,29 @@ struct TcArgs {
   const float* lamB;
   const float* lamC;
   void* out;
-  const uint16_t* Rt;  // the tensor-core copy of R the first pass read (FP16 = R * 2^shR, BF16 = R, or TF32 = R
-                       // in FP32 containers)
+  const uint16_t* Rt;  // the tensor-core copy of R the first pass read (FP16 = R * 2^shR, BF16 = R, TF32 = R
+                       // in FP32 containers, or the split form's hi plane)
   int rpitch;          // its row pitch (elements)
+  long long rplane;    // split form: 16-bit words from the hi plane of R~ to its lo plane
+  long long oplane;    // split form: 16-bit words from the hi plane of the output to its lo plane
   SolveState* st;
   double* partials;
   long long N;
   int* err;
 };
 
+// hi = bf16(v) at o, lo = bf16(v - hi) one plane further (v - hi is exact in FP32).
+__device__ __forceinline__ void store_pair(void* out, long long plane, long long o, float v) {
+  const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+  reinterpret_cast<__nv_bfloat16*>(out)[o] = hi;
+  reinterpret_cast<__nv_bfloat16*>(out)[plane + o] = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
 template <class OutT>
-__device__ __forceinline__ void store_out(void* out, long long o, float v) {
-  if constexpr (std::is_same<OutT, __half>::value)
+__device__ __forceinline__ void store_out(void* out, long long plane, long long o, float v) {
+  if constexpr (std::is_same<OutT, Bf16Pair>::value)
+    store_pair(out, plane, o, v);
+  else if constexpr (std::is_same<OutT, __half>::value)
     reinterpret_cast<__half*>(out)[o] = __float2half_rn(v);
   else if constexpr (sizeof(OutT) == 2)
     reinterpret_cast<__nv_bfloat16*>(out)[o] = __float2bfloat16_rn(v);
@@ -109,10 +136,27 @@ __device__ __forceinline__ void store_out(void* out, long long o, float v) {
     reinterpret_cast<float*>(out)[o] = v;
 }
 
-// 16 consecutive outputs starting at element offset o (16-byte aligned).
+// 16 consecutive outputs starting at element offset o (16-byte aligned); the split form writes the hi
+// words at o and the lo words one plane further.
 template <class OutT>
-__device__ __forceinline__ void store16(void* out, long long o, const float (&x)[16]) {
-  if constexpr (sizeof(OutT) == 2) {
+__device__ __forceinline__ void store16(void* out, long long plane, long long o, const float (&x)[16]) {
+  if constexpr (std::is_same<OutT, Bf16Pair>::value) {
+    uint32_t ph[8], pl[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const __nv_bfloat162 h2 = __floats2bfloat162_rn(x[2 * i], x[2 * i + 1]);
+      const float2 hf = __bfloat1622float2(h2);
+      const __nv_bfloat162 l2 = __floats2bfloat162_rn(x[2 * i] - hf.x, x[2 * i + 1] - hf.y);
+      ph[i] = *reinterpret_cast<const uint32_t*>(&h2);
+      pl[i] = *reinterpret_cast<const uint32_t*>(&l2);
+    }
+    uint4* dh = reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(out) + o);
+    uint4* dl = reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(out) + plane + o);
+    dh[0] = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+    dh[1] = make_uint4(ph[4], ph[5], ph[6], ph[7]);
+    dl[0] = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+    dl[1] = make_uint4(pl[4], pl[5], pl[6], pl[7]);
+  } else if constexpr (sizeof(OutT) == 2) {
     uint32_t pk[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -153,8 +197,10 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
   const uint32_t sbytes = (uint32_t)a.sbytes;
   const bool rtma = FINAL && a.rtma;
   const uint32_t sR = sD + (uint32_t)a.NS * sbytes;  // 1024-aligned: V and stages are multiples of 1 KB
-  // output staging: two [32][16] boxes per epilogue warp, after the R~ ring of the last pass
-  constexpr uint32_t kOBytes = 32u * 16u * (uint32_t)sizeof(OutT);
+  // output staging: two [32][16] boxes per epilogue warp, after the R~ ring of the last pass (the split
+  // form stores directly)
+  using StageT = typename std::conditional<std::is_same<OutT, Bf16Pair>::value, __nv_bfloat16, OutT>::type;
+  constexpr uint32_t kOBytes = 32u * 16u * (uint32_t)sizeof(StageT);
   const uint32_t sO = sR + (rtma ? (uint32_t)(2 * a.rhalf * kRBytes) : 0u);
   uint8_t* barp = sm + (size_t)vres + (size_t)a.NS * sbytes + (size_t)a.aux;
   const uint32_t bars = smem_u32(barp);
@@ -209,12 +255,13 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
   float zmax = 0.0f;
   const int shR = (FINAL && a.st) ? a.st->lp_shift_applied : 0;
   const float rs = std::is_same<InT, __half>::value ? 1.0f : ldexpf(1.0f, shR);
+  const uint16_t* Rlo = KS::split ? a.Rt + a.rplane : nullptr;  // split form: lo plane of R~
 
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA producer
       if (!a.wstream) {
-        mbar_expect_tx(vbar, (uint32_t)a.KT * a.VR * 128u);
+        mbar_expect_tx(vbar, vres);
         for (int kt = 0; kt < a.KT; ++kt) tma_load_2d(sV + (uint32_t)kt * a.VR * 128u, &tmW, kt * KS::tile, 0, vbar);
       }
       // the operand is the previous pass's output: wait until that grid has completed
@@ -226,8 +273,14 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
           const uint32_t ph = (uint32_t)((it / NS) & 1);
           if (!wait_bounded(empty(s), ph ^ 1u, ab)) break;
           mbar_expect_tx(full(s), sbytes);
-          tma_load_2d(sD + (uint32_t)s * sbytes, &tmX, kt * KS::tile, tile * kTileRows, full(s));
-          if (a.wstream) tma_load_2d(sD + (uint32_t)s * sbytes + kStageBytes, &tmW, kt * KS::tile, 0, full(s));
+          const uint32_t dst = sD + (uint32_t)s * sbytes;
+          if constexpr (KS::split) {  // 3D boxes {64, rows, 2}: the hi tile, then the lo tile, of data and V
+            tma_load_3d(dst, &tmX, kt * KS::tile, tile * kTileRows, 0, full(s));
+            tma_load_3d(dst + 2u * kStageBytes, &tmW, kt * KS::tile, 0, 0, full(s));
+          } else {
+            tma_load_2d(dst, &tmX, kt * KS::tile, tile * kTileRows, full(s));
+            if (a.wstream) tma_load_2d(dst + kStageBytes, &tmW, kt * KS::tile, 0, full(s));
+          }
         }
       }
       // drain: every issued load has completed before the CTA may exit
@@ -267,8 +320,11 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
           if (!(ok = wait_bounded(full(s), (uint32_t)((it / NS) & 1), ab))) break;
           tc_fence_after();
           const unsigned long long xd = dX0 + (uint32_t)s * (sbytes >> 4);
-          const unsigned long long vd =
-              a.wstream ? dX0 + (uint32_t)s * (sbytes >> 4) + (uint32_t)(kStageBytes >> 4) : dV0 + (uint32_t)kt * vkt;
+          // a streamed eigenbasis tile follows the data tile(s) of the stage
+          const uint32_t voff = (uint32_t)((KS::split ? 2 : 1) * kStageBytes) >> 4;
+          const unsigned long long vd = a.wstream ? xd + voff : dV0 + (uint32_t)kt * vkt;
+          // split form: lo planes one data tile / one eigenbasis tile (VR rows) after the hi planes
+          const uint32_t xlo = (uint32_t)kStageBytes >> 4, vlo = (uint32_t)(a.VR * 128) >> 4;
           const int nk = min(4, (a.C - kt * KS::tile + KS::step - 1) / KS::step);  // K steps inside C
           auto mma = [&](uint32_t d, unsigned long long ad, unsigned long long bd, uint32_t acc) {
             if constexpr (KS::tf32) tc_mma_tf32(d, ad, bd, idesc, acc);
@@ -280,9 +336,24 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
               const uint32_t accum = (kt > 0 || kk > 0) ? 1u : 0u;
               if (FORM == 1) {
                 mma(dacc, xd + 2u * kk, vd + 2u * kk, accum);
+                if constexpr (KS::split) {
+                  mma(dacc, xd + xlo + 2u * kk, vd + 2u * kk, 1u);
+                  mma(dacc, xd + 2u * kk, vd + vlo + 2u * kk, 1u);
+                }
               } else {
                 mma(dacc, vd + 2u * kk, xd + 2u * kk, accum);
-                if (two_mb) mma(dacc + 128u, vd + (uint32_t)(kStageBytes >> 4) + 2u * kk, xd + 2u * kk, accum);
+                if constexpr (KS::split) {
+                  mma(dacc, vd + 2u * kk, xd + xlo + 2u * kk, 1u);
+                  mma(dacc, vd + vlo + 2u * kk, xd + 2u * kk, 1u);
+                }
+                if (two_mb) {
+                  const unsigned long long v1 = vd + (uint32_t)(kStageBytes >> 4);  // rows 128.. of the tile
+                  mma(dacc + 128u, v1 + 2u * kk, xd + 2u * kk, accum);
+                  if constexpr (KS::split) {
+                    mma(dacc + 128u, v1 + 2u * kk, xd + xlo + 2u * kk, 1u);
+                    mma(dacc + 128u, v1 + vlo + 2u * kk, xd + 2u * kk, 1u);
+                  }
+                }
               }
             }
           }
@@ -348,7 +419,7 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
         if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
         __syncwarp();
       }
-      stage_row<OutT>(buf, lane, v);
+      stage_row<StageT>(buf, lane, v);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> async-proxy reads
       __syncwarp();
       if (lane == 0) {
@@ -404,7 +475,7 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
           return true;
         };
         auto fetch_r = [&](int j, uint4 (&rb)[2]) {
-          if (FINAL && !KS::tf32 && !rtma && vec && j < J && col(j) + 16 <= a.Cout) {
+          if (FINAL && !KS::tf32 && !KS::split && !rtma && vec && j < J && col(j) + 16 <= a.Cout) {
             const uint4* rp = reinterpret_cast<const uint4*>(a.Rt + (long long)r * a.rpitch + col(j));
             rb[0] = __ldg(rp);
             rb[1] = __ldg(rp + 1);
@@ -437,8 +508,25 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
           if (a.tstore) emit(v, c0, row0 + q * 32, 0);  // rows past `rows`, columns past Cout: clipped
           if (!valid) return;
           if (vec && c0 + 16 <= a.Cout) {
-            if (!a.tstore) store16<OutT>(a.out, obase + c0, v);
-            if (FINAL && KS::tf32) {  // R~ in FP32 containers, 16 values of this row
+            if (!a.tstore) store16<OutT>(a.out, a.oplane, obase + c0, v);
+            if (FINAL && KS::split) {  // R~ = hi + lo, 16 values of this row from each plane
+              const uint4* hp = reinterpret_cast<const uint4*>(a.Rt + (long long)r * a.rpitch + c0);
+              const uint4* lq = reinterpret_cast<const uint4*>(Rlo + (long long)r * a.rpitch + c0);
+              const uint4 h0 = __ldg(hp), h1 = __ldg(hp + 1), l0 = __ldg(lq), l1 = __ldg(lq + 1);
+              const uint32_t hw[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+              const uint32_t lw[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+              float d0 = 0.0f, d1 = 0.0f;
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                const float2 rh = lp2_to_f32<__nv_bfloat16>(hw[i]), rl = lp2_to_f32<__nv_bfloat16>(lw[i]);
+                d0 = fmaf((rh.x + rl.x) * rs, v[2 * i], d0);
+                d1 = fmaf((rh.y + rl.y) * rs, v[2 * i + 1], d1);
+                zmax = fmaxf(zmax, fmaxf(fabsf(v[2 * i]), fabsf(v[2 * i + 1])));
+              }
+              red0.add(d0 + d1);
+              red1.add(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) +
+                       (((v[8] + v[9]) + (v[10] + v[11])) + ((v[12] + v[13]) + (v[14] + v[15]))));
+            } else if (FINAL && KS::tf32) {  // R~ in FP32 containers, 16 values of this row
               const float4* rp =
                   reinterpret_cast<const float4*>(reinterpret_cast<const float*>(a.Rt) + (long long)r * a.rpitch + c0);
               float d0 = 0.0f, d1 = 0.0f;
@@ -453,7 +541,7 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
               red0.add(d0 + d1);
               red1.add(((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) +
                        (((v[8] + v[9]) + (v[10] + v[11])) + ((v[12] + v[13]) + (v[14] + v[15]))));
-            } else if (FINAL) {
+            } else if constexpr (FINAL && !KS::split) {
               const uint32_t rw[8] = {rcur[0].x, rcur[0].y, rcur[0].z, rcur[0].w,
                                       rcur[1].x, rcur[1].y, rcur[1].z, rcur[1].w};
               float d0 = 0.0f, d1 = 0.0f;
@@ -474,10 +562,13 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
               const int c = c0 + j;
               if (c < a.Cout) {
                 const long long o = obase + (long long)c * a.oc;
-                if (!a.tstore) store_out<OutT>(a.out, o, v[j]);
+                if (!a.tstore) store_out<OutT>(a.out, a.oplane, o, v[j]);
                 if (FINAL) {
                   float rv;
                   if constexpr (KS::tf32) rv = __ldg(reinterpret_cast<const float*>(a.Rt) + (long long)r * a.rpitch + c);
+                  else if constexpr (KS::split)
+                    rv = lp2_to_f32<__nv_bfloat16>(__ldg(a.Rt + (long long)r * a.rpitch + c)).x +
+                         lp2_to_f32<__nv_bfloat16>(__ldg(Rlo + (long long)r * a.rpitch + c)).x;
                   else rv = lp2_to_f32<InT>(__ldg(a.Rt + (long long)r * a.rpitch + c)).x;
                   red0.add(rv * rs * v[j]);
                   red1.add(v[j]);
@@ -544,12 +635,12 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
           }
           if (c >= a.Cout) return;
           if (a.vec && ib + 16 <= a.B && r0 + 16 <= a.rows) {
-            store16<OutT>(a.out, (long long)ia * a.oa + ib + (long long)c * a.oc, v);
+            store16<OutT>(a.out, a.oplane, (long long)ia * a.oa + ib + (long long)c * a.oc, v);
           } else {
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
               if (r0 + i < a.rows)
-                store_out<OutT>(a.out, (long long)ia * a.oa + (long long)ib * a.ob + (long long)c * a.oc, v[i]);
+                store_out<OutT>(a.out, a.oplane, (long long)ia * a.oa + (long long)ib * a.ob + (long long)c * a.oc, v[i]);
               if (++ib == a.B) {
                 ib = 0;
                 ++ia;
@@ -937,6 +1028,8 @@ struct TcStage {
 
 struct TcPlan {
   bool tf32 = false;  // TF32 form: FP32 containers, eigenbasis streamed, one launch per pass
+  bool split = false;  // split BF16 form: hi/lo planes, three MMAs per K step, eigenbasis streamed, one launch
+                       // per pass
   std::vector<TcStage> stages;  // one launch per pass of Algorithm 7
   std::vector<TcStage> fused;   // the same with the pass pair around G in one launch (empty when not possible)
   bool fp16 = false;
@@ -1016,6 +1109,23 @@ int encode_2d(CUtensorMap* map, const void* gaddr, int inner, long long outer, i
   return r == CUDA_SUCCESS ? 0 : -1;
 }
 
+// A split-form operand: the BF16 hi plane and, plane_elems further, the lo plane, as one 3D map
+// {inner, outer, 2} whose boxes {box_inner, box_outer, 2} land as the hi tile followed by the lo tile.
+int encode_pair(CUtensorMap* map, const void* gaddr, int inner, long long outer, int pitch_elems, long long plane_elems,
+                int box_inner, int box_outer) {
+  EncodeTiledFn cuTensorMapEncodeTiled = encoder();
+  if (!cuTensorMapEncodeTiled) return -1;
+  if (plane_elems < outer * pitch_elems || (plane_elems * 2) % 16 != 0) return -1;
+  cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)outer, 2};
+  cuuint64_t strides[2] = {(cuuint64_t)pitch_elems * 2, (cuuint64_t)plane_elems * 2};
+  cuuint32_t box[3] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer, 2};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = cuTensorMapEncodeTiled(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(gaddr), dims, strides,
+                                      box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : -1;
+}
+
 template <int FORM, class InT, class OutT, bool FINAL>
 int set_smem_attr(size_t smem) {
   return cudaFuncSetAttribute(k_modeprod_tc<FORM, InT, OutT, FINAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1043,6 +1153,15 @@ int set_tf32_smem_attrs() {
   bad |= set_smem_attr<1, float, float, false>(kMaxSmem);
   bad |= set_smem_attr<2, float, float, false>(kMaxSmem);
   bad |= set_smem_attr<1, float, float, true>(kMaxSmem);
+  return bad;
+}
+
+int set_split_smem_attrs() {
+  int bad = 0;
+  bad |= set_smem_attr<1, Bf16Pair, Bf16Pair, false>(kMaxSmem);
+  bad |= set_smem_attr<2, Bf16Pair, Bf16Pair, false>(kMaxSmem);
+  bad |= set_smem_attr<1, Bf16Pair, float, false>(kMaxSmem);
+  bad |= set_smem_attr<1, Bf16Pair, float, true>(kMaxSmem);
   return bad;
 }
 
@@ -1079,7 +1198,8 @@ void launch_pair(const TcStage& s, const TcArgs& a, cudaStream_t stream) {
 template <class InT>
 void launch_stage(const TcStage& s, const TcArgs& a, bool last, bool final_pcg, cudaStream_t stream) {
   if (s.pair) {
-    if constexpr (sizeof(InT) == 2) launch_pair<InT>(s, a, stream);  // (no fused pair in the TF32 form)
+    // (no fused pair in the TF32 and split forms)
+    if constexpr (!KShape<InT>::tf32 && !KShape<InT>::split) launch_pair<InT>(s, a, stream);
   } else if (!last) {
     if (s.form == 1) launch<1, InT, InT, false>(s, a, stream);
     else launch<2, InT, InT, false>(s, a, stream);
@@ -1127,11 +1247,13 @@ int slab_launches_per_apply(const tpcg_plan* p);
 int run_precond_slab(const tpcg_plan* p, float* Z, SolveState* st);
 
 int tc_plan_setup(tpcg_plan* p) {
-  if (p->prec != TPCG_MIXED_BF16 && p->prec != TPCG_MIXED_FP16 && p->prec != TPCG_MIXED_TF32)
+  if (p->prec != TPCG_MIXED_BF16 && p->prec != TPCG_MIXED_FP16 && p->prec != TPCG_MIXED_TF32 &&
+      p->prec != TPCG_MIXED_BF16X3)
     return TPCG_ERR_UNSUPPORTED;
   TcPlan* tp = new TcPlan();
   tp->fp16 = (p->prec == TPCG_MIXED_FP16);
   tp->tf32 = (p->prec == TPCG_MIXED_TF32);
+  tp->split = (p->prec == TPCG_MIXED_BF16X3);
   const OpType oty = tp->tf32 ? OpType::kF32 : (tp->fp16 ? OpType::kF16 : OpType::kBF16);
   const int ktile = tp->tf32 ? 32 : kKTile;  // elements per 128-byte K tile
   // FP16 range: R enters at unit RMS, so intermediates of the forward passes
@@ -1180,10 +1302,12 @@ int tc_plan_setup(tpcg_plan* p) {
     a.sG = sG;
     a.gscale = std::ldexp(1.0f, -sG);
     a.shift_src = tp->fp16 ? &p->d_state->lp_shift_applied : nullptr;
-    // TF32: the eigenbasis (up to 256 x 256 FP32, 256 KB) does not fit next to the stages; each stage then
-    // carries its K tile of the eigenbasis with the data tile
-    a.wstream = tp->tf32 ? 1 : 0;
-    a.sbytes = kStageBytes + (a.wstream ? a.VR * 128 : 0);
+    // TF32 and split: the eigenbasis (up to 256 x 256 FP32 or BF16 pairs, 256 KB) does not fit next to the
+    // stages; each stage then carries its K tile of the eigenbasis with the data tile (split: the hi and lo
+    // tiles of both).  (Keeping 128 eigenbasis rows resident per CTA, two CTAs per tile, measured slower:
+    // the ring left beside them is too shallow to hide the loads' latency behind the epilogue's stores.)
+    a.wstream = (tp->tf32 || tp->split) ? 1 : 0;
+    a.sbytes = (tp->split ? 2 : 1) * (kStageBytes + (a.wstream ? a.VR * 128 : 0));
     const size_t sbytes = (size_t)a.sbytes;
     const size_t vbytes = a.wstream ? 0 : (size_t)a.KT * a.VR * 128;
     size_t fixed = 1024 + vbytes + 512;  // alignment, eigenbasis, barriers and the TMEM address
@@ -1193,7 +1317,10 @@ int tc_plan_setup(tpcg_plan* p) {
     const int esz = (last || tp->tf32) ? 4 : 2;
     st.out = out_addr;
     st.tmO = st.tmX;
-    a.tstore = (encode_out(&st.tmO, out_addr, esz, tp->fp16, st.form, a, &a.tperm) == 0) ? 1 : 0;
+    // (the split form stores its two planes directly)
+    a.tstore = (!tp->split && encode_out(&st.tmO, out_addr, esz, tp->fp16, st.form, a, &a.tperm) == 0) ? 1 : 0;
+    a.oplane = (long long)p->t_plane;
+    a.rplane = (long long)p->lp_plane;
     // staging bytes: two [32][16] boxes per epilogue warp (sixteen warps; eight in the last pass of a solve)
     const size_t stage_plain = a.tstore ? (size_t)TcWarps<false>::epi * 2 * 32 * 16 * esz : 0;
     const size_t stage_final = (a.tstore && last) ? (size_t)TcWarps<true>::epi * 2 * 32 * 16 * esz : 0;
@@ -1201,7 +1328,7 @@ int tc_plan_setup(tpcg_plan* p) {
     // elements) by TMA through the largest ring (up to kRHalf slots per half) that leaves two stages
     a.rpitch = p->pitch16[0];
     a.rhalf = 0;
-    if (last && st.form == 1 && !tp->tf32) {  // (the TF32 form reads its FP32 R~ with global loads)
+    if (last && st.form == 1 && !tp->tf32 && !tp->split) {  // (TF32 and split read R~ with global loads)
       const size_t room = (size_t)kMaxSmem - fixed - 2 * sbytes;
       const size_t rh = room > stage_final ? (room - stage_final) / (2 * (size_t)kRBytes) : 0;
       a.rhalf = (int)std::min<size_t>(kRHalf, rh);
@@ -1219,8 +1346,14 @@ int tc_plan_setup(tpcg_plan* p) {
     const int ntiles = (a.rows + kTileRows - 1) / kTileRows;
     st.grid = std::max(1, std::min(ntiles, p->num_sms));
     const int wpitch = p->pitch16[sp.axis];
-    if (encode_2d(&st.tmX, xin, sp.C, (long long)a.rows, sp.in_pitch, ktile, kTileRows, oty) ||
-        encode_2d(&st.tmW, p->d_Wt16[sp.axis][sp.dir], sp.C, sp.Cout, wpitch, ktile, a.VR, oty))
+    if (tp->split) {
+      const long long xplane = (long long)((xin == p->d_Rlp) ? p->lp_plane : p->t_plane);
+      if (encode_pair(&st.tmX, xin, sp.C, (long long)a.rows, sp.in_pitch, xplane, ktile, kTileRows) ||
+          encode_pair(&st.tmW, p->d_Wt16[sp.axis][sp.dir], sp.C, sp.Cout, wpitch, (long long)sp.Cout * wpitch, ktile,
+                      a.VR))
+        return TPCG_ERR_CUDA;
+    } else if (encode_2d(&st.tmX, xin, sp.C, (long long)a.rows, sp.in_pitch, ktile, kTileRows, oty) ||
+               encode_2d(&st.tmW, p->d_Wt16[sp.axis][sp.dir], sp.C, sp.Cout, wpitch, ktile, a.VR, oty))
       return TPCG_ERR_CUDA;
     st.tmW2 = st.tmW;
     st.tmR = st.tmX;
@@ -1230,7 +1363,7 @@ int tc_plan_setup(tpcg_plan* p) {
   // Passes si (forward, with G, form 1) and si + 1 (backward along the same axis, form 2) as one
   // k_modeprod_pair launch; TPCG_ERR_UNSUPPORTED when the pair does not fit its layout rules.
   auto build_pair = [&](int si, const void* xin, void* out_addr, TcStage& st) -> int {
-    if (si + 1 >= ns || tp->tf32) return TPCG_ERR_UNSUPPORTED;
+    if (si + 1 >= ns || tp->tf32 || tp->split) return TPCG_ERR_UNSUPPORTED;
     const StageParams& s1 = p->stages[si];
     const StageParams& s2 = p->stages[si + 1];
     const bool shape_ok = s1.scale && !s1.final_stage && s1.oc == 1 && !s2.final_stage && s2.oc != 1 &&
@@ -1267,6 +1400,13 @@ int tc_plan_setup(tpcg_plan* p) {
     st.smem = fixed + (size_t)a.NS * kStageBytes;
     return TPCG_OK;
   };
+  const int bad = tp->tf32    ? set_tf32_smem_attrs()
+                  : tp->split ? set_split_smem_attrs()
+                              : (tp->fp16 ? set_all_smem_attrs<__half>() : set_all_smem_attrs<__nv_bfloat16>());
+  if (bad) {
+    delete tp;
+    return TPCG_ERR_CUDA;
+  }
   int rc = TPCG_OK;
   for (int si = 0; si < ns && rc == TPCG_OK; ++si) {
     TcStage st{};
@@ -1298,12 +1438,6 @@ int tc_plan_setup(tpcg_plan* p) {
   if (rc != TPCG_OK) {
     delete tp;
     return rc;
-  }
-  const int bad = tp->tf32 ? set_tf32_smem_attrs()
-                            : (tp->fp16 ? set_all_smem_attrs<__half>() : set_all_smem_attrs<__nv_bfloat16>());
-  if (bad) {
-    delete tp;
-    return TPCG_ERR_CUDA;
   }
   p->tc_state = tp;
   if (slab_applicable(p)) {
@@ -1345,6 +1479,7 @@ int run_precond_tc(const tpcg_plan* p, float* Z, SolveState* st) {
     a.partials = p->d_partials;
     LaunchScope ls(p, kKModeTC);
     if (tp->tf32) launch_stage<float>(s, a, last, st != nullptr, p->stream);
+    else if (tp->split) launch_stage<Bf16Pair>(s, a, last, st != nullptr, p->stream);
     else if (tp->fp16) launch_stage<__half>(s, a, last, st != nullptr, p->stream);
     else launch_stage<__nv_bfloat16>(s, a, last, st != nullptr, p->stream);
   }

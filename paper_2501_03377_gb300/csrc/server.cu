@@ -144,7 +144,8 @@ void pinned_put(tpcg_server* s, size_t bytes, void* p) {
 size_t estimate_slot_bytes(const PlanKey& k) {
   const size_t N = (size_t)k.nx * k.ny * k.nz;
   const bool fp64 = (k.prec == TPCG_FP64);
-  const size_t lpb = (k.prec == TPCG_MIXED_TF32) ? 4 : 2;  // bytes of a tensor-core operand
+  // bytes of a tensor-core operand (TF32: FP32 containers; split: hi and lo BF16 planes)
+  const size_t lpb = (k.prec == TPCG_MIXED_TF32 || k.prec == TPCG_MIXED_BF16X3) ? 4 : 2;
   size_t b = N * 8 + (fp64 ? N * 8 * 3 : N * 4 * 2);  // R; P[2] and W (FP64) or P[2] in int32
   b += N * (fp64 ? 8 : 4);                   // Z
   b += fp64 ? 0 : N * lpb + (size_t)k.ny * k.nz * 8 * lpb;  // low-precision copy of R (padded rows)

@@ -122,10 +122,13 @@ struct tpcg_plan {
   int p_slots = 2;   // mixed forms: 2 (in-place update), kPRing once TPCG_OPT_DEFER_U has been set
   double* d_W = nullptr;               // W = L P (FP64 form only)
   void* d_Z = nullptr;       // FP64 (FP64 form) or FP32 (mixed forms)
-  void* d_Rlp = nullptr;     // BF16 / FP16 copy of R (mixed forms), row pitch pitch16[0]
-  int lp_kind = 0;           // 0 none (FP64 form), 1 BF16, 2 FP16 scaled by 2^lp_shift
+  void* d_Rlp = nullptr;     // tensor-core copy of R (mixed forms), row pitch pitch16[0]
+  int lp_kind = 0;           // 0 none (FP64 form), 1 BF16, 2 FP16 scaled by 2^lp_shift, 3 TF32 (FP32
+                             // containers), 4 BF16 hi/lo pair (two planes of 16-bit words)
+  size_t lp_plane = 0;       // kind 4: 16-bit words from the hi plane of d_Rlp to its lo plane
   void* d_T[2] = {nullptr, nullptr};  // mode-product intermediates
   size_t t_elems = 0;
+  size_t t_plane = 0;        // kind 4: 16-bit words from the hi plane of a d_T buffer to its lo plane
   double* d_eta_h = nullptr;  // device copies for tpcg_solve_host
   double* d_ups_h = nullptr;
   // tpcg_solve_host_stream: the second slot of its two-slot pipeline (the first is d_eta_h / d_ups_h),

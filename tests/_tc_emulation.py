@@ -1,8 +1,9 @@
 """Numpy emulation of the mixed tensor-core preconditioner (Algorithm 7) with the device's rounding points.
 
 Test infrastructure shared by the GPU parity tests and the CPU experiments on the precision readings:
-BF16 / FP16 rounding of FP64 and FP32 values (nearest even), mode products in FP32, the power-of-two
-scalings of the FP16 form, and the order in which each launch sequence rounds its intermediates.
+BF16 / FP16 / TF32 rounding of FP64 and FP32 values (nearest even), mode products in FP32, the
+power-of-two scalings of the FP16 form, the hi/lo BF16 pairs of the split form, and the order in which
+each launch sequence rounds its intermediates.
 """
 import numpy as np
 
@@ -68,10 +69,63 @@ def fp16_gscale_exponent(lams, N):
     return max(0, int(np.ceil(np.log2(bound / 16384.0))))
 
 
+def split_f64(x):
+    """x -> (hi, lo) = (bf16(x), bf16(x - hi)), each rounded once from FP64; returned as float32."""
+    x = np.asarray(x, dtype=np.float64)
+    hi = bf16_from_f64(x)
+    return hi, bf16_from_f64(x - hi.astype(np.float64))
+
+
+def split_f32(x):
+    """The same split of FP32 values (x - hi is exact in FP32)."""
+    x = np.asarray(x, dtype=np.float32)
+    hi = bf16_from_f32(x)
+    return hi, bf16_from_f32((x - hi).astype(np.float32))
+
+
+def mode_split(M, X, m):
+    """Split-form mode product: hi.hi + lo.hi + hi.lo of the BF16 pairs M = (Mh, Ml), X = (Xh, Xl),
+    summed in FP64 and rounded once to FP32 (the device accumulates in FP32, in its own order)."""
+    (Mh, Ml), (Xh, Xl) = M, X
+
+    def prod(A, B):
+        Y = np.tensordot(A.astype(np.float64), np.moveaxis(B, m, 0).astype(np.float64), axes=(1, 0))
+        return np.moveaxis(Y, 0, m)
+
+    return (prod(Mh, Xh) + prod(Ml, Xh) + prod(Mh, Xl)).astype(np.float32)
+
+
+def emulate_split_precond(r_nqt, Vs, lams, singular):
+    """The split BF16 form of Algorithm 7, one launch per mode product (x, y, z forward; G; z, y, x
+    backward): R and the eigenbases split from FP64, every intermediate split from FP32, G applied in
+    FP32 before the split, Z in FP32."""
+    three_d = r_nqt.shape[2] > 1
+    VT = [split_f64(np.asarray(V, dtype=np.float64).T) for V in Vs]
+    VV = [split_f64(np.asarray(V, dtype=np.float64)) for V in Vs]
+    F = split_f64(r_nqt)
+    F = split_f32(mode_split(VT[0], F, 0))
+    F = mode_split(VT[1], F, 1)
+    if three_d:
+        F = mode_split(VT[2], split_f32(F), 2)
+    la = [np.asarray(l, dtype=np.float32) for l in lams]
+    S = (la[0][:, None, None] + la[1][None, :, None]) + la[2][None, None, :]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        F = (F * (np.float32(1.0) / S).astype(np.float32)).astype(np.float32)
+    if singular:
+        F[0, 0, 0] = 0.0
+    F = split_f32(F)
+    if three_d:
+        F = split_f32(mode_split(VV[2], F, 2))
+    F = split_f32(mode_split(VV[1], F, 1))
+    return mode_split(VV[0], F, 0)
+
+
 def emulate_precond(r_nqt, Vs, lams, singular, prec="bf16", slices=False):
     """The tensor-core form of Algorithm 7 with its rounding points (BF16, or FP16 with the
     power-of-two scalings that keep every intermediate in range).  slices: the frontal-slice launch
     sequence, whose backward x product precedes the backward y product."""
+    if prec == "bf16x3":
+        return emulate_split_precond(r_nqt, Vs, lams, singular)
     three_d = r_nqt.shape[2] > 1
     if prec == "bf16":
         rin, rd, Vb = (lambda x: bf16_from_f64(x)), bf16_from_f32, [bf16_from_f64(V) for V in Vs]

@@ -55,6 +55,7 @@ CASES = [
     ("bf16", (128, 128, 64), ("P", "P", "N")),
     ("fp16", (96, 64, 40), ("D", "ND", "N")),
     ("fp64", (64, 64, 32), ("P", "P", "N")),
+    ("bf16x3", (128, 128, 64), ("P", "P", "N")),
 ]
 
 
@@ -85,14 +86,15 @@ def test_cg_scalars_match_fp64_dots(prec, shape, bcs):
     print(f"\n{prec} {shape} {bcs}: iteration, rel. error of <W,P>, rho, alpha, beta vs FP64 dots")
     for r in rows:
         print("  s=%d  %.2e  %.2e  %.2e  %.2e" % r)
-    assert len(rows) >= (1 if prec == "fp64" else 3)
+    # (the split form reaches the FP64 floor after three iterations: two comparable ones)
+    assert len(rows) >= {"fp64": 1, "bf16x3": 2}.get(prec, 3)
     N = nx * ny * nz
     if prec == "fp64":
         bound_wp = bound_rho = 1e-12
     else:
         bound_wp = 1e-7  # FP32 partial sums per thread of exact integer differences (measured ~5e-9)
         # R~ rounding (uncorrelated with Z) plus FP32 partial sums (measured 1e-7..3e-6 FP16, 5e-6..1e-5 BF16)
-        ulp = 2.0 ** -11 if prec == "fp16" else 2.0 ** -8
+        ulp = {"fp16": 2.0 ** -11, "bf16x3": 2.0 ** -16}.get(prec, 2.0 ** -8)
         bound_rho = max(1e-5, 50 * ulp / np.sqrt(N))
     for s, e_wp, e_rho, e_alpha, e_beta in rows:
         assert e_wp <= bound_wp, (s, e_wp)

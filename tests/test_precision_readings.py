@@ -19,8 +19,8 @@ import pytest
 
 import oracle as o
 from inputs import synth
-from tests._tc_emulation import emulate_precond, f16_from_f64, lp_shift
-from tests._util import to_oracle
+from tests._tc_emulation import emulate_precond, f16_from_f64, lp_shift, split_f64
+from tests._util import oracle_bcs, to_oracle
 
 
 def _fixed(P, bound, bits):
@@ -53,6 +53,9 @@ def _pcg(shape, bcs, H, prec, dir_bits, rho_from_copy, tol=1e-10, maxit=30):
         if prec == "fp16":
             s = lp_shift(R)
             Rt = np.ldexp(f16_from_f64(R, s).astype(np.float64), -s)
+        elif prec == "bf16x3":
+            hi, lo = split_f64(R)
+            Rt = hi.astype(np.float64) + lo.astype(np.float64)
         else:
             from tests._tc_emulation import bf16_from_f64
 
@@ -107,3 +110,60 @@ def test_direction_rounding_and_rho_copy_leave_iterations_unchanged(prec):
         for a, b in zip(h[1:], ref_h[1:]):
             if max(a, b) > 1e-13:
                 assert 0.5 <= a / b <= 2.0, (name, a, b)
+
+
+def test_split_pair_represents_fp64_to_2_pow_minus_16():
+    """hi = bf16(x), lo = bf16(x - hi): a BF16 word has 8 significant bits, so rounding to nearest leaves
+    |x - hi| <= 2^-8 |x| and |x - (hi + lo)| <= 2^-8 |x - hi| <= 2^-16 |x| for values in the normal range."""
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(100000) * np.exp2(rng.integers(-60, 60, 100000))
+    hi, lo = split_f64(x)
+    err = np.abs(x - (hi.astype(np.float64) + lo.astype(np.float64)))
+    assert np.all(np.abs(x - hi) <= np.ldexp(np.abs(x), -8))
+    assert np.all(err <= np.ldexp(np.abs(x), -16))
+    assert np.median(err / np.abs(x)) < 2.0 ** -17.5  # uniformly spread rounding: well inside the bound
+    # exactly representable values split with lo = 0
+    h2, l2 = split_f64(np.array([1.0, -0.5, 3.0, 2.0 ** -100]))
+    assert np.all(l2 == 0) and np.array_equal(h2, np.array([1.0, -0.5, 3.0, 2.0 ** -100], np.float32))
+
+
+@pytest.mark.parametrize("shape,bcs", [((32, 24, 16), ("P", "P", "N")), ((20, 30, 1), ("D", "N", "N")),
+                                       ((17, 9, 12), ("ND", "D", "DN"))])
+def test_split_form_emulation_is_accurate_to_about_2_pow_minus_16(shape, bcs):
+    """Algorithm 7 in the split form (three BF16 products per K step, the lo.lo term dropped) against the
+    FP64 pseudoinverse: each product is accurate to about 2^-16 relative (the dropped term and the split
+    of its output), so six products leave the relative error of Z near 1e-5, against about 1e-2 for one
+    BF16 word per operand."""
+    nx, ny, nz = shape
+    sh, ob = (nx, ny, nz), oracle_bcs(bcs, nz)
+    singular = o.is_singular(sh, ob)
+    r = to_oracle(synth.random_field(nx, ny, nz, seed=4))
+    if singular:
+        r = o.center(r)
+    Vs, lams, G = o.pinv_init(sh, ob)
+    lams = [np.where(np.abs(lam) < 1e-12, 0.0, lam) for lam in lams]
+    ref = o.pinv_apply(r, Vs, G)
+
+    def rel(z):
+        z = z.astype(np.float64)
+        if singular:
+            z = o.center(z)
+        return np.linalg.norm(z - ref) / np.linalg.norm(ref)
+
+    e = rel(emulate_precond(r, Vs, lams, singular, "bf16x3"))
+    e1 = rel(emulate_precond(r, Vs, lams, singular, "bf16"))
+    print(f"\nsplit form {shape} {bcs}: |Z - Z_fp64| / |Z_fp64| = {e:.2e} (one BF16 word: {e1:.2e})")
+    assert e1 > 100 * e
+    assert e <= 3e-5
+
+
+def test_split_form_needs_three_iterations():
+    """The split form as the preconditioner of the mixed PCG (20-bit direction, rho from the hi + lo copy of
+    R): the true residual falls below 1e-10 in three iterations on the 64x64x32 P/P/N workload where the
+    one-word forms need six (FP16) and eleven (BF16)."""
+    shape, bcs = (64, 64, 32), ("P", "P", "N")
+    eta = synth.defect_rhs(*shape, bcs, 120, (1.0, 4.0), seed=5, mode="charge")
+    it, h = _pcg(shape, bcs, to_oracle(eta), "bf16x3", 20, True)
+    it16, _ = _pcg(shape, bcs, to_oracle(eta), "fp16", 20, True)
+    print(f"\nsplit form: {it} iterations (FP16: {it16}); residuals " + " ".join(f"{x:.1e}" for x in h))
+    assert it <= 3 < it16
