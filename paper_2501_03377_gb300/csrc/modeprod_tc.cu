@@ -117,6 +117,13 @@ struct TcArgs {
   int* err;
 };
 
+// 32 bytes to a 32-byte aligned global address in one store (a whole sector).
+__device__ __forceinline__ void st_global_v8(void* p, const uint32_t (&w)[8]) {
+  asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(w[0]), "r"(w[1]), "r"(w[2]),
+               "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+               : "memory");
+}
+
 // hi = bf16(v) at o, lo = bf16(v - hi) one plane further (v - hi is exact in FP32).
 __device__ __forceinline__ void store_pair(void* out, long long plane, long long o, float v) {
   const __nv_bfloat16 hi = __float2bfloat16_rn(v);
@@ -150,12 +157,17 @@ __device__ __forceinline__ void store16(void* out, long long plane, long long o,
       ph[i] = *reinterpret_cast<const uint32_t*>(&h2);
       pl[i] = *reinterpret_cast<const uint32_t*>(&l2);
     }
-    uint4* dh = reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(out) + o);
-    uint4* dl = reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(out) + plane + o);
-    dh[0] = make_uint4(ph[0], ph[1], ph[2], ph[3]);
-    dh[1] = make_uint4(ph[4], ph[5], ph[6], ph[7]);
-    dl[0] = make_uint4(pl[0], pl[1], pl[2], pl[3]);
-    dl[1] = make_uint4(pl[4], pl[5], pl[6], pl[7]);
+    uint16_t* dh = reinterpret_cast<uint16_t*>(out) + o;
+    uint16_t* dl = reinterpret_cast<uint16_t*>(out) + plane + o;
+    if ((o & 15) == 0 && (plane & 15) == 0) {  // 32-byte aligned: one full sector per store
+      st_global_v8(dh, ph);
+      st_global_v8(dl, pl);
+    } else {
+      reinterpret_cast<uint4*>(dh)[0] = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+      reinterpret_cast<uint4*>(dh)[1] = make_uint4(ph[4], ph[5], ph[6], ph[7]);
+      reinterpret_cast<uint4*>(dl)[0] = make_uint4(pl[0], pl[1], pl[2], pl[3]);
+      reinterpret_cast<uint4*>(dl)[1] = make_uint4(pl[4], pl[5], pl[6], pl[7]);
+    }
   } else if constexpr (sizeof(OutT) == 2) {
     uint32_t pk[8];
 #pragma unroll
