@@ -10,7 +10,7 @@ plans (default 3), each on its own stream: the library runs the queues of
 different plans concurrently.  single_plan reports the same steps solved one
 after the other on one plan with tpcg_solve.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16|fp64] [--nz 128]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16x3|fp16|bf16|tf32|fp64] [--nz 128]
     python bench.py --impl reference   # the CPU oracle as the reference arm
 
 Multi-GPU: replicas only (each rank solves its own right-hand sides; no data
@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="auto", choices=["auto", "fp16", "bf16", "fp64"])
+    ap.add_argument("--prec", default="auto", choices=["auto", "fp16", "bf16", "tf32", "bf16x3", "fp64"])
     ap.add_argument("--no-bf16-compare", action="store_true")
     ap.add_argument("--nz", type=int, default=128)
     ap.add_argument("--tol", type=float, default=1e-10)
@@ -202,7 +202,9 @@ def pick_prec(args):
         return args.prec
     from paper_2501_03377_gb300 import Plan
 
-    for prec in ("fp16", "bf16"):
+    # the split BF16 form first: its three refinement iterations beat the six of the FP16 form (measured on the
+    # 256x256x128 cuboid: 950 against 833 solves/s on one plan)
+    for prec in ("bf16x3", "fp16", "bf16"):
         try:
             Plan(16, 16, 16, ("P", "P", "N"), prec=prec).close()
             return prec
@@ -435,18 +437,24 @@ def run_batched(prec, torch):
             "autotuned_sequences": chosen, "autotune_timed": sum(t["candidates"] for t in tunes)}
 
 
-# DRAM bytes (read + write) per launch measured by ncu on the 256x256x128 FP16 workload (one capture
-# per kernel; ncu flushes the caches before each launch).  Summaries and commands are under
-# profiles/.  Set an entry to None when its kernel changes.
+# DRAM bytes (read + write) per launch measured by ncu on the 256x256x128 workload, per mixed form (one
+# capture per kernel; ncu flushes the caches before each launch).  Summaries and commands are under
+# profiles/.  Remove an entry when its kernel changes.
 NCU_TRAFFIC_PER_LAUNCH = {
-    # DRAM bytes (read + write) per launch from the ncu captures summarised under profiles/ (cold caches)
-    # tensor-core launches: mean over the three launches of one application (frontal-slice sequence): the
-    # forward x-y pair (17.1 MB), the tube pair (16.9 MB) and the backward x-y pair (34.7 MB)
-    "modeprod_tc": (17.1e6 + 16.9e6 + 34.7e6) / 3,
-    "update": 275.0e6,  # the in-place update the instrumented (one-plan) pass runs
-    "form_u": 248.0e6,  # the formation before a check (six recorded directions; TPCG_OPT_DEFER_U)
-    "direction": 76.2e6,
-    "true_residual": 197.8e6,  # a launch that checks (the others return at once)
+    "fp16": {
+        # tensor-core launches: mean over the three launches of one application (frontal-slice sequence): the
+        # forward x-y pair (17.1 MB), the tube pair (16.9 MB) and the backward x-y pair (34.7 MB)
+        "modeprod_tc": (17.1e6 + 16.9e6 + 34.7e6) / 3,
+        "update": 275.0e6,  # the in-place update the instrumented (one-plan) pass runs
+        "form_u": 248.0e6,  # the formation before a check (six recorded directions; TPCG_OPT_DEFER_U)
+        "direction": 76.2e6,
+        "true_residual": 197.8e6,  # a launch that checks (the others return at once)
+    },
+    "bf16x3": {
+        # the six launches of one application (one per mode product): 33.7-33.9 MB read each (the hi and lo
+        # planes of the input), under 0.7 MB written (the outputs stay in L2 until the next launch reads them)
+        "modeprod_tc": 206.29e6 / 6,
+    },
 }
 
 
@@ -458,6 +466,8 @@ def kernel_work(kind, plan_prec, N, dims, iters_total, applies_total, solves, ch
     reduction scratch excluded); flops are the FP64 operations of the FP64 form."""
     n, q, t = dims
     mixed = plan_prec != "fp64"
+    # bytes per point of a tensor-core operand (and of the copy of R): FP16/BF16 2, TF32 4, split BF16 pair 4
+    lpb = {"fp16": 2, "bf16": 2, "tf32": 4, "bf16x3": 4}.get(plan_prec, 0)
     if kind == "modeprod_f64":
         return applies_total * 4.0 * N * (n + q + t + 0.25) / 1e12, "TFLOP", "alu", applies_total * (6 if t > 1 else 4)
     if kind == "modeprod_tc":
@@ -467,12 +477,13 @@ def kernel_work(kind, plan_prec, N, dims, iters_total, applies_total, solves, ch
         return applies_total * 30.0 * N / 1e9, "GB", "hbm", applies_total * npass
     if kind == "modeprod_tc_design":
         # the launch sequence's own algorithmic bytes per application (3D): every launch but the last reads +
-        # writes FP16/BF16 (2 + 2 B); the last reads its input (2 B) and the copy of R (2 B) and writes Z in
-        # FP32 (4 B).  `launches` is the plan's count per application: three with the frontal-slice launches
-        # (16 B per point), four when the z products run as two launches (20 B), five or six with one launch
-        # per mode product (24 or 28 B)
+        # writes one operand per point (lpb + lpb); the last reads its input (lpb) and the copy of R (lpb) and
+        # writes Z in FP32 (4 B).  `launches` is the plan's count per application.  FP16/BF16: three with the
+        # frontal-slice launches (16 B per point), four when the z products run as two launches (20 B), five or
+        # six with one launch per mode product (24 or 28 B); TF32 and split BF16 (4-byte operands): six launches,
+        # 52 B
         npass = launches or (6 if t > 1 else 4)
-        per_apply = ((npass - 1) * 4 + 8) * N
+        per_apply = ((npass - 1) * 2 * lpb + 2 * lpb + 4) * N
         return applies_total * per_apply / 1e9, "GB", "hbm", applies_total * npass
     if kind == "direction":
         if mixed:  # Z (FP32) + P_old (int32) in, P (int32) out
@@ -480,20 +491,20 @@ def kernel_work(kind, plan_prec, N, dims, iters_total, applies_total, solves, ch
         # FP64 form: FP64 flops per point: P = (Z - m) + beta P_old (3), 7-point stencil (7), <W, P> (2)
         return iters_total * 12.0 * N / 1e12, "TFLOP", "alu", iters_total
     if kind == "update":
-        # the instrumented plan updates U in place: mixed P (4) + R (8+8) + U (8+8) + FP16 copy of R (2);
-        # FP64 form: P and W (8+8) + R + U
-        per = (4 + 16 + 16 + 2) if mixed else (16 + 16 + 16)
+        # the instrumented plan updates U in place: mixed P (4) + R (8+8) + U (8+8) + tensor-core copy of R
+        # (lpb); FP64 form: P and W (8+8) + R + U
+        per = (4 + 16 + 16 + lpb) if mixed else (16 + 16 + 16)
         return iters_total * per * N / 1e9, "GB", "hbm", iters_total
     if kind == "form_u":
         # mixed forms, zero initial guess: once per check, the recorded directions (4 B each) in and U (8) out
         return (4.0 * iters_total + 8.0 * checks_total) * N / 1e9, "GB", "hbm", checks_total
     if kind == "true_residual":
-        # eta (8) + U (8) in, R (8) + FP16 copy (2, mixed) out
-        return checks_total * (24 + (2 if mixed else 0)) * N / 1e9, "GB", "hbm", checks_total
+        # eta (8) + U (8) in, R (8) + tensor-core copy (lpb, mixed) out
+        return checks_total * (24 + lpb) * N / 1e9, "GB", "hbm", checks_total
     if kind == "eta_sum":
         return solves * 8.0 * N / 1e9, "GB", "hbm", solves
-    if kind == "init_residual":  # zero initial guess: eta in, R (+ FP16 copy) out
-        return solves * (16 + (2 if mixed else 0)) * N / 1e9, "GB", "hbm", solves
+    if kind == "init_residual":  # zero initial guess: eta in, R (+ tensor-core copy) out
+        return solves * (16 + lpb) * N / 1e9, "GB", "hbm", solves
     if kind == "center":
         return solves * 16.0 * N / 1e9, "GB", "hbm", solves
     return None, None, None, None
@@ -695,7 +706,7 @@ def run_ours(args, rank, world, torch):
                     "frac": achieved / peak, "traffic": None,
                     "peak_source": "derived FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz" if bound == "alu"
                     else f"{peak_src} bf16 sustained"}
-        traffic = NCU_TRAFFIC_PER_LAUNCH.get(kind) if prec == "fp16" and nz == 128 else None
+        traffic = NCU_TRAFFIC_PER_LAUNCH.get(prec, {}).get(kind) if nz == 128 else None
         return {"kernel": kind, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": traffic,
                 "traffic_unit": "DRAM bytes per launch (ncu, cold caches)" if traffic else None,
@@ -755,32 +766,34 @@ def run_ours(args, rank, world, torch):
            "status": max((r[0] for r in e2e_out if r), default=0),
            "worst_rel_res_true": max(i["rel_res_true"] for i in e2e_infos)}
 
-    # the BF16 mixed form, same workload and timing rules
-    bf16_cmp = None
-    if prec == "fp16" and not args.no_bf16_compare:
-        pb = Plan(nx, ny, nz, w0["bcs"], prec="bf16")
+    # the other mixed forms, same workload and timing rules (one plan each), with the preconditioner's time
+    # per application from an instrumented pass
+    def form_record(fprec):
+        pf = Plan(nx, ny, nz, w0["bcs"], prec=fprec)
         for s in range(args.warmup):
-            pb.solve(etas[s % 4], ups, tol=args.tol, maxit=60, zero_guess=True)
-        dtb, infb, _ = time_steps(pb, etas, ups, args.steps, args.tol, torch, barrier)
-        dtb = max_over_ranks(dtb, world, torch, dev)
-        bf16_cmp = {"value": whole_job_rate(world, args.steps, dtb), "unit": "solves/s", "steps": args.steps,
-                    "iters_per_solve": sum(i["iters"] for (_, i) in infb) / args.steps,
-                    "worst_rel_res_true": max(i["rel_res_true"] for (_, i) in infb)}
-        pb.close()
+            pf.solve(etas[s % 4], ups, tol=args.tol, maxit=60, zero_guess=True)
+        dtf, inff, _ = time_steps(pf, etas, ups, args.steps, args.tol, torch, barrier)
+        dtf = max_over_ranks(dtf, world, torch, dev)
+        pf.profile_begin()
+        _, pinf, _ = time_steps(pf, etas, ups, min(args.steps, 6), args.tol, torch, barrier)
+        kst = pf.profile_end()
+        applies = sum(i["precond_applies"] for (_, i) in pinf)
+        rec = {"value": whole_job_rate(world, args.steps, dtf), "unit": "solves/s", "steps": args.steps,
+               "ms_per_solve": 1e3 * dtf / args.steps, "api": "tpcg_solve, one plan",
+               "iters_per_solve": sum(i["iters"] for (_, i) in inff) / args.steps,
+               "worst_rel_res_true": max(i["rel_res_true"] for (_, i) in inff),
+               "failed": sum(1 for (st, _) in inff if st != 0),
+               "tc_launches_per_apply": pf.precond_launches(),
+               "precond_us_per_apply": 1e3 * kst["modeprod_tc"]["total_ms"] / max(1, applies)
+               if "modeprod_tc" in kst else None}
+        pf.close()
+        return rec
 
-    # the TF32 mixed form (one launch per mode product, FP32 intermediates), same workload and timing rules
-    tf32_cmp = None
-    if prec == "fp16" and not args.no_bf16_compare:
-        pt = Plan(nx, ny, nz, w0["bcs"], prec="tf32")
-        for s in range(args.warmup):
-            pt.solve(etas[s % 4], ups, tol=args.tol, maxit=60, zero_guess=True)
-        dtt, inft, _ = time_steps(pt, etas, ups, args.steps, args.tol, torch, barrier)
-        dtt = max_over_ranks(dtt, world, torch, dev)
-        tf32_cmp = {"value": whole_job_rate(world, args.steps, dtt), "unit": "solves/s", "steps": args.steps,
-                    "iters_per_solve": sum(i["iters"] for (_, i) in inft) / args.steps,
-                    "worst_rel_res_true": max(i["rel_res_true"] for (_, i) in inft),
-                    "tc_launches_per_apply": pt.precond_launches()}
-        pt.close()
+    forms = {}
+    if prec != "fp64" and not args.no_bf16_compare:
+        for fprec in ("fp16", "bf16", "tf32", "bf16x3"):
+            if fprec != prec:
+                forms[f"{fprec}_form"] = form_record(fprec)
 
     # the plain FP64 form for comparison (fewer steps: it is ~100x slower)
     fp64_cmp = None
@@ -840,7 +853,7 @@ def run_ours(args, rank, world, torch):
             "worst_rel_res_true": worst_res, "failed_solves": len(bad),
             "gpu_launches": launches, "single_plan": single,
             "roofline": roofline, "kernels": kernels,
-            "e2e": e2e, "cpu_baseline": cpu, "fp64_form": fp64_cmp, "bf16_form": bf16_cmp, "tf32_form": tf32_cmp,
+            "e2e": e2e, "cpu_baseline": cpu, "fp64_form": fp64_cmp, **forms,
             "serving": serving, "batched": batched, "comparators": comparators, "efield": efield,
             "cube_256": cube, "clocks": clocks,
         }

@@ -87,3 +87,13 @@ def test_kernel_work_counts_the_algorithmic_bytes():
     assert amount * 1e9 == pytest.approx(6 * 38 * N)  # P 4, R 8+8, U 8+8, FP16 copy 2
     amount, _, _, worked = bench.kernel_work("true_residual", "fp16", N, dims, 6, 7, 1, 2)
     assert worked == 2 and amount * 1e9 == pytest.approx(2 * 26 * N)
+    # 4-byte operands (TF32, split BF16 pair): six launches of 8 B per point, the last 12 -> 52 B; the copy
+    # of R is 4 B in the update, the check and the initial residual
+    amount, _, _, worked = bench.kernel_work("modeprod_tc_design", "bf16x3", N, dims, 3, 4, 1, 1, 6)
+    assert worked == 24 and amount * 1e9 == pytest.approx(4 * 52 * N)
+    amount, _, _, _ = bench.kernel_work("update", "bf16x3", N, dims, 3, 4, 1, 1)
+    assert amount * 1e9 == pytest.approx(3 * 40 * N)
+    amount, _, _, _ = bench.kernel_work("true_residual", "tf32", N, dims, 3, 4, 1, 2)
+    assert amount * 1e9 == pytest.approx(2 * 28 * N)
+    amount, _, _, _ = bench.kernel_work("init_residual", "bf16x3", N, dims, 3, 4, 1, 2)
+    assert amount * 1e9 == pytest.approx(1 * 20 * N)
