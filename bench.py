@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-solves", type=int, default=10, help="oracle solves of the cpu_baseline (all cores)")
     ap.add_argument("--no-cube", action="store_true", help="skip the 256x256x256 record")
+    ap.add_argument("--no-variants", action="store_true", help="skip the odd-nx / unequal-spacing record")
     ap.add_argument("--concurrency", type=int, default=3,
                     help="plans (each on its own stream) the timed steps are spread over")
     return ap.parse_args()
@@ -390,6 +391,71 @@ def run_efield(plan, ups, torch, reps=10):
     dt = e0.elapsed_time(e1) / 1e3 / reps
     return {"us_per_call": 1e6 * dt, "achieved_gbs": 32.0 * nx * ny * nz / dt / 1e9, "unit": "GB/s",
             "bytes_per_point": 32}
+
+
+def run_laplacian(ups, torch, hbm_peak, reps=10):
+    """The FP64 form's stencil w = L x (tpcg_apply_laplacian) on the bench grid: 16 B per point (x in, w out)."""
+    from paper_2501_03377_gb300 import Plan
+
+    nz, ny, nx = ups.shape
+    p64 = Plan(nx, ny, nz, ("P", "P", "N"), prec="fp64")
+    x = torch.randn_like(ups)
+    w = torch.empty_like(ups)
+    p64.laplacian(x, w)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        p64.laplacian(x, w)
+    e1.record()
+    torch.cuda.synchronize()
+    dt = e0.elapsed_time(e1) / 1e3 / reps
+    p64.close()
+    gbs = 16.0 * nx * ny * nz / dt / 1e9
+    return {"kernel": "k_apply_laplacian", "us_per_call": 1e6 * dt, "achieved_gbs": gbs, "unit": "GB/s",
+            "bytes_per_point": 16, "frac": gbs / hbm_peak}
+
+
+def run_variants(args, prec, torch, hbm_peak, steps=10):
+    """The stencil variants off the main workload's path: odd nx (one-point-per-thread direction and update,
+    the per-pass tensor-core sequence) and unequal spacings (three stencil weights), 255 x 256 x 128 P/P/N with
+    h = (1, 0.5, 2), 2000 charged defects; one plan, tpcg_solve, with the per-kernel fractions of an
+    instrumented pass."""
+    from inputs import synth
+    from paper_2501_03377_gb300 import Plan
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    nx, ny, nz, bcs, h = 255, 256, 128, ("P", "P", "N"), (1.0, 0.5, 2.0)
+    etas = [torch.from_numpy(synth.defect_rhs(nx, ny, nz, bcs, 2000, (1.0, 4.0), seed=s)).to(dev) for s in range(4)]
+    ups = torch.zeros_like(etas[0])
+    pl = Plan(nx, ny, nz, bcs, h=h, prec=prec)
+    nobar = lambda: None  # noqa: E731
+    for s in range(3):
+        pl.solve(etas[s % 4], ups, tol=args.tol, maxit=60, zero_guess=True)
+    dt, infos, _ = time_steps(pl, etas, ups, steps, args.tol, torch, nobar)
+    pl.profile_begin()
+    _, pinfos, _ = time_steps(pl, etas, ups, steps, args.tol, torch, nobar)
+    kst = pl.profile_end()
+    N = nx * ny * nz
+    iters = sum(i["iters"] for (_, i) in pinfos)
+    applies = sum(i["precond_applies"] for (_, i) in pinfos)
+    checks = sum(i.get("checks", 0) for (_, i) in pinfos)
+    kernels = {}
+    for k, v in kst.items():
+        amount, unit, bound, _ = kernel_work(k, prec, N, (nx, ny, nz), iters, applies, steps, checks,
+                                             pl.precond_launches())
+        rec = {"launches": v["launches"], "ms": round(v["total_ms"], 4)}
+        if amount is not None and unit == "GB":
+            rec["frac"] = round(amount / (v["total_ms"] / 1e3) / hbm_peak, 4)
+        kernels[k] = rec
+    out = {"grid": [nx, ny, nz], "bcs": ",".join(bcs), "h": list(h), "form": f"mixed-{prec}",
+           "value": steps / dt, "unit": "solves/s", "ms_per_solve": 1e3 * dt / steps,
+           "iters_per_solve": sum(i["iters"] for (_, i) in infos) / steps,
+           "worst_rel_res_true": max(i["rel_res_true"] for (_, i) in infos),
+           "failed": sum(1 for (st, _) in infos if st != 0), "tc_launches_per_apply": pl.precond_launches(),
+           "kernels": kernels}
+    pl.close()
+    return out
 
 
 def run_batched(prec, torch):
@@ -809,7 +875,7 @@ def run_ours(args, rank, world, torch):
                     "worst_rel_res_true": max(i["rel_res_true"] for (_, i) in inf64)}
         p64.close()
 
-    serving = batched = comparators = efield = None
+    serving = batched = comparators = efield = laplacian = variants = None
     if rank == 0 and world == 1 and prec != "fp64":
         if args.serving_requests > 0:
             serving = run_serving(args, prec, torch)
@@ -818,6 +884,9 @@ def run_ours(args, rank, world, torch):
         if not args.no_comparators:
             comparators = run_comparators(torch)
         efield = run_efield(plan, ups, torch)
+        laplacian = run_laplacian(ups, torch, hbm_peak)
+        if not args.no_variants:
+            variants = run_variants(args, prec, torch, hbm_peak)
     cube = None
     if rank == 0 and world == 1 and prec != "fp64" and nz == 128 and not args.no_cube:
         cube = run_cube(args, prec, torch, hbm_peak, peak_src)
@@ -855,6 +924,7 @@ def run_ours(args, rank, world, torch):
             "roofline": roofline, "kernels": kernels,
             "e2e": e2e, "cpu_baseline": cpu, "fp64_form": fp64_cmp, **forms,
             "serving": serving, "batched": batched, "comparators": comparators, "efield": efield,
+            "laplacian_fp64": laplacian, "variants": variants,
             "cube_256": cube, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
