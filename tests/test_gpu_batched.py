@@ -58,7 +58,7 @@ SMALL = [dict(nx=16, ny=12, nz=8, bcs=("P", "N", "P"), nrhs=2, seed=1),
          dict(nx=32, ny=32, nz=16, bcs=("P", "P", "DN"), nrhs=2, seed=5)]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp16", "bf16"])
+@pytest.mark.parametrize("prec", ["fp64", "fp16", "bf16", "tf32", "bf16x3"])
 def test_batched_equals_solo_and_oracle(prec):
     from paper_2501_03377_gb300 import Plan
 
@@ -104,20 +104,22 @@ def test_batched_same_plan_twice_and_argument_errors():
         binding.TPCG_ERR_INVALID_ARG
 
 
-def test_batched_48_mixed_solves_fp16():
+@pytest.mark.parametrize("prec", ["fp16", "bf16x3"])
+def test_batched_48_mixed_solves(prec):
     """48 independent solves, grids {64..160}^2 x {32..96}, BC per axis from {P,D,N,DN,ND}, 1-8 RHS each,
-    FP16 mixed preconditioner, tol 1e-10; a sample of them is re-solved alone and must match bitwise."""
+    FP16 or split BF16 mixed preconditioner (the bench's batched record runs the latter), tol 1e-10; a sample
+    of them is re-solved alone and must match bitwise."""
     from paper_2501_03377_gb300 import Plan
 
     specs = synth.batched_specs(seed=0)
-    plans, etas, ups, _ = _make_batch(specs, "fp16")
+    plans, etas, ups, _ = _make_batch(specs, prec)
     st, infos = _run_batch(plans, etas, ups, specs)
     assert st == 0, [i["status"] for i in infos if i["status"]]
     assert len(infos) == sum(s["nrhs"] for s in specs)
     assert max(i["rel_res_true"] for i in infos) <= 1e-10
     for s in (0, 7, 23, 47):
         spec = specs[s]
-        solo = Plan(spec["nx"], spec["ny"], spec["nz"], spec["bcs"], prec="fp16")
+        solo = Plan(spec["nx"], spec["ny"], spec["nz"], spec["bcs"], prec=prec)
         us = torch.zeros_like(etas[s][0])
         solo.solve(etas[s][0].contiguous(), us, tol=1e-10, maxit=60, zero_guess=True)
         assert torch.equal(us, ups[s][0])

@@ -29,6 +29,8 @@ SESSIONS = [  # (seed, nx, ny, nz, bcs, prec)
     (12, 40, 40, 1, ("D", "D", "D"), "fp64"),
     (13, 24, 32, 20, ("N", "D", "DN"), "bf16"),
     (14, 48, 16, 12, ("P", "N", "P"), "fp16"),
+    (15, 40, 24, 16, ("P", "P", "N"), "bf16x3"),
+    (16, 33, 20, 12, ("ND", "P", "D"), "tf32"),
 ]
 STEPS = 3
 
