@@ -316,7 +316,7 @@ typedef struct {
   double wp;                 /* <W_s, P_s> = <L P_s, P_s>                              */
   double rr, sum_r;          /* ||R_{s+1}||^2 and sum(R_{s+1}) of the recurrence       */
   double mean_z;             /* mean(Z_s) (singular operators; 0 otherwise)            */
-  int    lp_shift;           /* FP16 form: R_s entered the preconditioner as R_s*2^k   */
+  int    lp_shift;           /* FP16, split: R_s entered the preconditioner as R_s*2^k */
   int    direction_exponent; /* mixed forms: P_s = P_int * 2^-k (int32 fixed point)   */
 } tpcg_cg_scalars;
 int tpcg_plan_cg_scalars(tpcg_plan* plan, tpcg_cg_scalars* out);

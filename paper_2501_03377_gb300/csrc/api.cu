@@ -1049,7 +1049,7 @@ int tpcg_plan_cg_scalars(tpcg_plan* plan, tpcg_cg_scalars* out) {
   out->rr = hs->rr;
   out->sum_r = hs->sumR;
   out->mean_z = hs->mZ;
-  out->lp_shift = (plan->lp_kind == 2) ? hs->lp_shift_applied : 0;
+  out->lp_shift = (plan->lp_kind == 2 || plan->lp_kind == 4) ? hs->lp_shift_applied : 0;
   out->direction_exponent = (plan->prec == TPCG_FP64) ? 0 : hs->kp;
   return TPCG_OK;
 }

@@ -151,8 +151,8 @@ __global__ void __launch_bounds__(TX* TY) k_apply_laplacian(Geom g, int zchunk, 
 
 // ------------------------------------------------------------------ low-precision copy of R
 // Input of the first tensor-core pass: BF16, FP16 of R * 2^shift, TF32, or the
-// BF16 pair hi = bf16(R), lo = bf16(R - hi) in two planes; rows padded to
-// `pitch` elements.  ptr == nullptr in the FP64 form.
+// BF16 pair of R * 2^shift (hi = bf16(R * 2^shift), lo = bf16 of the rest) in two
+// planes; rows padded to `pitch` elements.  ptr == nullptr in the FP64 form.
 struct LowPrec {
   void* ptr;
   int kind;  // 1 BF16, 2 FP16, 3 TF32 (FP32 containers, rounded to nearest even), 4 BF16 hi/lo planes
@@ -160,14 +160,15 @@ struct LowPrec {
   long long plane;  // kind 4: 16-bit words from the hi plane to the lo plane
 };
 
-// The value of a BF16 bit pattern, exactly.
-__device__ __forceinline__ double bf16_bits_to_f64(uint16_t b) { return (double)__uint_as_float((uint32_t)b << 16); }
-
-// r -> (hi, lo) = (bf16(r), bf16(r - hi)), each rounded once to nearest even from FP64 (r - hi is exact).
-__device__ __forceinline__ uint32_t f64_to_bf16_split(double r) {
-  const uint16_t hi = f64_to_bf16_bits(r);
-  const uint16_t lo = f64_to_bf16_bits(r - bf16_bits_to_f64(hi));
-  return (uint32_t)hi | ((uint32_t)lo << 16);
+// The split pair of a value from its FP32 round-to-odd image r32o (= r * 2^shift rounded to odd at 24
+// bits): hi = bf16(r32o), which is the correctly rounded bf16(r * 2^shift), and lo = bf16(r32o - hi), the
+// difference exact in FP32.  lo equals bf16(r * 2^shift - hi) whenever lo's leading bit lies within 13 bits
+// of hi's; below that it may differ from it by one unit of its last place (2^-24 of r), far under the
+// pair's 2^-16.  FP32 and conversion arithmetic only: no FP64-pipe work per point.
+__device__ __forceinline__ uint32_t f32o_to_bf16_split(float r32o) {
+  const __nv_bfloat16 hi = __float2bfloat16_rn(r32o);
+  const __nv_bfloat16 lo = __float2bfloat16_rn(r32o - __bfloat162float(hi));
+  return (uint32_t)__bfloat16_as_ushort(hi) | ((uint32_t)__bfloat16_as_ushort(lo) << 16);
 }
 
 // r -> TF32 in an FP32 container: FP64 -> FP32 round-to-odd on the bit pattern, then round to nearest even
@@ -192,7 +193,7 @@ __device__ __forceinline__ void store_lp(const LowPrec& lp, long long i, double 
     return;
   }
   if (lp.kind == 4) {
-    const uint32_t hl = f64_to_bf16_split(r);
+    const uint32_t hl = f32o_to_bf16_split(r32o);
     reinterpret_cast<uint16_t*>(lp.ptr)[j] = (uint16_t)hl;
     reinterpret_cast<uint16_t*>(lp.ptr)[lp.plane + j] = (uint16_t)(hl >> 16);
     return;
@@ -215,7 +216,7 @@ __device__ __forceinline__ void store_lp_pair(const LowPrec& lp, long long i, do
     return;
   }
   if (lp.kind == 4) {
-    const uint32_t h0 = f64_to_bf16_split(r0), h1 = f64_to_bf16_split(r1);
+    const uint32_t h0 = f32o_to_bf16_split(a32), h1 = f32o_to_bf16_split(b32);
     uint16_t* q = reinterpret_cast<uint16_t*>(lp.ptr);
     *reinterpret_cast<uint32_t*>(q + j) = (h0 & 0xffffu) | (h1 << 16);
     *reinterpret_cast<uint32_t*>(q + lp.plane + j) = (h0 >> 16) | (h1 & 0xffff0000u);

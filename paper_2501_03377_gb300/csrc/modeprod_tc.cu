@@ -107,7 +107,7 @@ struct TcArgs {
   const float* lamC;
   void* out;
   const uint16_t* Rt;  // the tensor-core copy of R the first pass read (FP16 = R * 2^shR, BF16 = R, TF32 = R
-                       // in FP32 containers, or the split form's hi plane)
+                       // in FP32 containers, or the hi plane of the split pair of R * 2^shR)
   int rpitch;          // its row pitch (elements)
   long long rplane;    // split form: 16-bit words from the hi plane of R~ to its lo plane
   long long oplane;    // split form: 16-bit words from the hi plane of the output to its lo plane
@@ -260,13 +260,13 @@ __global__ void __launch_bounds__(TcWarps<FINAL>::threads, 1)
   const uint32_t tmem = *tmem_holder;
   const int ntiles = (a.rows + kTileRows - 1) / kTileRows;
 
-  // last pass: rho = <R~, Z>, R~ the 16-bit copy of R the first pass consumed (FP16: R * 2^shR, BF16: R,
-  // brought to the same 2^shR scale), from FP32 products in compensated FP32 per thread; sum(Z)
+  // last pass: rho = <R~, Z>, R~ the copy of R the first pass consumed (FP16 and split: R * 2^shR; BF16 and
+  // TF32: R, brought to the same 2^shR scale), from FP32 products in compensated FP32 per thread; sum(Z)
   // likewise; max |Z|
   Acc32 red0, red1;
   float zmax = 0.0f;
   const int shR = (FINAL && a.st) ? a.st->lp_shift_applied : 0;
-  const float rs = std::is_same<InT, __half>::value ? 1.0f : ldexpf(1.0f, shR);
+  const float rs = (std::is_same<InT, __half>::value || KS::split) ? 1.0f : ldexpf(1.0f, shR);
   const uint16_t* Rlo = KS::split ? a.Rt + a.rplane : nullptr;  // split form: lo plane of R~
 
   if (warp == 0) {
@@ -1313,7 +1313,9 @@ int tc_plan_setup(tpcg_plan* p) {
     a.last = sp.final_stage;
     a.sG = sG;
     a.gscale = std::ldexp(1.0f, -sG);
-    a.shift_src = tp->fp16 ? &p->d_state->lp_shift_applied : nullptr;
+    // FP16 and split: R~ holds R * 2^shift (the FP16 range, and the split's lo words far from BF16's
+    // underflow); the last pass undoes the scale on Z
+    a.shift_src = (tp->fp16 || tp->split) ? &p->d_state->lp_shift_applied : nullptr;
     // TF32 and split: the eigenbasis (up to 256 x 256 FP32 or BF16 pairs, 256 KB) does not fit next to the
     // stages; each stage then carries its K tile of the eigenbasis with the data tile (split: the hi and lo
     // tiles of both).  (Keeping 128 eigenbasis rows resident per CTA, two CTAs per tile, measured slower:
