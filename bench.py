@@ -519,7 +519,7 @@ NCU_TRAFFIC_PER_LAUNCH = {
     "bf16x3": {
         # the six launches of one application (one per mode product): 33.7-33.9 MB read each (the hi and lo
         # planes of the input), under 0.7 MB written (the outputs stay in L2 until the next launch reads them)
-        "modeprod_tc": 206.29e6 / 6,
+        "modeprod_tc": 206.11e6 / 6,
     },
 }
 
