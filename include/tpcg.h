@@ -87,7 +87,10 @@ extern "C" {
                                 about 2^-16 instead of 2^-8, so CG needs fewer
                                 refinement iterations; one launch per mode product,
                                 the eigenbasis streamed with the data, intermediates
-                                4 B per point (hi and lo planes)                    */
+                                4 B per point (hi and lo planes).  R enters scaled
+                                by a power of two to unit RMS, split from its FP32
+                                round-to-odd image (lo exact to one unit of its last
+                                place); the scale is undone exactly on Z           */
 
 /* ---- tpcg_solve flags ---------------------------------------------------- */
 #define TPCG_ZERO_GUESS   1u  /* ignore ups on entry and start from ups = 0 */
