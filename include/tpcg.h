@@ -207,6 +207,18 @@ int tpcg_solve_host_stream(tpcg_plan* plan, int nrhs, const double* const* eta_h
  * per z-plane.  Same products, same precision; the rounding points of the
  * intermediates differ (x before y in the backward products).  0 keeps one
  * launch per mode product.
+ * TPCG_OPT_GRAPHS (0 = off, the default): a solve's launch sequences -- the
+ * set-up and each chunk of iterations the host enqueues between reads of the
+ * device state -- are captured as CUDA graphs the first time they occur on
+ * the plan and replayed afterwards (one graph launch instead of some ten
+ * kernel launches per iteration; the kernels read the solve's eta and ups
+ * from the device state, so one graph serves every solve of the plan).
+ * Same kernels, same order, bitwise the same results.  It pays where one
+ * plan solves the same shape of chunk many times and the host's launches
+ * are the limit; each new chunk length costs a capture and an instantiation
+ * first.  Plans on the legacy default stream (stream NULL) and plans being
+ * profiled launch directly.  Changing any option, the comparator
+ * preconditioner or the autotuned launch sequence drops the plan's graphs.
  * Returns TPCG_OK, TPCG_ERR_OOM (above), or TPCG_ERR_INVALID_ARG (NULL plan,
  * unknown option, value not 0 or 1).  Set options between solves only: not
  * while another host thread, tpcg_solve_batched or a server request is using
@@ -215,6 +227,7 @@ int tpcg_solve_host_stream(tpcg_plan* plan, int nrhs, const double* const* eta_h
 #define TPCG_OPT_DEFER_U 1
 #define TPCG_OPT_FUSE_G 2
 #define TPCG_OPT_SLICES 3
+#define TPCG_OPT_GRAPHS 4
 int tpcg_plan_set_option(tpcg_plan* plan, int option, int value);
 
 /* Autotuner of the preconditioner's launch sequence (no counterpart in the

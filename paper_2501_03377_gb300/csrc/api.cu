@@ -146,6 +146,7 @@ void free_plan(tpcg_plan* p) {
   if (!p) return;
   if (p->stream) cudaStreamSynchronize(p->stream);
   else cudaDeviceSynchronize();
+  graph_reset(p);
   tc_plan_release(p);
   for (int a = 0; a < 3; ++a) {
     for (int d = 0; d < 2; ++d) {
@@ -276,9 +277,8 @@ int enqueue_state_readback(tpcg_plan* p) {
   return last_cuda_error();
 }
 
-// `count` iterations of the PCG loop of Algorithm 1; kernels of iterations after
-// convergence return at once
-int enqueue_iterations(SolveJob& j, int count) {
+// The launches of `count` iterations starting at j.issued.
+int launch_iterations(SolveJob& j, int count) {
   tpcg_plan* p = j.p;
   const Geom g = make_geom(p);
   for (int c = 0; c < count; ++c) {
@@ -292,11 +292,80 @@ int enqueue_iterations(SolveJob& j, int count) {
   }
   // singular operators: centre U on the device if the stop test succeeded inside this chunk
   if (p->singular) launch_center_u(p, g, j.ups, j.issued);
+  return TPCG_OK;
+}
+
+// Graphs kept per plan; the least recently used is dropped beyond this.
+constexpr size_t kGraphCap = 48;
+
+// Runs the launch sequence `launch` on the plan's stream, as a CUDA graph when the plan allows it: the
+// sequence of `key` is captured the first time it is needed (stream capture of the same launches) and
+// replayed afterwards.  The kernels read the solve's buffers from the device state, so a captured sequence
+// serves every solve of the plan.  Profiling (per-launch events) and the legacy default stream launch
+// directly; a sequence that fails to capture turns graphs off for the plan.
+template <class F>
+int run_graphed(tpcg_plan* p, const GraphKey& key, F&& launch) {
+  if (!p->use_graphs || !p->stream || p->prof.on) return launch();
+  auto it = p->graphs.find(key);
+  if (it == p->graphs.end()) {
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      p->use_graphs = 0;
+      return launch();
+    }
+    const unsigned long long lc0 = p->launch_count;
+    const int rc = launch();
+    const cudaError_t ec = cudaStreamEndCapture(p->stream, &graph);
+    const unsigned long long kernels = p->launch_count - lc0;
+    p->launch_count = lc0;
+    cudaGraphExec_t exec = nullptr;
+    if (rc != TPCG_OK || ec != cudaSuccess || !graph || cudaGraphInstantiate(&exec, graph, 0ull) != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      if (rc != TPCG_OK) return rc;
+      p->use_graphs = 0;
+      return launch();
+    }
+    cudaGraphDestroy(graph);
+    if (p->graphs.size() >= kGraphCap) {
+      auto old = p->graphs.begin();
+      for (auto q = p->graphs.begin(); q != p->graphs.end(); ++q)
+        if (q->second.used < old->second.used) old = q;
+      cudaGraphExecDestroy(old->second.exec);
+      p->graphs.erase(old);
+    }
+    it = p->graphs.emplace(key, GraphEntry{exec, kernels, 0}).first;
+  }
+  it->second.used = ++p->graph_clock;
+  p->launch_count += it->second.kernels;
+  return cudaGraphLaunch(it->second.exec, p->stream) == cudaSuccess ? TPCG_OK : TPCG_ERR_CUDA;
+}
+
+unsigned graph_flags(const SolveJob& j) {
+  return ((j.flags & TPCG_ZERO_GUESS) ? 1u : 0u) | ((((uintptr_t)j.eta & 15) == 0) ? 2u : 0u) |
+         ((((uintptr_t)j.ups & 15) == 0) ? 4u : 0u);
+}
+
+// `count` iterations of the PCG loop of Algorithm 1; kernels of iterations after
+// convergence return at once
+int enqueue_iterations(SolveJob& j, int count) {
+  tpcg_plan* p = j.p;
+  const int rc = run_graphed(p, GraphKey{1, j.issued, count, graph_flags(j), p->graph_gen},
+                             [&]() { return launch_iterations(j, count); });
+  if (rc) return rc;
   j.issued += count;
   return TPCG_OK;
 }
 
 }  // namespace
+
+// Drop the plan's captured launch sequences (an option or a buffer they hold has changed).
+void graph_reset(tpcg_plan* p) {
+  for (auto& kv : p->graphs) cudaGraphExecDestroy(kv.second.exec);
+  p->graphs.clear();
+  p->graph_gen += 1;
+}
 
 int job_start(SolveJob& j) {
   tpcg_plan* p = j.p;
@@ -313,13 +382,17 @@ int job_start(SolveJob& j) {
   hs->u_valid = zero_guess ? 0 : 1;  // mixed forms: U holds the initial guess
   hs->singular = p->singular ? 1 : 0;
   hs->status = TPCG_OK;
+  hs->eta = j.eta;
+  hs->ups = j.ups;
   if (cudaMemcpyAsync(p->d_state, hs, sizeof(SolveState), cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
     return TPCG_ERR_CUDA;
   // Algorithm 1 set-up: initial residual, Z_0, rho_0 (eq. centering first when singular)
-  launch_eta_sum(p, g, j.eta, zero_guess ? nullptr : j.ups);  // mean, first low-precision exponent, max|U_0|
-  launch_init_residual(p, g, j.eta, j.ups, zero_guess);
-  if (p->lp_kind == 2 && !zero_guess) launch_to_lp(p, g, p->d_R);  // re-scale FP16 copy to the actual R_0
-  int rc = run_precond(p, p->d_R, p->d_Z, p->d_state);
+  int rc = run_graphed(p, GraphKey{0, 0, 0, graph_flags(j), p->graph_gen}, [&]() {
+    launch_eta_sum(p, g, j.eta, zero_guess ? nullptr : j.ups);  // mean, first low-precision exponent, max|U_0|
+    launch_init_residual(p, g, j.eta, j.ups, zero_guess);
+    if (p->lp_kind == 2 && !zero_guess) launch_to_lp(p, g, p->d_R);  // re-scale FP16 copy to the actual R_0
+    return run_precond(p, p->d_R, p->d_Z, p->d_state);
+  });
   if (rc) return rc;
   j.issued = 0;
   // first chunk: the iteration count of the plan's previous converged solve (similar problems repeat
@@ -848,14 +921,22 @@ int tpcg_plan_set_option(tpcg_plan* plan, int option, int value) {
       plan->p_slots = kPRing;
     }
     plan->defer_u = value;
+    graph_reset(plan);
     return TPCG_OK;
   }
   if (option == TPCG_OPT_FUSE_G) {
     plan->tc_fuse = value;
+    graph_reset(plan);
     return TPCG_OK;
   }
   if (option == TPCG_OPT_SLICES) {
     plan->tc_slab = value;
+    graph_reset(plan);
+    return TPCG_OK;
+  }
+  if (option == TPCG_OPT_GRAPHS) {
+    plan->use_graphs = value;
+    graph_reset(plan);
     return TPCG_OK;
   }
   return TPCG_ERR_INVALID_ARG;
@@ -928,6 +1009,7 @@ int tpcg_plan_set_precond(tpcg_plan* plan, int kind, int p, double omega) {
         for (int cx = 0; cx < 3; ++cx)
           plan->jac_invd[cx + 3 * cy + 9 * cz] = 1.0 / (omega * (dg[0][cx] + dg[1][cy] + dg[2][cz]));
   }
+  graph_reset(plan);
   return TPCG_OK;
 }
 
@@ -960,6 +1042,7 @@ int tpcg_plan_autotune(tpcg_plan* plan, const char* cache_path, int applies, tpc
             (a[5] == 0 || a[5] == 1)) {
           plan->tc_slab = a[4];
           plan->tc_fuse = a[5];
+          graph_reset(plan);
           out->slices = a[4];
           out->fuse_g = a[5];
           out->us_per_apply = us;
@@ -1016,6 +1099,7 @@ int tpcg_plan_autotune(tpcg_plan* plan, const char* cache_path, int applies, tpc
   cudaEventDestroy(e1);
   plan->tc_slab = rc ? slab0 : best_s;
   plan->tc_fuse = rc ? fuse0 : best_f;
+  graph_reset(plan);
   if (rc) {
     last_cuda_error();
     return rc;

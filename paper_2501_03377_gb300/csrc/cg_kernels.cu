@@ -464,6 +464,9 @@ __global__ void __launch_bounds__(TX* TY) k_residual_fx(Geom g, const double* __
                                                         const double* __restrict__ U, double* __restrict__ R,
                                                         LowPrec lp, SolveState* st, double* partials, int force) {
   if (!INIT && !force && (st->done || !st->need_check)) return;
+  // the solve's buffers come from the state (a captured launch sequence serves every solve of the plan)
+  eta = st->eta;
+  U = st->ups;
   const int ku = st->ku, sr = st->sr;
   FieldFixed64 f{U, ku};
   OpResidualFx<INIT> op{eta, R, lp, st->mean_eta, g.nih2[0], g.nih2[1], g.nih2[2], st->lp_shift, sr, ku, g.uniform,
@@ -1115,6 +1118,8 @@ __global__ void __launch_bounds__(TX* TY, 4) k_update_u_int(Geom g, double* __re
                                                           const int* __restrict__ P, double* __restrict__ R,
                                                           LowPrec lp, SolveState* st, double* partials) {
   if (st->done) return;
+  // the solve's buffers come from the state (a captured launch sequence serves every solve of the plan)
+  U = st->ups;
   const double alpha = st->alpha;
   const double na0 = st->nah[0], na1 = st->nah[1], na2 = st->nah[2];  // -alpha / h^2 per axis
   const int kp = st->kp;
@@ -1218,6 +1223,8 @@ __global__ void __launch_bounds__(TX* TY, 4) k_update_u_pair(Geom g, double* __r
                                                            const int* __restrict__ P, double* __restrict__ R,
                                                            LowPrec lp, SolveState* st, double* partials) {
   if (st->done) return;
+  // the solve's buffers come from the state (a captured launch sequence serves every solve of the plan)
+  U = st->ups;
   const double alpha = st->alpha;
   const double na0 = st->nah[0], na1 = st->nah[1], na2 = st->nah[2];  // -alpha / h^2 per axis
   const int kp = st->kp;
@@ -1331,6 +1338,8 @@ __global__ void __launch_bounds__(256) k_update(Geom g, double* __restrict__ U, 
                                                 SolveState* st, double* partials) {
   const long long N = g.N;
   if (st->done) return;
+  // the solve's buffers come from the state (a captured launch sequence serves every solve of the plan)
+  U = st->ups;
   const double alpha = st->alpha;
   const double nalpha = -alpha;
   const int zg = st->zero_guess;
@@ -1363,6 +1372,8 @@ __global__ void __launch_bounds__(256) k_update(Geom g, double* __restrict__ U, 
 __global__ void __launch_bounds__(256) k_init_zero(long long N, const double* __restrict__ eta,
                                                    double* __restrict__ R, LowPrec lp, SolveState* st,
                                                    double* partials) {
+  // the solve's buffers come from the state (a captured launch sequence serves every solve of the plan)
+  eta = st->eta;
   const double mean = st->mean_eta;
   const int shift = st->lp_shift;
   double e2 = 0.0;
@@ -1387,6 +1398,9 @@ __global__ void __launch_bounds__(256) k_init_zero(long long N, const double* __
 // with a given initial guess also max|U_0| for the fixed-point residual.
 __global__ void __launch_bounds__(256) k_eta_sum(Geom g, const double* __restrict__ eta,
                                                  const double* __restrict__ U0, SolveState* st, double* partials) {
+  // the solve's buffers come from the state (a captured launch sequence serves every solve of the plan)
+  eta = st->eta;
+  if (U0) U0 = st->ups;  // (NULL: zero initial guess)
   const long long N = g.N;
   double acc[2] = {0.0, 0.0};
   unsigned long long um = 0;
@@ -1426,6 +1440,8 @@ __global__ void __launch_bounds__(256) k_form_u(Geom g, double* __restrict__ U, 
                                                 int force) {
   const int n = st->n_pend;
   if (n == 0 || (!force && (st->done || (!st->need_check && n < kPRing - 1)))) return;
+  // the solve's buffers come from the state (a captured launch sequence serves every solve of the plan)
+  U = st->ups;
   const bool valid = st->u_valid != 0;
   double al[kPRing - 1];
   int kpn[kPRing - 1];
@@ -1493,6 +1509,8 @@ __global__ void __launch_bounds__(256) k_form_u(Geom g, double* __restrict__ U, 
 __global__ void __launch_bounds__(256) k_init_zero2(unsigned npair, long long N, const double* __restrict__ eta,
                                                     double* __restrict__ R, LowPrec lp, SolveState* st,
                                                     double* partials) {
+  // the solve's buffers come from the state (a captured launch sequence serves every solve of the plan)
+  eta = st->eta;
   const double mean = st->mean_eta;
   const int shift = st->lp_shift;
   double e2 = 0.0;
@@ -1516,6 +1534,9 @@ __global__ void __launch_bounds__(256) k_init_zero2(unsigned npair, long long N,
 
 __global__ void __launch_bounds__(256) k_eta_sum2(Geom g, unsigned npair, const double* __restrict__ eta,
                                                   const double* __restrict__ U0, SolveState* st, double* partials) {
+  // the solve's buffers come from the state (a captured launch sequence serves every solve of the plan)
+  eta = st->eta;
+  if (U0) U0 = st->ups;  // (NULL: zero initial guess)
   const long long N = g.N;
   double acc[2] = {0.0, 0.0};
   unsigned long long um = 0;
@@ -1564,6 +1585,8 @@ __global__ void __launch_bounds__(256) k_norm_shift(long long N, const double* _
 __global__ void __launch_bounds__(256) k_center_u(long long N, double* __restrict__ U, const SolveState* st,
                                                   int iter_lo) {
   if (iter_lo >= 0 && !(st->done == 1 && st->status == TPCG_OK && st->done_iter > iter_lo)) return;
+  // the solve's buffers come from the state (a captured launch sequence serves every solve of the plan)
+  U = st->ups;
   const double m = st->sumU / (double)N;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x)
     U[i] -= m;

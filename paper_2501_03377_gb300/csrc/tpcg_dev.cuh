@@ -30,6 +30,8 @@ struct SolveState {
   double true_rr;      // ||eta_hat - L U||^2 at the last FP64 check
   double sumU;         // sum(U) at the last FP64 check
   double zscale;       // power-of-two scale applied to R before low-precision conversion
+  const double* eta;   // the solve's right-hand side and iterate (device pointers): the kernels that touch
+  double* ups;         // them read them here, so one captured launch sequence serves every solve of a plan
   int iter;            // s
   int maxit;
   int done;            // 1: stop issuing work

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <map>
 #include <vector>
 
 #include "../../include/tpcg.h"
@@ -89,9 +90,30 @@ struct SolveJob {
   int status = 0;
   tpcg_info info{};
 };
+// A launch sequence of a solve captured as a CUDA graph: the set-up (what = 0) or a chunk of `count`
+// iterations starting at iteration k0 (what = 1); flags: zero initial guess and the 16-byte alignment of
+// the caller's arrays (they choose kernel variants); gen: the plan's option generation.
+struct GraphKey {
+  int what, k0, count;
+  unsigned flags, gen;
+  bool operator<(const GraphKey& o) const {
+    if (what != o.what) return what < o.what;
+    if (k0 != o.k0) return k0 < o.k0;
+    if (count != o.count) return count < o.count;
+    if (flags != o.flags) return flags < o.flags;
+    return gen < o.gen;
+  }
+};
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long kernels = 0;  // kernel launches the sequence holds (the plan's launch count)
+  unsigned long long used = 0;     // last use (eviction order)
+};
+
 int job_start(SolveJob& j);
 bool job_ready(const SolveJob& j);
 int job_step(SolveJob& j);
+void graph_reset(tpcg_plan* p);
 
 }  // namespace tpcg
 
@@ -166,4 +188,9 @@ struct tpcg_plan {
   int tc_fuse = 1;          // mixed forms: TPCG_OPT_FUSE_G (the two passes around G in one launch)
   int tc_slab = 1;          // mixed forms: TPCG_OPT_SLICES (frontal-slice launches where they apply)
   int last_iters = 0;      // iterations of the plan's previous converged solve (first chunk of the next)
+  // TPCG_OPT_GRAPHS: the solve's launch sequences captured as CUDA graphs on first use and replayed
+  int use_graphs = 0;
+  unsigned graph_gen = 0;               // bumped whenever an option or buffer the sequences hold changes
+  unsigned long long graph_clock = 0;
+  std::map<tpcg::GraphKey, tpcg::GraphEntry> graphs;
 };
