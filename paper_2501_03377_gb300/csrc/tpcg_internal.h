@@ -176,7 +176,7 @@ struct tpcg_plan {
   // launch configuration (fixed per plan so that reductions are reproducible)
   dim3 st_grid, st_block;   // stencil kernels
   int st_zchunk = 1;
-  int fx_blocks[4] = {1, 1, 1, 1};  // FxKernel -> blocks of the persistent fixed-point sweeps
+  int fx_blocks[tpcg::kFxCount] = {1, 1, 1, 1};  // FxKernel -> blocks of the persistent fixed-point sweeps
   // comparator preconditioner of the FP64 form (TPCG_PRECOND_*), Jacobi(p, omega) and its table of
   // 1 / (omega d) indexed by the boundary class (start, interior, end) of x + 3 y + 9 z
   int pc_kind = 0;
