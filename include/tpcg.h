@@ -219,8 +219,18 @@ int tpcg_solve_host_stream(tpcg_plan* plan, int nrhs, const double* const* eta_h
  * first.  Plans on the legacy default stream (stream NULL) and plans being
  * profiled launch directly.  Changing any option, the comparator
  * preconditioner or the autotuned launch sequence drops the plan's graphs.
+ * TPCG_OPT_SWEEP_GRAIN (1..64; 4 = the default): the least work one block
+ * of the persistent stencil and pointwise sweeps takes -- this many (32 x 8
+ * tile, z-plane) pairs, or 256 x this many grid points -- below the grid of
+ * every SM's resident blocks.  Larger grains run the sweeps of a small grid
+ * on fewer SMs, so that the kernels of other plans' streams share the GPU
+ * (tpcg_solve_batched over many small grids: 16 measured faster than 4);
+ * a plan solved alone keeps the smaller grain (lower latency).  Grids of
+ * 256 x 256 x 128 points and more fill every SM at grains up to 8.  The
+ * grain sets the reductions' block count, so results are bitwise
+ * reproducible per grain, not across grains.
  * Returns TPCG_OK, TPCG_ERR_OOM (above), or TPCG_ERR_INVALID_ARG (NULL plan,
- * unknown option, value not 0 or 1).  Set options between solves only: not
+ * unknown option, value not 0 or 1, a grain outside 1..64).  Set options between solves only: not
  * while another host thread, tpcg_solve_batched or a server request is using
  * the plan.  Setting TPCG_OPT_DEFER_U first waits for the work already
  * enqueued on the plan's stream, then replaces the direction storage.      */
@@ -228,6 +238,7 @@ int tpcg_solve_host_stream(tpcg_plan* plan, int nrhs, const double* const* eta_h
 #define TPCG_OPT_FUSE_G 2
 #define TPCG_OPT_SLICES 3
 #define TPCG_OPT_GRAPHS 4
+#define TPCG_OPT_SWEEP_GRAIN 5
 int tpcg_plan_set_option(tpcg_plan* plan, int option, int value);
 
 /* Autotuner of the preconditioner's launch sequence (no counterpart in the

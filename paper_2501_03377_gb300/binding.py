@@ -46,6 +46,7 @@ TPCG_OPT_DEFER_U = 1
 TPCG_OPT_FUSE_G = 2
 TPCG_OPT_SLICES = 3
 TPCG_OPT_GRAPHS = 4
+TPCG_OPT_SWEEP_GRAIN = 5
 TPCG_REQ_BORROW_HOST = 1
 TPCG_REQ_BORROW_DEVICE = 2
 
@@ -531,8 +532,9 @@ class Plan:
     def set_option(self, option, value):
         """Plan option: TPCG_OPT_DEFER_U (1: record U += alpha P and form U before each check),
         TPCG_OPT_FUSE_G (0: the products around G in separate launches), TPCG_OPT_SLICES (0: one
-        launch per mode product instead of the frontal-slice launches) or TPCG_OPT_GRAPHS (0: launch
-        every kernel directly instead of replaying captured launch sequences)."""
+        launch per mode product instead of the frontal-slice launches), TPCG_OPT_GRAPHS (0: launch
+        every kernel directly instead of replaying captured launch sequences) or TPCG_OPT_SWEEP_GRAIN
+        (1..64, default 4: least work per block of the sweeps; larger for many small plans at once)."""
         st = tpcg_plan_set_option(self.handle, option, value)
         if st != TPCG_OK:
             raise TpcgError(st, "tpcg_plan_set_option")

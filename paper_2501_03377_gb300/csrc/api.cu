@@ -675,8 +675,6 @@ int tpcg_plan_create(int nx, int ny, int nz, const int bc[3], const double h[3],
     zsplit = (nz + zchunk - 1) / zchunk;
     p->st_grid = dim3(bx, by, zsplit);
     p->st_zchunk = zchunk;
-    const long long want = (N + 255) / 256;
-    p->stream_blocks = (int)std::max(1LL, std::min<long long>(want, (long long)p->num_sms * 8));
     if ((size_t)bx * by * zsplit * 4 > p->partial_slots) rc = TPCG_ERR_UNSUPPORTED;
     if (!rc && setup_fx_grids(p)) rc = TPCG_ERR_CUDA;
     for (int i = 0; i < kFxCount && !rc; ++i)
@@ -904,7 +902,21 @@ int tpcg_solve_host_stream(tpcg_plan* plan, int nrhs, const double* const* eta_h
 }
 
 int tpcg_plan_set_option(tpcg_plan* plan, int option, int value) {
-  if (!plan || (value != 0 && value != 1)) return TPCG_ERR_INVALID_ARG;
+  if (!plan) return TPCG_ERR_INVALID_ARG;
+  if (option == TPCG_OPT_SWEEP_GRAIN) {
+    if (value < 1 || value > 64) return TPCG_ERR_INVALID_ARG;
+    DeviceGuard dg(plan->device);
+    const int old = plan->sweep_grain;
+    plan->sweep_grain = value;
+    if (setup_fx_grids(plan)) {
+      plan->sweep_grain = old;
+      setup_fx_grids(plan);
+      return TPCG_ERR_CUDA;
+    }
+    graph_reset(plan);
+    return TPCG_OK;
+  }
+  if (value != 0 && value != 1) return TPCG_ERR_INVALID_ARG;
   if (option == TPCG_OPT_DEFER_U) {
     if (plan->prec == TPCG_FP64) return TPCG_OK;  // the FP64 form always updates U in place
     if (value && plan->p_slots < kPRing) {  // the recorded directions need the whole ring

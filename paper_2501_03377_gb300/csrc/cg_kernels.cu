@@ -1757,9 +1757,14 @@ void launch_apply_laplacian(const tpcg_plan* p, const Geom& g, const double* x, 
   k_apply_laplacian<<<p->st_grid, p->st_block, 0, p->stream>>>(g, p->st_zchunk, x, w);
 }
 // Persistent grids of the fixed-point sweeps: every SM holds as many blocks as
-// the kernel's resources allow (at most 8), no more blocks than (tile, plane)
-// pairs.
+// the kernel's resources allow (at most 8), and every block takes at least
+// sweep_grain (tile, plane) pairs; the grid-stride kernels at most 8 blocks per
+// SM of at least 256 * sweep_grain points.  A small grid thus leaves SMs to the
+// kernels of other plans.
 int setup_fx_grids(tpcg_plan* p) {
+  const long long grain = p->sweep_grain;
+  p->stream_blocks = (int)std::max(1LL, std::min<long long>((p->N + 256 * grain - 1) / (256 * grain),
+                                                           (long long)p->num_sms * 8));
   const bool pair = p->nx % 2 == 0;  // direction and update take two x points per thread
   const bool quad = p->nx % 4 == 0;  // direction takes four
   const void* fns[kFxCount] = {quad ? (const void*)k_direction_quad
@@ -1772,7 +1777,7 @@ int setup_fx_grids(tpcg_plan* p) {
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[i], TX * TY, 0) != cudaSuccess) return -1;
     per_sm = std::max(1, std::min(per_sm, 8));
-    p->fx_blocks[i] = (int)std::max(1LL, std::min<long long>(T, (long long)p->num_sms * per_sm));
+    p->fx_blocks[i] = (int)std::max(1LL, std::min<long long>((T + grain - 1) / grain, (long long)p->num_sms * per_sm));
   }
   return 0;
 }

@@ -176,6 +176,7 @@ struct tpcg_plan {
   // launch configuration (fixed per plan so that reductions are reproducible)
   dim3 st_grid, st_block;   // stencil kernels
   int st_zchunk = 1;
+  int sweep_grain = 4;  // TPCG_OPT_SWEEP_GRAIN: least (tile, plane) pairs (x 256 points) per sweep block
   int fx_blocks[tpcg::kFxCount] = {1, 1, 1, 1};  // FxKernel -> blocks of the persistent fixed-point sweeps
   // comparator preconditioner of the FP64 form (TPCG_PRECOND_*), Jacobi(p, omega) and its table of
   // 1 / (omega d) indexed by the boundary class (start, interior, end) of x + 3 y + 9 z

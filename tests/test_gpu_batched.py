@@ -104,15 +104,17 @@ def test_batched_same_plan_twice_and_argument_errors():
         binding.TPCG_ERR_INVALID_ARG
 
 
-@pytest.mark.parametrize("prec", ["fp16", "bf16x3"])
-def test_batched_48_mixed_solves(prec):
+@pytest.mark.parametrize("prec,grain", [("fp16", 4), ("bf16x3", 4), ("bf16x3", 16)])
+def test_batched_48_mixed_solves(prec, grain):
     """48 independent solves, grids {64..160}^2 x {32..96}, BC per axis from {P,D,N,DN,ND}, 1-8 RHS each,
-    FP16 or split BF16 mixed preconditioner (the bench's batched record runs the latter), tol 1e-10; a sample
-    of them is re-solved alone and must match bitwise."""
-    from paper_2501_03377_gb300 import Plan
+    FP16 or split BF16 mixed preconditioner (the bench's batched record runs the latter at sweep grain 16),
+    tol 1e-10; a sample of them is re-solved alone (same grain) and must match bitwise."""
+    from paper_2501_03377_gb300 import Plan, binding
 
     specs = synth.batched_specs(seed=0)
     plans, etas, ups, _ = _make_batch(specs, prec)
+    for pl in plans:
+        pl.set_option(binding.TPCG_OPT_SWEEP_GRAIN, grain)
     st, infos = _run_batch(plans, etas, ups, specs)
     assert st == 0, [i["status"] for i in infos if i["status"]]
     assert len(infos) == sum(s["nrhs"] for s in specs)
@@ -120,6 +122,7 @@ def test_batched_48_mixed_solves(prec):
     for s in (0, 7, 23, 47):
         spec = specs[s]
         solo = Plan(spec["nx"], spec["ny"], spec["nz"], spec["bcs"], prec=prec)
+        solo.set_option(binding.TPCG_OPT_SWEEP_GRAIN, grain)
         us = torch.zeros_like(etas[s][0])
         solo.solve(etas[s][0].contiguous(), us, tol=1e-10, maxit=60, zero_guess=True)
         assert torch.equal(us, ups[s][0])
@@ -136,3 +139,29 @@ def test_batched_48_mixed_solves(prec):
             eh = o.center(eh)
         res = np.linalg.norm(o.vec(eh) - L @ o.vec(to_oracle(u[r].cpu().numpy()))) / np.linalg.norm(eh)
         assert res <= 1e-10, (spec, res)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
+def test_sweep_grain_range_and_results(prec):
+    """TPCG_OPT_SWEEP_GRAIN accepts 1..64 only; at the extremes the solve still matches the oracle, and a grain
+    is bitwise reproducible (two solves at grain 64 agree)."""
+    from paper_2501_03377_gb300 import Plan, binding
+    from paper_2501_03377_gb300.binding import TpcgError
+
+    spec = dict(nx=40, ny=24, nz=12, bcs=("P", "P", "N"), nrhs=1, seed=11)
+    pl = Plan(spec["nx"], spec["ny"], spec["nz"], spec["bcs"], prec=prec)
+    for bad in (0, 65, -3):
+        with pytest.raises(TpcgError):
+            pl.set_option(binding.TPCG_OPT_SWEEP_GRAIN, bad)
+    e = torch.from_numpy(synth.batched_rhs(spec, 0)).cuda()
+    ref = o.pcg((40, 24, 12), oracle_bcs(spec["bcs"], 12), (1, 1, 1), to_oracle(e.cpu().numpy()), tol=1e-13)
+    outs = []
+    for grain in (1, 64, 64, 4):
+        pl.set_option(binding.TPCG_OPT_SWEEP_GRAIN, grain)
+        u = torch.zeros_like(e)
+        st, info = pl.solve(e, u, tol=1e-10, maxit=60, zero_guess=True)
+        assert st == 0 and info["rel_res_true"] <= 1e-10
+        assert rel_err(u.cpu().numpy(), from_oracle(ref.U)) <= 1e-9
+        outs.append(u)
+    assert torch.equal(outs[1], outs[2])
+    pl.close()
