@@ -222,7 +222,9 @@ int tpcg_solve_host_stream(tpcg_plan* plan, int nrhs, const double* const* eta_h
  * TPCG_OPT_SWEEP_GRAIN (1..64; 4 = the default): the least work one block
  * of the persistent stencil and pointwise sweeps takes -- this many (32 x 8
  * tile, z-plane) pairs, or 256 x this many grid points -- below the grid of
- * every SM's resident blocks.  Larger grains run the sweeps of a small grid
+ * every SM's resident blocks; the per-pass tensor-core launches take at
+ * least grain / 8 row tiles of 128 per CTA (one per SM below grain 16).
+ * Larger grains run the sweeps of a small grid
  * on fewer SMs, so that the kernels of other plans' streams share the GPU
  * (tpcg_solve_batched over many small grids: 16 measured faster than 4);
  * a plan solved alone keeps the smaller grain (lower latency).  Grids of

@@ -38,6 +38,7 @@ int run_precond_tc(const tpcg_plan* pl, float* Z, SolveState* st);
 int tc_plan_setup(tpcg_plan* pl);
 void tc_plan_release(tpcg_plan* pl);
 int tc_launches_per_apply(const tpcg_plan* pl);
+void tc_apply_grain(tpcg_plan* pl);
 
 const char* kernel_kind_name(int kind) {
   static const char* names[kKindCount] = {"eta_sum", "init_residual", "direction", "update", "true_residual",
@@ -913,6 +914,7 @@ int tpcg_plan_set_option(tpcg_plan* plan, int option, int value) {
       setup_fx_grids(plan);
       return TPCG_ERR_CUDA;
     }
+    tc_apply_grain(plan);
     graph_reset(plan);
     return TPCG_OK;
   }

@@ -1035,8 +1035,16 @@ struct TcStage {
   TcArgs args;
   void* out;  // output buffer of a pass that is not the last
   int grid;
+  int ntiles;  // 128-row tiles of the pass (the persistent CTAs stride over them)
   size_t smem;
 };
+
+// CTAs of a pass: one per SM, or fewer so that each takes at least sweep_grain / 8 row tiles (plans
+// solved many at once leave SMs to one another's launches).
+int tc_grid(const tpcg_plan* p, int ntiles) {
+  const int per = std::max(1, p->sweep_grain / 8);
+  return std::max(1, std::min((ntiles + per - 1) / per, p->num_sms));
+}
 
 struct TcPlan {
   bool tf32 = false;  // TF32 form: FP32 containers, eigenbasis streamed, one launch per pass
@@ -1358,7 +1366,8 @@ int tc_plan_setup(tpcg_plan* p) {
     a.NS = (int)std::min<size_t>(8, (kMaxSmem - fixed) / sbytes);
     st.smem = fixed + (size_t)a.NS * sbytes;
     const int ntiles = (a.rows + kTileRows - 1) / kTileRows;
-    st.grid = std::max(1, std::min(ntiles, p->num_sms));
+    st.ntiles = ntiles;
+    st.grid = tc_grid(p, ntiles);
     const int wpitch = p->pitch16[sp.axis];
     if (tp->split) {
       const long long xplane = (long long)((xin == p->d_Rlp) ? p->lp_plane : p->t_plane);
@@ -1459,6 +1468,14 @@ int tc_plan_setup(tpcg_plan* p) {
     if (r != TPCG_OK && r != TPCG_ERR_UNSUPPORTED) return r;
   }
   return TPCG_OK;
+}
+
+// Re-derive the CTA counts after the plan's sweep grain changed.
+void tc_apply_grain(tpcg_plan* p) {
+  TcPlan* tp = reinterpret_cast<TcPlan*>(p->tc_state);
+  if (!tp) return;
+  for (auto* v : {&tp->stages, &tp->fused})
+    for (TcStage& st : *v) st.grid = tc_grid(p, st.ntiles);
 }
 
 int tc_launches_per_apply(const tpcg_plan* p) {
