@@ -39,7 +39,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12  # SMs x FP64 FMA/clk/SM x 2 flop
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 200; the reference arm, one full oracle solve per step: 20)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="auto", choices=["auto", "fp16", "bf16", "tf32", "bf16x3", "fp64"])
@@ -56,9 +57,15 @@ def parse():
     ap.add_argument("--cpu-solves", type=int, default=10, help="oracle solves of the cpu_baseline (all cores)")
     ap.add_argument("--no-cube", action="store_true", help="skip the 256x256x256 record")
     ap.add_argument("--no-variants", action="store_true", help="skip the odd-nx / unequal-spacing record")
+    ap.add_argument("--sweep-grain", type=int, default=16,
+                    help="TPCG_OPT_SWEEP_GRAIN of the concurrent timed plans (0: the library's default; a single "
+                         "plan keeps the default)")
     ap.add_argument("--concurrency", type=int, default=3,
                     help="plans (each on its own stream) the timed steps are spread over")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 20 if args.impl == "reference" else 200
+    return args
 
 
 def peaks():
@@ -71,7 +78,8 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples (200 ms) during the timed region."""
+    """nvidia-smi samples (every 50 ms) during the timed region: start() returns once the first sample has
+    arrived, and stop() keeps the samples that arrived after that (all of them if none did)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -81,16 +89,22 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
+        self.skip = 0
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "50",
                  "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except Exception:
             self.proc = None
+            return
+        t0 = time.perf_counter()
+        while not self.lines and time.perf_counter() - t0 < 5.0 and self.proc.poll() is None:
+            time.sleep(0.005)
+        self.skip = len(self.lines)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -106,7 +120,8 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = self.lines[self.skip:] or self.lines
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -587,7 +602,8 @@ def run_cube(args, prec, torch, hbm_peak, peak_src):
     on `concurrency` plans (tpcg_solve_batched, TPCG_OPT_DEFER_U), the FP64 form on one plan, and the
     roofline of the tensor-core launches at this shape (CUDA events of an instrumented pass)."""
     from paper_2501_03377_gb300 import Plan
-    from paper_2501_03377_gb300.binding import TPCG_OPT_DEFER_U, TPCG_ZERO_GUESS, tpcg_solve_batched
+    from paper_2501_03377_gb300.binding import (TPCG_OPT_DEFER_U, TPCG_OPT_SWEEP_GRAIN, TPCG_ZERO_GUESS,
+                                                tpcg_solve_batched)
 
     dev = torch.device("cuda", torch.cuda.current_device())
     ws = workload(256, [0, 1, 2, 3])
@@ -680,7 +696,8 @@ def whole_job_rate(world, steps, seconds):
 
 def run_ours(args, rank, world, torch):
     from paper_2501_03377_gb300 import Plan
-    from paper_2501_03377_gb300.binding import TPCG_OPT_DEFER_U, TPCG_ZERO_GUESS, tpcg_solve_batched
+    from paper_2501_03377_gb300.binding import (TPCG_OPT_DEFER_U, TPCG_OPT_SWEEP_GRAIN, TPCG_ZERO_GUESS,
+                                                tpcg_solve_batched)
 
     dev = torch.device("cuda", torch.cuda.current_device())
     prec = pick_prec(args)
@@ -717,6 +734,9 @@ def run_ours(args, rank, world, torch):
     if prec != "fp64" and conc > 1:  # several plans in flight: record U += alpha P and form U before each check
         for cp in cplans:
             cp.set_option(TPCG_OPT_DEFER_U, 1)
+    if args.sweep_grain and conc > 1:  # several plans in flight: fuller blocks so that their kernels share SMs
+        for cp in cplans:
+            cp.set_option(TPCG_OPT_SWEEP_GRAIN, args.sweep_grain)
     counts = [args.steps // conc + (1 if q < args.steps % conc else 0) for q in range(conc)]
     firsts = [sum(counts[:q]) for q in range(conc)]
     E = [torch.stack([etas[(firsts[q] + r) % 4] for r in range(max(1, counts[q]))]).contiguous() for q in range(conc)]
@@ -922,7 +942,9 @@ def run_ours(args, rank, world, torch):
                              "workspace per plan > 129 MB L2",
                        "parallelism": f"replicas x{world}",
                        "concurrency": f"{conc} plans on {conc} streams (tpcg_solve_batched)"
-                                      + (", TPCG_OPT_DEFER_U" if prec != "fp64" and conc > 1 else "")},
+                                      + (", TPCG_OPT_DEFER_U" if prec != "fp64" and conc > 1 else "")
+                                      + (f", TPCG_OPT_SWEEP_GRAIN {args.sweep_grain}"
+                                         if args.sweep_grain and conc > 1 else "")},
             "mpoints_per_s": value * N / 1e6,
             "iters_per_solve": iters_total / args.steps, "precond_applies_per_solve": applies_total / args.steps,
             "worst_rel_res_true": worst_res, "failed_solves": len(bad),
