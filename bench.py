@@ -648,6 +648,8 @@ def run_cube(args, prec, torch, hbm_peak, peak_src):
     if conc > 1:
         for cp in cps:
             cp.set_option(TPCG_OPT_DEFER_U, 1)
+            if args.sweep_grain:
+                cp.set_option(TPCG_OPT_SWEEP_GRAIN, args.sweep_grain)
     counts = [steps // conc + (1 if q < steps % conc else 0) for q in range(conc)]
     E = [torch.stack([etas[(sum(counts[:q]) + r) % 4] for r in range(max(1, counts[q]))]).contiguous()
          for q in range(conc)]
