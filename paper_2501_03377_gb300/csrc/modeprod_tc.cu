@@ -1024,6 +1024,313 @@ __global__ void __launch_bounds__(kPairThreads, 1)
 }
 
 // ------------------------------------------------------------------ host side
+// Fused pair of passes, split BF16 form.  The same two products as
+// k_modeprod_pair (Algorithm 7: forward product along one axis, Hadamard step
+// by G, backward product along the same axis) on hi/lo BF16 pairs: each K step
+// issues hi.hi, lo.hi and hi.lo into one FP32 accumulator in the order of the
+// per-pass split kernel, the epilogue of stage 1 multiplies by G in FP32 and
+// splits into hi = bf16(v), lo = bf16(v - hi) (T, both planes, K-major with
+// the 128-byte swizzle), and stage 2 writes the backward pass's output planes
+// with the per-pass kernel's stores: the output is bitwise that of the two
+// split passes.  Both split eigenbases stay resident (2 x 64 KB at 128
+// points), so T has one buffer and the data one stage: the epilogue writes T
+// for tile i once it has drained stage 2 of tile i-1 (whose MMAs read T), while
+// the tensor core runs stage 1 of tile i+1.
+constexpr int kPairSplitEpi = 16;
+constexpr int kPairSplitThreads = (2 + kPairSplitEpi) * 32;
+
+__global__ void __launch_bounds__(kPairSplitThreads, 1)
+    k_modeprod_pair_split(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW1,
+                          const __grid_constant__ CUtensorMap tmW2, TcArgs a) {
+  if (a.st && a.st->done) return;
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* sm = smem_raw + (base - raw);
+  const int KT = a.KT, NS = a.NS;
+  // per K tile: the hi tile, then the lo tile (one 3D TMA box {64, rows, 2})
+  const uint32_t w1kt = 2u * (uint32_t)a.VR * 128u, w2kt = 2u * 128u * 128u, tkt = 2u * (uint32_t)kTBytes;
+  const uint32_t sW1 = base;
+  const uint32_t sW2 = sW1 + (uint32_t)KT * w1kt;  // VR % 8 == 0: 1024-aligned
+  const uint32_t sT = sW2 + (uint32_t)KT * w2kt;
+  const uint32_t sD = sT + (uint32_t)KT * tkt;
+  const uint32_t sbytes = 2u * (uint32_t)kStageBytes;
+  uint8_t* barp = sm + (sD - base) + (size_t)NS * sbytes;
+  const uint32_t bars = smem_u32(barp);
+  auto full = [&](int s) { return bars + 8u * s; };
+  auto empty = [&](int s) { return bars + 8u * (NS + s); };
+  auto d1full = [&](int b) { return bars + 8u * (2 * NS + b); };
+  auto d1empty = [&](int b) { return bars + 8u * (2 * NS + 2 + b); };
+  auto d2full = [&](int b) { return bars + 8u * (2 * NS + 4 + b); };
+  auto d2empty = [&](int b) { return bars + 8u * (2 * NS + 6 + b); };
+  const uint32_t tready = bars + 8u * (2 * NS + 8);
+  const uint32_t vbar = bars + 8u * (2 * NS + 9);
+  const uint32_t drain = bars + 8u * (2 * NS + 10);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(barp + 8 * (2 * NS + 11));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+  const Abort ab{abort_flag, a.err, a.st};
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(d1full(b), 1);
+      mbar_init(d1empty(b), kPairSplitEpi * 32);
+      mbar_init(d2full(b), 1);
+      mbar_init(d2empty(b), kPairSplitEpi * 32);
+    }
+    mbar_init(tready, kPairSplitEpi * 32);
+    mbar_init(vbar, 1);
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                 "r"(512u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+  const int ntiles = (a.rows + kTileRows - 1) / kTileRows;
+  const int nmine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer: both split eigenbases once, then the K tiles of every row tile
+      mbar_expect_tx(vbar, (uint32_t)KT * (w1kt + w2kt));
+      for (int kt = 0; kt < KT; ++kt) {
+        tma_load_3d(sW1 + (uint32_t)kt * w1kt, &tmW1, kt * kKTile, 0, 0, vbar);
+        tma_load_3d(sW2 + (uint32_t)kt * w2kt, &tmW2, kt * kKTile, 0, 0, vbar);
+      }
+      asm volatile("griddepcontrol.wait;" ::: "memory");
+      int it = 0;
+      for (int i = 0; i < nmine && !*abort_flag; ++i) {
+        const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+        for (int kt = 0; kt < KT; ++kt, ++it) {
+          const int s = it % NS;
+          if (!wait_bounded(empty(s), (uint32_t)(((it / NS) & 1) ^ 1), ab)) break;
+          mbar_expect_tx(full(s), sbytes);
+          tma_load_3d(sD + (uint32_t)s * sbytes, &tmX, kt * kKTile, tile * kTileRows, 0, full(s));
+        }
+      }
+      if (*abort_flag) {  // every issued load completes before the CTA may exit
+        for (int j = (it > NS ? it - NS : 0); j < it; ++j) {
+          const unsigned long long t0 = gtimer();
+          while (!mbar_try_wait(full(j % NS), (uint32_t)((j / NS) & 1)) && gtimer() - t0 < kWaitLimitNs) {
+          }
+        }
+        const unsigned long long t0 = gtimer();
+        while (!mbar_try_wait(vbar, 0) && gtimer() - t0 < kWaitLimitNs) {
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer (BF16 operands; the order of the per-pass split kernel)
+      const uint32_t idesc1 = idesc_f16kind(128, a.Np, 1u), idesc2 = idesc_f16kind(128, 128, 1u);
+      const unsigned long long dX0 = sw128_desc(sD), dW1 = sw128_desc(sW1), dW2 = sw128_desc(sW2), dT = sw128_desc(sT);
+      // lo planes: one tile after the hi tile of the same K tile (descriptor units of 16 bytes)
+      const uint32_t xlo = (uint32_t)kStageBytes >> 4, w1lo = (uint32_t)(a.VR * 128) >> 4,
+                     w2lo = (uint32_t)(128 * 128) >> 4, tlo = (uint32_t)kTBytes >> 4;
+      bool ok = wait_bounded(vbar, 0, ab);
+      int it = 0;
+      auto stage1 = [&](int i) {  // forward product of tile i into D1[i & 1]
+        const int b = i & 1;
+        if (!wait_bounded(d1empty(b), (uint32_t)(((i >> 1) & 1) ^ 1), ab)) return false;
+        tc_fence_after();
+        const uint32_t dacc = tmem + (uint32_t)(b * 128);
+        for (int kt = 0; kt < KT; ++kt, ++it) {
+          const int s = it % NS;
+          if (!wait_bounded(full(s), (uint32_t)((it / NS) & 1), ab)) return false;
+          tc_fence_after();
+          const unsigned long long xd = dX0 + (uint32_t)s * (sbytes >> 4);
+          const unsigned long long wd = dW1 + (uint32_t)kt * (w1kt >> 4);
+          const int nk = min(4, (a.C - kt * kKTile + 15) >> 4);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            if (kk < nk) {
+              tc_mma(dacc, xd + 2u * kk, wd + 2u * kk, idesc1, (kt > 0 || kk > 0) ? 1u : 0u);
+              tc_mma(dacc, xd + xlo + 2u * kk, wd + 2u * kk, idesc1, 1u);
+              tc_mma(dacc, xd + 2u * kk, wd + w1lo + 2u * kk, idesc1, 1u);
+            }
+          }
+          tc_commit(empty(s));
+        }
+        tc_commit(d1full(b));
+        return true;
+      };
+      auto stage2 = [&](int i) {  // backward product of tile i (T in shared memory) into D2[i & 1]
+        const int b = i & 1;
+        if (!wait_bounded(tready, (uint32_t)(i & 1), ab)) return false;
+        if (!wait_bounded(d2empty(b), (uint32_t)(((i >> 1) & 1) ^ 1), ab)) return false;
+        tc_fence_after();
+        const uint32_t dacc = tmem + 256u + (uint32_t)(b * 128);
+        for (int kt = 0; kt < KT; ++kt) {
+          const unsigned long long wd = dW2 + (uint32_t)kt * (w2kt >> 4), td = dT + (uint32_t)kt * (tkt >> 4);
+          const int nk = min(4, (a.C - kt * kKTile + 15) >> 4);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            if (kk < nk) {
+              tc_mma(dacc, wd + 2u * kk, td + 2u * kk, idesc2, (kt > 0 || kk > 0) ? 1u : 0u);
+              tc_mma(dacc, wd + 2u * kk, td + tlo + 2u * kk, idesc2, 1u);
+              tc_mma(dacc, wd + w2lo + 2u * kk, td + 2u * kk, idesc2, 1u);
+            }
+          }
+        }
+        tc_commit(d2full(b));
+        return true;
+      };
+      if (ok && nmine > 0) ok = stage1(0);
+      for (int i = 0; ok && i < nmine; ++i) {
+        if (i + 1 < nmine && !(ok = stage1(i + 1))) break;
+        ok = stage2(i);
+      }
+      tc_commit(drain);  // every MMA this thread issued is complete once `drain` fires
+      const unsigned long long t0 = gtimer();
+      while (!mbar_try_wait(drain, 0) && gtimer() - t0 < kWaitLimitNs) {
+      }
+    }
+    __syncwarp();
+  } else if (warp >= 2) {
+    // ---------------- epilogue: four warps per TMEM lane quadrant, warp h of a quadrant taking the 16-column
+    // chunks h*16 + 64*j
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    const int trow = q * 32 + lane;
+    const int J1 = (a.Np - h * 16 + 63) / 64;  // stage-1 chunks of this warp (at most 2)
+    // stage 1 of tile i: v = D1[row][c'] * G(row, c') * 2^-sG in FP32 (as the per-pass kernel), then
+    // T[row][c'] = (bf16(v), bf16(v - hi)); rows past the grid hold zeros
+    auto epi1 = [&](int i) {
+      const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+      const int b = i & 1;
+      const int r = tile * kTileRows + trow;
+      const bool valid = r < a.rows;
+      const int ia = valid ? r / a.B1 : 0;
+      const int ib = valid ? r - ia * a.B1 : 0;
+      const float sab = valid ? a.lamA[ia] + a.lamB[ib] : 0.0f;
+      const bool null_row = a.singular && ia == 0 && ib == 0;
+      if (!__all_sync(0xffffffffu, wait_bounded(d1full(b), (uint32_t)((i >> 1) & 1), ab))) return false;
+      tc_fence_after();
+      const uint32_t tacc = tmem + (uint32_t)(b * 128) + ((uint32_t)(q * 32) << 16);
+      uint32_t t0[16], t1[16];
+      if (J1 > 0) tc_ld16_issue(tacc + (uint32_t)(h * 16), t0);
+      if (J1 > 1) tc_ld16_issue(tacc + (uint32_t)(h * 16 + 64), t1);
+      if (J1 > 0) tc_ld16_wait(t0);
+      if (J1 > 1) tc_ld16_wait(t1);
+      tc_fence_before();
+      mbar_arrive(d1empty(b));
+      auto put = [&](int c0, const uint32_t (&t)[16]) {
+        float v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(t[k]);
+        const float4* lc4 = reinterpret_cast<const float4*>(a.lamC + c0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const float4 l = __ldg(lc4 + k);
+          v[4 * k + 0] *= rcp_approx(sab + l.x) * a.gscale;
+          v[4 * k + 1] *= rcp_approx(sab + l.y) * a.gscale;
+          v[4 * k + 2] *= rcp_approx(sab + l.z) * a.gscale;
+          v[4 * k + 3] *= rcp_approx(sab + l.w) * a.gscale;
+        }
+        if (null_row && c0 == 0) v[0] = 0.0f;
+        uint32_t ph[8], pl[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+          const float2 hf = __bfloat1622float2(h2);
+          const __nv_bfloat162 l2 = __floats2bfloat162_rn(v[2 * k] - hf.x, v[2 * k + 1] - hf.y);
+          ph[k] = valid ? *reinterpret_cast<const uint32_t*>(&h2) : 0u;
+          pl[k] = valid ? *reinterpret_cast<const uint32_t*>(&l2) : 0u;
+        }
+        // 128-byte swizzle: 16-byte piece p of row trow sits at piece p ^ (trow % 8); lo one tile further
+        const uint32_t rowa = sT + (uint32_t)(c0 >> 6) * tkt + (uint32_t)trow * 128u;
+        const uint32_t p0 = (uint32_t)((c0 & 63) >> 3);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const uint32_t off = ((p0 + k) ^ (uint32_t)(trow & 7)) << 4;
+          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(rowa + off), "r"(ph[4 * k]),
+                       "r"(ph[4 * k + 1]), "r"(ph[4 * k + 2]), "r"(ph[4 * k + 3])
+                       : "memory");
+          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(rowa + (uint32_t)kTBytes + off),
+                       "r"(pl[4 * k]), "r"(pl[4 * k + 1]), "r"(pl[4 * k + 2]), "r"(pl[4 * k + 3])
+                       : "memory");
+        }
+      };
+      if (J1 > 0) put(h * 16, t0);
+      if (J1 > 1) put(h * 16 + 64, t1);
+      // generic-proxy writes of T -> the tensor core's (async-proxy) reads
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(tready);
+      return true;
+    };
+    // stage 2 of tile i: thread = output index c = q*32 + lane, chunk = 16 consecutive rows; the stores of
+    // the per-pass kernel's form 2 (hi and lo planes)
+    auto epi2 = [&](int i) {
+      const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+      const int b = i & 1;
+      const int row0 = tile * kTileRows;
+      if (!__all_sync(0xffffffffu, wait_bounded(d2full(b), (uint32_t)((i >> 1) & 1), ab))) return false;
+      tc_fence_after();
+      const uint32_t tacc = tmem + 256u + (uint32_t)(b * 128) + ((uint32_t)(q * 32) << 16);
+      uint32_t t0[16], t1[16];
+      tc_ld16_issue(tacc + (uint32_t)(h * 16), t0);
+      tc_ld16_issue(tacc + (uint32_t)(h * 16 + 64), t1);
+      tc_ld16_wait(t0);
+      tc_ld16_wait(t1);
+      tc_fence_before();
+      mbar_arrive(d2empty(b));
+      const int c = q * 32 + lane;
+      auto out = [&](int c0, const uint32_t (&t)[16]) {
+        const int r0 = row0 + c0;
+        if (r0 >= a.rows || c >= a.Cout) return;
+        float v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(t[k]);
+        int ia = r0 / a.B;
+        int ib = r0 - ia * a.B;
+        if (a.vec && ib + 16 <= a.B && r0 + 16 <= a.rows) {
+          store16<Bf16Pair>(a.out, a.oplane, (long long)ia * a.oa + ib + (long long)c * a.oc, v);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            if (r0 + k < a.rows)
+              store_out<Bf16Pair>(a.out, a.oplane, (long long)ia * a.oa + (long long)ib * a.ob + (long long)c * a.oc,
+                                  v[k]);
+            if (++ib == a.B) {
+              ib = 0;
+              ++ia;
+            }
+          }
+        }
+      };
+      out(h * 16, t0);
+      out(h * 16 + 64, t1);
+      return true;
+    };
+    // T has one buffer: stage 2 of tile i-1 (drained by epi2) has read it before epi1 writes tile i
+    bool ok = nmine > 0 ? epi1(0) : true;
+    for (int i = 1; ok && i < nmine; ++i) {
+      ok = epi2(i - 1);
+      if (ok) ok = epi1(i);
+    }
+    if (ok && nmine > 0) epi2(nmine - 1);
+  }
+
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+  }
+}
+
 struct TcStage {
   CUtensorMap tmX;
   CUtensorMap tmW;
@@ -1182,6 +1489,9 @@ int set_split_smem_attrs() {
   bad |= set_smem_attr<2, Bf16Pair, Bf16Pair, false>(kMaxSmem);
   bad |= set_smem_attr<1, Bf16Pair, float, false>(kMaxSmem);
   bad |= set_smem_attr<1, Bf16Pair, float, true>(kMaxSmem);
+  if (cudaFuncSetAttribute(k_modeprod_pair_split, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem) !=
+      cudaSuccess)
+    bad |= -1;
   return bad;
 }
 
@@ -1215,11 +1525,26 @@ void launch_pair(const TcStage& s, const TcArgs& a, cudaStream_t stream) {
   cudaLaunchKernelEx(&cfg, k_modeprod_pair<InT>, s.tmX, s.tmW, s.tmW2, s.tmO, a);
 }
 
+void launch_pair_split(const TcStage& s, const TcArgs& a, cudaStream_t stream) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)s.grid);
+  cfg.blockDim = dim3(kPairSplitThreads);
+  cfg.dynamicSmemBytes = s.smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_modeprod_pair_split, s.tmX, s.tmW, s.tmW2, a);
+}
+
 template <class InT>
 void launch_stage(const TcStage& s, const TcArgs& a, bool last, bool final_pcg, cudaStream_t stream) {
   if (s.pair) {
-    // (no fused pair in the TF32 and split forms)
-    if constexpr (!KShape<InT>::tf32 && !KShape<InT>::split) launch_pair<InT>(s, a, stream);
+    // (no fused pair in the TF32 form; the split form has a kernel of its own)
+    if constexpr (KShape<InT>::split) launch_pair_split(s, a, stream);
+    else if constexpr (!KShape<InT>::tf32) launch_pair<InT>(s, a, stream);
   } else if (!last) {
     if (s.form == 1) launch<1, InT, InT, false>(s, a, stream);
     else launch<2, InT, InT, false>(s, a, stream);
@@ -1386,7 +1711,7 @@ int tc_plan_setup(tpcg_plan* p) {
   // Passes si (forward, with G, form 1) and si + 1 (backward along the same axis, form 2) as one
   // k_modeprod_pair launch; TPCG_ERR_UNSUPPORTED when the pair does not fit its layout rules.
   auto build_pair = [&](int si, const void* xin, void* out_addr, TcStage& st) -> int {
-    if (si + 1 >= ns || tp->tf32 || tp->split) return TPCG_ERR_UNSUPPORTED;
+    if (si + 1 >= ns || tp->tf32) return TPCG_ERR_UNSUPPORTED;
     const StageParams& s1 = p->stages[si];
     const StageParams& s2 = p->stages[si + 1];
     const bool shape_ok = s1.scale && !s1.final_stage && s1.oc == 1 && !s2.final_stage && s2.oc != 1 &&
@@ -1398,6 +1723,29 @@ int tc_plan_setup(tpcg_plan* p) {
     TcStage f{}, b{};
     int rc;
     if ((rc = build_one(si, xin, out_addr, f)) || (rc = build_one(si + 1, xin, out_addr, b))) return rc;
+    if (tp->split) {  // k_modeprod_pair_split: both split eigenbases resident, one T buffer, direct stores
+      if (f.form != 1 || b.form != 2 || b.args.MB != 1) return TPCG_ERR_UNSUPPORTED;
+      st = b;
+      st.pair = 1;
+      st.tmX = f.tmX;   // the forward pass's input pair, boxes {64, 128, 2}
+      st.tmW = f.tmW;   // W1: the forward eigenbasis pair, boxes {64, VR, 2}
+      st.tmW2 = b.tmW;  // W2: the backward eigenbasis pair, boxes {64, 128, 2}
+      TcArgs& a = st.args;
+      a.Np = f.args.Np;
+      a.VR = f.args.VR;
+      a.B1 = s1.B;
+      a.scale = 1;
+      a.gscale = f.args.gscale;
+      a.lamA = f.args.lamA;
+      a.lamB = f.args.lamB;
+      a.lamC = f.args.lamC;
+      // alignment, both eigenbases (hi and lo), T (hi and lo), barriers and the TMEM address
+      const size_t fixed = 1024 + (size_t)a.KT * 2 * (a.VR + 128) * 128 + (size_t)a.KT * 2 * kTBytes + 512;
+      if (fixed + 2 * (size_t)kStageBytes > (size_t)kMaxSmem) return TPCG_ERR_UNSUPPORTED;
+      a.NS = (int)std::min<size_t>(8, (kMaxSmem - fixed) / (2 * (size_t)kStageBytes));
+      st.smem = fixed + (size_t)a.NS * 2 * kStageBytes;
+      return TPCG_OK;
+    }
     if (f.form != 1 || b.form != 2 || !b.args.tstore || b.args.MB != 1 || b.args.B % 16 != 0)
       return TPCG_ERR_UNSUPPORTED;
     st = b;

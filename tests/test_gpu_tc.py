@@ -183,8 +183,10 @@ def test_cuboid_256_tc_full_size(prec, nz):
     assembled operator, zero mean) and against the oracle's direct pseudoinverse solution."""
     w = synth.workload_cuboid_256(seed=0, nz=nz)
     pl = _plan(w["nx"], w["ny"], w["nz"], w["bcs"], prec)
-    if prec in ("tf32", "bf16x3"):
+    if prec == "tf32":
         assert pl.precond_launches() == 6
+    elif prec == "bf16x3":  # the z products around G fused while the z axis has at most 128 points
+        assert pl.precond_launches() == (5 if nz <= 128 else 6)
     else:
         assert uses_slices(pl, nz) and pl.precond_launches() == (3 if nz <= 128 else 4)
     ed = _dev(w["eta"])
@@ -338,13 +340,14 @@ FUSE_CASES = [
 
 
 @pytest.mark.parametrize("slices", [0, 1])
-@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("prec", ["fp16", "bf16", "bf16x3"])
 @pytest.mark.parametrize("shape,bcs", FUSE_CASES)
 def test_fused_pair_is_bitwise_the_two_passes(shape, bcs, prec, slices):
     """TPCG_OPT_FUSE_G runs the forward and the backward mode product around G in one kernel: the same
     MMAs in the same order and the same rounding of the intermediate, so Z is bitwise that of one launch
     per pass.  With the frontal-slice launches the z products and G form one tube-pair launch instead of
-    two single tube passes, with the same guarantee."""
+    two single tube passes, with the same guarantee.  The split form (no frontal-slice launches) fuses the
+    pair with its own kernel, both split eigenbases resident and one buffer for the intermediate."""
     from paper_2501_03377_gb300 import binding as b
 
     nx, ny, nz = shape
@@ -361,7 +364,7 @@ def test_fused_pair_is_bitwise_the_two_passes(shape, bcs, prec, slices):
         outs.append(zd.cpu().numpy())
     assert np.isfinite(outs[1]).all()
     assert np.array_equal(outs[0], outs[1])
-    if slices and nz > 1 and nx % 16 == 0:
+    if slices and prec != "bf16x3" and nz > 1 and nx % 16 == 0:
         assert pl.precond_launches() == (3 if nz <= 128 else 4)
     else:
         fusable = shape != (37, 9, 5)
@@ -369,7 +372,7 @@ def test_fused_pair_is_bitwise_the_two_passes(shape, bcs, prec, slices):
         assert pl.precond_launches() == full - (1 if fusable else 0)
 
 
-@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("prec", ["fp16", "bf16", "bf16x3"])
 def test_fused_pair_solve_is_bitwise(prec):
     from paper_2501_03377_gb300 import binding as b
 
