@@ -1032,10 +1032,12 @@ __global__ void __launch_bounds__(kPairThreads, 1)
 // splits into hi = bf16(v), lo = bf16(v - hi) (T, both planes, K-major with
 // the 128-byte swizzle), and stage 2 writes the backward pass's output planes
 // with the per-pass kernel's stores: the output is bitwise that of the two
-// split passes.  Both split eigenbases stay resident (2 x 64 KB at 128
-// points), so T has one buffer and the data one stage: the epilogue writes T
-// for tile i once it has drained stage 2 of tile i-1 (whose MMAs read T), while
-// the tensor core runs stage 1 of tile i+1.
+// split passes.  One split eigenbasis stays resident (64 KB at 128 points):
+// the backward product's A operand W2[c][c'] = W1^T holds the values of the
+// forward product's B operand W1[c'][c], so stage 2 reads W1's tiles as an
+// MN-major operand (the two 64-row K tiles of W1 are its two 64-element M
+// atoms).  T is double-buffered, as in k_modeprod_pair: the epilogue scales
+// tile i while the tensor core runs stage 2 of tile i-1.
 constexpr int kPairSplitEpi = 16;
 constexpr int kPairSplitThreads = (2 + kPairSplitEpi) * 32;
 
@@ -1050,11 +1052,10 @@ __global__ void __launch_bounds__(kPairSplitThreads, 1)
   uint8_t* sm = smem_raw + (base - raw);
   const int KT = a.KT, NS = a.NS;
   // per K tile: the hi tile, then the lo tile (one 3D TMA box {64, rows, 2})
-  const uint32_t w1kt = 2u * (uint32_t)a.VR * 128u, w2kt = 2u * 128u * 128u, tkt = 2u * (uint32_t)kTBytes;
+  const uint32_t w1kt = 2u * (uint32_t)a.VR * 128u, tkt = 2u * (uint32_t)kTBytes;
   const uint32_t sW1 = base;
-  const uint32_t sW2 = sW1 + (uint32_t)KT * w1kt;  // VR % 8 == 0: 1024-aligned
-  const uint32_t sT = sW2 + (uint32_t)KT * w2kt;
-  const uint32_t sD = sT + (uint32_t)KT * tkt;
+  const uint32_t sT = sW1 + (uint32_t)KT * w1kt;  // VR % 8 == 0: 1024-aligned; two buffers of KT K tiles
+  const uint32_t sD = sT + 2u * (uint32_t)KT * tkt;
   const uint32_t sbytes = 2u * (uint32_t)kStageBytes;
   uint8_t* barp = sm + (sD - base) + (size_t)NS * sbytes;
   const uint32_t bars = smem_u32(barp);
@@ -1064,10 +1065,10 @@ __global__ void __launch_bounds__(kPairSplitThreads, 1)
   auto d1empty = [&](int b) { return bars + 8u * (2 * NS + 2 + b); };
   auto d2full = [&](int b) { return bars + 8u * (2 * NS + 4 + b); };
   auto d2empty = [&](int b) { return bars + 8u * (2 * NS + 6 + b); };
-  const uint32_t tready = bars + 8u * (2 * NS + 8);
-  const uint32_t vbar = bars + 8u * (2 * NS + 9);
-  const uint32_t drain = bars + 8u * (2 * NS + 10);
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(barp + 8 * (2 * NS + 11));
+  auto tready = [&](int b) { return bars + 8u * (2 * NS + 8 + b); };
+  const uint32_t vbar = bars + 8u * (2 * NS + 10);
+  const uint32_t drain = bars + 8u * (2 * NS + 11);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(barp + 8 * (2 * NS + 12));
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
   const Abort ab{abort_flag, a.err, a.st};
 
@@ -1082,8 +1083,8 @@ __global__ void __launch_bounds__(kPairSplitThreads, 1)
       mbar_init(d1empty(b), kPairSplitEpi * 32);
       mbar_init(d2full(b), 1);
       mbar_init(d2empty(b), kPairSplitEpi * 32);
+      mbar_init(tready(b), kPairSplitEpi * 32);
     }
-    mbar_init(tready, kPairSplitEpi * 32);
     mbar_init(vbar, 1);
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -1104,12 +1105,9 @@ __global__ void __launch_bounds__(kPairSplitThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      // ---------------- TMA producer: both split eigenbases once, then the K tiles of every row tile
-      mbar_expect_tx(vbar, (uint32_t)KT * (w1kt + w2kt));
-      for (int kt = 0; kt < KT; ++kt) {
-        tma_load_3d(sW1 + (uint32_t)kt * w1kt, &tmW1, kt * kKTile, 0, 0, vbar);
-        tma_load_3d(sW2 + (uint32_t)kt * w2kt, &tmW2, kt * kKTile, 0, 0, vbar);
-      }
+      // ---------------- TMA producer: the split eigenbasis once, then the K tiles of every row tile
+      mbar_expect_tx(vbar, (uint32_t)KT * w1kt);
+      for (int kt = 0; kt < KT; ++kt) tma_load_3d(sW1 + (uint32_t)kt * w1kt, &tmW1, kt * kKTile, 0, 0, vbar);
       asm volatile("griddepcontrol.wait;" ::: "memory");
       int it = 0;
       for (int i = 0; i < nmine && !*abort_flag; ++i) {
@@ -1136,11 +1134,12 @@ __global__ void __launch_bounds__(kPairSplitThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer (BF16 operands; the order of the per-pass split kernel)
-      const uint32_t idesc1 = idesc_f16kind(128, a.Np, 1u), idesc2 = idesc_f16kind(128, 128, 1u);
-      const unsigned long long dX0 = sw128_desc(sD), dW1 = sw128_desc(sW1), dW2 = sw128_desc(sW2), dT = sw128_desc(sT);
+      // stage 2: A (W1 read as W2) MN-major, transpose-A bit
+      const uint32_t idesc1 = idesc_f16kind(128, a.Np, 1u), idesc2 = idesc_f16kind(128, 128, 1u) | (1u << 15);
+      const unsigned long long dX0 = sw128_desc(sD), dW1 = sw128_desc(sW1), dT = sw128_desc(sT);
       // lo planes: one tile after the hi tile of the same K tile (descriptor units of 16 bytes)
       const uint32_t xlo = (uint32_t)kStageBytes >> 4, w1lo = (uint32_t)(a.VR * 128) >> 4,
-                     w2lo = (uint32_t)(128 * 128) >> 4, tlo = (uint32_t)kTBytes >> 4;
+                     tlo = (uint32_t)kTBytes >> 4;
       bool ok = wait_bounded(vbar, 0, ab);
       int it = 0;
       auto stage1 = [&](int i) {  // forward product of tile i into D1[i & 1]
@@ -1170,19 +1169,24 @@ __global__ void __launch_bounds__(kPairSplitThreads, 1)
       };
       auto stage2 = [&](int i) {  // backward product of tile i (T in shared memory) into D2[i & 1]
         const int b = i & 1;
-        if (!wait_bounded(tready, (uint32_t)(i & 1), ab)) return false;
+        if (!wait_bounded(tready(b), (uint32_t)((i >> 1) & 1), ab)) return false;
         if (!wait_bounded(d2empty(b), (uint32_t)(((i >> 1) & 1) ^ 1), ab)) return false;
         tc_fence_after();
         const uint32_t dacc = tmem + 256u + (uint32_t)(b * 128);
         for (int kt = 0; kt < KT; ++kt) {
-          const unsigned long long wd = dW2 + (uint32_t)kt * (w2kt >> 4), td = dT + (uint32_t)kt * (tkt >> 4);
+          const unsigned long long td = dT + (uint32_t)(b * KT + kt) * (tkt >> 4);
           const int nk = min(4, (a.C - kt * kKTile + 15) >> 4);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
             if (kk < nk) {
-              tc_mma(dacc, wd + 2u * kk, td + 2u * kk, idesc2, (kt > 0 || kk > 0) ? 1u : 0u);
-              tc_mma(dacc, wd + 2u * kk, td + tlo + 2u * kk, idesc2, 1u);
-              tc_mma(dacc, wd + w2lo + 2u * kk, td + 2u * kk, idesc2, 1u);
+              // K step kg: rows 16 kg.. of every W1 tile (two row groups of 1024 bytes each); the M atoms
+              // (W1's K tiles) w1kt bytes apart; lo rows VR * 128 bytes after the hi rows
+              const uint32_t ka = sW1 + 2048u * (uint32_t)(kt * 4 + kk);
+              const unsigned long long wd = mn128_desc(ka, w1kt, 1024u);
+              const unsigned long long wdl = mn128_desc(ka + (uint32_t)a.VR * 128u, w1kt, 1024u);
+              tc_mma(dacc, wd, td + 2u * kk, idesc2, (kt > 0 || kk > 0) ? 1u : 0u);
+              tc_mma(dacc, wd, td + tlo + 2u * kk, idesc2, 1u);
+              tc_mma(dacc, wdl, td + 2u * kk, idesc2, 1u);
             }
           }
         }
@@ -1251,7 +1255,7 @@ __global__ void __launch_bounds__(kPairSplitThreads, 1)
           pl[k] = valid ? *reinterpret_cast<const uint32_t*>(&l2) : 0u;
         }
         // 128-byte swizzle: 16-byte piece p of row trow sits at piece p ^ (trow % 8); lo one tile further
-        const uint32_t rowa = sT + (uint32_t)(c0 >> 6) * tkt + (uint32_t)trow * 128u;
+        const uint32_t rowa = sT + (uint32_t)(b * KT + (c0 >> 6)) * tkt + (uint32_t)trow * 128u;
         const uint32_t p0 = (uint32_t)((c0 & 63) >> 3);
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
@@ -1268,7 +1272,7 @@ __global__ void __launch_bounds__(kPairSplitThreads, 1)
       if (J1 > 1) put(h * 16 + 64, t1);
       // generic-proxy writes of T -> the tensor core's (async-proxy) reads
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_arrive(tready);
+      mbar_arrive(tready(b));
       return true;
     };
     // stage 2 of tile i: thread = output index c = q*32 + lane, chunk = 16 consecutive rows; the stores of
@@ -1315,11 +1319,11 @@ __global__ void __launch_bounds__(kPairSplitThreads, 1)
       out(h * 16 + 64, t1);
       return true;
     };
-    // T has one buffer: stage 2 of tile i-1 (drained by epi2) has read it before epi1 writes tile i
-    bool ok = nmine > 0 ? epi1(0) : true;
-    for (int i = 1; ok && i < nmine; ++i) {
-      ok = epi2(i - 1);
-      if (ok) ok = epi1(i);
+    // T buffer i & 1 was last read by stage 2 of tile i-2, drained (epi2) before epi1 writes tile i
+    bool ok = true;
+    for (int i = 0; ok && i < nmine; ++i) {
+      ok = epi1(i);
+      if (ok && i > 0) ok = epi2(i - 1);
     }
     if (ok && nmine > 0) epi2(nmine - 1);
   }
@@ -1729,7 +1733,7 @@ int tc_plan_setup(tpcg_plan* p) {
       st.pair = 1;
       st.tmX = f.tmX;   // the forward pass's input pair, boxes {64, 128, 2}
       st.tmW = f.tmW;   // W1: the forward eigenbasis pair, boxes {64, VR, 2}
-      st.tmW2 = b.tmW;  // W2: the backward eigenbasis pair, boxes {64, 128, 2}
+      st.tmW2 = b.tmW;  // (unused: stage 2 reads W1 transposed)
       TcArgs& a = st.args;
       a.Np = f.args.Np;
       a.VR = f.args.VR;
@@ -1739,8 +1743,9 @@ int tc_plan_setup(tpcg_plan* p) {
       a.lamA = f.args.lamA;
       a.lamB = f.args.lamB;
       a.lamC = f.args.lamC;
-      // alignment, both eigenbases (hi and lo), T (hi and lo), barriers and the TMEM address
-      const size_t fixed = 1024 + (size_t)a.KT * 2 * (a.VR + 128) * 128 + (size_t)a.KT * 2 * kTBytes + 512;
+      // alignment, the forward eigenbasis (hi and lo; stage 2 reads it transposed), two T buffers (hi and
+      // lo), barriers and the TMEM address
+      const size_t fixed = 1024 + (size_t)a.KT * 2 * a.VR * 128 + 2 * (size_t)a.KT * 2 * kTBytes + 512;
       if (fixed + 2 * (size_t)kStageBytes > (size_t)kMaxSmem) return TPCG_ERR_UNSUPPORTED;
       a.NS = (int)std::min<size_t>(8, (kMaxSmem - fixed) / (2 * (size_t)kStageBytes));
       st.smem = fixed + (size_t)a.NS * 2 * kStageBytes;
