@@ -538,9 +538,10 @@ NCU_TRAFFIC_PER_LAUNCH = {
         "true_residual": 197.8e6,  # a launch that checks (the others return at once)
     },
     "bf16x3": {
-        # the six launches of one application (one per mode product): 33.7-33.9 MB read each (the hi and lo
-        # planes of the input), under 0.7 MB written (the outputs stay in L2 until the next launch reads them)
-        "modeprod_tc": 206.11e6 / 6,
+        # the five launches of one application (one per mode product, the z pair around G fused): 33.7-33.9 MB
+        # read each (the hi and lo planes of the input), under 0.9 MB written (the outputs stay in L2 until the
+        # next launch reads them)
+        "modeprod_tc": 172.24e6 / 5,
     },
 }
 
