@@ -239,13 +239,13 @@ __device__ __forceinline__ void store_lp_pair(const LowPrec& lp, long long i, do
 //  * persistent and balanced: the (tile, plane) pairs are numbered tile-major
 //    and block b takes a contiguous range of T / G or T / G + 1 of them,
 //    walked as one or two runs of consecutive planes of a tile;
-//  * software-pipelined: the global loads of ring plane k+2 (Field::load, raw
-//    values in registers) and of the per-point operands of point k+1
-//    (Op::load) are issued before the barrier of plane k, so their latency
-//    overlaps the work on plane k; Field::convert forms the integer value
-//    when the raw values are committed to the ring.  With four slots the
-//    commit of plane k+1 never touches a slot that a thread still on plane
-//    k-1 reads.
+//  * software-pipelined, two planes per block barrier: the global loads of
+//    ring planes k+3 and k+4 (Field::load, raw values in registers) and of the
+//    per-point operands of planes k+2 and k+3 (Op::load) are issued before the
+//    barrier of planes k and k+1, so their latency overlaps the work on those
+//    two planes; Field::convert forms the integer value when the raw values
+//    are committed to the ring.  With six slots the commits of planes k+3 and
+//    k+4 never touch a slot that a thread still on planes k and k+1 reads.
 // op(i, x, y, k, pre, c, xl, xr, yl, yr, zl, zr) receives the point value and
 // its six neighbours with the ghosts applied (zl = zr = c in 2D), so every
 // second difference is exact.  op.flush(acc) turns the op's own per-thread
@@ -255,7 +255,7 @@ __device__ __forceinline__ void stencil_sweep_fx(const Geom& g, const Field& fie
                                                  unsigned* ticket, Fin fin) {
   constexpr int NT = TX * TY;
   constexpr int PER = (SX * SY + NT - 1) / NT;
-  __shared__ IT ring[4][SY][SX];
+  __shared__ IT ring[6][SY][SX];
   using Raw = typename Field::Raw;
   using Pre = typename Op::Pre;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -269,7 +269,7 @@ __device__ __forceinline__ void stencil_sweep_fx(const Geom& g, const Field& fie
   const unsigned G = gridDim.x, q = T / G, rm = T - q * G;  // block b: q + (b < rm) consecutive pairs
   const unsigned t_begin = blockIdx.x * q + min(blockIdx.x, rm);
   const unsigned t_end = t_begin + q + (blockIdx.x < rm ? 1u : 0u);
-  Raw raw[PER];
+  Raw rawA[PER], rawB[PER];
   unsigned off[PER];
   bool okxy[PER];
   for (unsigned t = t_begin; t < t_end;) {
@@ -289,13 +289,14 @@ __device__ __forceinline__ void stencil_sweep_fx(const Geom& g, const Field& fie
       okxy[j] = (e < SX * SY) && gx >= 0 && gy >= 0;
       off[j] = (unsigned)gy * (unsigned)g.nx + (unsigned)gx;
     }
-    auto issue = [&](int kk) {
+    auto slot = [](int kk) { return (kk + 6) % 6; };  // kk >= -1
+    auto issue = [&](Raw(&raw)[PER], int kk) {
       const int kz = has_z ? ghost_index(kk, g.nz, g.bc[2]) : kk;
 #pragma unroll
       for (int j = 0; j < PER; ++j) raw[j] = (okxy[j] && kz >= 0) ? field.load((unsigned)kz * plane + off[j]) : Raw{};
     };
-    auto commit = [&](int kk) {
-      IT(*dst)[SX] = ring[kk & 3];
+    auto commit = [&](const Raw(&raw)[PER], int kk) {
+      IT(*dst)[SX] = ring[slot(kk)];
 #pragma unroll
       for (int j = 0; j < PER; ++j) {
         const int e = tid + j * NT;
@@ -303,32 +304,47 @@ __device__ __forceinline__ void stencil_sweep_fx(const Geom& g, const Field& fie
       }
     };
     const unsigned col = (unsigned)y * (unsigned)g.nx + (unsigned)x;
-    __syncthreads();  // the previous run's last plane has been consumed
+    __syncthreads();  // the previous run's last planes have been consumed
     if (has_z) {
-      issue(k0 - 1);
-      commit(k0 - 1);
+      issue(rawA, k0 - 1);
+      commit(rawA, k0 - 1);
     }
-    issue(k0);
-    commit(k0);
-    if (has_z) issue(k0 + 1);
-    Pre pre = active ? op.load((unsigned)k0 * plane + col) : Pre{};
-    for (int k = k0; k < k1; ++k) {
+    issue(rawA, k0);
+    commit(rawA, k0);
+    if (has_z) {
+      issue(rawA, k0 + 1);
+      if (k0 + 1 < k1) issue(rawB, k0 + 2);
+    }
+    Pre pre0 = active ? op.load((unsigned)k0 * plane + col) : Pre{};
+    Pre pre1 = (active && k0 + 1 < k1) ? op.load((unsigned)(k0 + 1) * plane + col) : Pre{};
+    auto point = [&](int k, const Pre& pre) {
+      const IT(*cur)[SX] = ring[slot(k)];
+      const IT c = cur[ty + 1][tx + 1];
+      const IT zl = has_z ? ring[slot(k - 1)][ty + 1][tx + 1] : c;
+      const IT zr = has_z ? ring[slot(k + 1)][ty + 1][tx + 1] : c;
+      op((unsigned)k * plane + col, x, y, k, pre, c, cur[ty + 1][tx], cur[ty + 1][tx + 2], cur[ty][tx + 1],
+         cur[ty + 2][tx + 1], zl, zr);
+    };
+    // two planes per block barrier: planes k and k+1 read ring planes k-1 .. k+2; the commits of k+3 and k+4
+    // (next step, before its barrier) go to the two other slots of the six
+    for (int k = k0; k < k1; k += 2) {
+      const bool two = k + 1 < k1;
       if (has_z) {
-        commit(k + 1);
-        if (k + 1 < k1) issue(k + 2);
+        commit(rawA, k + 1);
+        if (two) commit(rawB, k + 2);
+        if (k + 2 < k1) issue(rawA, k + 3);
+        if (k + 3 < k1) issue(rawB, k + 4);
       }
-      Pre pre_next{};
-      if (active && k + 1 < k1) pre_next = op.load((unsigned)(k + 1) * plane + col);
+      Pre next0{}, next1{};
+      if (active && k + 2 < k1) next0 = op.load((unsigned)(k + 2) * plane + col);
+      if (active && k + 3 < k1) next1 = op.load((unsigned)(k + 3) * plane + col);
       __syncthreads();
       if (active) {
-        const IT(*cur)[SX] = ring[k & 3];
-        const IT c = cur[ty + 1][tx + 1];
-        const IT zl = has_z ? ring[(k - 1) & 3][ty + 1][tx + 1] : c;
-        const IT zr = has_z ? ring[(k + 1) & 3][ty + 1][tx + 1] : c;
-        op((unsigned)k * plane + col, x, y, k, pre, c, cur[ty + 1][tx], cur[ty + 1][tx + 2], cur[ty][tx + 1],
-           cur[ty + 2][tx + 1], zl, zr);
+        point(k, pre0);
+        if (two) point(k + 1, pre1);
       }
-      pre = pre_next;
+      pre0 = next0;
+      pre1 = next1;
     }
   }
   double acc[NQ];
