@@ -85,8 +85,9 @@ extern "C" {
                                 into one FP32 accumulator (the lo.lo term, 2^-16
                                 relative, is dropped): mode products accurate to
                                 about 2^-16 instead of 2^-8, so CG needs fewer
-                                refinement iterations; one launch per mode product,
-                                the eigenbasis streamed with the data, intermediates
+                                refinement iterations; one launch per mode product
+                                (the pair around G fused, TPCG_OPT_FUSE_G), the
+                                eigenbasis streamed with the data, intermediates
                                 4 B per point (hi and lo planes).  R enters scaled
                                 by a power of two to unit RMS, split from its FP32
                                 round-to-odd image (lo exact to one unit of its last
@@ -194,8 +195,10 @@ int tpcg_solve_host_stream(tpcg_plan* plan, int nrhs, const double* const* eta_h
  * intermediate through memory fewer per preconditioner application, the same
  * operations, bitwise the same Z.  0 runs one launch per mode product.  Used
  * when the axis has at most 128 points, a multiple of 16, and the pass
- * layouts allow it; ignored otherwise and for TPCG_FP64, TPCG_MIXED_TF32 and
- * TPCG_MIXED_BF16X3 (one launch per mode product).
+ * layouts allow it (TPCG_MIXED_BF16X3 with a kernel of its own: split
+ * operands, the eigenbasis of that axis resident once, the intermediate's two
+ * planes double-buffered); ignored otherwise and for TPCG_FP64 and
+ * TPCG_MIXED_TF32 (one launch per mode product).
  * TPCG_OPT_SLICES (TPCG_MIXED_BF16 and TPCG_MIXED_FP16; 1 = on, the
  * default; ignored for the other forms): 3D grids with nx a
  * multiple of 16 and every axis at most 256 points group the six mode products
