@@ -568,8 +568,8 @@ def kernel_work(kind, plan_prec, N, dims, iters_total, applies_total, solves, ch
         # writes one operand per point (lpb + lpb); the last reads its input (lpb) and the copy of R (lpb) and
         # writes Z in FP32 (4 B).  `launches` is the plan's count per application.  FP16/BF16: three with the
         # frontal-slice launches (16 B per point), four when the z products run as two launches (20 B), five or
-        # six with one launch per mode product (24 or 28 B); TF32 and split BF16 (4-byte operands): six launches,
-        # 52 B
+        # six with one launch per mode product (24 or 28 B); 4-byte operands: TF32 six launches (52 B), split BF16
+        # five with the z pair around G fused (44 B), six when the z axis exceeds 128 points
         npass = launches or (6 if t > 1 else 4)
         per_apply = ((npass - 1) * 2 * lpb + 2 * lpb + 4) * N
         return applies_total * per_apply / 1e9, "GB", "hbm", applies_total * npass
