@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--cpu-solves", type=int, default=10, help="oracle solves of the cpu_baseline (all cores)")
     ap.add_argument("--no-cube", action="store_true", help="skip the 256x256x256 record")
     ap.add_argument("--no-variants", action="store_true", help="skip the odd-nx / unequal-spacing record")
-    ap.add_argument("--sweep-grain", type=int, default=16,
+    ap.add_argument("--sweep-grain", type=int, default=32,
                     help="TPCG_OPT_SWEEP_GRAIN of the concurrent timed plans (0: the library's default; a single "
                          "plan keeps the default)")
     ap.add_argument("--concurrency", type=int, default=3,
