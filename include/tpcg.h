@@ -229,8 +229,9 @@ int tpcg_solve_host_stream(tpcg_plan* plan, int nrhs, const double* const* eta_h
  * least grain / 8 row tiles of 128 per CTA (one per SM below grain 16).
  * Larger grains run the sweeps of a small grid
  * on fewer SMs, so that the kernels of other plans' streams share the GPU
- * (tpcg_solve_batched over many small grids: 16 measured faster than 4);
- * a plan solved alone keeps the smaller grain (lower latency).  Grids of
+ * (tpcg_solve_batched over many small grids: 16 measured faster than 4;
+ * three concurrent 256 x 256 x 128 plans: 32 fastest of 4..64); a plan
+ * solved alone keeps the smaller grain (lower latency).  Grids of
  * 256 x 256 x 128 points and more fill every SM at grains up to 8.  The
  * grain sets the reductions' block count, so results are bitwise
  * reproducible per grain, not across grains.
