@@ -6,7 +6,7 @@ preconditioner, zero initial guess, tol 1e-10) of a synthetic charged-defect
 right-hand side already resident in HBM, each step its own 67 MB copy (four
 seeded right-hand sides in rotation), so every step's data exceed the 129 MB
 L2.  The timed steps go through tpcg_solve_batched spread over --concurrency
-plans (default 3), each on its own stream: the library runs the queues of
+plans (default 5; sweep grain 32 on them), each on its own stream: the library runs the queues of
 different plans concurrently.  single_plan reports the same steps solved one
 after the other on one plan with tpcg_solve.
 
@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--sweep-grain", type=int, default=32,
                     help="TPCG_OPT_SWEEP_GRAIN of the concurrent timed plans (0: the library's default; a single "
                          "plan keeps the default)")
-    ap.add_argument("--concurrency", type=int, default=3,
+    ap.add_argument("--concurrency", type=int, default=5,
                     help="plans (each on its own stream) the timed steps are spread over")
     args = ap.parse_args()
     if args.steps is None:
